@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the exact point-in-polygon join (SPADE §5.2 polygon x point join).
+
+Default workload (the join at scale): 100M clustered points (64-component
+Gaussian mixture, sigma 0.5-5 % of the box, 10 % uniform background) in int32
+fixed point, joined against a 2000-cell tessellation of jittered quads with
+noisily subdivided edges (52-2000 vertices per cell); output: (point, polygon)
+pairs sorted by point id plus per-polygon counts.
+
+One step = one join of the whole resident point table against the resident
+grid index (point -> cell, candidate dispatch, exact crossing tests with the
+FP32 filter, order-preserving compaction, per-polygon counts).  The index is
+built once before timing; its build time is reported separately.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead
+(the reference arm), on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "billion points joined/sec and % HBM roofline; serving p50/p99 ms vs plain kernel"
+UNIT = "Gpoints/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(name: str, n_override: int | None, rank: int):
+    from paper_2203_14362_gb300 import datagen as g
+
+    if name == "tess2000_100m":
+        n = n_override or 100_000_000
+        seed = g.SEED_BASE + 2
+        nx, ny = g.tessellation_shape(2000)
+        t = g.quad_tessellation(nx, ny, seed, kmin=12, kmax=499)
+        mix = g.make_mixture(seed)
+        pts = g.mixture_points(n, seed, mix, start=rank * n)
+        desc = (f"{n} mixture points (64 Gaussians, sigma 0.5-5% of box, 10% uniform) x 2000-cell tessellation "
+                f"(jittered quads, noisy edges, 52-2000 vertices/cell); pairs + counts")
+        return pts, t.verts, t.ring_off, desc
+    if name == "stars_1m":
+        n = n_override or 1_000_000
+        seed = g.SEED_BASE + 1
+        v, o = g.star_polygons(seed)
+        pts = g.uniform_points(n * (rank + 1), seed)[rank * n:]
+        return pts, v, o, f"{n} uniform points x 256 star polygons (16-64 vertices); pairs + counts"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples with host timestamps."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int, period_ms: int = 50):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", f"-lms={period_ms}",
+                 f"-i={gpu}"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        win = [s for t, s in self.samples if t0 <= t <= t1]
+        if not win and self.samples:  # timed region shorter than the sampling period: nearest samples
+            mid = 0.5 * (t0 + t1)
+            win = [min(self.samples, key=lambda ts: abs(ts[0] - mid))[1]]
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(s[1]) for s in win if len(s) > 8 and num(s[1]) is not None]
+        mx = [num(s[2]) for s in win if len(s) > 8 and num(s[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in win if len(s) > 8 for k in range(4) if s[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(win)}
+
+
+# -------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int, torch):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------- CPU baseline
+def cpu_baseline(pts, verts, ring_off, budget_s: float = 12.0, chunk: int = 1_000_000):
+    import oracle
+    pr = oracle.Prepared(verts, ring_off)
+    threads = oracle.default_threads()
+    done, t0 = 0, time.perf_counter()
+    while done < pts.shape[0] and time.perf_counter() - t0 < budget_s:
+        m = min(chunk, pts.shape[0] - done)
+        pr.join(pts[done:done + m], threads=threads)
+        done += m
+    el = time.perf_counter() - t0
+    pr.close()
+    return {"value": done / el / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {done} points of the same table (pairs + counts, fast oracle, {el:.1f} s)"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2203_14362_gb300 import datagen as g
+
+    sample = args.ref_sample
+    pts, v, o, desc = make_workload(args.workload, sample, 0)
+    pr = oracle.Prepared(v, o)
+    threads = oracle.default_threads()
+    for _ in range(max(args.warmup, 0)):
+        pr.join(pts, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pr.join(pts, threads=threads)
+        times.append(time.perf_counter() - t0)
+    pr.close()
+    sec = sum(times) / len(times)
+    val = sample / sec / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "sample_points_per_step": sample,
+                   "polygons": int(o.shape[0] - 1), "vertices": int(v.shape[0])},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"first {sample} points of the workload per step (pairs + counts, fast oracle)"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- GPU arm
+def run_spx(args, world, rank, local):
+    import torch
+
+    from paper_2203_14362_gb300 import spx
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    clocks = ClockSampler(local)
+    pts, v, o, desc = make_workload(args.workload, args.points, rank)
+    N, P = pts.shape[0], int(o.shape[0] - 1)
+
+    eng = spx.Engine(local)
+    dpts = torch.from_numpy(pts).cuda()
+    ph = eng.load_points(dpts)
+    gh = eng.load_polygons(v, o)
+    ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32))
+    info = eng.index_info(ih)
+    cap = N if args.cap is None else args.cap
+    pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+    counts = torch.zeros(max(P, 1), dtype=torch.int64, device="cuda")
+    total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n_pairs = eng.join(ph, ih, pairs, counts, total, sync=True, plain=args.plain)
+    assert int(counts.sum().item()) == n_pairs
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        eng.join(ph, ih, pairs, counts, total, sync=False, stream=stream, plain=args.plain)
+    torch.cuda.synchronize()
+    eng.stats(reset=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        eng.join(ph, ih, pairs, counts, total, sync=False, stream=stream, plain=args.plain)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    st = eng.stats(reset=True)
+    ms_max = max_over_ranks(ms, world, torch)
+    clk = clocks.summary(t_host0, t_host1)
+
+    # end to end through the C ABI on pinned host buffers (H2D points, join, D2H pairs + counts)
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty((N, 2), dtype=torch.int32, pin_memory=True)
+        hx.numpy()[:] = pts
+        hp = torch.empty((cap, 2), dtype=torch.int32, pin_memory=True)
+        hc = torch.empty(max(P, 1), dtype=torch.int64, pin_memory=True)
+        hxn, hpn, hcn = hx.numpy(), hp.numpy().view(np.uint32), hc.numpy().view(np.uint64)
+        eng.join_host(hxn, ih, cap, P, pairs_out=hpn, counts_out=hcn)
+        k_e2e = max(1, min(args.steps, args.e2e_steps))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            _, _, m = eng.join_host(hxn, ih, cap, P, pairs_out=hpn, counts_out=hcn)
+        sec = (time.perf_counter() - t0) / k_e2e
+        sec = max_over_ranks(sec, world, torch)
+        e2e = {"value": world * N / sec / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
+               "d2h_bytes_per_step": int(m * 8 + P * 8 + 8), "ms_per_step": sec * 1e3}
+    clocks.stop()
+
+    idx_bytes = info["n_cells"] * 4 + info["n_entries"] * 16 + info["n_edge_refs"] * 16
+    alg_bytes = 8 * N + 8 * n_pairs + 8 * P + idx_bytes
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    out = None
+    if rank == 0:
+        cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(pts, v, o, args.cpu_budget)
+        out = {
+            "metric": METRIC, "value": world * N / (ms_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {
+                "workload": args.workload, "desc": desc, "points_per_gpu": N, "polygons": P,
+                "vertices": int(v.shape[0]), "pairs": int(n_pairs), "grid_log2": info["grid_log2"],
+                "fp32_filter": bool(args.fp32), "kernel": "plain two-pass" if args.plain else "fused single-pass",
+                "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": int(info["device_bytes"]),
+                "l2": "inputs larger than L2 (points 8 B x N + pairs 8 B x N >> 129 MB); no flush",
+                "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
+                "fp32_escalation_fraction": st["fp32_escalations"] / max(st["edge_tests"], 1),
+                "parallelism": f"points sharded by rank, index replicated, dp{world}",
+            },
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                         "algorithmic_bytes_per_launch": int(alg_bytes)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * (3 if args.plain else 1),
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    eng.free(ih)
+    eng.free(gh)
+    eng.free(ph)
+    eng.close()
+    del dpts
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["spx", "reference"], default="spx")
+    ap.add_argument("--workload", default="tess2000_100m", choices=["tess2000_100m", "stars_1m"])
+    ap.add_argument("--points", type=int, default=None, help="points per GPU (default: the workload's)")
+    ap.add_argument("--grid", type=int, default=0, help="grid_log2 (0 = automatic)")
+    ap.add_argument("--fp32", type=int, default=1)
+    ap.add_argument("--plain", action="store_true", help="time the plain two-pass comparison kernels")
+    ap.add_argument("--cap", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "spx":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_spx(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

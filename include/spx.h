@@ -1,0 +1,214 @@
+/*
+ * spx.h -- C ABI of libspx, an exact point-in-polygon join, selection and
+ * count-aggregate over a large point table resident in GPU memory (GB300,
+ * sm_103a), through a device-resident uniform-grid index.
+ *
+ * The operations follow SPADE's statement of the problem (Doraiswamy and
+ * Freire, "SPADE: GPU-Powered Spatial Database Engine for Commodity
+ * Hardware"):
+ *   - selection of points by a polygonal constraint (§5.2, "Spatial Selection"),
+ *   - the polygon-point join as a collection of selections (§5.2, "Spatial Joins"),
+ *   - the count aggregation, with and without materialising the join
+ *     (§5.2, "Spatial Aggregations"),
+ *   - exact tests where the discretisation is ambiguous (§4.3, "Boundary Index"),
+ *   - for points, intersection is containment (§7, "Containment Queries"),
+ *   - the two-pass Map sizing of outputs (§5.1, "Map"): a call that runs out of
+ *     output space returns SPX_ECAPACITY and the size that is needed.
+ *
+ * Coordinates are int32 fixed point: points in [0, 2^30)^2, polygon vertices in
+ * [0, 2^30]^2.  A point p lies in polygon R iff the number of edges (a, b) of R
+ * with (a.y > p.y) != (b.y > p.y) and orient(a, b, p) != 0 of the sign of
+ * (b.y - a.y) is odd, orient(a, b, p) = (b.x-a.x)(p.y-a.y) - (b.y-a.y)(p.x-a.x)
+ * evaluated exactly: p + (eps, eps^2) is in the even-odd interior of R.  Every
+ * result is exact and deterministic (byte-identical across runs, grid sizes and
+ * launch shapes).
+ *
+ * Conventions for every call:
+ *   - Status codes only; nothing throws across the ABI.  On failure,
+ *     spx_last_error(ctx) describes the cause (valid until the next call on
+ *     that ctx from the same thread).
+ *   - A ctx is bound to one device and is not thread-safe; use one per thread.
+ *   - "Device" pointers are CUDA device memory of the ctx's device (e.g. the
+ *     data_ptr() of a torch tensor on that device).  The caller owns every
+ *     buffer it passes; handles are owned by the ctx and released by spx_free
+ *     or spx_destroy.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     calls are asynchronous on that stream, except where a host out-parameter
+ *     is requested: then the call synchronises the stream before returning.
+ */
+#ifndef SPX_H
+#define SPX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spx_ctx spx_ctx;
+typedef uint64_t spx_points; /* handle: a point table in device memory */
+typedef uint64_t spx_polys;  /* handle: a polygon set (host copy + device copy) */
+typedef uint64_t spx_index;  /* handle: a built grid index over a polygon set */
+
+typedef enum {
+    SPX_OK = 0,
+    SPX_EINVAL = -1,    /* bad argument: null pointer, bad handle, coordinate out of range */
+    SPX_ENOMEM = -2,    /* host or device allocation failed */
+    SPX_ECUDA = -3,     /* a CUDA runtime call failed (message has the CUDA error) */
+    SPX_ECAPACITY = -4, /* output buffer too small; the required size was written */
+    SPX_ETIMEOUT = -5,  /* a bounded device wait gave up (the kernel returned early) */
+    SPX_EBUSY = -6,     /* result not ready yet (serving) */
+    SPX_EKERNEL = -7    /* a kernel reported an internal error through its status word */
+} spx_status;
+
+/* Create a context on CUDA device `device`.  *out receives the context. */
+spx_status spx_create(int device, spx_ctx **out);
+
+/* Destroy a context and every handle it owns.  Safe on NULL. */
+void spx_destroy(spx_ctx *ctx);
+
+/* Text of the last error on this ctx (never NULL; "" after success). */
+const char *spx_last_error(const spx_ctx *ctx);
+
+/*
+ * Load a point table (§5.2 "Spatial Selection": the point data set that every
+ * selection scans).  xy holds n interleaved (x, y) int32 pairs, 8 bytes per
+ * point, point id = row index (n < 2^32).  With xy_is_device = 0, xy is host
+ * memory and is copied to a device buffer owned by the handle (coordinates are
+ * validated: 0 <= x, y < 2^30, else SPX_EINVAL).  With xy_is_device = 1 the
+ * handle borrows the caller's device buffer, which must stay alive and
+ * unchanged while the handle is used; it is not validated (a point outside the
+ * box lies in no polygon, as the exact definition says, and the kernels skip it).
+ * Device buffers must be 16-byte aligned.
+ */
+spx_status spx_load_points(spx_ctx *ctx, const int32_t *xy, uint64_t n, int xy_is_device, spx_points *out);
+
+/*
+ * Load a polygon set from host memory (§4.2, polygons are the constraint
+ * canvases of selections and joins).  Polygon q is the implicitly closed ring
+ * xy[2*ring_off[q] .. 2*ring_off[q+1]) of int32 (x, y) vertices, 0 <= x, y <=
+ * 2^30; ring_off has P + 1 non-decreasing entries with ring_off[0] = 0.  Rings
+ * may be clockwise or counter-clockwise, concave, self-intersecting (even-odd)
+ * or degenerate (then nothing is inside).  Polygons may overlap.  P < 2^30.
+ * The data are copied.
+ */
+spx_status spx_load_polygons(spx_ctx *ctx, const int32_t *xy, const uint64_t *ring_off, uint32_t P, spx_polys *out);
+
+/* Grid-index parameters (§4.3 canvas indexes; §5.3 grid cell size, §7 tuning). */
+typedef struct {
+    int grid_log2;   /* the grid has 2^grid_log2 cells per side, 1..13; 0 = choose automatically */
+    int fp32_filter; /* 1: orientation in FP32 with exact int64 redo inside the error bound; 0: int64 only */
+    int reserved[6]; /* must be zero */
+} spx_index_params;
+
+/*
+ * Build the grid index of a polygon set (§4.2 canvas creation with conservative
+ * rasterisation of the boundary; §4.3 boundary index).  Each cell of a 2^g x 2^g
+ * grid over the box lists the polygons that may contain its points: INSIDE when
+ * no edge meets the open cell square (every point of the cell is inside), or
+ * BOUNDARY with the polygon's edges that can cross a rightward ray from a point
+ * of the cell (the exact test runs on those).  params may be NULL (defaults:
+ * automatic grid, FP32 filter on).  The index is built on the host and copied
+ * to the device; the polygon handle must stay alive while the index is used.
+ */
+spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params *params, spx_index *out);
+
+/* Sizes of a built index. */
+typedef struct {
+    int grid_log2;
+    uint32_t n_polys;
+    uint64_t n_cells;        /* 4^grid_log2 */
+    uint64_t n_entries;      /* (cell, polygon) list entries stored (cells with one INSIDE polygon store none) */
+    uint64_t n_boundary;     /* BOUNDARY (cell, polygon) pairs */
+    uint64_t n_inside;       /* INSIDE (cell, polygon) pairs */
+    uint64_t n_edge_refs;    /* edges stored in per-row edge lists */
+    uint64_t device_bytes;   /* device memory held by the index */
+    double build_ms;         /* host build + upload time */
+} spx_index_info;
+
+spx_status spx_index_info_get(spx_ctx *ctx, spx_index index, spx_index_info *out);
+
+/*
+ * Polygon-point join (§5.2 "Spatial Joins", Polygon x Point), one pass over the
+ * points.  Output: every (point_id, polygon_id) with the point inside the
+ * polygon, as uint32 pairs pairs_dev[2k] = point id, pairs_dev[2k+1] = polygon
+ * id, sorted by point id then polygon id; counts_dev[q] (uint64, P entries,
+ * may be NULL) = number of pairs with polygon q.  All device pointers.
+ *   cap       capacity of pairs_dev in pairs; pairs past cap are not written.
+ *   total_dev device uint64 that receives the total number of pairs (may be NULL).
+ *   n_pairs   host uint64 (may be NULL).  If given, the call synchronises the
+ *             stream, writes the total, and returns SPX_ECAPACITY if it
+ *             exceeds cap (the first cap pairs are valid).
+ * Without n_pairs the call is asynchronous and capture-safe once a first call
+ * of at least this size has run on the ctx outside capture.
+ */
+spx_status spx_join(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev, uint64_t cap,
+                    uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream);
+
+/*
+ * The same join through the plain comparison kernels: exact int64 orientation
+ * only, one thread per point, a counting pass, a scan and a writing pass (the
+ * two-pass Map of §5.1).  Same arguments and results as spx_join.
+ */
+spx_status spx_join_plain(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev, uint64_t cap,
+                          uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream);
+
+/*
+ * Count aggregation without materialising the join (§5.2 "Spatial
+ * Aggregations", the plan for point data): counts_dev[q] (uint64, P entries,
+ * device) = number of points inside polygon q.
+ */
+spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint64_t *counts_dev, void *stream);
+
+/*
+ * End-to-end join on host buffers: copies the n points at xy_host to the
+ * device, joins them against the index, and copies pairs and counts back.
+ * pairs_host holds cap pairs (2*cap uint32), counts_host P uint64 (may be
+ * NULL); *n_pairs receives the total (SPX_ECAPACITY if above cap).  Device
+ * staging buffers are owned by the ctx and reused.  Pinned host memory makes
+ * the copies faster.  Synchronous.
+ */
+spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_index index, uint32_t *pairs_host,
+                         uint64_t cap, uint64_t *counts_host, uint64_t *n_pairs);
+
+/*
+ * Host-only build of the same grid index, for inspection (no device, no ctx):
+ * the index build runs on the host, so its output can be checked without a
+ * GPU.  spx_host_index_build builds it and reports the array sizes
+ * (sizes[0] = cell words, sizes[1] = entries, sizes[2] = edges);
+ * spx_host_index_copy copies the arrays into caller buffers of those sizes
+ * (cells: uint32 each; entries: 4 uint32 each; edges: 4 int32 each); free the
+ * handle with spx_host_index_free.  Layout of the arrays:
+ *   cell word c = (cy << g) | cx: bits 31..30 kind (0 none, 1 one INSIDE
+ *     polygon = bits 29..0, 2 list starting at entry bits 29..0);
+ *   entry = (polygon id, first edge, edge count, flags: 1 BOUNDARY, 2 last of list);
+ *   edge = (a.x, a.y, b.x, b.y); a BOUNDARY entry's edges are the polygon's
+ *     non-horizontal edges meeting the cell's row strip with max x > the cell's
+ *     left x, sorted by max x descending.
+ */
+typedef struct spx_host_index spx_host_index;
+spx_status spx_host_index_build(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int grid_log2,
+                                spx_host_index **out, uint64_t sizes[3]);
+spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *cells, uint32_t *entries, int32_t *edges);
+void spx_host_index_free(spx_host_index *h);
+
+/* Counters accumulated by the kernels of this ctx since the last reset. */
+typedef struct {
+    uint64_t points_scanned;
+    uint64_t edge_tests;      /* straddling-edge tests that needed an orientation */
+    uint64_t fp32_escalations;/* of those, orientations redone in int64 because |d_f| <= E */
+    uint64_t pairs_emitted;
+} spx_stats_t;
+
+/* Read (synchronising the device) and optionally reset the counters. */
+spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset);
+
+/* Release one handle (points, polygons or index).  An index must be freed
+ * before the polygon set it was built from. */
+spx_status spx_free(spx_ctx *ctx, uint64_t handle);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPX_H */

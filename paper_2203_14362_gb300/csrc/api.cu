@@ -1,0 +1,575 @@
+// C ABI of libspx (declared in include/spx.h): contexts, handles, argument
+// checks, device memory of the index and the scratch, and dispatch to the
+// kernels.  Every step of the join runs in kernels.cu; this file only moves
+// bytes and checks arguments.
+#include "kernels.h"
+#include "spx.h"
+#include "spx_internal.h"
+
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+using namespace spx;
+
+namespace {
+
+enum : uint64_t { kTagPoints = 1, kTagPolys = 2, kTagIndex = 3 };
+constexpr int kTagShift = 56;
+
+struct PointsObj {
+    int32_t *dev = nullptr;
+    uint64_t n = 0;
+    bool owned = false;
+};
+
+struct PolysObj {
+    std::vector<int32_t> xy;
+    std::vector<uint64_t> off;
+    uint32_t P = 0;
+    int n_index = 0; // live indexes built from it
+};
+
+struct IndexObj {
+    uint64_t polys = 0;
+    IndexView view{};
+    int fp32 = 1;
+    void *mem = nullptr; // one allocation: cells | entries | edges
+    spx_index_info info{};
+};
+
+// Persistent per-ctx device words.
+struct Aux {
+    unsigned err;                       // kernel error bits, cleared when reported
+    unsigned pad;
+    unsigned long long stats[kStatCount];
+    unsigned long long total;           // internal total when the caller passes none
+};
+
+} // namespace
+
+struct spx_ctx {
+    int device = 0;
+    std::string err;
+    uint64_t next_id = 1;
+    std::map<uint64_t, std::unique_ptr<PointsObj>> points;
+    std::map<uint64_t, std::unique_ptr<PolysObj>> polys;
+    std::map<uint64_t, std::unique_ptr<IndexObj>> indexes;
+    Aux *aux = nullptr;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // staging buffers of spx_join_host
+    void *st_pts = nullptr, *st_pairs = nullptr, *st_counts = nullptr;
+    size_t st_pts_b = 0, st_pairs_b = 0, st_counts_b = 0;
+    cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+spx_status fail(spx_ctx *c, spx_status s, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    return s;
+}
+
+spx_status cuda_fail(spx_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, SPX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SPX_CUDA(call, what)                                                                                           \
+    do {                                                                                                               \
+        cudaError_t e_ = (call);                                                                                       \
+        if (e_ != cudaSuccess)                                                                                         \
+            return cuda_fail(ctx, e_, what);                                                                           \
+    } while (0)
+
+uint64_t make_handle(spx_ctx *c, uint64_t tag) { return (tag << kTagShift) | (c->next_id++); }
+
+template <class T>
+T *lookup(std::map<uint64_t, std::unique_ptr<T>> &m, uint64_t h)
+{
+    auto it = m.find(h);
+    return it == m.end() ? nullptr : it->second.get();
+}
+
+bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess)
+        return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Grow a device buffer (never while the stream is being captured).
+spx_status ensure(spx_ctx *ctx, void **buf, size_t *have, size_t need, cudaStream_t s, const char *what)
+{
+    if (*have >= need)
+        return SPX_OK;
+    if (capturing(s))
+        return fail(ctx, SPX_EINVAL,
+                    std::string(what) + ": scratch must be sized by a first call outside stream capture");
+    if (*buf) {
+        cudaStreamSynchronize(s);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
+    }
+    size_t sz = need < 256 ? 256 : need;
+    cudaError_t e = cudaMalloc(buf, sz);
+    if (e != cudaSuccess)
+        return fail(ctx, SPX_ENOMEM, std::string(what) + ": cudaMalloc failed: " + cudaGetErrorString(e));
+    *have = sz;
+    return SPX_OK;
+}
+
+// Read and clear the kernel error word (synchronises the stream).
+spx_status check_kernel_err(spx_ctx *ctx, cudaStream_t s)
+{
+    SPX_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    unsigned w = 0;
+    SPX_CUDA(cudaMemcpy(&w, &ctx->aux->err, sizeof(w), cudaMemcpyDeviceToHost), "read error word");
+    if (w) {
+        SPX_CUDA(cudaMemset(&ctx->aux->err, 0, sizeof(unsigned)), "clear error word");
+        if (w & kErrTimeout)
+            return fail(ctx, SPX_ETIMEOUT, "a bounded device wait gave up; results of that call are invalid");
+        return fail(ctx, SPX_EKERNEL, "kernel reported an internal error");
+    }
+    return SPX_OK;
+}
+
+spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev, uint64_t cap,
+                       uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream, bool plain)
+{
+    if (!ctx)
+        return SPX_EINVAL;
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    PointsObj *pts = lookup(ctx->points, points);
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!pts || !ix)
+        return fail(ctx, SPX_EINVAL, "join: bad points or index handle");
+    if (cap && !pairs_dev)
+        return fail(ctx, SPX_EINVAL, "join: pairs_dev is NULL with cap > 0");
+    if ((reinterpret_cast<uintptr_t>(pairs_dev) & 7) || (reinterpret_cast<uintptr_t>(counts_dev) & 7) ||
+        (reinterpret_cast<uintptr_t>(total_dev) & 7))
+        return fail(ctx, SPX_EINVAL, "join: output pointers must be 8-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t need = plain ? plain_scratch_bytes(pts->n) : join_scratch_bytes(pts->n);
+    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, need, s, "join");
+    if (st != SPX_OK)
+        return st;
+    JoinLaunch a{};
+    a.ix = ix->view;
+    a.pts = reinterpret_cast<const int2 *>(pts->dev);
+    a.n = pts->n;
+    a.pairs = reinterpret_cast<uint2 *>(pairs_dev);
+    a.cap = pairs_dev ? cap : 0;
+    a.counts = reinterpret_cast<unsigned long long *>(counts_dev);
+    a.total = total_dev ? reinterpret_cast<unsigned long long *>(total_dev) : (n_pairs ? &ctx->aux->total : nullptr);
+    a.err = &ctx->aux->err;
+    a.stats = ctx->aux->stats;
+    a.fp32 = ix->fp32;
+    cudaError_t e = plain ? launch_join_plain(a, ctx->scratch, s) : launch_join(a, ctx->scratch, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "join launch");
+    if (n_pairs) {
+        st = check_kernel_err(ctx, s);
+        if (st != SPX_OK)
+            return st;
+        unsigned long long t = 0;
+        SPX_CUDA(cudaMemcpy(&t, a.total, sizeof(t), cudaMemcpyDeviceToHost), "read total");
+        *n_pairs = t;
+        if (t > cap)
+            return fail(ctx, SPX_ECAPACITY, "join: " + std::to_string(t) + " pairs exceed capacity " +
+                                                std::to_string(cap));
+    }
+    return SPX_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+spx_status spx_create(int device, spx_ctx **out)
+{
+    if (!out)
+        return SPX_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return SPX_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return SPX_ECUDA;
+    std::unique_ptr<spx_ctx> c(new spx_ctx());
+    c->device = device;
+    if (cudaMalloc(reinterpret_cast<void **>(&c->aux), sizeof(Aux)) != cudaSuccess)
+        return SPX_ENOMEM;
+    if (cudaMemset(c->aux, 0, sizeof(Aux)) != cudaSuccess)
+        return SPX_ECUDA;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return SPX_ECUDA;
+    *out = c.release();
+    return SPX_OK;
+}
+
+void spx_destroy(spx_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->indexes)
+        cudaFree(kv.second->mem);
+    for (auto &kv : ctx->points)
+        if (kv.second->owned)
+            cudaFree(kv.second->dev);
+    cudaFree(ctx->aux);
+    cudaFree(ctx->scratch);
+    cudaFree(ctx->st_pts);
+    cudaFree(ctx->st_pairs);
+    cudaFree(ctx->st_counts);
+    if (ctx->stream)
+        cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *spx_last_error(const spx_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+spx_status spx_load_points(spx_ctx *ctx, const int32_t *xy, uint64_t n, int xy_is_device, spx_points *out)
+{
+    if (!ctx || !out || (!xy && n))
+        return fail(ctx, SPX_EINVAL, "load_points: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    if (n >= (1ull << 32))
+        return fail(ctx, SPX_EINVAL, "load_points: n must be < 2^32 (point ids are uint32)");
+    auto p = std::make_unique<PointsObj>();
+    p->n = n;
+    if (xy_is_device) {
+        if (reinterpret_cast<uintptr_t>(xy) & 15)
+            return fail(ctx, SPX_EINVAL, "load_points: device buffer must be 16-byte aligned");
+        p->dev = const_cast<int32_t *>(xy);
+        p->owned = false;
+    } else {
+        for (uint64_t i = 0; i < 2 * n; ++i)
+            if (xy[i] < 0 || xy[i] >= int32_t(kBox))
+                return fail(ctx, SPX_EINVAL, "load_points: coordinate " + std::to_string(xy[i]) + " at point " +
+                                                 std::to_string(i / 2) + " outside [0, 2^30)");
+        void *d = nullptr;
+        if (cudaMalloc(&d, n ? n * 8 : 16) != cudaSuccess)
+            return fail(ctx, SPX_ENOMEM, "load_points: cudaMalloc failed");
+        if (n)
+            SPX_CUDA(cudaMemcpy(d, xy, n * 8, cudaMemcpyHostToDevice), "load_points copy");
+        p->dev = static_cast<int32_t *>(d);
+        p->owned = true;
+    }
+    const uint64_t h = make_handle(ctx, kTagPoints);
+    ctx->points[h] = std::move(p);
+    *out = h;
+    return SPX_OK;
+}
+
+spx_status spx_load_polygons(spx_ctx *ctx, const int32_t *xy, const uint64_t *ring_off, uint32_t P, spx_polys *out)
+{
+    if (!ctx || !out || !ring_off)
+        return fail(ctx, SPX_EINVAL, "load_polygons: null argument");
+    ctx->err.clear();
+    if (P >= (1u << 30))
+        return fail(ctx, SPX_EINVAL, "load_polygons: P must be < 2^30");
+    if (ring_off[0] != 0)
+        return fail(ctx, SPX_EINVAL, "load_polygons: ring_off[0] must be 0");
+    for (uint32_t q = 0; q < P; ++q)
+        if (ring_off[q + 1] < ring_off[q])
+            return fail(ctx, SPX_EINVAL, "load_polygons: ring_off must be non-decreasing");
+    const uint64_t V = ring_off[P];
+    if (V && !xy)
+        return fail(ctx, SPX_EINVAL, "load_polygons: xy is NULL");
+    for (uint64_t i = 0; i < 2 * V; ++i)
+        if (xy[i] < 0 || xy[i] > int32_t(kBox))
+            return fail(ctx, SPX_EINVAL, "load_polygons: vertex coordinate " + std::to_string(xy[i]) +
+                                             " outside [0, 2^30]");
+    auto p = std::make_unique<PolysObj>();
+    p->xy.assign(xy, xy + 2 * V);
+    p->off.assign(ring_off, ring_off + P + 1);
+    p->P = P;
+    const uint64_t h = make_handle(ctx, kTagPolys);
+    ctx->polys[h] = std::move(p);
+    *out = h;
+    return SPX_OK;
+}
+
+spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params *params, spx_index *out)
+{
+    if (!ctx || !out)
+        return fail(ctx, SPX_EINVAL, "build_index: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    PolysObj *pg = lookup(ctx->polys, polys);
+    if (!pg)
+        return fail(ctx, SPX_EINVAL, "build_index: bad polygon handle");
+    spx_index_params prm{};
+    prm.grid_log2 = 0;
+    prm.fp32_filter = 1;
+    if (params) {
+        prm = *params;
+        for (int r : prm.reserved)
+            if (r)
+                return fail(ctx, SPX_EINVAL, "build_index: reserved fields must be zero");
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    int g = prm.grid_log2 ? prm.grid_log2 : default_grid_log2(pg->xy.data(), pg->off.data(), pg->P);
+    if (g < 1 || g > kMaxGridLog2)
+        return fail(ctx, SPX_EINVAL, "build_index: grid_log2 must be in [1, 13] (or 0 = automatic)");
+    HostIndex hi;
+    std::string err;
+    const int threads = std::max(1u, std::thread::hardware_concurrency());
+    if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, threads, hi, err))
+        return fail(ctx, SPX_EINVAL, "build_index: " + err);
+    const size_t b_cell = hi.cell.size() * 4, b_ent = hi.entries.size() * 4, b_edge = hi.edges.size() * 4;
+    auto up16 = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t total = up16(b_cell) + up16(b_ent) + up16(b_edge) + 256;
+    auto ix = std::make_unique<IndexObj>();
+    if (cudaMalloc(&ix->mem, total) != cudaSuccess)
+        return fail(ctx, SPX_ENOMEM, "build_index: cudaMalloc of " + std::to_string(total) + " bytes failed");
+    char *m = static_cast<char *>(ix->mem);
+    char *p_cell = m, *p_ent = m + up16(b_cell), *p_edge = p_ent + up16(b_ent);
+    cudaError_t e = cudaMemcpy(p_cell, hi.cell.data(), b_cell, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b_ent)
+        e = cudaMemcpy(p_ent, hi.entries.data(), b_ent, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b_edge)
+        e = cudaMemcpy(p_edge, hi.edges.data(), b_edge, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(ix->mem);
+        return cuda_fail(ctx, e, "build_index upload");
+    }
+    ix->polys = polys;
+    ix->fp32 = prm.fp32_filter ? 1 : 0;
+    ix->view.cell = reinterpret_cast<const uint32_t *>(p_cell);
+    ix->view.ent = reinterpret_cast<const uint4 *>(p_ent);
+    ix->view.edge = reinterpret_cast<const int4 *>(p_edge);
+    ix->view.shift = kBoxLog2 - g;
+    ix->view.glog2 = g;
+    ix->view.P = pg->P;
+    spx_index_info &inf = ix->info;
+    inf.grid_log2 = g;
+    inf.n_polys = pg->P;
+    inf.n_cells = hi.cell.size();
+    inf.n_entries = hi.entries.size() / 4;
+    inf.n_boundary = hi.n_boundary;
+    inf.n_inside = hi.n_inside;
+    inf.n_edge_refs = hi.edges.size() / 4;
+    inf.device_bytes = total;
+    inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    pg->n_index++;
+    const uint64_t h = make_handle(ctx, kTagIndex);
+    ctx->indexes[h] = std::move(ix);
+    *out = h;
+    return SPX_OK;
+}
+
+spx_status spx_index_info_get(spx_ctx *ctx, spx_index index, spx_index_info *out)
+{
+    if (!ctx || !out)
+        return fail(ctx, SPX_EINVAL, "index_info: null argument");
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!ix)
+        return fail(ctx, SPX_EINVAL, "index_info: bad index handle");
+    *out = ix->info;
+    return SPX_OK;
+}
+
+spx_status spx_join(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev, uint64_t cap,
+                    uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream)
+{
+    return join_common(ctx, points, index, pairs_dev, cap, counts_dev, total_dev, n_pairs, stream, false);
+}
+
+spx_status spx_join_plain(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev, uint64_t cap,
+                          uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream)
+{
+    return join_common(ctx, points, index, pairs_dev, cap, counts_dev, total_dev, n_pairs, stream, true);
+}
+
+spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint64_t *counts_dev, void *stream)
+{
+    if (!ctx || !counts_dev)
+        return fail(ctx, SPX_EINVAL, "aggregate: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    PointsObj *pts = lookup(ctx->points, points);
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!pts || !ix)
+        return fail(ctx, SPX_EINVAL, "aggregate: bad points or index handle");
+    if (reinterpret_cast<uintptr_t>(counts_dev) & 7)
+        return fail(ctx, SPX_EINVAL, "aggregate: counts_dev must be 8-byte aligned");
+    JoinLaunch a{};
+    a.ix = ix->view;
+    a.pts = reinterpret_cast<const int2 *>(pts->dev);
+    a.n = pts->n;
+    a.counts = reinterpret_cast<unsigned long long *>(counts_dev);
+    a.err = &ctx->aux->err;
+    a.stats = ctx->aux->stats;
+    a.fp32 = ix->fp32;
+    cudaError_t e = launch_aggregate(a, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "aggregate launch");
+    return SPX_OK;
+}
+
+spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_index index, uint32_t *pairs_host,
+                         uint64_t cap, uint64_t *counts_host, uint64_t *n_pairs)
+{
+    if (!ctx || (!xy_host && n) || (!pairs_host && cap) || !n_pairs)
+        return fail(ctx, SPX_EINVAL, "join_host: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!ix)
+        return fail(ctx, SPX_EINVAL, "join_host: bad index handle");
+    if (n >= (1ull << 32))
+        return fail(ctx, SPX_EINVAL, "join_host: n must be < 2^32");
+    cudaStream_t s = ctx->stream;
+    spx_status st;
+    if ((st = ensure(ctx, &ctx->st_pts, &ctx->st_pts_b, n * 8 + 16, s, "join_host")) != SPX_OK ||
+        (st = ensure(ctx, &ctx->st_pairs, &ctx->st_pairs_b, cap * 8 + 16, s, "join_host")) != SPX_OK ||
+        (st = ensure(ctx, &ctx->st_counts, &ctx->st_counts_b, size_t(ix->view.P) * 8 + 16, s, "join_host")) != SPX_OK ||
+        (st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, join_scratch_bytes(n), s, "join_host")) != SPX_OK)
+        return st;
+    if (n)
+        SPX_CUDA(cudaMemcpyAsync(ctx->st_pts, xy_host, n * 8, cudaMemcpyHostToDevice, s), "join_host H2D");
+    JoinLaunch a{};
+    a.ix = ix->view;
+    a.pts = reinterpret_cast<const int2 *>(ctx->st_pts);
+    a.n = n;
+    a.pairs = reinterpret_cast<uint2 *>(ctx->st_pairs);
+    a.cap = cap;
+    a.counts = reinterpret_cast<unsigned long long *>(ctx->st_counts);
+    a.total = &ctx->aux->total;
+    a.err = &ctx->aux->err;
+    a.stats = ctx->aux->stats;
+    a.fp32 = ix->fp32;
+    cudaError_t e = launch_join(a, ctx->scratch, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "join_host launch");
+    unsigned long long t = 0;
+    SPX_CUDA(cudaMemcpyAsync(&t, &ctx->aux->total, sizeof(t), cudaMemcpyDeviceToHost, s), "join_host total");
+    if (counts_host && ix->view.P)
+        SPX_CUDA(cudaMemcpyAsync(counts_host, ctx->st_counts, size_t(ix->view.P) * 8, cudaMemcpyDeviceToHost, s),
+                 "join_host counts D2H");
+    if ((st = check_kernel_err(ctx, s)) != SPX_OK)
+        return st;
+    const uint64_t m = t < cap ? t : cap;
+    if (m)
+        SPX_CUDA(cudaMemcpyAsync(pairs_host, ctx->st_pairs, m * 8, cudaMemcpyDeviceToHost, s), "join_host D2H");
+    SPX_CUDA(cudaStreamSynchronize(s), "join_host sync");
+    *n_pairs = t;
+    if (t > cap)
+        return fail(ctx, SPX_ECAPACITY, "join_host: " + std::to_string(t) + " pairs exceed capacity");
+    return SPX_OK;
+}
+
+struct spx_host_index {
+    HostIndex hi;
+};
+
+spx_status spx_host_index_build(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int grid_log2,
+                                spx_host_index **out, uint64_t sizes[3])
+{
+    if (!out || !ring_off || !sizes || (!xy && ring_off[P]))
+        return SPX_EINVAL;
+    *out = nullptr;
+    int g = grid_log2 ? grid_log2 : default_grid_log2(xy, ring_off, P);
+    auto h = std::make_unique<spx_host_index>();
+    std::string err;
+    const int threads = std::max(1u, std::thread::hardware_concurrency());
+    if (!build_grid_index(xy, ring_off, P, g, threads, h->hi, err))
+        return SPX_EINVAL;
+    sizes[0] = h->hi.cell.size();
+    sizes[1] = h->hi.entries.size() / 4;
+    sizes[2] = h->hi.edges.size() / 4;
+    *out = h.release();
+    return SPX_OK;
+}
+
+spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *cells, uint32_t *entries, int32_t *edges)
+{
+    if (!h)
+        return SPX_EINVAL;
+    if (cells)
+        std::memcpy(cells, h->hi.cell.data(), h->hi.cell.size() * 4);
+    if (entries)
+        std::memcpy(entries, h->hi.entries.data(), h->hi.entries.size() * 4);
+    if (edges)
+        std::memcpy(edges, h->hi.edges.data(), h->hi.edges.size() * 4);
+    return SPX_OK;
+}
+
+void spx_host_index_free(spx_host_index *h) { delete h; }
+
+spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset)
+{
+    if (!ctx || !out)
+        return fail(ctx, SPX_EINVAL, "stats: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    SPX_CUDA(cudaDeviceSynchronize(), "stats synchronize");
+    unsigned long long v[kStatCount];
+    SPX_CUDA(cudaMemcpy(v, ctx->aux->stats, sizeof(v), cudaMemcpyDeviceToHost), "stats read");
+    out->points_scanned = v[kStatPoints];
+    out->edge_tests = v[kStatTests];
+    out->fp32_escalations = v[kStatEscalations];
+    out->pairs_emitted = v[kStatPairs];
+    if (reset)
+        SPX_CUDA(cudaMemset(ctx->aux->stats, 0, sizeof(v)), "stats reset");
+    return check_kernel_err(ctx, nullptr);
+}
+
+spx_status spx_free(spx_ctx *ctx, uint64_t handle)
+{
+    if (!ctx)
+        return SPX_EINVAL;
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    const uint64_t tag = handle >> kTagShift;
+    if (tag == kTagIndex) {
+        IndexObj *ix = lookup(ctx->indexes, handle);
+        if (!ix)
+            return fail(ctx, SPX_EINVAL, "free: bad index handle");
+        cudaDeviceSynchronize();
+        cudaFree(ix->mem);
+        PolysObj *pg = lookup(ctx->polys, ix->polys);
+        if (pg)
+            pg->n_index--;
+        ctx->indexes.erase(handle);
+        return SPX_OK;
+    }
+    if (tag == kTagPolys) {
+        PolysObj *pg = lookup(ctx->polys, handle);
+        if (!pg)
+            return fail(ctx, SPX_EINVAL, "free: bad polygon handle");
+        if (pg->n_index)
+            return fail(ctx, SPX_EINVAL, "free: an index built from this polygon set is still alive");
+        ctx->polys.erase(handle);
+        return SPX_OK;
+    }
+    if (tag == kTagPoints) {
+        PointsObj *p = lookup(ctx->points, handle);
+        if (!p)
+            return fail(ctx, SPX_EINVAL, "free: bad points handle");
+        cudaDeviceSynchronize();
+        if (p->owned)
+            cudaFree(p->dev);
+        ctx->points.erase(handle);
+        return SPX_OK;
+    }
+    return fail(ctx, SPX_EINVAL, "free: unknown handle");
+}
+
+} // extern "C"

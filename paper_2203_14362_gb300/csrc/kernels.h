@@ -1,0 +1,51 @@
+// Launch wrappers of libspx's kernels (internal; called from api.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spx {
+
+struct IndexView {
+    const uint32_t *cell; // 4^g cell words
+    const uint4 *ent;     // entries
+    const int4 *edge;     // per-row edge lists
+    int shift;            // 30 - g
+    int glog2;            // g
+    uint32_t P;           // number of polygons
+};
+
+// Device status word bits (ORed into the ctx's persistent error word).
+constexpr unsigned kErrTimeout = 1u;   // a bounded wait on another tile's status gave up
+constexpr unsigned kErrInternal = 2u;  // an internal consistency check failed
+
+// Per-ctx device counters, in this order.
+enum { kStatPoints = 0, kStatTests = 1, kStatEscalations = 2, kStatPairs = 3, kStatCount = 4 };
+
+struct JoinLaunch {
+    IndexView ix;
+    const int2 *pts;
+    uint64_t n;
+    uint2 *pairs;                 // may be null when cap == 0
+    uint64_t cap;
+    unsigned long long *counts;   // P entries or null; zeroed by the launcher
+    unsigned long long *total;    // device total or null
+    unsigned long long *tile_status;
+    unsigned *tile_counter;
+    unsigned *err;                // persistent error word
+    unsigned long long *stats;    // kStatCount counters
+    int fp32;
+};
+
+// Scratch bytes the fused join needs for n points (tile status + counter).
+size_t join_scratch_bytes(uint64_t n);
+size_t plain_scratch_bytes(uint64_t n);
+
+// scratch: device memory of join_scratch_bytes(n) bytes; zeroed inside.
+cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s);
+cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s);
+cudaError_t launch_aggregate(const JoinLaunch &a, cudaStream_t s);
+
+int device_sm_count();
+
+} // namespace spx

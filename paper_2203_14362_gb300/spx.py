@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libspx (include/spx.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name; `Engine` wraps a
+context for callers that hold torch tensors or numpy arrays.  All computation
+runs in libspx's CUDA kernels; there is no CPU fallback, and a missing or
+unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspx.so")
+
+SPX_OK, SPX_EINVAL, SPX_ENOMEM, SPX_ECUDA, SPX_ECAPACITY, SPX_ETIMEOUT, SPX_EBUSY, SPX_EKERNEL = 0, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "SPX_OK", -1: "SPX_EINVAL", -2: "SPX_ENOMEM", -3: "SPX_ECUDA", -4: "SPX_ECAPACITY",
+                -5: "SPX_ETIMEOUT", -6: "SPX_EBUSY", -7: "SPX_EKERNEL"}
+
+EXPORTS = [
+    "spx_create", "spx_destroy", "spx_last_error", "spx_load_points", "spx_load_polygons", "spx_build_index",
+    "spx_index_info_get", "spx_join", "spx_join_plain", "spx_aggregate", "spx_join_host", "spx_host_index_build",
+    "spx_host_index_copy", "spx_host_index_free", "spx_stats", "spx_free",
+]
+
+
+class SpxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class IndexParams(C.Structure):
+    _fields_ = [("grid_log2", C.c_int), ("fp32_filter", C.c_int), ("reserved", C.c_int * 6)]
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("grid_log2", C.c_int), ("n_polys", C.c_uint32), ("n_cells", C.c_uint64),
+                ("n_entries", C.c_uint64), ("n_boundary", C.c_uint64), ("n_inside", C.c_uint64),
+                ("n_edge_refs", C.c_uint64), ("device_bytes", C.c_uint64), ("build_ms", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("points_scanned", C.c_uint64), ("edge_tests", C.c_uint64),
+                ("fp32_escalations", C.c_uint64), ("pairs_emitted", C.c_uint64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libspx.so (built by paper_2203_14362_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libspx.so not found at {path}: run paper_2203_14362_gb300.build.build() first")
+    lib = C.CDLL(path)
+    V, U64, U32, I = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int
+    P64 = C.POINTER(C.c_uint64)
+    sig = {
+        "spx_create": ([I, C.POINTER(V)], I),
+        "spx_destroy": ([V], None),
+        "spx_last_error": ([V], C.c_char_p),
+        "spx_load_points": ([V, V, U64, I, P64], I),
+        "spx_load_polygons": ([V, V, V, U32, P64], I),
+        "spx_build_index": ([V, U64, C.POINTER(IndexParams), P64], I),
+        "spx_index_info_get": ([V, U64, C.POINTER(IndexInfo)], I),
+        "spx_join": ([V, U64, U64, V, U64, V, V, P64, V], I),
+        "spx_join_plain": ([V, U64, U64, V, U64, V, V, P64, V], I),
+        "spx_aggregate": ([V, U64, U64, V, V], I),
+        "spx_join_host": ([V, V, U64, U64, V, U64, V, P64], I),
+        "spx_host_index_build": ([V, V, U32, I, C.POINTER(V), P64], I),
+        "spx_host_index_copy": ([V, V, V, V], I),
+        "spx_host_index_free": ([V], None),
+        "spx_stats": ([V, C.POINTER(Stats), I], I),
+        "spx_free": ([V, U64], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t):
+    """Device pointer of a torch tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return C.c_void_p(t)
+    return C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------- host index build
+def host_index(verts: np.ndarray, ring_off: np.ndarray, grid_log2: int = 0):
+    """Build the grid index on the host only (spx_host_index_build) and return
+    (cells uint32 (G*G,), entries uint32 (E, 4), edges int32 (M, 4), g)."""
+    lib = load()
+    xy = np.ascontiguousarray(verts, dtype=np.int32)
+    off = np.ascontiguousarray(ring_off, dtype=np.uint64)
+    h = C.c_void_p()
+    sizes = (C.c_uint64 * 3)()
+    st = lib.spx_host_index_build(_np_ptr(xy), _np_ptr(off), off.shape[0] - 1, grid_log2, C.byref(h), sizes)
+    if st != SPX_OK:
+        raise SpxError(st, "spx_host_index_build failed")
+    try:
+        cells = np.zeros(sizes[0], np.uint32)
+        ent = np.zeros((sizes[1], 4), np.uint32)
+        edges = np.zeros((sizes[2], 4), np.int32)
+        lib.spx_host_index_copy(h, _np_ptr(cells), _np_ptr(ent), _np_ptr(edges))
+    finally:
+        lib.spx_host_index_free(h)
+    g = int(round(np.log2(cells.shape[0]) / 2))
+    return cells, ent, edges, g
+
+
+# ------------------------------------------------------------------- the engine
+class Engine:
+    """One libspx context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.ctx = C.c_void_p()
+        st = self.lib.spx_create(device, C.byref(self.ctx))
+        if st != SPX_OK:
+            raise SpxError(st, f"spx_create(device={device}) failed")
+        self.device = device
+
+    def close(self):
+        if self.ctx:
+            self.lib.spx_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != SPX_OK:
+            raise SpxError(st, f"{what}: {self.lib.spx_last_error(self.ctx).decode()}")
+
+    # -- loading
+    def load_points(self, xy) -> int:
+        """Host numpy (N, 2) int32 (copied) or a CUDA torch tensor (borrowed)."""
+        h = C.c_uint64()
+        if isinstance(xy, np.ndarray):
+            a = np.ascontiguousarray(xy, dtype=np.int32)
+            self._check(self.lib.spx_load_points(self.ctx, _np_ptr(a), a.shape[0], 0, C.byref(h)), "spx_load_points")
+        else:
+            assert xy.is_cuda and xy.is_contiguous() and str(xy.dtype) == "torch.int32"
+            self._check(self.lib.spx_load_points(self.ctx, _dev_ptr(xy), xy.shape[0], 1, C.byref(h)),
+                        "spx_load_points")
+        return h.value
+
+    def load_polygons(self, verts: np.ndarray, ring_off: np.ndarray) -> int:
+        xy = np.ascontiguousarray(verts, dtype=np.int32)
+        off = np.ascontiguousarray(ring_off, dtype=np.uint64)
+        h = C.c_uint64()
+        self._check(self.lib.spx_load_polygons(self.ctx, _np_ptr(xy), _np_ptr(off), off.shape[0] - 1, C.byref(h)),
+                    "spx_load_polygons")
+        return h.value
+
+    def build_index(self, polys: int, grid_log2: int = 0, fp32_filter: bool = True) -> int:
+        p = IndexParams(grid_log2, 1 if fp32_filter else 0)
+        h = C.c_uint64()
+        self._check(self.lib.spx_build_index(self.ctx, polys, C.byref(p), C.byref(h)), "spx_build_index")
+        return h.value
+
+    def index_info(self, index: int) -> dict:
+        inf = IndexInfo()
+        self._check(self.lib.spx_index_info_get(self.ctx, index, C.byref(inf)), "spx_index_info_get")
+        return {f: getattr(inf, f) for f, _ in IndexInfo._fields_}
+
+    def free(self, handle: int):
+        self._check(self.lib.spx_free(self.ctx, handle), "spx_free")
+
+    # -- queries (device tensors)
+    def join(self, points: int, index: int, pairs, counts=None, total=None, sync: bool = True, stream=None,
+             plain: bool = False):
+        """pairs: int32/uint32-compatible CUDA tensor of shape (cap, 2); counts: int64 (P,);
+        total: int64 (1,).  Returns the total number of pairs when sync, else None."""
+        cap = 0 if pairs is None else pairs.shape[0]
+        n = C.c_uint64()
+        f = self.lib.spx_join_plain if plain else self.lib.spx_join
+        st = f(self.ctx, points, index, _dev_ptr(pairs), cap, _dev_ptr(counts), _dev_ptr(total),
+               C.byref(n) if sync else None, _stream(stream))
+        if st == SPX_ECAPACITY:
+            raise SpxError(st, f"join needs {n.value} pairs, capacity {cap}")
+        self._check(st, "spx_join")
+        return n.value if sync else None
+
+    def aggregate(self, points: int, index: int, counts, stream=None):
+        self._check(self.lib.spx_aggregate(self.ctx, points, index, _dev_ptr(counts), _stream(stream)),
+                    "spx_aggregate")
+
+    def join_host(self, xy: np.ndarray, index: int, cap: int, n_polys: int, pairs_out=None, counts_out=None):
+        """End-to-end join on host arrays; returns (pairs view, counts, total)."""
+        a = np.ascontiguousarray(xy, dtype=np.int32)
+        pairs = pairs_out if pairs_out is not None else np.zeros((cap, 2), np.uint32)
+        counts = counts_out if counts_out is not None else np.zeros(max(n_polys, 1), np.uint64)
+        n = C.c_uint64()
+        st = self.lib.spx_join_host(self.ctx, _np_ptr(a), a.shape[0], index, _np_ptr(pairs), cap,
+                                    _np_ptr(counts), C.byref(n))
+        if st == SPX_ECAPACITY:
+            raise SpxError(st, f"join needs {n.value} pairs, capacity {cap}")
+        self._check(st, "spx_join_host")
+        return pairs[:n.value], counts[:n_polys], n.value
+
+    def stats(self, reset: bool = False) -> dict:
+        s = Stats()
+        self._check(self.lib.spx_stats(self.ctx, C.byref(s), 1 if reset else 0), "spx_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
