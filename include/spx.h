@@ -94,34 +94,44 @@ spx_status spx_load_points(spx_ctx *ctx, const int32_t *xy, uint64_t n, int xy_i
  */
 spx_status spx_load_polygons(spx_ctx *ctx, const int32_t *xy, const uint64_t *ring_off, uint32_t P, spx_polys *out);
 
-/* Grid-index parameters (§4.3 canvas indexes; §5.3 grid cell size, §7 tuning). */
+/* Grid-index parameters (§4.3 canvas indexes; §5.3 grid cell size; §7 tuning). */
 typedef struct {
-    int grid_log2;   /* the grid has 2^grid_log2 cells per side, 1..13; 0 = choose automatically */
+    int grid_log2;   /* coarse grid of 2^grid_log2 cells per side, 1..13; 0 = choose automatically */
     int fp32_filter; /* 1: orientation in FP32 with exact int64 redo inside the error bound; 0: int64 only */
-    int reserved[6]; /* must be zero */
+    int sub_log2;    /* a coarse cell cut by a polygon boundary is split into 2^sub_log2 x 2^sub_log2
+                        fine cells, 1..3 (grid_log2 + sub_log2 <= 16); 0 = default (3) */
+    int reserved[5]; /* must be zero */
 } spx_index_params;
 
 /*
  * Build the grid index of a polygon set (§4.2 canvas creation with conservative
- * rasterisation of the boundary; §4.3 boundary index).  Each cell of a 2^g x 2^g
- * grid over the box lists the polygons that may contain its points: INSIDE when
- * no edge meets the open cell square (every point of the cell is inside), or
- * BOUNDARY with the polygon's edges that can cross a rightward ray from a point
- * of the cell (the exact test runs on those).  params may be NULL (defaults:
- * automatic grid, FP32 filter on).  The index is built on the host and copied
- * to the device; the polygon handle must stay alive while the index is used.
+ * rasterisation of the boundary; §4.3 boundary index).  Two levels: each cell
+ * of a 2^g x 2^g coarse grid over the box is empty, wholly INSIDE exactly one
+ * polygon, or mixed; a mixed cell is split into F x F fine cells (F =
+ * 2^sub_log2), each of which is empty, INSIDE one polygon, or lists its
+ * candidate polygons: INSIDE ones, and BOUNDARY ones with the polygon's edges
+ * that can cross a rightward ray from a point of the fine cell (the exact test
+ * runs on those).  A cell is INSIDE when no edge meets its open square and its
+ * lower-left corner is inside.  params may be NULL (defaults: automatic grid,
+ * FP32 filter on, sub_log2 3).  The index is built on the host (all cores) and
+ * copied to the device; the polygon handle must stay alive while the index is
+ * used.
  */
 spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params *params, spx_index *out);
 
 /* Sizes of a built index. */
 typedef struct {
     int grid_log2;
+    int sub_log2;
     uint32_t n_polys;
-    uint64_t n_cells;        /* 4^grid_log2 */
-    uint64_t n_entries;      /* (cell, polygon) list entries stored (cells with one INSIDE polygon store none) */
-    uint64_t n_boundary;     /* BOUNDARY (cell, polygon) pairs */
-    uint64_t n_inside;       /* INSIDE (cell, polygon) pairs */
-    uint64_t n_edge_refs;    /* edges stored in per-row edge lists */
+    uint32_t pad;
+    uint64_t n_cells;        /* 4^grid_log2 coarse cells */
+    uint64_t n_blocks;       /* mixed coarse cells (each holds 4^sub_log2 fine cells) */
+    uint64_t n_entries;      /* list entries stored for fine cells */
+    uint64_t n_inside;       /* (coarse cell, polygon) pairs wholly inside */
+    uint64_t n_mixed;        /* (coarse cell, polygon) pairs split into fine cells */
+    uint64_t n_boundary;     /* (fine cell, polygon) pairs that run the exact test */
+    uint64_t n_edge_refs;    /* edges stored in per-fine-row edge lists */
     uint64_t device_bytes;   /* device memory held by the index */
     double build_ms;         /* host build + upload time */
 } spx_index_info;
@@ -174,22 +184,27 @@ spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_i
 /*
  * Host-only build of the same grid index, for inspection (no device, no ctx):
  * the index build runs on the host, so its output can be checked without a
- * GPU.  spx_host_index_build builds it and reports the array sizes
- * (sizes[0] = cell words, sizes[1] = entries, sizes[2] = edges);
- * spx_host_index_copy copies the arrays into caller buffers of those sizes
- * (cells: uint32 each; entries: 4 uint32 each; edges: 4 int32 each); free the
- * handle with spx_host_index_free.  Layout of the arrays:
- *   cell word c = (cy << g) | cx: bits 31..30 kind (0 none, 1 one INSIDE
- *     polygon = bits 29..0, 2 list starting at entry bits 29..0);
- *   entry = (polygon id, first edge, edge count, flags: 1 BOUNDARY, 2 last of list);
+ * GPU.  spx_host_index_build builds it (grid_log2 0 = automatic, sub_log2 0 =
+ * default) and reports the array sizes: sizes[0] = coarse words, sizes[1] =
+ * fine words, sizes[2] = entries, sizes[3] = edges, sizes[4] = grid_log2,
+ * sizes[5] = sub_log2.  spx_host_index_copy copies the arrays into caller
+ * buffers of those sizes (words: uint32; entries: 4 uint32 each; edges: 4
+ * int32 each); free the handle with spx_host_index_free.  Layout:
+ *   coarse word c = (cy << g) | cx: bits 31..30 kind (0 none, 1 one INSIDE
+ *     polygon = bits 29..0, 2 mixed: block b = bits 29..0);
+ *   fine word of mixed block b, fine cell (fx, fy) = fine[b * F*F + (fy mod F)
+ *     * F + (fx mod F)]: kind 0 none, 1 one INSIDE polygon, 2 list starting at
+ *     entry bits 29..0;
+ *   entry = (polygon id, first edge, edge count, flags: 1 BOUNDARY, 2 last);
  *   edge = (a.x, a.y, b.x, b.y); a BOUNDARY entry's edges are the polygon's
- *     non-horizontal edges meeting the cell's row strip with max x > the cell's
- *     left x, sorted by max x descending.
+ *     non-horizontal edges meeting the fine cell's row strip with max x > the
+ *     cell's left x, sorted by max x descending.
  */
 typedef struct spx_host_index spx_host_index;
 spx_status spx_host_index_build(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int grid_log2,
-                                spx_host_index **out, uint64_t sizes[3]);
-spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *cells, uint32_t *entries, int32_t *edges);
+                                int sub_log2, spx_host_index **out, uint64_t sizes[6]);
+spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *coarse, uint32_t *fine, uint32_t *entries,
+                               int32_t *edges);
 void spx_host_index_free(spx_host_index *h);
 
 /* Counters accumulated by the kernels of this ctx since the last reset. */

@@ -315,7 +315,6 @@ spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params
     if (!pg)
         return fail(ctx, SPX_EINVAL, "build_index: bad polygon handle");
     spx_index_params prm{};
-    prm.grid_log2 = 0;
     prm.fp32_filter = 1;
     if (params) {
         prm = *params;
@@ -324,23 +323,28 @@ spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params
                 return fail(ctx, SPX_EINVAL, "build_index: reserved fields must be zero");
     }
     const auto t0 = std::chrono::steady_clock::now();
-    int g = prm.grid_log2 ? prm.grid_log2 : default_grid_log2(pg->xy.data(), pg->off.data(), pg->P);
-    if (g < 1 || g > kMaxGridLog2)
-        return fail(ctx, SPX_EINVAL, "build_index: grid_log2 must be in [1, 13] (or 0 = automatic)");
+    const int g = prm.grid_log2 ? prm.grid_log2 : default_grid_log2(pg->xy.data(), pg->off.data(), pg->P);
+    const int sb = prm.sub_log2 ? prm.sub_log2 : kMaxSubLog2;
+    if (g < 1 || g > kMaxGridLog2 || sb < 1 || sb > kMaxSubLog2 || g + sb > kMaxFineLog2)
+        return fail(ctx, SPX_EINVAL, "build_index: grid_log2 must be in [1, 13] (0 = automatic), sub_log2 in "
+                                     "[1, 3] (0 = default), grid_log2 + sub_log2 <= 16");
     HostIndex hi;
     std::string err;
     const int threads = std::max(1u, std::thread::hardware_concurrency());
-    if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, threads, hi, err))
+    if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, sb, threads, hi, err))
         return fail(ctx, SPX_EINVAL, "build_index: " + err);
-    const size_t b_cell = hi.cell.size() * 4, b_ent = hi.entries.size() * 4, b_edge = hi.edges.size() * 4;
-    auto up16 = [](size_t v) { return (v + 255) & ~size_t(255); };
-    const size_t total = up16(b_cell) + up16(b_ent) + up16(b_edge) + 256;
+    const size_t b_cell = hi.cell.size() * 4, b_fine = hi.fine.size() * 4, b_ent = hi.entries.size() * 4,
+                 b_edge = hi.edges.size() * 4;
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t total = up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + 256;
     auto ix = std::make_unique<IndexObj>();
     if (cudaMalloc(&ix->mem, total) != cudaSuccess)
         return fail(ctx, SPX_ENOMEM, "build_index: cudaMalloc of " + std::to_string(total) + " bytes failed");
     char *m = static_cast<char *>(ix->mem);
-    char *p_cell = m, *p_ent = m + up16(b_cell), *p_edge = p_ent + up16(b_ent);
+    char *p_cell = m, *p_fine = p_cell + up(b_cell), *p_ent = p_fine + up(b_fine), *p_edge = p_ent + up(b_ent);
     cudaError_t e = cudaMemcpy(p_cell, hi.cell.data(), b_cell, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b_fine)
+        e = cudaMemcpy(p_fine, hi.fine.data(), b_fine, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && b_ent)
         e = cudaMemcpy(p_ent, hi.entries.data(), b_ent, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && b_edge)
@@ -352,18 +356,24 @@ spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params
     ix->polys = polys;
     ix->fp32 = prm.fp32_filter ? 1 : 0;
     ix->view.cell = reinterpret_cast<const uint32_t *>(p_cell);
+    ix->view.fine = reinterpret_cast<const uint32_t *>(p_fine);
     ix->view.ent = reinterpret_cast<const uint4 *>(p_ent);
     ix->view.edge = reinterpret_cast<const int4 *>(p_edge);
-    ix->view.shift = kBoxLog2 - g;
-    ix->view.glog2 = g;
+    ix->view.sc = kBoxLog2 - g;
+    ix->view.gc = g;
+    ix->view.sf = kBoxLog2 - g - sb;
+    ix->view.sb = sb;
     ix->view.P = pg->P;
     spx_index_info &inf = ix->info;
     inf.grid_log2 = g;
+    inf.sub_log2 = sb;
     inf.n_polys = pg->P;
     inf.n_cells = hi.cell.size();
+    inf.n_blocks = hi.n_blocks;
     inf.n_entries = hi.entries.size() / 4;
-    inf.n_boundary = hi.n_boundary;
     inf.n_inside = hi.n_inside;
+    inf.n_mixed = hi.n_mixed;
+    inf.n_boundary = hi.n_boundary;
     inf.n_edge_refs = hi.edges.size() / 4;
     inf.device_bytes = total;
     inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -417,7 +427,11 @@ spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint6
     a.err = &ctx->aux->err;
     a.stats = ctx->aux->stats;
     a.fp32 = ix->fp32;
-    cudaError_t e = launch_aggregate(a, reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, 16, s, "aggregate");
+    if (st != SPX_OK)
+        return st;
+    cudaError_t e = launch_aggregate(a, ctx->scratch, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "aggregate launch");
     return SPX_OK;
@@ -480,30 +494,37 @@ struct spx_host_index {
 };
 
 spx_status spx_host_index_build(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int grid_log2,
-                                spx_host_index **out, uint64_t sizes[3])
+                                int sub_log2, spx_host_index **out, uint64_t sizes[6])
 {
     if (!out || !ring_off || !sizes || (!xy && ring_off[P]))
         return SPX_EINVAL;
     *out = nullptr;
-    int g = grid_log2 ? grid_log2 : default_grid_log2(xy, ring_off, P);
+    const int g = grid_log2 ? grid_log2 : default_grid_log2(xy, ring_off, P);
+    const int sb = sub_log2 ? sub_log2 : kMaxSubLog2;
     auto h = std::make_unique<spx_host_index>();
     std::string err;
     const int threads = std::max(1u, std::thread::hardware_concurrency());
-    if (!build_grid_index(xy, ring_off, P, g, threads, h->hi, err))
+    if (!build_grid_index(xy, ring_off, P, g, sb, threads, h->hi, err))
         return SPX_EINVAL;
     sizes[0] = h->hi.cell.size();
-    sizes[1] = h->hi.entries.size() / 4;
-    sizes[2] = h->hi.edges.size() / 4;
+    sizes[1] = h->hi.fine.size();
+    sizes[2] = h->hi.entries.size() / 4;
+    sizes[3] = h->hi.edges.size() / 4;
+    sizes[4] = uint64_t(g);
+    sizes[5] = uint64_t(sb);
     *out = h.release();
     return SPX_OK;
 }
 
-spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *cells, uint32_t *entries, int32_t *edges)
+spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *coarse, uint32_t *fine, uint32_t *entries,
+                               int32_t *edges)
 {
     if (!h)
         return SPX_EINVAL;
-    if (cells)
-        std::memcpy(cells, h->hi.cell.data(), h->hi.cell.size() * 4);
+    if (coarse)
+        std::memcpy(coarse, h->hi.cell.data(), h->hi.cell.size() * 4);
+    if (fine)
+        std::memcpy(fine, h->hi.fine.data(), h->hi.fine.size() * 4);
     if (entries)
         std::memcpy(entries, h->hi.entries.data(), h->hi.entries.size() * 4);
     if (edges)

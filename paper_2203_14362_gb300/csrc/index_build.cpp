@@ -1,24 +1,27 @@
-// Host build of the grid index (SPADE §4.2 canvas creation, §4.3 boundary
-// index; the paper rasterises polygons into a texture, here they are
-// rasterised into the cells of a 2^g x 2^g grid over the coordinate box).
+// Host build of the two-level grid index (SPADE §4.2 canvas creation with
+// conservative rasterisation of polygon boundaries, §4.3 boundary index; the
+// paper rasterises polygons into a texture, here into the cells of a grid
+// over the coordinate box, refined once where a cell is cut by a boundary).
 //
-// Per polygon:
-//  1. Conservative rasterisation of the boundary (the paper's conservative
-//     rasterisation of polygon edges): for every row strip an edge meets,
-//     the edge's piece inside the closed strip is clipped with exact rational
-//     arithmetic and every cell whose OPEN square it can meet is marked
-//     BOUNDARY.
-//  2. Every other cell of the polygon's bounding box holds points of one status
-//     only: its perturbed points p + (eps, eps^2) all lie in the open square,
-//     which no edge meets.  The status of the cell's lower-left corner is
-//     decided for a whole row at once by a scanline: each edge straddling the
-//     row's bottom line counts for exactly the cells whose corner x is left of
-//     the edge's crossing, i.e. cx <= floor((a.x + ceil(num/den) - 1) / S).
-//  3. For every row with a BOUNDARY cell, the edges meeting the row's open
-//     strip are stored once, sorted by max x descending; a BOUNDARY entry
-//     points at the prefix with max x > the cell's x0.
-// Then the (cell, polygon) records of all polygons are bucketed by cell in
-// polygon order, so every cell's list is sorted by polygon id.
+// Per polygon, with coarse cells of side Sc = 2^(30-g) and fine cells of side
+// Sf = Sc / F, F = 2^sub:
+//  1. Conservative rasterisation of the boundary at both levels: for every row
+//     strip an edge meets, the edge's piece inside the closed strip is clipped
+//     with exact rational arithmetic and every cell whose OPEN square it can
+//     meet is marked.  Coarse marks make a coarse cell "mixed"; fine marks make
+//     a fine cell BOUNDARY.
+//  2. A cell no edge meets holds points of one status only: its perturbed
+//     points p + (eps, eps^2) all lie in its open square.  The status of the
+//     lower-left corner (x0, y0) is decided for a whole row by a scanline: an
+//     edge straddling y0 counts for exactly the corners left of its crossing,
+//     x0 <= a.x + ceil(num/den) - 1 with num/den the crossing's offset from a.x.
+//     Coarse rows classify coarse cells that are not mixed; fine rows classify
+//     the fine cells of mixed coarse cells.
+//  3. For every fine row with a BOUNDARY fine cell, the edges meeting the row's
+//     open strip are stored once, sorted by max x descending; a BOUNDARY entry
+//     points at the prefix with max x > the fine cell's x0.
+// Then the records of all polygons are bucketed by coarse cell in polygon
+// order, so every list is sorted by polygon id.
 #include "spx_internal.h"
 
 #include <algorithm>
@@ -39,15 +42,24 @@ inline int64_t ceil_div(int64_t a, int64_t b) // b > 0
     return (a % b != 0 && a > 0) ? q + 1 : q;
 }
 
+// (coarse cell, polygon): wholly inside, or mixed with its fine detail
 struct Rec {
-    uint32_t cell, poly, flags, edge_begin, edge_cnt;
+    uint32_t cell, poly, mixed, fine_idx;
+};
+
+// fine detail of one mixed (coarse cell, polygon)
+struct FineRec {
+    uint64_t inside = 0, bnd = 0;        // bit (fy mod F) * F + (fx mod F)
+    uint32_t row_begin[1 << kMaxSubLog2] = {}; // first edge of each fine row's list
+    uint16_t cnt[1 << (2 * kMaxSubLog2)] = {};  // edges listed for each BOUNDARY fine cell
 };
 
 struct Part {
     std::vector<Rec> recs;
+    std::vector<FineRec> fine;
     std::vector<int32_t> edges; // 4 per edge
-    uint64_t n_boundary = 0, n_inside = 0;
-    bool overflow = false;
+    uint64_t n_inside = 0, n_mixed = 0, n_boundary = 0;
+    std::string err;
 };
 
 struct RowEdge {
@@ -55,13 +67,37 @@ struct RowEdge {
     uint32_t idx;
 };
 
-void build_polygon(const int32_t *r, uint64_t nv, uint32_t q, int g, Part &out)
+// x of edge a->b at height Y, as floor and ceil (exact)
+inline void x_at(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t Y, int64_t &fl, int64_t &ce)
+{
+    int64_t num = (bx - ax) * (Y - ay), den = by - ay;
+    if (den < 0) {
+        num = -num;
+        den = -den;
+    }
+    fl = ax + floor_div(num, den);
+    ce = ax + ceil_div(num, den);
+}
+
+// largest corner x (in cells of side S) that edge a->b counts for at height y0,
+// where the edge straddles y0: x0 counts iff x0 < crossing
+inline int64_t corner_threshold(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t y0, int64_t S)
+{
+    int64_t num = (bx - ax) * (y0 - ay), den = by - ay;
+    if (den < 0) {
+        num = -num;
+        den = -den;
+    }
+    return floor_div(ax + ceil_div(num, den) - 1, S);
+}
+
+void build_polygon(const int32_t *r, uint64_t nv, uint32_t q, int gc, int sb, Part &out)
 {
     if (nv < 3)
         return; // fewer than 3 vertices: no point is inside (the crossings cancel)
-    const int shift = kBoxLog2 - g;
-    const int64_t S = int64_t(1) << shift;
-    const int64_t G = int64_t(1) << g;
+    const int gf = gc + sb, sc = kBoxLog2 - gc, sf = kBoxLog2 - gf, F = 1 << sb;
+    const int64_t Sc = int64_t(1) << sc, Sf = int64_t(1) << sf;
+    const int64_t Gc = int64_t(1) << gc, Gf = int64_t(1) << gf;
     int64_t xmin = INT64_MAX, xmax = INT64_MIN, ymin = INT64_MAX, ymax = INT64_MIN;
     for (uint64_t k = 0; k < nv; ++k) {
         xmin = std::min<int64_t>(xmin, r[2 * k]);
@@ -71,60 +107,67 @@ void build_polygon(const int32_t *r, uint64_t nv, uint32_t q, int g, Part &out)
     }
     if (xmax <= xmin || ymax <= ymin)
         return; // inside implies xmin <= px < xmax and ymin <= py < ymax: empty
-    const int64_t cx0 = xmin >> shift, cx1 = std::min((xmax - 1) >> shift, G - 1);
-    const int64_t cy0 = ymin >> shift, cy1 = std::min((ymax - 1) >> shift, G - 1);
-    const int64_t W = cx1 - cx0 + 1, H = cy1 - cy0 + 1;
-    std::vector<uint8_t> bnd(size_t(W * H), 0);
-    std::vector<std::pair<uint32_t, uint32_t>> row_edge; // (row - cy0, edge index)
+    const int64_t cx0 = xmin >> sc, cx1 = std::min((xmax - 1) >> sc, Gc - 1);
+    const int64_t cy0 = ymin >> sc, cy1 = std::min((ymax - 1) >> sc, Gc - 1);
+    const int64_t fx0 = xmin >> sf, fx1 = std::min((xmax - 1) >> sf, Gf - 1);
+    const int64_t fy0 = ymin >> sf, fy1 = std::min((ymax - 1) >> sf, Gf - 1);
+    const int64_t Wc = cx1 - cx0 + 1, Hc = cy1 - cy0 + 1, Hf = fy1 - fy0 + 1;
+    std::vector<uint8_t> cb(size_t(Wc * Hc), 0);   // coarse cell is mixed
+    std::vector<uint64_t> fm(size_t(Wc * Hc), 0);  // fine BOUNDARY bits per coarse cell
+    std::vector<std::pair<uint32_t, uint32_t>> row_edge; // (fine row - fy0, edge index)
 
-    auto mark = [&](int64_t row, int64_t clo, int64_t chi) {
+    auto mark_c = [&](int64_t row, int64_t lo, int64_t hi) {
         if (row < cy0 || row > cy1)
             return;
-        clo = std::max(clo, cx0);
-        chi = std::min(chi, cx1);
-        uint8_t *b = &bnd[size_t((row - cy0) * W)];
-        for (int64_t c = clo; c <= chi; ++c)
+        lo = std::max(lo, cx0);
+        hi = std::min(hi, cx1);
+        uint8_t *b = &cb[size_t((row - cy0) * Wc)];
+        for (int64_t c = lo; c <= hi; ++c)
             b[c - cx0] = 1;
     };
-    // x of the edge at height Y as floor and ceil (exact rational arithmetic)
-    auto x_at = [](int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t Y, int64_t &fl, int64_t &ce) {
-        int64_t num = (bx - ax) * (Y - ay), den = by - ay;
-        if (den < 0) {
-            num = -num;
-            den = -den;
-        }
-        fl = ax + floor_div(num, den);
-        ce = ax + ceil_div(num, den);
+    auto mark_f = [&](int64_t frow, int64_t lo, int64_t hi) {
+        if (frow < fy0 || frow > fy1)
+            return;
+        lo = std::max(lo, fx0);
+        hi = std::min(hi, fx1);
+        const int64_t crow = (frow >> sb) - cy0;
+        const int bit0 = int(frow & (F - 1)) * F;
+        for (int64_t fx = lo; fx <= hi; ++fx)
+            fm[size_t(crow * Wc + ((fx >> sb) - cx0))] |= uint64_t(1) << (bit0 + int(fx & (F - 1)));
     };
 
     for (uint64_t i = 0; i < nv; ++i) {
-        uint64_t j = (i + 1 == nv) ? 0 : i + 1;
+        const uint64_t j = (i + 1 == nv) ? 0 : i + 1;
         const int64_t ax = r[2 * i], ay = r[2 * i + 1], bx = r[2 * j], by = r[2 * j + 1];
         if (ay == by) {
-            if (ay % S == 0)
-                continue; // on a row border: meets no open cell square
+            // a horizontal edge meets the open squares of its row unless it lies on a row border
             const int64_t lo = std::min(ax, bx), hi = std::max(ax, bx);
-            mark(ay >> shift, floor_div(lo, S), ceil_div(hi, S) - 1);
-            continue; // horizontal edges never straddle: not in any row list
+            if (ay % Sc != 0)
+                mark_c(ay >> sc, floor_div(lo, Sc), ceil_div(hi, Sc) - 1);
+            if (ay % Sf != 0)
+                mark_f(ay >> sf, floor_div(lo, Sf), ceil_div(hi, Sf) - 1);
+            continue; // never straddles: in no row list
         }
         const int64_t lo_y = std::min(ay, by), hi_y = std::max(ay, by);
-        const int64_t r0 = std::max(lo_y >> shift, cy0);
-        const int64_t r1 = std::min(ceil_div(hi_y, S) - 1, cy1);
-        for (int64_t row = r0; row <= r1; ++row) {
-            row_edge.emplace_back(uint32_t(row - cy0), uint32_t(i));
-            const int64_t Ya = std::max(lo_y, row * S), Yb = std::min(hi_y, (row + 1) * S);
-            int64_t fa, ca, fb, cb;
-            x_at(ax, ay, bx, by, Ya, fa, ca);
-            x_at(ax, ay, bx, by, Yb, fb, cb);
-            const int64_t xlo = std::min(fa, fb), xhi = std::max(ca, cb);
-            mark(row, floor_div(xlo, S), ceil_div(xhi, S) - 1);
+        for (int64_t row = std::max(lo_y >> sc, cy0), r1 = std::min(ceil_div(hi_y, Sc) - 1, cy1); row <= r1; ++row) {
+            int64_t fa, ca, fb, cb2;
+            x_at(ax, ay, bx, by, std::max(lo_y, row * Sc), fa, ca);
+            x_at(ax, ay, bx, by, std::min(hi_y, (row + 1) * Sc), fb, cb2);
+            mark_c(row, floor_div(std::min(fa, fb), Sc), ceil_div(std::max(ca, cb2), Sc) - 1);
+        }
+        for (int64_t fr = std::max(lo_y >> sf, fy0), r1 = std::min(ceil_div(hi_y, Sf) - 1, fy1); fr <= r1; ++fr) {
+            row_edge.emplace_back(uint32_t(fr - fy0), uint32_t(i));
+            int64_t fa, ca, fb, cb2;
+            x_at(ax, ay, bx, by, std::max(lo_y, fr * Sf), fa, ca);
+            x_at(ax, ay, bx, by, std::min(hi_y, (fr + 1) * Sf), fb, cb2);
+            mark_f(fr, floor_div(std::min(fa, fb), Sf), ceil_div(std::max(ca, cb2), Sf) - 1);
         }
     }
-    // bucket the row list by row (stable: edges keep ring order within a row)
-    std::vector<uint32_t> row_off(size_t(H + 1), 0);
+    // fine row lists (bucketed, ring order kept within a row)
+    std::vector<uint32_t> row_off(size_t(Hf + 1), 0);
     for (auto &p : row_edge)
         row_off[p.first + 1]++;
-    for (int64_t k = 0; k < H; ++k)
+    for (int64_t k = 0; k < Hf; ++k)
         row_off[k + 1] += row_off[k];
     std::vector<uint32_t> row_list(row_edge.size());
     {
@@ -132,77 +175,138 @@ void build_polygon(const int32_t *r, uint64_t nv, uint32_t q, int g, Part &out)
         for (auto &p : row_edge)
             row_list[cur[p.first]++] = p.second;
     }
+    auto edge_of = [&](uint32_t i, int64_t &ax, int64_t &ay, int64_t &bx, int64_t &by) {
+        const uint64_t j = (uint64_t(i) + 1 == nv) ? 0 : uint64_t(i) + 1;
+        ax = r[2 * uint64_t(i)];
+        ay = r[2 * uint64_t(i) + 1];
+        bx = r[2 * j];
+        by = r[2 * j + 1];
+    };
 
-    std::vector<uint8_t> flip(size_t(W), 0);
-    std::vector<RowEdge> sorted;
-    for (int64_t row = cy0; row <= cy1; ++row) {
-        const int64_t y0 = row * S;
-        const uint32_t *le = row_list.data() + row_off[row - cy0];
-        const uint32_t ne = row_off[row - cy0 + 1] - row_off[row - cy0];
-        // scanline status of the cell corners (x0, y0) of this row
-        std::fill(flip.begin(), flip.end(), 0);
-        uint8_t all = 0; // parity of edges that count for every cell of the row
-        for (uint32_t k = 0; k < ne; ++k) {
-            uint64_t i = le[k], j = (i + 1 == nv) ? 0 : i + 1;
-            const int64_t ax = r[2 * i], ay = r[2 * i + 1], bx = r[2 * j], by = r[2 * j + 1];
-            if ((ay > y0) == (by > y0))
-                continue;
-            int64_t num = (bx - ax) * (y0 - ay), den = by - ay;
-            if (den < 0) {
-                num = -num;
-                den = -den;
-            }
-            // corner x counts iff x < a.x + num/den  <=>  x <= a.x + ceil(num/den) - 1
-            const int64_t kx = floor_div(ax + ceil_div(num, den) - 1, S);
-            if (kx >= cx1)
-                all ^= 1;
-            else if (kx >= cx0)
-                flip[size_t(kx - cx0)] ^= 1;
+    // one FineRec per mixed coarse cell
+    std::vector<int64_t> fr_idx(size_t(Wc * Hc), -1);
+    for (size_t k = 0; k < cb.size(); ++k)
+        if (cb[k]) {
+            fr_idx[k] = int64_t(out.fine.size());
+            out.fine.emplace_back();
+            out.fine.back().bnd = fm[k];
         }
-        const uint8_t *b = &bnd[size_t((row - cy0) * W)];
-        bool any_b = false;
-        for (int64_t c = 0; c < W; ++c)
-            any_b |= b[c] != 0;
+
+    // coarse scanline: status of the corners of the coarse cells that are not mixed
+    std::vector<uint8_t> flip(size_t(Wc), 0);
+    for (int64_t cy = cy0; cy <= cy1; ++cy) {
+        const int64_t y0 = cy * Sc;
+        const int64_t fr = cy << sb; // the fine row whose strip starts at y0
+        std::fill(flip.begin(), flip.end(), 0);
+        uint8_t all = 0;
+        if (fr >= fy0 && fr <= fy1) {
+            for (uint32_t k = row_off[fr - fy0]; k < row_off[fr - fy0 + 1]; ++k) {
+                int64_t ax, ay, bx, by;
+                edge_of(row_list[k], ax, ay, bx, by);
+                if ((ay > y0) == (by > y0))
+                    continue;
+                const int64_t kx = corner_threshold(ax, ay, bx, by, y0, Sc);
+                if (kx >= cx1)
+                    all ^= 1;
+                else if (kx >= cx0)
+                    flip[size_t(kx - cx0)] ^= 1;
+            }
+        } // else every vertex lies above y0: nothing straddles it
+        uint8_t par = all;
+        for (int64_t c = Wc - 1; c >= 0; --c) {
+            par ^= flip[size_t(c)]; // parity of thresholds >= cx0 + c
+            const size_t k = size_t((cy - cy0) * Wc + c);
+            const uint32_t cell = uint32_t((cy << gc) | (cx0 + c));
+            if (cb[k]) {
+                out.recs.push_back({cell, q, 1u, uint32_t(fr_idx[k])});
+                out.n_mixed++;
+            } else if (par) {
+                out.recs.push_back({cell, q, 0u, 0u});
+                out.n_inside++;
+            }
+        }
+    }
+
+    // fine rows: classify the fine cells of mixed coarse cells, store edge lists
+    std::vector<int64_t> thr;
+    std::vector<RowEdge> sorted;
+    const uint64_t row_bits = (F == 8) ? 0xFFull : ((uint64_t(1) << F) - 1);
+    for (int64_t fy = fy0; fy <= fy1; ++fy) {
+        const int64_t y0 = fy * Sf;
+        const uint32_t *le = row_list.data() + row_off[fy - fy0];
+        const uint32_t ne = row_off[fy - fy0 + 1] - row_off[fy - fy0];
+        const int64_t crow = (fy >> sb) - cy0;
+        const int rb = int(fy & (F - 1));
+        const uint64_t rmask = row_bits << (rb * F);
+        bool any_b = false, any_m = false;
+        for (int64_t c = 0; c < Wc; ++c) {
+            const size_t k = size_t(crow * Wc + c);
+            if (cb[k]) {
+                any_m = true;
+                any_b |= (fm[k] & rmask) != 0;
+            }
+        }
+        if (!any_m)
+            continue;
+        thr.clear();
+        for (uint32_t k = 0; k < ne; ++k) {
+            int64_t ax, ay, bx, by;
+            edge_of(le[k], ax, ay, bx, by);
+            if ((ay > y0) != (by > y0))
+                thr.push_back(corner_threshold(ax, ay, bx, by, y0, Sf));
+        }
+        std::sort(thr.begin(), thr.end());
         uint32_t list_begin = 0;
+        sorted.clear();
         if (any_b) {
-            sorted.clear();
             for (uint32_t k = 0; k < ne; ++k) {
-                uint64_t i = le[k], j = (i + 1 == nv) ? 0 : i + 1;
-                sorted.push_back({std::max<int64_t>(r[2 * i], r[2 * j]), le[k]});
+                int64_t ax, ay, bx, by;
+                edge_of(le[k], ax, ay, bx, by);
+                sorted.push_back({std::max(ax, bx), le[k]});
             }
             std::stable_sort(sorted.begin(), sorted.end(),
                              [](const RowEdge &u, const RowEdge &v) { return u.xmax > v.xmax; });
             if (out.edges.size() / 4 + sorted.size() >= (uint64_t(1) << 32)) {
-                out.overflow = true;
+                out.err = "index too large (edge list limit 2^32)";
                 return;
             }
             list_begin = uint32_t(out.edges.size() / 4);
             for (auto &e : sorted) {
-                uint64_t i = e.idx, j = (i + 1 == nv) ? 0 : i + 1;
-                out.edges.push_back(r[2 * i]);
-                out.edges.push_back(r[2 * i + 1]);
-                out.edges.push_back(r[2 * j]);
-                out.edges.push_back(r[2 * j + 1]);
+                int64_t ax, ay, bx, by;
+                edge_of(e.idx, ax, ay, bx, by);
+                out.edges.push_back(int32_t(ax));
+                out.edges.push_back(int32_t(ay));
+                out.edges.push_back(int32_t(bx));
+                out.edges.push_back(int32_t(by));
             }
         }
-        uint8_t par = all;
-        uint32_t n_right = 0; // edges of `sorted` with xmax > x0, tracked from the right
-        for (int64_t c = W - 1; c >= 0; --c) {
-            const int64_t cx = cx0 + c;
-            if (c < W - 1)
-                par ^= flip[size_t(c)];
-            else
-                par ^= flip[size_t(c)]; // kx == cx1 was folded into `all`; flip[W-1] is always 0
-            const uint32_t cell = uint32_t((row << g) | cx);
-            if (b[c]) {
-                const int64_t x0 = cx * S;
-                while (n_right < sorted.size() && sorted[n_right].xmax > x0)
-                    ++n_right;
-                out.recs.push_back({cell, q, kEntBoundary, list_begin, n_right});
-                out.n_boundary++;
-            } else if (par) {
-                out.recs.push_back({cell, q, 0u, 0u, 0u});
-                out.n_inside++;
+        for (int64_t c = 0; c < Wc; ++c) {
+            const size_t k = size_t(crow * Wc + c);
+            if (!cb[k])
+                continue;
+            FineRec &fr = out.fine[size_t(fr_idx[k])];
+            fr.row_begin[rb] = list_begin;
+            const int64_t ccx = cx0 + c;
+            for (int64_t fx = std::max(ccx << sb, fx0), fe = std::min((ccx << sb) + F - 1, fx1); fx <= fe; ++fx) {
+                const int bit = rb * F + int(fx & (F - 1));
+                if ((fr.bnd >> bit) & 1) {
+                    const int64_t x0 = fx * Sf;
+                    // edges with max x > x0: a prefix of the descending list
+                    const auto it = std::partition_point(sorted.begin(), sorted.end(),
+                                                         [x0](const RowEdge &e) { return e.xmax > x0; });
+                    const size_t n = size_t(it - sorted.begin());
+                    if (n > 0xFFFF) {
+                        out.err = "a fine row edge list exceeds 65535 edges; use a finer grid";
+                        return;
+                    }
+                    fr.cnt[bit] = uint16_t(n);
+                    out.n_boundary++;
+                } else {
+                    // corners right of fx count no threshold below fx
+                    const size_t n_ge = size_t(thr.end() - std::lower_bound(thr.begin(), thr.end(), fx));
+                    if (n_ge & 1)
+                        fr.inside |= uint64_t(1) << bit;
+                }
             }
         }
     }
@@ -231,16 +335,20 @@ int default_grid_log2(const int32_t *xy, const uint64_t *ring_off, uint32_t P)
         return 6;
     std::nth_element(side.begin(), side.begin() + side.size() / 2, side.end());
     const double med = side[side.size() / 2];
-    // about 16 cells across a typical polygon
-    int g = int(std::lround(std::log2(16.0 / std::max(med, 1e-9))));
-    return std::min(std::max(g, 6), 12);
+    // about 8 coarse cells across a typical polygon (64 fine cells with F = 8)
+    int g = int(std::lround(std::log2(8.0 / std::max(med, 1e-9))));
+    return std::min(std::max(g, 5), 11);
 }
 
-bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int g, int threads, HostIndex &out,
-                      std::string &err)
+bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int g, int sb, int threads,
+                      HostIndex &out, std::string &err)
 {
     if (g < 1 || g > kMaxGridLog2) {
         err = "grid_log2 out of range [1, 13]";
+        return false;
+    }
+    if (sb < 0 || sb > kMaxSubLog2 || g + sb > kMaxFineLog2) {
+        err = "sub_log2 out of range [0, 3] (and grid_log2 + sub_log2 <= 16)";
         return false;
     }
     if (P >= (1u << 30)) {
@@ -249,7 +357,7 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
     }
     threads = std::max(1, std::min(threads, int(P ? P : 1)));
     std::vector<Part> parts(static_cast<size_t>(threads));
-    // polygons are split by vertex count so the threads get similar work
+    // polygons split by vertex count, so the threads get similar work
     std::vector<uint32_t> split(static_cast<size_t>(threads + 1), P);
     split[0] = 0;
     {
@@ -262,8 +370,9 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
             split[size_t(t)] = P;
     }
     auto work = [&](int t) {
-        for (uint32_t q = split[size_t(t)]; q < split[size_t(t + 1)] && !parts[size_t(t)].overflow; ++q)
-            build_polygon(xy + 2 * ring_off[q], ring_off[q + 1] - ring_off[q], q, g, parts[size_t(t)]);
+        Part &pt = parts[size_t(t)];
+        for (uint32_t q = split[size_t(t)]; q < split[size_t(t + 1)] && pt.err.empty(); ++q)
+            build_polygon(xy + 2 * ring_off[q], ring_off[q + 1] - ring_off[q], q, g, sb, pt);
     };
     std::vector<std::thread> pool;
     for (int t = 1; t < threads; ++t)
@@ -274,84 +383,116 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
 
     out = HostIndex();
     out.grid_log2 = g;
+    out.sub_log2 = sb;
     out.n_polys = P;
+    const int F = 1 << sb, FF = F * F;
     const uint64_t n_cells = uint64_t(1) << (2 * g);
-    uint64_t n_recs = 0, n_edges = 0;
+    // concatenate fine records and edges; fix part-local indices
+    std::vector<FineRec> fine_all;
+    uint64_t n_edges = 0, n_fine = 0;
     for (auto &p : parts) {
-        if (p.overflow) {
-            err = "index too large (edge list limit 2^32)";
+        if (!p.err.empty()) {
+            err = p.err;
             return false;
         }
-        n_recs += p.recs.size();
         n_edges += p.edges.size() / 4;
-        out.n_boundary += p.n_boundary;
+        n_fine += p.fine.size();
         out.n_inside += p.n_inside;
+        out.n_mixed += p.n_mixed;
+        out.n_boundary += p.n_boundary;
     }
     if (n_edges >= (uint64_t(1) << 32)) {
         err = "index too large (edge list limit 2^32)";
         return false;
     }
-    // bucket records by cell; parts and records within a part are in polygon order
+    out.edges.resize(size_t(n_edges) * 4);
+    fine_all.reserve(size_t(n_fine));
     std::vector<uint32_t> cnt(size_t(n_cells) + 1, 0);
-    for (auto &p : parts)
-        for (auto &rc : p.recs)
-            cnt[rc.cell + 1]++;
-    out.cell.assign(size_t(n_cells), 0);
-    uint64_t n_entries = 0;
-    std::vector<uint32_t> ent_off(size_t(n_cells), 0);
-    for (uint64_t c = 0; c < n_cells; ++c) {
-        ent_off[c] = uint32_t(n_entries);
-        const uint32_t k = cnt[c + 1];
-        if (k >= 2 || k == 1) {
-            // a single INSIDE polygon is stored in the cell word itself (decided below)
-            n_entries += k;
+    {
+        uint64_t eb = 0, fb = 0;
+        for (auto &p : parts) {
+            for (auto &fr : p.fine) {
+                for (int k = 0; k < F; ++k)
+                    fr.row_begin[k] += uint32_t(eb);
+                fine_all.push_back(fr);
+            }
+            for (auto &rc : p.recs) {
+                rc.fine_idx += uint32_t(fb);
+                cnt[rc.cell + 1]++;
+            }
+            std::copy(p.edges.begin(), p.edges.end(), out.edges.begin() + ptrdiff_t(eb * 4));
+            eb += p.edges.size() / 4;
+            fb += p.fine.size();
+            std::vector<FineRec>().swap(p.fine);
+            std::vector<int32_t>().swap(p.edges);
         }
-        if (n_entries >= (uint64_t(1) << 30)) {
-            err = "index too large (entry limit 2^30)";
+    }
+    for (uint64_t c = 0; c < n_cells; ++c)
+        cnt[c + 1] += cnt[c];
+    std::vector<Rec> recs(cnt[n_cells]);
+    {
+        std::vector<uint32_t> cur(cnt.begin(), cnt.end() - 1);
+        for (auto &p : parts) {
+            for (auto &rc : p.recs)
+                recs[cur[rc.cell]++] = rc;
+            std::vector<Rec>().swap(p.recs);
+        }
+    }
+    out.cell.assign(size_t(n_cells), 0);
+    std::vector<uint32_t> list; // scratch: (poly, flags, edge_begin, edge_cnt) per entry
+    for (uint64_t c = 0; c < n_cells; ++c) {
+        const uint32_t b0 = cnt[c], b1 = cnt[c + 1];
+        if (b0 == b1)
+            continue;
+        if (b1 - b0 == 1 && !recs[b0].mixed) {
+            out.cell[c] = (kCellInsideOne << 30) | recs[b0].poly;
+            continue;
+        }
+        const uint64_t blk = out.n_blocks++;
+        if ((blk + 1) * uint64_t(FF) >= (uint64_t(1) << 32) || blk >= (uint64_t(1) << 30)) {
+            err = "index too large (fine block limit)";
             return false;
         }
-    }
-    out.entries.assign(size_t(n_entries) * 4, 0);
-    out.edges.resize(size_t(n_edges) * 4);
-    std::vector<uint32_t> fill(ent_off);
-    uint64_t edge_base = 0;
-    for (auto &p : parts) {
-        for (auto &rc : p.recs) {
-            uint32_t *e = &out.entries[size_t(fill[rc.cell]++) * 4];
-            e[0] = rc.poly;
-            e[1] = uint32_t(rc.edge_begin + edge_base);
-            e[2] = rc.edge_cnt;
-            e[3] = rc.flags;
+        out.cell[c] = (kCellSub << 30) | uint32_t(blk);
+        out.fine.resize(size_t((blk + 1) * FF), 0);
+        for (int f = 0; f < FF; ++f) {
+            list.clear();
+            for (uint32_t m = b0; m < b1; ++m) {
+                const Rec &rc = recs[m];
+                if (!rc.mixed) {
+                    list.insert(list.end(), {rc.poly, 0u, 0u, 0u});
+                    continue;
+                }
+                const FineRec &fr = fine_all[rc.fine_idx];
+                if ((fr.bnd >> f) & 1)
+                    list.insert(list.end(), {rc.poly, kEntBoundary, fr.row_begin[f / F], uint32_t(fr.cnt[f])});
+                else if ((fr.inside >> f) & 1)
+                    list.insert(list.end(), {rc.poly, 0u, 0u, 0u});
+            }
+            const size_t n = list.size() / 4;
+            uint32_t w = 0;
+            if (n == 1 && list[1] == 0u) {
+                w = (kCellInsideOne << 30) | list[0];
+            } else if (n >= 1) {
+                const uint64_t e0 = out.entries.size() / 4;
+                if (e0 + n >= (uint64_t(1) << 30)) {
+                    err = "index too large (entry limit 2^30)";
+                    return false;
+                }
+                for (size_t m = 0; m < n; ++m) {
+                    // entry = (poly, edge_begin, edge_cnt, flags)
+                    out.entries.push_back(list[4 * m]);
+                    out.entries.push_back(list[4 * m + 2]);
+                    out.entries.push_back(list[4 * m + 3]);
+                    out.entries.push_back(list[4 * m + 1] | (m + 1 == n ? kEntLast : 0u));
+                }
+                w = (kCellList << 30) | uint32_t(e0);
+            }
+            out.fine[size_t(blk * FF + uint64_t(f))] = w;
         }
-        std::copy(p.edges.begin(), p.edges.end(), out.edges.begin() + ptrdiff_t(edge_base * 4));
-        edge_base += p.edges.size() / 4;
-        std::vector<Rec>().swap(p.recs);
-        std::vector<int32_t>().swap(p.edges);
     }
-    // cell words; drop the entry of cells whose only polygon is INSIDE
-    std::vector<uint32_t> keep(size_t(n_entries) * 4);
-    uint64_t kept = 0;
-    for (uint64_t c = 0; c < n_cells; ++c) {
-        const uint32_t k = cnt[c + 1];
-        if (k == 0)
-            continue;
-        const uint32_t *e = &out.entries[size_t(ent_off[c]) * 4];
-        if (k == 1 && (e[3] & kEntBoundary) == 0) {
-            out.cell[c] = (kCellInsideOne << 30) | e[0];
-            continue;
-        }
-        out.cell[c] = (kCellList << 30) | uint32_t(kept);
-        for (uint32_t m = 0; m < k; ++m) {
-            uint32_t *d = &keep[size_t(kept + m) * 4];
-            d[0] = e[4 * m];
-            d[1] = e[4 * m + 1];
-            d[2] = e[4 * m + 2];
-            d[3] = e[4 * m + 3] | (m + 1 == k ? kEntLast : 0u);
-        }
-        kept += k;
-    }
-    keep.resize(size_t(kept) * 4);
-    out.entries.swap(keep);
+    // sentinel entry: the kernels read entries two at a time
+    out.entries.insert(out.entries.end(), {0u, 0u, 0u, kEntLast});
     return true;
 }
 

@@ -7,17 +7,21 @@
 namespace spx {
 
 struct IndexView {
-    const uint32_t *cell; // 4^g cell words
+    const uint32_t *cell; // 4^g coarse words
+    const uint32_t *fine; // blocks of 4^sub fine words
     const uint4 *ent;     // entries
-    const int4 *edge;     // per-row edge lists
-    int shift;            // 30 - g
-    int glog2;            // g
+    const int4 *edge;     // per-fine-row edge lists
+    int sc;               // coarse shift: 30 - g
+    int gc;               // g
+    int sf;               // fine shift: 30 - g - sub
+    int sb;               // sub
     uint32_t P;           // number of polygons
 };
 
 // Device status word bits (ORed into the ctx's persistent error word).
 constexpr unsigned kErrTimeout = 1u;   // a bounded wait on another tile's status gave up
 constexpr unsigned kErrInternal = 2u;  // an internal consistency check failed
+constexpr unsigned kErrCopy = 4u;      // a bounded wait for a bulk copy gave up
 
 // Per-ctx device counters, in this order.
 enum { kStatPoints = 0, kStatTests = 1, kStatEscalations = 2, kStatPairs = 3, kStatCount = 4 };
@@ -44,7 +48,8 @@ size_t plain_scratch_bytes(uint64_t n);
 // scratch: device memory of join_scratch_bytes(n) bytes; zeroed inside.
 cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s);
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s);
-cudaError_t launch_aggregate(const JoinLaunch &a, cudaStream_t s);
+// scratch: at least 16 bytes of device memory (zeroed inside).
+cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s);
 
 int device_sm_count();
 

@@ -11,47 +11,60 @@ namespace spx {
 
 constexpr int kBoxLog2 = 30;            // points in [0, 2^30)^2, vertices in [0, 2^30]^2
 constexpr uint32_t kBox = 1u << kBoxLog2;
-constexpr int kMaxGridLog2 = 13;
+constexpr int kMaxGridLog2 = 13;       // coarse grid: at most 2^13 cells per side
+constexpr int kMaxSubLog2 = 3;         // a mixed coarse cell splits into at most 8 x 8 fine cells
+constexpr int kMaxFineLog2 = 16;       // fine cells at least 2^14 units wide
 
-// Cell word (uint32, one per grid cell, row-major, cell = (cy << g) | cx):
+// Two-level grid.  Coarse cell word (uint32, row-major, cell = (cy << g) | cx):
 //   bits 31..30 = kind, bits 29..0 = payload
 //   kind 0: no polygon can contain a point of this cell
-//   kind 1: exactly one polygon, and the cell is INSIDE it: payload = polygon id
-//   kind 2: a list: payload = index of the cell's first entry in `entries`
+//   kind 1: exactly one polygon, and the whole cell is INSIDE it: payload = polygon id
+//   kind 2: mixed: payload = block b; the cell's F x F fine cells (F = 2^sub)
+//           have words fine[b * F*F + (fy mod F) * F + (fx mod F)]
+// Fine cell word: kind 0 none, kind 1 one INSIDE polygon (payload = id),
+//   kind 2 list: payload = index of the fine cell's first entry in `entries`.
 constexpr uint32_t kCellEmpty = 0u;
 constexpr uint32_t kCellInsideOne = 1u;
-constexpr uint32_t kCellList = 2u;
+constexpr uint32_t kCellSub = 2u;  // coarse words
+constexpr uint32_t kCellList = 2u; // fine words
 constexpr uint32_t kPayloadMask = (1u << 30) - 1;
 
 // Entry (uint4): x = polygon id, y = first edge (index into `edges`),
-// z = number of edges, w = flags.  A cell's entries are contiguous and sorted
-// by polygon id; the last one carries kEntLast.
+// z = number of edges, w = flags.  A fine cell's entries are contiguous and
+// sorted by polygon id; the last one carries kEntLast.
 constexpr uint32_t kEntBoundary = 1u; // run the exact crossing test on the listed edges
 constexpr uint32_t kEntLast = 2u;
 
 // Edge (int4): (a.x, a.y, b.x, b.y), the directed edge a -> b of the ring.
-// A BOUNDARY entry of cell (cx, cy) points at the polygon's edge list of row
-// cy: every non-horizontal edge whose y-span meets the row's open strip, sorted
-// by max(a.x, b.x) descending, cut to the edges with max(a.x, b.x) > x0 of the
-// cell.  Any edge that a rightward ray from a point of the cell can cross is in
-// that list, so the parity over it equals the parity over the whole ring.
+// A BOUNDARY entry of fine cell (fx, fy) points at the polygon's edge list of
+// fine row fy: every non-horizontal edge whose y-span meets the row's open
+// strip, sorted by max(a.x, b.x) descending, cut to the edges with
+// max(a.x, b.x) > x0 of the cell.  Every edge that a rightward ray from a
+// point of the cell can cross is in that list, so the parity over it equals
+// the parity over the whole ring.
 
 struct HostIndex {
     int grid_log2 = 0;
+    int sub_log2 = 0;
     uint32_t n_polys = 0;
-    std::vector<uint32_t> cell;      // 4^g words
+    std::vector<uint32_t> cell;      // 4^g coarse words
+    std::vector<uint32_t> fine;      // n_blocks * 4^sub fine words
     std::vector<uint32_t> entries;   // 4 words per entry
     std::vector<int32_t> edges;      // 4 ints per edge
-    uint64_t n_boundary = 0, n_inside = 0;
+    uint64_t n_blocks = 0;
+    uint64_t n_inside = 0;           // (coarse cell, polygon) pairs wholly inside
+    uint64_t n_mixed = 0;            // (coarse cell, polygon) pairs split into fine cells
+    uint64_t n_boundary = 0;         // (fine cell, polygon) pairs that need the exact test
 };
 
 // Build the index of P rings (xy: interleaved int32 pairs, ring_off: P + 1
-// offsets in vertices).  Returns false and sets err on bad input or if a limit
-// is exceeded (P, entries < 2^30, edges < 2^32).
-bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int grid_log2, int threads,
-                      HostIndex &out, std::string &err);
+// offsets in vertices) with 2^grid_log2 coarse cells per side, each mixed
+// cell split into 2^sub_log2 x 2^sub_log2 fine cells.  Returns false and sets
+// err on bad input or if a limit is exceeded.
+bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int grid_log2, int sub_log2,
+                      int threads, HostIndex &out, std::string &err);
 
-// Heuristic grid resolution from the polygon set alone.
+// Heuristic coarse grid resolution from the polygon set alone.
 int default_grid_log2(const int32_t *xy, const uint64_t *ring_off, uint32_t P);
 
 } // namespace spx

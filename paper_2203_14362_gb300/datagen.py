@@ -209,7 +209,7 @@ def _left_normal(d: np.ndarray) -> np.ndarray:
 
 
 def quad_tessellation(nx: int, ny: int, seed: int, kmin: int = 12, kmax: int = 499,
-                      jitter: float = 0.2, smooth: bool = True) -> Tessellation:
+                      jitter: float = 0.2, amp: float = 0.35, white: float = 0.03) -> Tessellation:
     """A tessellation of the closed box [0, 2^30]^2 into nx * ny cells.
 
     The cell corners form a lattice jittered by up to `jitter` of the spacing
@@ -218,8 +218,11 @@ def quad_tessellation(nx: int, ny: int, seed: int, kmin: int = 12, kmax: int = 4
     function over the edge, kept strictly inside the edge's kite (the two
     triangles spanned by the edge and the centroids of its two cells) with a
     10 % margin; kites of different edges do not overlap, so no two cell
-    boundaries cross.  Border edges get collinear extra vertices.  Each cell
-    ring is counter-clockwise and has 4 + the sum of its sides' k vertices.
+    boundaries cross.  The height profile is smooth like real boundaries: one
+    or two slow waves of amplitude `amp` of the kite height plus a small
+    vertex-to-vertex jitter (`white`).  Border edges get collinear extra
+    vertices.  Each cell ring is counter-clockwise and has 4 + the sum of its
+    sides' k vertices.
     """
     assert jitter <= 0.2 and nx >= 1 and ny >= 1
     sx, sy = BOX / nx, BOX / ny
@@ -275,13 +278,10 @@ def quad_tessellation(nx: int, ny: int, seed: int, kmin: int = 12, kmax: int = 4
         hl, hr = hmax(cl), hmax(cr)
         ks = stream_key(int(kk), "noise")
         w = unif(ks, 0, 8)
-        if smooth:
-            amps = 0.2 + w[:3]
-            ph = 2 * math.pi * w[3:6]
-            nz = sum(amps[f] * np.sin(2 * math.pi * (f + 1) * t + ph[f]) for f in range(3)) / amps.sum()
-            nz = 0.7 * nz + 0.3 * (2 * unif(stream_key(int(ks), "w"), 0, k) - 1)
-        else:
-            nz = 2 * unif(stream_key(int(ks), "w"), 0, k) - 1
+        amps = 0.2 + w[:2]
+        ph = 2 * math.pi * w[2:4]
+        nz = sum(amps[f] * np.sin(math.pi * (f + 1) * t + ph[f]) for f in range(2)) / amps.sum()
+        nz = amp * nz + white * (2 * unif(stream_key(int(ks), "w"), 0, k) - 1)
         nz = np.clip(nz, -1.0, 1.0)
         h = 0.9 * np.where(nz >= 0, nz * hl, nz * hr)
         return np.rint(base + h[:, None] * nrm[None, :])

@@ -33,12 +33,13 @@ class SpxError(RuntimeError):
 
 
 class IndexParams(C.Structure):
-    _fields_ = [("grid_log2", C.c_int), ("fp32_filter", C.c_int), ("reserved", C.c_int * 6)]
+    _fields_ = [("grid_log2", C.c_int), ("fp32_filter", C.c_int), ("sub_log2", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class IndexInfo(C.Structure):
-    _fields_ = [("grid_log2", C.c_int), ("n_polys", C.c_uint32), ("n_cells", C.c_uint64),
-                ("n_entries", C.c_uint64), ("n_boundary", C.c_uint64), ("n_inside", C.c_uint64),
+    _fields_ = [("grid_log2", C.c_int), ("sub_log2", C.c_int), ("n_polys", C.c_uint32), ("pad", C.c_uint32),
+                ("n_cells", C.c_uint64), ("n_blocks", C.c_uint64), ("n_entries", C.c_uint64),
+                ("n_inside", C.c_uint64), ("n_mixed", C.c_uint64), ("n_boundary", C.c_uint64),
                 ("n_edge_refs", C.c_uint64), ("device_bytes", C.c_uint64), ("build_ms", C.c_double)]
 
 
@@ -72,8 +73,8 @@ def load(path: str = LIB_PATH):
         "spx_join_plain": ([V, U64, U64, V, U64, V, V, P64, V], I),
         "spx_aggregate": ([V, U64, U64, V, V], I),
         "spx_join_host": ([V, V, U64, U64, V, U64, V, P64], I),
-        "spx_host_index_build": ([V, V, U32, I, C.POINTER(V), P64], I),
-        "spx_host_index_copy": ([V, V, V, V], I),
+        "spx_host_index_build": ([V, V, U32, I, I, C.POINTER(V), P64], I),
+        "spx_host_index_copy": ([V, V, V, V, V], I),
         "spx_host_index_free": ([V], None),
         "spx_stats": ([V, C.POINTER(Stats), I], I),
         "spx_free": ([V, U64], I),
@@ -100,26 +101,28 @@ def _dev_ptr(t):
 
 
 # ------------------------------------------------------------- host index build
-def host_index(verts: np.ndarray, ring_off: np.ndarray, grid_log2: int = 0):
-    """Build the grid index on the host only (spx_host_index_build) and return
-    (cells uint32 (G*G,), entries uint32 (E, 4), edges int32 (M, 4), g)."""
+def host_index(verts: np.ndarray, ring_off: np.ndarray, grid_log2: int = 0, sub_log2: int = 0):
+    """Build the grid index on the host only (spx_host_index_build); returns a
+    dict with coarse (uint32), fine (uint32), entries (E, 4) uint32, edges
+    (M, 4) int32, g and sub."""
     lib = load()
     xy = np.ascontiguousarray(verts, dtype=np.int32)
     off = np.ascontiguousarray(ring_off, dtype=np.uint64)
     h = C.c_void_p()
-    sizes = (C.c_uint64 * 3)()
-    st = lib.spx_host_index_build(_np_ptr(xy), _np_ptr(off), off.shape[0] - 1, grid_log2, C.byref(h), sizes)
+    sizes = (C.c_uint64 * 6)()
+    st = lib.spx_host_index_build(_np_ptr(xy), _np_ptr(off), off.shape[0] - 1, grid_log2, sub_log2, C.byref(h),
+                                  sizes)
     if st != SPX_OK:
         raise SpxError(st, "spx_host_index_build failed")
     try:
-        cells = np.zeros(sizes[0], np.uint32)
-        ent = np.zeros((sizes[1], 4), np.uint32)
-        edges = np.zeros((sizes[2], 4), np.int32)
-        lib.spx_host_index_copy(h, _np_ptr(cells), _np_ptr(ent), _np_ptr(edges))
+        coarse = np.zeros(sizes[0], np.uint32)
+        fine = np.zeros(max(sizes[1], 1), np.uint32)
+        ent = np.zeros((sizes[2], 4), np.uint32)
+        edges = np.zeros((sizes[3], 4), np.int32)
+        lib.spx_host_index_copy(h, _np_ptr(coarse), _np_ptr(fine), _np_ptr(ent), _np_ptr(edges))
     finally:
         lib.spx_host_index_free(h)
-    g = int(round(np.log2(cells.shape[0]) / 2))
-    return cells, ent, edges, g
+    return {"coarse": coarse, "fine": fine, "entries": ent, "edges": edges, "g": int(sizes[4]), "sub": int(sizes[5])}
 
 
 # ------------------------------------------------------------------- the engine
@@ -170,8 +173,8 @@ class Engine:
                     "spx_load_polygons")
         return h.value
 
-    def build_index(self, polys: int, grid_log2: int = 0, fp32_filter: bool = True) -> int:
-        p = IndexParams(grid_log2, 1 if fp32_filter else 0)
+    def build_index(self, polys: int, grid_log2: int = 0, fp32_filter: bool = True, sub_log2: int = 0) -> int:
+        p = IndexParams(grid_log2, 1 if fp32_filter else 0, sub_log2)
         h = C.c_uint64()
         self._check(self.lib.spx_build_index(self.ctx, polys, C.byref(p), C.byref(h)), "spx_build_index")
         return h.value

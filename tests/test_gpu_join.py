@@ -28,12 +28,12 @@ def eng():
     e.close()
 
 
-def run_join(eng, pts, v, o, gl, fp32=True, plain=False, cap=None):
+def run_join(eng, pts, v, o, gl, fp32=True, plain=False, cap=None, sub=0):
     P = o.shape[0] - 1
     dpts = torch.from_numpy(np.ascontiguousarray(pts)).cuda()  # borrowed: keep alive while the handle is used
     ph = eng.load_points(dpts)
     gh = eng.load_polygons(v, o)
-    ih = eng.build_index(gh, grid_log2=gl, fp32_filter=fp32)
+    ih = eng.build_index(gh, grid_log2=gl, fp32_filter=fp32, sub_log2=sub)
     cap = pts.shape[0] * 2 + 16 if cap is None else cap
     pairs = torch.full((max(cap, 1), 2), -1, dtype=torch.int32, device="cuda")
     counts = torch.zeros(max(P, 1), dtype=torch.int64, device="cuda")
@@ -48,12 +48,12 @@ def run_join(eng, pts, v, o, gl, fp32=True, plain=False, cap=None):
     return out, cnt, n
 
 
-def run_aggregate(eng, pts, v, o, gl, fp32=True):
+def run_aggregate(eng, pts, v, o, gl, fp32=True, sub=0):
     P = o.shape[0] - 1
     dpts = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
     ph = eng.load_points(dpts)
     gh = eng.load_polygons(v, o)
-    ih = eng.build_index(gh, grid_log2=gl, fp32_filter=fp32)
+    ih = eng.build_index(gh, grid_log2=gl, fp32_filter=fp32, sub_log2=sub)
     counts = torch.zeros(max(P, 1), dtype=torch.int64, device="cuda")
     eng.aggregate(ph, ih, counts)
     torch.cuda.synchronize()
@@ -84,23 +84,25 @@ def scaled_tiny(s_log2=26):
     return pts, v, off
 
 
-def check(eng, pts, v, o, gls=(4, 8, 11), aggregate=True):
+def check(eng, pts, v, o, gls=(4, 8, 11), aggregate=True, subs=(3,)):
     want_p, want_c = oracle.join_fast(pts, v, o)
+    cap = want_p.shape[0] + 5
     for gl in gls:
-        for fp32 in (True, False):
-            p, c, n = run_join(eng, pts, v, o, gl, fp32)
-            assert n == want_p.shape[0]
-            assert np.array_equal(p, want_p), f"pairs differ at g={gl} fp32={fp32}"
-            assert np.array_equal(c, want_c), f"counts differ at g={gl} fp32={fp32}"
-            if aggregate:
-                assert np.array_equal(run_aggregate(eng, pts, v, o, gl, fp32), want_c)
-    p, c, n = run_join(eng, pts, v, o, gls[0], plain=True)
+        for sub in subs:
+            for fp32 in (True, False):
+                p, c, n = run_join(eng, pts, v, o, gl, fp32, cap=cap, sub=sub)
+                assert n == want_p.shape[0]
+                assert np.array_equal(p, want_p), f"pairs differ at g={gl} sub={sub} fp32={fp32}"
+                assert np.array_equal(c, want_c), f"counts differ at g={gl} sub={sub} fp32={fp32}"
+                if aggregate:
+                    assert np.array_equal(run_aggregate(eng, pts, v, o, gl, fp32, sub), want_c)
+    p, c, n = run_join(eng, pts, v, o, gls[0], plain=True, cap=cap)
     assert np.array_equal(p, want_p) and np.array_equal(c, want_c), "plain kernels differ"
 
 
 def test_grid_aligned_tiny(eng):
     pts, v, o = scaled_tiny()
-    check(eng, pts, v, o, gls=(1, 2, 4, 5, 9))
+    check(eng, pts, v, o, gls=(1, 2, 4, 5, 9), subs=(1, 2, 3))
 
 
 def test_stars_uniform(eng):
@@ -119,7 +121,7 @@ def test_tessellation_mixture(eng):
     pts = np.concatenate([pts, extra])
     want_p, want_c = oracle.join_fast(pts, t.verts, t.ring_off)
     assert int(want_c.sum()) == pts.shape[0]  # tessellation invariant holds on the oracle side
-    check(eng, pts, t.verts, t.ring_off, gls=(6, 9, 12))
+    check(eng, pts, t.verts, t.ring_off, gls=(6, 9, 12), subs=(1, 3))
 
 
 def test_overlapping_queries(eng):

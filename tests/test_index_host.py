@@ -30,30 +30,36 @@ def parity(px, py, lst):
     return cnt.sum(0) & 1
 
 
-def walk(cells, ent, edges, gl, pts, check_structure=True):
-    """The kernels' traversal, vectorised over the points of each cell."""
-    shift = 30 - gl
+def walk(ix, pts, check_structure=True):
+    """The kernels' traversal (coarse word, fine word of a mixed cell, entry
+    list, crossing parity), vectorised over the points of each fine cell."""
+    gl, sb = ix["g"], ix["sub"]
+    sc, sf, F = 30 - gl, 30 - gl - sb, 1 << sb
+    coarse, fine, ent, edges = ix["coarse"], ix["fine"], ix["entries"], ix["edges"]
     px = pts[:, 0].astype(np.int64)
     py = pts[:, 1].astype(np.int64)
-    cell = ((py >> shift) << gl) | (px >> shift)
-    order = np.argsort(cell, kind="stable")
-    uc, start = np.unique(cell[order], return_index=True)
-    bounds = list(start) + [len(order)]
-    out_pid, out_q = [], []
-    for k, c in enumerate(uc):
-        idx = order[bounds[k]:bounds[k + 1]]
-        w = int(cells[c])
-        kind = w >> 30
-        if kind == 0:
-            continue
-        if kind == 1:
-            out_pid.append(idx)
-            out_q.append(np.full(idx.shape[0], w & MASK, np.int64))
-            continue
-        assert kind == 2
-        e = w & MASK
+    w = coarse[((py >> sc) << gl) | (px >> sc)].astype(np.int64)
+    kind = w >> 30
+    sub = kind == 2
+    fidx = ((w & MASK) << (2 * sb)) | (((py >> sf) & (F - 1)) << sb) | ((px >> sf) & (F - 1))
+    w = np.where(sub, fine[np.where(sub, fidx, 0)].astype(np.int64), w)
+    kind = w >> 30
+    out_pid, out_q = [np.nonzero(kind == 1)[0]], [(w[kind == 1] & MASK)]
+    lst_pts = np.nonzero(kind == 2)[0]
+    e0 = w[lst_pts] & MASK
+    fcell = ((py[lst_pts] >> sf) << 20) | (px[lst_pts] >> sf)
+    order = np.lexsort((fcell, e0))
+    lst_pts, e0, fcell = lst_pts[order], e0[order], fcell[order]
+    if lst_pts.size:
+        brk = np.nonzero((np.diff(e0) != 0) | (np.diff(fcell) != 0))[0] + 1
+        groups = np.split(np.arange(lst_pts.size), brk)
+    else:
+        groups = []
+    for gi in groups:
+        idx = lst_pts[gi]
+        e = int(e0[gi[0]])
+        x0 = int(px[idx[0]] >> sf) << sf
         last_q = -1
-        x0 = (int(c) & ((1 << gl) - 1)) << shift
         while True:
             q, eb, ec, fl = (int(v) for v in ent[e])
             if check_structure:
@@ -74,8 +80,6 @@ def walk(cells, ent, edges, gl, pts, check_structure=True):
             if fl & 2:
                 break
             e += 1
-    if not out_pid:
-        return np.zeros((0, 2), np.uint32)
     pid = np.concatenate(out_pid)
     q = np.concatenate(out_q)
     o = np.lexsort((q, pid))
@@ -142,19 +146,19 @@ def case(name):
 
 
 @pytest.mark.parametrize("name", ["stars", "tess", "queries", "grid_aligned"])
-@pytest.mark.parametrize("gl", [1, 3, 6, 9, 11])
-def test_host_index_matches_oracle(name, gl):
+@pytest.mark.parametrize("gl,sb", [(1, 1), (3, 3), (6, 1), (6, 3), (9, 2), (11, 3)])
+def test_host_index_matches_oracle(name, gl, sb):
     v, o, pts, want = case(name)
-    cells, ent, edges, g_out = spx.host_index(v, o, gl)
-    assert g_out == gl and cells.shape[0] == 1 << (2 * gl)
-    got = walk(cells, ent, edges, gl, pts)
+    ix = spx.host_index(v, o, gl, sb)
+    assert ix["g"] == gl and ix["sub"] == sb and ix["coarse"].shape[0] == 1 << (2 * gl)
+    got = walk(ix, pts)
     assert np.array_equal(got, want)
 
 
 def test_default_grid_choice():
     v, o = g.star_polygons(g.SEED_BASE + 1)
-    cells, _, _, gl = spx.host_index(v, o, 0)
-    assert 6 <= gl <= 12
+    ix = spx.host_index(v, o, 0, 0)
+    assert 5 <= ix["g"] <= 11 and ix["sub"] == 3
 
 
 def test_library_exports_every_declared_symbol():
