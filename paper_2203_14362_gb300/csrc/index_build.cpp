@@ -335,9 +335,10 @@ int default_grid_log2(const int32_t *xy, const uint64_t *ring_off, uint32_t P)
         return 6;
     std::nth_element(side.begin(), side.begin() + side.size() / 2, side.end());
     const double med = side[side.size() / 2];
-    // about 8 coarse cells across a typical polygon (64 fine cells with F = 8)
-    int g = int(std::lround(std::log2(8.0 / std::max(med, 1e-9))));
-    return std::min(std::max(g, 5), 11);
+    // about 40 coarse cells across a typical polygon: then a point meets a
+    // boundary-cut coarse cell rarely and a listed fine cell more rarely still
+    int g = int(std::lround(std::log2(40.0 / std::max(med, 1e-9))));
+    return std::min(std::max(g, 5), 12);
 }
 
 bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int g, int sb, int threads,
@@ -491,8 +492,12 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
             out.fine[size_t(blk * FF + uint64_t(f))] = w;
         }
     }
-    // sentinel entry: the kernels read entries two at a time
+    // sentinels: the kernels read entries two at a time, and load fine word 0
+    // and edge 0 in place of a missing one
     out.entries.insert(out.entries.end(), {0u, 0u, 0u, kEntLast});
+    if (out.fine.empty())
+        out.fine.push_back(0u);
+    out.edges.insert(out.edges.end(), {0, 0, 0, 0});
     return true;
 }
 

@@ -32,21 +32,26 @@
 namespace spx {
 namespace {
 
-constexpr int kThreads = 256;
+#ifndef SPX_TILE_THREADS
+#define SPX_TILE_THREADS 256
+#endif
+#ifndef SPX_TILE_ITEMS
+#define SPX_TILE_ITEMS 8
+#endif
+constexpr int kThreads = SPX_TILE_THREADS;  // threads per CTA of the tile kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 8;                   // points per thread per tile
-constexpr int kTile = kThreads * kItems;    // 2048 points per tile
-constexpr uint32_t kTileBytes = kTile * 8;  // 16 KB of points
-constexpr int kQueue = 1024;                // list points compacted per tile (more are walked in place)
-constexpr int kBufs = 3;                    // tile buffers: working, arriving, staged
+constexpr int kItems = SPX_TILE_ITEMS;      // points per thread per tile
+constexpr int kTile = kThreads * kItems;    // points per tile
+constexpr uint32_t kTileBytes = kTile * 8;  // bytes of points per tile
+constexpr int kQueue = kTile / 2;           // list points compacted per tile (more are walked in place)
+constexpr int kPlainThreads = 256;          // threads per CTA of the plain kernels
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kPending = 0xffffffffu;
+constexpr uint32_t kResNone = 0xffffffffu;  // pass-1 result: in no polygon
+constexpr uint32_t kResMulti = 0x80000000u; // pass-1 result flag: in several polygons (low bits: the first)
 constexpr int kHistMax = 11776;             // polygons counted in shared memory (46 KB)
-constexpr size_t kSmemFixed = kBufs * kTileBytes + kQueue * sizeof(uint2);
+constexpr size_t kCountSmem = 3 * kTileBytes + kQueue * sizeof(uint2);
 
-constexpr unsigned long long kFlagAgg = 1ull << 62;   // tile total published
-constexpr unsigned long long kFlagPre = 2ull << 62;   // inclusive prefix published
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr unsigned kSpinLimit = 1u << 22;             // ~ seconds with the back-off below
 
 // ------------------------------------------------------------------- PTX helpers
@@ -245,10 +250,12 @@ __device__ __forceinline__ uint32_t entry_in(const IndexView &ix, const uint4 &e
 }
 
 // Walk an entry list: number of polygons containing (px, py), smallest id.
-// The common case (at most two entries of at most four edges each) takes two
-// dependent round trips with every load issued up front and no data-dependent
-// branch around a load; longer lists continue one entry at a time.  The entry
-// array ends with a sentinel, so reading two entries is always in bounds.
+// Written so that the lanes of a warp stay converged around every load: the
+// common case (at most two entries, at most four edges each) issues all its
+// loads unconditionally, from clamped addresses that always lie inside the
+// arrays (both end with a sentinel), and selects the results; divergent lanes
+// of a warp would otherwise serialise their memory round trips.  Longer lists
+// finish in a loop.
 template <bool FP32>
 __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, int px, int py, uint32_t &first,
                                               uint32_t &tests, uint32_t &esc, uint64_t pol)
@@ -256,48 +263,63 @@ __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, 
     const uint4 *e = ix.ent + e0;
     const uint4 en0 = ld_idx(e, pol), en1 = ld_idx(e + 1, pol);
     const bool two = !(en0.w & kEntLast);
-    const uint32_t n0 = (en0.w & kEntBoundary) ? en0.z : 0u;
-    const uint32_t n1 = (two && (en1.w & kEntBoundary)) ? en1.z : 0u;
+    const uint32_t n0 = (en0.w & kEntBoundary) ? min(en0.z, 4u) : 0u;
+    const uint32_t n1 = (two && (en1.w & kEntBoundary)) ? min(en1.z, 4u) : 0u;
     int4 v0[4], v1[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        v0[j] = (uint32_t)j < n0 ? ld_idx(ix.edge + en0.y + j, pol) : make_int4(0, 0, 0, 0);
-        v1[j] = (uint32_t)j < n1 ? ld_idx(ix.edge + en1.y + j, pol) : make_int4(0, 0, 0, 0);
+        v0[j] = ld_idx(ix.edge + ((uint32_t)j < n0 ? en0.y + j : 0u), pol);
+        v1[j] = ld_idx(ix.edge + ((uint32_t)j < n1 ? en1.y + j : 0u), pol);
     }
-    uint32_t c = 0;
-    if (entry_in<FP32>(ix, en0, v0, px, py, tests, esc, pol)) {
-        first = en0.x;
-        c = 1;
+    uint32_t p0 = 0, p1 = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t c0 = edge_cross<FP32>(v0[j], px, py, tests, esc);
+        const uint32_t c1 = edge_cross<FP32>(v1[j], px, py, tests, esc);
+        p0 ^= (uint32_t)j < n0 ? c0 : 0u;
+        p1 ^= (uint32_t)j < n1 ? c1 : 0u;
     }
-    if (two) {
-        if (entry_in<FP32>(ix, en1, v1, px, py, tests, esc, pol)) {
-            if (!c)
-                first = en1.x;
-            ++c;
-        }
-        if (!(en1.w & kEntLast)) {
-            for (const uint4 *p = e + 2;; ++p) {
-                const uint4 en = ld_idx(p, pol);
-                if (!(en.w & kEntBoundary) || row_parity<FP32>(ix.edge + en.y, en.z, px, py, tests, esc, pol)) {
-                    if (!c)
-                        first = en.x;
-                    ++c;
-                }
-                if (en.w & kEntLast)
-                    break;
+    // lists longer than four edges: the rest, in row order
+    if ((en0.w & kEntBoundary) && en0.z > 4 && max(v0[3].x, v0[3].z) > px)
+        p0 ^= row_parity<FP32>(ix.edge + en0.y + 4, en0.z - 4, px, py, tests, esc, pol);
+    if (two && (en1.w & kEntBoundary) && en1.z > 4 && max(v1[3].x, v1[3].z) > px)
+        p1 ^= row_parity<FP32>(ix.edge + en1.y + 4, en1.z - 4, px, py, tests, esc, pol);
+    const uint32_t in0 = (en0.w & kEntBoundary) ? p0 : 1u;
+    const uint32_t in1 = two ? ((en1.w & kEntBoundary) ? p1 : 1u) : 0u;
+    uint32_t c = in0 + in1;
+    first = in0 ? en0.x : en1.x;
+    if (two && !(en1.w & kEntLast)) {
+        // three or more polygons share this fine cell
+        for (const uint4 *q = e + 2;; ++q) {
+            const uint4 en = ld_idx(q, pol);
+            if (!(en.w & kEntBoundary) || row_parity<FP32>(ix.edge + en.y, en.z, px, py, tests, esc, pol)) {
+                if (!c)
+                    first = en.x;
+                ++c;
             }
+            if (en.w & kEntLast)
+                break;
         }
     }
     return c;
 }
 
-// Shared-memory histogram update, aggregated over the lanes that add to the
-// same polygon (clustered points put many lanes on one counter).
-__device__ __forceinline__ void hist_add(uint32_t *h, uint32_t q)
+// Shared-memory histogram update for one item of every lane of a converged
+// warp (lanes with has = false add nothing).  Clustered points often put the
+// whole warp on one polygon: then one atomic adds the lane count.
+__device__ __forceinline__ void hist_add_warp(uint32_t *h, bool has, uint32_t q)
 {
-    const uint32_t peers = __match_any_sync(__activemask(), q);
-    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1)
-        atomicAdd(h + q, (uint32_t)__popc(peers));
+    const uint32_t m = __ballot_sync(kFull, has);
+    if (!m)
+        return;
+    const uint32_t qmin = __reduce_min_sync(kFull, has ? q : 0xffffffffu);
+    const uint32_t qmax = __reduce_max_sync(kFull, has ? q : 0u);
+    if (qmin == qmax) {
+        if ((int)(threadIdx.x & 31) == __ffs(m) - 1)
+            atomicAdd(h + qmin, (uint32_t)__popc(m));
+    } else if (has) {
+        atomicAdd(h + q, 1u);
+    }
 }
 
 // Whole predicate for one point (plain kernels, overflow path).
@@ -357,102 +379,170 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t pt
     }
 }
 
-// Decoupled look-back (single-pass chained scan): after this tile's total is
-// published, walk back over predecessor tiles until one has published its
-// inclusive prefix.  Each lane reads kLookLanes consecutive predecessors per step, so one
-// L2 round trip covers 32 * kLookLanes tiles.  Tiles are claimed in order from
-// an atomic counter, so every tile waited on belongs to a CTA that is already
-// running and publishes its total without waiting on later tiles: the wait
-// always ends.  It is still bounded; on expiry the error word gets kErrTimeout.
-constexpr int kLookLanes = 4;
+// ------------------------------------------------------------ tile kernels
+// Both kernels are persistent: CTAs claim kTile-point tiles in order from an
+// atomic counter and TMA bulk-copy each tile's points into a ring of shared-
+// memory buffers (mbarrier completion) one tile ahead.  Per tile, every worker
+// thread resolves kItems points with independent loads; points whose fine
+// cell holds a list are compacted into a shared-memory queue and walked by
+// all workers (dynamic assignment).
 
-__device__ unsigned long long lookback(unsigned long long *status, uint32_t tile, uint32_t total, unsigned *err)
+// worker-only barrier (named barrier 1): the join's flush warp never joins it
+template <int N>
+__device__ __forceinline__ void workers_sync()
 {
-    const int lane = threadIdx.x & 31;
-    if (tile == 0) {
-        if (lane == 0)
-            st_relaxed(status, kFlagPre | total);
-        return 0;
-    }
-    // (the caller has published this tile's total with kFlagAgg)
-    unsigned long long excl = 0;
-    long long top = (long long)tile - 1;
-    unsigned spins = 0;
-    for (;;) {
-        // lane l covers tiles top - 4l .. top - 4l - 3 (nearest first)
-        unsigned long long s[kLookLanes];
-#pragma unroll
-        for (int j = 0; j < kLookLanes; ++j) {
-            const long long k = top - (long long)(lane * kLookLanes + j);
-            s[j] = (k >= 0) ? ld_relaxed(status + k) : kFlagPre;
-        }
-        // within the lane: the first inclusive prefix, and whether a needed slot is unpublished
-        int jp = kLookLanes;
-        bool hole = false;
-#pragma unroll
-        for (int j = kLookLanes - 1; j >= 0; --j)
-            if ((s[j] >> 62) == 2)
-                jp = j;
-#pragma unroll
-        for (int j = 0; j < kLookLanes; ++j)
-            if (j <= jp && (s[j] >> 62) == 0)
-                hole = true;
-        const uint32_t pm = __ballot_sync(kFull, jp < kLookLanes);
-        // lanes up to the first lane holding a prefix are needed
-        const uint32_t need = pm ? ((pm & (0u - pm)) << 1) - 1 : kFull;
-        if (__ballot_sync(kFull, hole) & need) {
-            if (++spins > kSpinLimit) {
-                if (lane == 0)
-                    atomicOr(err, kErrTimeout);
-                break;
-            }
-            __nanosleep(32);
-            continue;
-        }
-        unsigned long long v = 0;
-        if ((1u << lane) & need) {
-#pragma unroll
-            for (int j = 0; j < kLookLanes; ++j)
-                if (j <= jp)
-                    v += s[j] & kValMask;
-        }
-        excl += warp_sum64(v);
-        if (pm)
-            break;
-        top -= 32 * kLookLanes;
-    }
-    if (lane == 0)
-        st_relaxed(status + tile, kFlagPre | (excl + total));
-    return excl;
+    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
 }
 
-// ------------------------------------------------------------ the tile kernel
-// JOIN = true: pairs (sorted) + counts; JOIN = false: counts only (the
-// aggregation plan that never materialises the join, §5.2).
-//
-// Three shared-memory tile buffers rotate: while tile k is worked on, tile
-// k+1 is being bulk-copied in, and (join) tile k-1's pairs wait in their own
-// buffer for their output offset.  A tile's pairs are staged in place: once
-// its points are consumed, pair i of the tile (in point order) is written to
-// slot i of the same buffer.  Its total is published at once, and its
-// look-back runs during the next tile, by warp 0 while the other warps walk
-// that tile's list points; then all threads copy the staged pairs out,
-// coalesced.  A tile whose pairs do not fit in place (a point in several
-// polygons) takes the look-back at once and writes directly.
-template <bool FP32, bool JOIN>
-__global__ void __launch_bounds__(kThreads) k_tiles(JoinLaunch a, uint32_t ntiles, int use_hist)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait for phase `parity` of an mbarrier; on expiry sets `code` in err
+__device__ __forceinline__ void mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err, unsigned code)
+{
+    unsigned spins = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if (++spins > kSpinLimit) {
+            atomicOr(err, code);
+            return;
+        }
+        __nanosleep(20);
+    }
+}
+
+// Copy of tile t into ring buffer dst: TMA for the 16-byte part, a plain
+// store for an odd last point.  Completes on `bar`.
+__device__ __forceinline__ void issue_tile(const JoinLaunch &a, uint32_t t, int2 *dst, uint64_t *bar)
+{
+    const uint64_t base = (uint64_t)t * kTile;
+    const uint64_t rem = a.n - base;
+    const uint32_t np = rem < (uint64_t)kTile ? (uint32_t)rem : (uint32_t)kTile;
+    const uint32_t bytes = (np & ~1u) * 8u;
+    if (np & 1u)
+        dst[np - 1] = a.pts[base + np - 1];
+    if (bytes) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, bytes);
+        tma_load_1d(dst, a.pts + base, bytes, bar, policy_evict_first());
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+// Resolve, queue and walk one tile: cnt[i] / first[i] of the point at
+// tile location i * kThreads + wtid.  SYNC is the barrier among the workers.
+template <bool FP32, class SYNC>
+__device__ __forceinline__ void eval_tile(const IndexView &ix, const int2 *tb, uint32_t npts, uint2 *s_q,
+                                          uint32_t *s_qn, uint32_t *s_qj, uint32_t (&cnt)[kItems],
+                                          uint32_t (&first)[kItems], uint32_t &n_tests, uint32_t &n_esc,
+                                          uint32_t &n_pts, uint64_t keep, int wtid, SYNC sync)
+{
+    const int lane = wtid & 31;
+    // every lane loads (from cell 0 / fine word 0 when it has nothing to look
+    // up) and keeps or drops the result, so the warp stays converged
+    uint32_t w[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const uint32_t loc = i * kThreads + wtid;
+        const int2 p = tb[loc < npts ? loc : 0u];
+        const bool ok = loc < npts && (unsigned)p.x < kBox && (unsigned)p.y < kBox;
+        n_pts += loc < npts ? 1u : 0u;
+        const uint32_t px = ok ? (uint32_t)p.x : 0u, py = ok ? (uint32_t)p.y : 0u;
+        const uint32_t cw = coarse_word(ix, px, py, keep);
+        w[i] = ok ? cw : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const bool sub = (w[i] >> 30) == kCellSub;
+        const int2 p = tb[sub ? i * kThreads + wtid : 0u];
+        const uint32_t fw = fine_word(ix, sub ? w[i] : 0u, sub ? (uint32_t)p.x : 0u, sub ? (uint32_t)p.y : 0u, keep);
+        w[i] = sub ? fw : w[i];
+    }
+    // one INSIDE polygon: done; a list: into the queue
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const uint32_t kind = w[i] >> 30;
+        cnt[i] = kind == kCellInsideOne ? 1u : 0u;
+        first[i] = w[i] & kPayloadMask;
+        const bool is_list = kind == kCellList;
+        const uint32_t bl = __ballot_sync(kFull, is_list);
+        if (bl) {
+            const int leader = __ffs(bl) - 1;
+            uint32_t slot0 = 0;
+            if (lane == leader)
+                slot0 = atomicAdd(s_qn, (uint32_t)__popc(bl));
+            slot0 = __shfl_sync(kFull, slot0, leader);
+            if (is_list) {
+                const uint32_t slot = slot0 + __popc(bl & lanemask_lt());
+                const uint32_t loc = i * kThreads + wtid;
+                if (slot < (uint32_t)kQueue) {
+                    s_q[slot] = make_uint2(loc, w[i] & kPayloadMask);
+                    cnt[i] = kPending;
+                    first[i] = slot;
+                } else {
+                    const int2 p = tb[loc];
+                    uint32_t f = 0;
+                    cnt[i] = walk_list<FP32>(ix, w[i] & kPayloadMask, p.x, p.y, f, n_tests, n_esc, keep);
+                    first[i] = f;
+                }
+            }
+        }
+    }
+    sync();
+    {
+        // warp-synchronous: a warp takes 32 queued points at a time, one per lane
+        const uint32_t qn = min(*s_qn, (uint32_t)kQueue);
+        for (;;) {
+            uint32_t j0 = 0;
+            if (lane == 0)
+                j0 = atomicAdd(s_qj, 32u);
+            j0 = __shfl_sync(kFull, j0, 0);
+            if (j0 >= qn)
+                break;
+            const uint32_t j = j0 + lane;
+            const bool has = j < qn;
+            const uint2 it = s_q[has ? j : j0];
+            const int2 p = tb[it.x];
+            uint32_t f = 0;
+            const uint32_t c = walk_list<FP32>(ix, it.y, p.x, p.y, f, n_tests, n_esc, keep);
+            __syncwarp();
+            if (has)
+                s_q[j] = make_uint2(c, f);
+            __syncwarp();
+        }
+    }
+    sync();
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        if (cnt[i] == kPending) {
+            const uint2 r = s_q[first[i]];
+            cnt[i] = r.x;
+            first[i] = r.y;
+        }
+    }
+}
+
+// ------------------------------------------------- count / resolve (pass 1)
+// Counts only (the aggregation plan that never materialises the join, §5.2):
+// per-polygon counts in a shared-memory histogram.  With RESOLVE, the same
+// pass is also the first pass of the join (the counting pass of the two-pass
+// Map, §5.1): it stores every point's result (none / its polygon / "several",
+// 4 bytes) and every tile's pair total, so the writing pass needs no index
+// lookups.  Three buffers: one worked on, one arriving, one spare.
+template <bool FP32, bool RESOLVE>
+__global__ void __launch_bounds__(kThreads) k_count(JoinLaunch a, uint32_t ntiles, int use_hist)
+{
+    constexpr int R = 3;
     extern __shared__ __align__(128) unsigned char dsm[];
-    int2 *s_buf = reinterpret_cast<int2 *>(dsm);                       // kBufs x kTile points (or staged pairs)
-    uint2 *s_q = reinterpret_cast<uint2 *>(dsm + kBufs * kTileBytes);  // list-point queue
-    uint32_t *s_hist = reinterpret_cast<uint32_t *>(dsm + kSmemFixed); // P counters
-    __shared__ __align__(8) uint64_t s_bar[kBufs];
-    __shared__ uint32_t s_tile[kBufs];
-    __shared__ uint32_t s_qn, s_qj, s_multi;
-    __shared__ uint32_t s_off[kItems * kWarps];
-    __shared__ uint32_t s_total;
-    __shared__ unsigned long long s_excl, s_prev_excl;
-    __shared__ uint32_t s_prev_tile, s_prev_total, s_prev_buf; // staged tile waiting for its offset
+    int2 *s_buf = reinterpret_cast<int2 *>(dsm);
+    uint2 *s_q = reinterpret_cast<uint2 *>(dsm + R * kTileBytes);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(dsm + R * kTileBytes + kQueue * sizeof(uint2));
+    __shared__ __align__(8) uint64_t s_full[R];
+    __shared__ uint32_t s_tile[R];
+    __shared__ uint32_t s_qn, s_qj;
+    __shared__ uint32_t s_wsum[kWarps];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const IndexView &ix = a.ix;
@@ -460,336 +550,79 @@ __global__ void __launch_bounds__(kThreads) k_tiles(JoinLaunch a, uint32_t ntile
     if (use_hist)
         for (uint32_t i = tid; i < ix.P; i += kThreads)
             s_hist[i] = 0;
-
-    // copy of tile t into buffer b: TMA for the 16-byte part, a plain store for an odd last point
-    auto issue = [&](uint32_t t, int b) {
-        const uint64_t base = (uint64_t)t * kTile;
-        const uint64_t rem = a.n - base;
-        const uint32_t np = rem < (uint64_t)kTile ? (uint32_t)rem : (uint32_t)kTile;
-        const uint32_t bytes = (np & ~1u) * 8u;
-        int2 *dst = s_buf + b * kTile;
-        if (np & 1u)
-            dst[np - 1] = a.pts[base + np - 1];
-        if (bytes) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive_expect_tx(&s_bar[b], bytes);
-            tma_load_1d(dst, a.pts + base, bytes, &s_bar[b], policy_evict_first());
-        } else {
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_bar[b])) : "memory");
-        }
-    };
-    auto claim_next = [&](int b) {
+    auto claim = [&](int b) {
         const uint32_t nt = atomicAdd(a.tile_counter, 1u);
         s_tile[b] = nt;
         if (nt < ntiles)
-            issue(nt, b);
+            issue_tile(a, nt, s_buf + b * kTile, &s_full[b]);
     };
-    // copy a staged tile's pairs to their final place (all threads)
-    auto flush = [&](uint32_t buf, uint32_t total, unsigned long long excl) {
-        const uint2 *st = reinterpret_cast<const uint2 *>(s_buf + buf * kTile);
-        for (uint32_t j = tid; j < total; j += kThreads)
-            if (excl + j < a.cap)
-                __stcs(a.pairs + excl + j, st[j]);
-    };
-
     if (tid == 0) {
-        for (int b = 0; b < kBufs; ++b)
-            mbar_init(&s_bar[b], 1);
+        for (int b = 0; b < R; ++b)
+            mbar_init(&s_full[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_qn = 0;
         s_qj = 0;
-        s_multi = 0;
-        s_prev_tile = kPending; // none staged
-        claim_next(0);
+        claim(0);
     }
     __syncthreads();
-
     uint32_t n_tests = 0, n_esc = 0, n_pts = 0, n_pairs = 0;
+    auto sync = [] { __syncthreads(); };
     for (uint32_t k = 0;; ++k) {
-        const int b = int(k % kBufs);
+        const int b = int(k % R);
         const uint32_t tile = s_tile[b];
         if (tile >= ntiles)
             break;
         if (tid == 0)
-            claim_next(int((k + 1) % kBufs)); // that buffer's tile (k-2) was flushed during tile k-1
-        {
-            unsigned spins = 0;
-            while (!mbar_try_wait(&s_bar[b], (k / kBufs) & 1u)) {
-                if (++spins > kSpinLimit) {
-                    if (tid == 0)
-                        atomicOr(a.err, kErrCopy);
-                    break;
-                }
-                __nanosleep(20);
-            }
-        }
+            claim(int((k + 1) % R)); // that buffer's tile (k-2) ended with a barrier
+        mbar_wait(&s_full[b], (k / R) & 1u, a.err, kErrCopy);
         const int2 *tb = s_buf + b * kTile;
         const uint64_t base = (uint64_t)tile * kTile;
         const uint64_t rem = a.n - base;
         const uint32_t npts = rem < (uint64_t)kTile ? (uint32_t)rem : (uint32_t)kTile;
-
-        // resolve every point's word with independent loads
-        uint32_t w[kItems];
+        uint32_t cnt[kItems], first[kItems];
+        eval_tile<FP32>(ix, tb, npts, s_q, &s_qn, &s_qj, cnt, first, n_tests, n_esc, n_pts, keep, tid, sync);
+        uint32_t tsum = 0;
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const uint32_t loc = i * kThreads + tid;
-            w[i] = 0;
-            if (loc < npts) {
-                const int2 p = tb[loc];
-                ++n_pts;
-                if ((unsigned)p.x < kBox && (unsigned)p.y < kBox)
-                    w[i] = coarse_word(ix, (uint32_t)p.x, (uint32_t)p.y, keep);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            if ((w[i] >> 30) == kCellSub) {
-                const int2 p = tb[i * kThreads + tid];
-                w[i] = fine_word(ix, w[i], (uint32_t)p.x, (uint32_t)p.y, keep);
-            }
-        }
-        // one INSIDE polygon: done; a list: into the queue
-        uint32_t cnt[kItems], first[kItems];
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const uint32_t kind = w[i] >> 30;
-            cnt[i] = kind == kCellInsideOne ? 1u : 0u;
-            first[i] = w[i] & kPayloadMask;
-            const bool is_list = kind == kCellList;
-            const uint32_t bl = __ballot_sync(kFull, is_list);
-            if (bl) {
-                const int leader = __ffs(bl) - 1;
-                uint32_t slot0 = 0;
-                if (lane == leader)
-                    slot0 = atomicAdd(&s_qn, (uint32_t)__popc(bl));
-                slot0 = __shfl_sync(kFull, slot0, leader);
-                if (is_list) {
-                    const uint32_t slot = slot0 + __popc(bl & lanemask_lt());
-                    const uint32_t loc = i * kThreads + tid;
-                    if (slot < (uint32_t)kQueue) {
-                        s_q[slot] = make_uint2(loc, w[i] & kPayloadMask);
-                        cnt[i] = kPending;
-                        first[i] = slot;
-                    } else {
-                        const int2 p = tb[loc];
-                        uint32_t f = 0;
-                        cnt[i] = walk_list<FP32>(ix, w[i] & kPayloadMask, p.x, p.y, f, n_tests, n_esc, keep);
-                        first[i] = f;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // walk the queued list points (dynamic assignment); in a join, warp 0
-        // first settles the offset of the tile staged during the previous round
-        if (JOIN && warp == 0 && s_prev_tile != kPending) {
-            const unsigned long long ex = lookback(a.tile_status, s_prev_tile, s_prev_total, a.err);
-            if (lane == 0)
-                s_prev_excl = ex;
-        }
-        {
-            const uint32_t qn = min(s_qn, (uint32_t)kQueue);
-            for (;;) {
-                const uint32_t j = atomicAdd(&s_qj, 1u);
-                if (j >= qn)
-                    break;
-                const uint2 it = s_q[j];
-                const int2 p = tb[it.x];
-                uint32_t f = 0;
-                const uint32_t c = walk_list<FP32>(ix, it.y, p.x, p.y, f, n_tests, n_esc, keep);
-                s_q[j] = make_uint2(c, f);
-            }
-        }
-        __syncthreads();
-        bool multi = false;
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            if (cnt[i] == kPending) {
-                const uint2 r = s_q[first[i]];
-                cnt[i] = r.x;
-                first[i] = r.y;
-            }
-            multi |= cnt[i] > 1;
-        }
-
-        if (!JOIN) {
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                if (!cnt[i])
-                    continue;
-                n_pairs += cnt[i];
-                if (cnt[i] == 1) {
-                    if (use_hist)
-                        hist_add(s_hist, first[i]);
-                    else
-                        atomicAdd(a.counts + first[i], 1ull);
-                } else {
-                    const int2 p = tb[i * kThreads + tid];
-                    point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) {
-                        if (use_hist)
-                            atomicAdd(&s_hist[q], 1u);
-                        else
-                            atomicAdd(a.counts + q, 1ull);
-                    });
-                }
-            }
-            if (tid == 0) {
-                s_qn = 0;
-                s_qj = 0;
-            }
-            __syncthreads(); // buffer b and the queue are free for the next tile
-            continue;
-        }
-
-        // tile-local exclusive offsets of every point's pairs, in point order
-        multi = __any_sync(kFull, multi);
-        if (multi && lane == 0)
-            s_multi = 1;
-        uint32_t pre[kItems];
-        if (!multi) {
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                const uint32_t bl = __ballot_sync(kFull, cnt[i] != 0);
-                pre[i] = __popc(bl & lanemask_lt());
-                if (lane == 0)
-                    s_off[i * kWarps + warp] = __popc(bl);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                uint32_t inc = cnt[i];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(kFull, inc, o);
-                    if (lane >= o)
-                        inc += t;
-                }
-                pre[i] = inc - cnt[i];
-                if (lane == 31)
-                    s_off[i * kWarps + warp] = inc;
-            }
-        }
-        __syncthreads();
-        const bool staged_prev = s_prev_tile != kPending;
-        if (warp == 0) {
-            static_assert(kItems * kWarps == 64, "one warp scans two values per lane");
-            const uint32_t v0 = s_off[2 * lane], v1 = s_off[2 * lane + 1];
-            const uint32_t pair_sum = v0 + v1;
-            uint32_t inc = pair_sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, inc, o);
-                if (lane >= o)
-                    inc += t;
-            }
-            const uint32_t ex = inc - pair_sum;
-            const uint32_t tile_total = __shfl_sync(kFull, inc, 31);
-            s_off[2 * lane] = ex;
-            s_off[2 * lane + 1] = ex + v0;
-            if (lane == 0)
-                s_total = tile_total;
-            if (tile == 0) {
-                if (lane == 0) {
-                    st_relaxed(a.tile_status, kFlagPre | tile_total);
-                    s_excl = 0;
-                }
-            } else {
-                if (lane == 0)
-                    st_relaxed(a.tile_status + tile, kFlagAgg | tile_total);
-                __syncwarp();
-                if (s_multi) { // cannot stage in place: settle the offset now
-                    const unsigned long long excl = lookback(a.tile_status, tile, tile_total, a.err);
-                    if (lane == 0)
-                        s_excl = excl;
-                }
-            }
-        }
-        __syncthreads();
-        const uint32_t tile_total = s_total;
-        const bool stage = !s_multi && tile != 0;
-        // the previous round's staged tile goes out now that its offset is known
-        if (staged_prev) {
-            flush(s_prev_buf, s_prev_total, s_prev_excl);
-            if (tid == 0 && s_prev_tile == ntiles - 1 && a.total)
-                *a.total = s_prev_excl + s_prev_total;
-        }
-        if (!stage) {
-            // direct writes at the settled offset
-            const unsigned long long tbase = s_excl;
-            if (tid == 0 && tile == ntiles - 1 && a.total)
-                *a.total = tbase + tile_total;
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                if (!cnt[i])
-                    continue;
-                const uint32_t loc = i * kThreads + tid;
-                const uint32_t pid = (uint32_t)(base + loc);
-                unsigned long long o = tbase + s_off[i * kWarps + warp] + pre[i];
-                n_pairs += cnt[i];
-                if (cnt[i] == 1) {
-                    if (o < a.cap)
-                        __stcs(a.pairs + o, make_uint2(pid, first[i]));
-                    if (use_hist)
-                        hist_add(s_hist, first[i]);
-                    else if (a.counts)
-                        atomicAdd(a.counts + first[i], 1ull);
-                } else {
-                    const int2 p = tb[loc];
-                    point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) {
-                        if (o < a.cap)
-                            __stcs(a.pairs + o, make_uint2(pid, q));
-                        ++o;
-                        if (use_hist)
-                            atomicAdd(&s_hist[q], 1u);
-                        else if (a.counts)
-                            atomicAdd(a.counts + q, 1ull);
-                    });
-                }
-            }
-        } else {
-            // every point has at most one pair and all reads of this buffer's
-            // points are done (the barrier above): stage pair i in slot i
-            uint2 *st = reinterpret_cast<uint2 *>(s_buf + b * kTile);
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                if (!cnt[i])
-                    continue;
-                const uint32_t loc = i * kThreads + tid;
-                st[s_off[i * kWarps + warp] + pre[i]] = make_uint2((uint32_t)(base + loc), first[i]);
-                ++n_pairs;
-                if (use_hist)
-                    hist_add(s_hist, first[i]);
-                else if (a.counts)
+            if (use_hist)
+                hist_add_warp(s_hist, cnt[i] == 1, first[i]);
+            if (RESOLVE && loc < npts)
+                __stcg(a.res + base + loc, cnt[i] == 0 ? kResNone : (cnt[i] == 1 ? first[i] : (kResMulti | first[i])));
+            tsum += cnt[i];
+            if (!cnt[i])
+                continue;
+            n_pairs += cnt[i];
+            if (cnt[i] == 1) {
+                if (!use_hist && a.counts)
                     atomicAdd(a.counts + first[i], 1ull);
+            } else if (a.counts) {
+                const int2 p = tb[loc];
+                point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) {
+                    if (use_hist)
+                        atomicAdd(&s_hist[q], 1u);
+                    else
+                        atomicAdd(a.counts + q, 1ull);
+                });
             }
         }
-        __syncthreads(); // staged pairs complete; the previous staged buffer is free
+        if (RESOLVE) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                tsum += __shfl_xor_sync(kFull, tsum, o);
+            if (lane == 0)
+                s_wsum[warp] = tsum;
+        }
         if (tid == 0) {
             s_qn = 0;
             s_qj = 0;
-            s_multi = 0;
-            if (stage) {
-                s_prev_tile = tile;
-                s_prev_total = tile_total;
-                s_prev_buf = (uint32_t)b;
-            } else {
-                s_prev_tile = kPending;
-            }
         }
-        __syncthreads();
-    }
-    // the last staged tile
-    if (JOIN) {
-        if (warp == 0 && s_prev_tile != kPending) {
-            const unsigned long long ex = lookback(a.tile_status, s_prev_tile, s_prev_total, a.err);
-            if (lane == 0)
-                s_prev_excl = ex;
-        }
-        __syncthreads();
-        if (s_prev_tile != kPending) {
-            flush(s_prev_buf, s_prev_total, s_prev_excl);
-            if (tid == 0 && s_prev_tile == ntiles - 1 && a.total)
-                *a.total = s_prev_excl + s_prev_total;
+        __syncthreads(); // buffer b, the queue and the warp sums are complete
+        if (RESOLVE && tid == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < kWarps; ++w)
+                t += s_wsum[w];
+            a.tile_tot[tile] = t;
         }
     }
     add_stats(a.stats, n_pts, n_tests, n_esc, n_pairs);
@@ -801,14 +634,120 @@ __global__ void __launch_bounds__(kThreads) k_tiles(JoinLaunch a, uint32_t ntile
     }
 }
 
+// ------------------------------------------------------ write pairs (pass 3)
+// One tile per CTA: the tile's results (4 bytes per point) are read, a ballot
+// scan gives every point's place in the tile's output, and the pairs go to
+// tile_off[tile] + place, in point order.  A point in several polygons is
+// walked again to emit all of them, ascending.
+template <bool FP32>
+__global__ void __launch_bounds__(kThreads) k_emit(JoinLaunch a, const unsigned long long *tile_off)
+{
+    __shared__ uint32_t s_off[kItems * kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t tile = blockIdx.x;
+    const uint64_t base = (uint64_t)tile * kTile;
+    const uint64_t rem = a.n - base;
+    const uint32_t npts = rem < (uint64_t)kTile ? (uint32_t)rem : (uint32_t)kTile;
+    const uint64_t keep = policy_evict_last();
+    uint32_t res[kItems], cnt[kItems];
+    bool multi = false;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const uint32_t loc = i * kThreads + tid;
+        res[i] = loc < npts ? __ldcs(a.res + base + loc) : kResNone;
+        cnt[i] = res[i] == kResNone ? 0u : 1u;
+        if (res[i] != kResNone && (res[i] & kResMulti)) {
+            // count again (rare): the point lies in several polygons
+            const int2 p = a.pts[base + loc];
+            uint32_t f = 0, t = 0, e = 0;
+            cnt[i] = point_count<FP32>(a.ix, p.x, p.y, f, t, e, keep);
+            multi = true;
+        }
+    }
+    multi = __any_sync(kFull, multi);
+    uint32_t pre[kItems];
+    if (!multi) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const uint32_t bl = __ballot_sync(kFull, cnt[i] != 0);
+            pre[i] = __popc(bl & lanemask_lt());
+            if (lane == 0)
+                s_off[i * kWarps + warp] = __popc(bl);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            uint32_t inc = cnt[i];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o)
+                    inc += t;
+            }
+            pre[i] = inc - cnt[i];
+            if (lane == 31)
+                s_off[i * kWarps + warp] = inc;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive scan of the kItems x kWarps row totals, VPL per lane
+        constexpr int VPL = (kItems * kWarps + 31) / 32;
+        static_assert(kItems * kWarps <= 32 * VPL && VPL <= 4, "row totals per lane");
+        uint32_t v[VPL], lsum = 0;
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) {
+            const int r = lane * VPL + j;
+            v[j] = r < kItems * kWarps ? s_off[r] : 0u;
+            lsum += v[j];
+        }
+        uint32_t inc = lsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o)
+                inc += t;
+        }
+        uint32_t run = inc - lsum;
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) {
+            const int r = lane * VPL + j;
+            if (r < kItems * kWarps)
+                s_off[r] = run;
+            run += v[j];
+        }
+    }
+    __syncthreads();
+    const unsigned long long tbase = tile_off[tile];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        if (!cnt[i])
+            continue;
+        const uint32_t loc = i * kThreads + tid;
+        const uint32_t pid = (uint32_t)(base + loc);
+        unsigned long long o = tbase + s_off[i * kWarps + warp] + pre[i];
+        if (!(res[i] & kResMulti)) {
+            if (o < a.cap)
+                __stcs(a.pairs + o, make_uint2(pid, res[i]));
+        } else {
+            const int2 p = a.pts[base + loc];
+            point_emit<FP32>(a.ix, p.x, p.y, keep, [&](uint32_t q) {
+                if (o < a.cap)
+                    __stcs(a.pairs + o, make_uint2(pid, q));
+                ++o;
+            });
+        }
+    }
+}
+
 // ------------------------------------------------------- plain comparison join
 // Exact int64 only; one thread per point; pass 1 counts per 256-point block,
 // a one-block scan makes block offsets, pass 2 recounts and writes.  Counts by
 // global atomics.
-__global__ void __launch_bounds__(kThreads) k_plain_count(JoinLaunch a, unsigned long long *block_cnt)
+__global__ void __launch_bounds__(kPlainThreads) k_plain_count(JoinLaunch a, unsigned long long *block_cnt)
 {
-    __shared__ uint32_t s_w[kWarps];
-    const uint64_t idx = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    __shared__ uint32_t s_w[(kPlainThreads / 32)];
+    const uint64_t idx = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
     uint32_t c = 0, first = 0, t = 0, e = 0;
     if (idx < a.n) {
         const int2 p = a.pts[idx];
@@ -823,13 +762,13 @@ __global__ void __launch_bounds__(kThreads) k_plain_count(JoinLaunch a, unsigned
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long b = 0;
-        for (int w = 0; w < kWarps; ++w)
+        for (int w = 0; w < (kPlainThreads / 32); ++w)
             b += s_w[w];
         block_cnt[blockIdx.x] = b;
     }
 }
 
-__global__ void __launch_bounds__(1024) k_plain_scan(unsigned long long *v, uint64_t n, unsigned long long *total)
+__global__ void __launch_bounds__(1024) k_scan(unsigned long long *v, uint64_t n, unsigned long long *total)
 {
     // exclusive scan of n values by one block: chunks of 1024 with a carried total
     __shared__ unsigned long long s_w[32];
@@ -875,11 +814,11 @@ __global__ void __launch_bounds__(1024) k_plain_scan(unsigned long long *v, uint
         *total = s_carry;
 }
 
-__global__ void __launch_bounds__(kThreads) k_plain_write(JoinLaunch a, const unsigned long long *block_off)
+__global__ void __launch_bounds__(kPlainThreads) k_plain_write(JoinLaunch a, const unsigned long long *block_off)
 {
-    __shared__ uint32_t s_w[kWarps];
+    __shared__ uint32_t s_w[(kPlainThreads / 32)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t idx = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint64_t idx = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
     uint32_t c = 0, first = 0, t = 0, e = 0;
     int2 p = make_int2(0, 0);
     const uint64_t keep = policy_evict_last();
@@ -917,29 +856,43 @@ __global__ void __launch_bounds__(kThreads) k_plain_write(JoinLaunch a, const un
     }
 }
 
-template <bool FP32, bool JOIN>
-cudaError_t launch_tiles(const JoinLaunch &a, uint32_t ntiles, int use_hist, cudaStream_t s)
+// Opt a kernel in to the shared memory it needs (once per device).
+template <class K>
+cudaError_t smem_opt_in(K kernel, size_t bytes, bool (&done)[64])
 {
-    const size_t smem = kSmemFixed + (use_hist ? sizeof(uint32_t) * a.ix.P : 0);
-    static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 64 || !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tiles<FP32, JOIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(kSmemFixed + sizeof(uint32_t) * kHistMax));
-        if (e != cudaSuccess)
-            return e;
-        if (dev < 64)
-            attr_set[dev] = true;
-    }
+    if (dev < 64 && done[dev])
+        return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess && dev < 64)
+        done[dev] = true;
+    return e;
+}
+
+template <class K>
+int persistent_grid(K kernel, int threads, size_t smem, uint32_t ntiles)
+{
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles<FP32, JOIN>, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
     if (per_sm < 1)
         per_sm = 1;
     int grid = per_sm * device_sm_count();
     if ((uint32_t)grid > ntiles)
         grid = (int)ntiles;
-    k_tiles<FP32, JOIN><<<grid, kThreads, smem, s>>>(a, ntiles, use_hist);
+    return grid;
+}
+
+template <bool FP32, bool RESOLVE>
+cudaError_t launch_count_kernel(const JoinLaunch &a, uint32_t ntiles, int use_hist, cudaStream_t s)
+{
+    static bool done[64] = {};
+    const size_t smem = kCountSmem + (use_hist ? sizeof(uint32_t) * a.ix.P : 0);
+    cudaError_t e = smem_opt_in(k_count<FP32, RESOLVE>, kCountSmem + sizeof(uint32_t) * kHistMax, done);
+    if (e != cudaSuccess)
+        return e;
+    k_count<FP32, RESOLVE><<<persistent_grid(k_count<FP32, RESOLVE>, kThreads, smem, ntiles), kThreads, smem, s>>>(
+        a, ntiles, use_hist);
     return cudaGetLastError();
 }
 
@@ -956,13 +909,14 @@ int device_sm_count()
 
 size_t join_scratch_bytes(uint64_t n)
 {
+    // per-point results | per-tile totals (then offsets) | tile counter
     const uint64_t ntiles = (n + kTile - 1) / kTile;
-    return size_t(ntiles * 8 + 16);
+    return size_t(((n * 4 + 15) & ~uint64_t(15)) + ntiles * 8 + 16);
 }
 
 size_t plain_scratch_bytes(uint64_t n)
 {
-    const uint64_t nb = (n + kThreads - 1) / kThreads;
+    const uint64_t nb = (n + kPlainThreads - 1) / kPlainThreads;
     return size_t(nb * 8 + 16);
 }
 
@@ -975,9 +929,11 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s)
         return cudaErrorMisalignedAddress;
     const uint32_t ntiles = uint32_t(ntiles64);
     JoinLaunch b = a;
-    b.tile_status = reinterpret_cast<unsigned long long *>(scratch);
-    b.tile_counter = reinterpret_cast<unsigned *>(b.tile_status + ntiles);
-    cudaError_t e = cudaMemsetAsync(scratch, 0, join_scratch_bytes(a.n), s);
+    char *sc = static_cast<char *>(scratch);
+    b.res = reinterpret_cast<uint32_t *>(sc);
+    b.tile_tot = reinterpret_cast<unsigned long long *>(sc + ((a.n * 4 + 15) & ~uint64_t(15)));
+    b.tile_counter = reinterpret_cast<unsigned *>(b.tile_tot + ntiles);
+    cudaError_t e = cudaMemsetAsync(b.tile_counter, 0, 16, s);
     if (e != cudaSuccess)
         return e;
     if (a.counts && a.ix.P) {
@@ -990,8 +946,22 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s)
             return cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s);
         return cudaSuccess;
     }
+    // pass 1: resolve every point, count per polygon and per tile
     const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
-    return a.fp32 ? launch_tiles<true, true>(b, ntiles, use_hist, s) : launch_tiles<false, true>(b, ntiles, use_hist, s);
+    e = a.fp32 ? launch_count_kernel<true, true>(b, ntiles, use_hist, s)
+               : launch_count_kernel<false, true>(b, ntiles, use_hist, s);
+    if (e != cudaSuccess)
+        return e;
+    // pass 2: tile offsets and the total
+    k_scan<<<1, 1024, 0, s>>>(b.tile_tot, ntiles, a.total);
+    // pass 3: pairs in point order
+    if (a.cap) {
+        if (a.fp32)
+            k_emit<true><<<ntiles, kThreads, 0, s>>>(b, b.tile_tot);
+        else
+            k_emit<false><<<ntiles, kThreads, 0, s>>>(b, b.tile_tot);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s)
@@ -1006,18 +976,18 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s)
         return cudaErrorInvalidValue;
     const uint32_t ntiles = uint32_t(ntiles64);
     JoinLaunch b = a;
-    b.tile_status = nullptr;
     b.tile_counter = reinterpret_cast<unsigned *>(scratch);
     e = cudaMemsetAsync(scratch, 0, 16, s);
     if (e != cudaSuccess)
         return e;
     const int use_hist = a.ix.P <= (uint32_t)kHistMax ? 1 : 0;
-    return a.fp32 ? launch_tiles<true, false>(b, ntiles, use_hist, s) : launch_tiles<false, false>(b, ntiles, use_hist, s);
+    return a.fp32 ? launch_count_kernel<true, false>(b, ntiles, use_hist, s)
+                  : launch_count_kernel<false, false>(b, ntiles, use_hist, s);
 }
 
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s)
 {
-    const uint64_t nb = (a.n + kThreads - 1) / kThreads;
+    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
     if (nb >= (1ull << 31))
         return cudaErrorInvalidValue;
     unsigned long long *block = reinterpret_cast<unsigned long long *>(scratch);
@@ -1032,9 +1002,9 @@ cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s
             return cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s);
         return cudaSuccess;
     }
-    k_plain_count<<<(unsigned)nb, kThreads, 0, s>>>(a, block);
-    k_plain_scan<<<1, 1024, 0, s>>>(block, nb, a.total);
-    k_plain_write<<<(unsigned)nb, kThreads, 0, s>>>(a, block);
+    k_plain_count<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
+    k_scan<<<1, 1024, 0, s>>>(block, nb, a.total);
+    k_plain_write<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
     return cudaGetLastError();
 }
 

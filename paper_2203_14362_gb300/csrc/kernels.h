@@ -19,7 +19,7 @@ struct IndexView {
 };
 
 // Device status word bits (ORed into the ctx's persistent error word).
-constexpr unsigned kErrTimeout = 1u;   // a bounded wait on another tile's status gave up
+constexpr unsigned kErrTimeout = 1u;   // a bounded wait gave up
 constexpr unsigned kErrInternal = 2u;  // an internal consistency check failed
 constexpr unsigned kErrCopy = 4u;      // a bounded wait for a bulk copy gave up
 
@@ -34,14 +34,15 @@ struct JoinLaunch {
     uint64_t cap;
     unsigned long long *counts;   // P entries or null; zeroed by the launcher
     unsigned long long *total;    // device total or null
-    unsigned long long *tile_status;
-    unsigned *tile_counter;
+    uint32_t *res;                // join pass 1 -> 3: per-point result (scratch)
+    unsigned long long *tile_tot; // join: per-tile pair totals, then offsets (scratch)
+    unsigned *tile_counter;       // tile claims (scratch)
     unsigned *err;                // persistent error word
     unsigned long long *stats;    // kStatCount counters
     int fp32;
 };
 
-// Scratch bytes the fused join needs for n points (tile status + counter).
+// Scratch bytes the join needs for n points (per-point results, tile totals, counter).
 size_t join_scratch_bytes(uint64_t n);
 size_t plain_scratch_bytes(uint64_t n);
 
