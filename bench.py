@@ -35,6 +35,11 @@ if ROOT not in sys.path:
 METRIC = "billion points joined/sec and % HBM roofline; serving p50/p99 ms vs plain kernel"
 UNIT = "Gpoints/s"
 L2_BYTES = 129 * 1024 * 1024
+# DRAM bytes (read + write) per point of the dominant kernel (join pass 1) from
+# the ncu capture summarised in profiles/k_count_resolve_tess2000_20m.md; only
+# valid for that kernel version, the default index (g = 11, sub = 3) and the
+# default workload.
+RESOLVE_TRAFFIC_BYTES_PER_POINT = (297.893376e6 + 59.560704e6) / 20e6
 
 
 # ------------------------------------------------------------------ workloads
@@ -78,7 +83,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu: int, period_ms: int = 50):
+    def __init__(self, gpu: int, period_ms: int = 20):
         self.samples = []
         self.proc = None
         try:
@@ -218,7 +223,7 @@ def run_spx(args, world, rank, local):
     dpts = torch.from_numpy(pts).cuda()
     ph = eng.load_points(dpts)
     gh = eng.load_polygons(v, o)
-    ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32))
+    ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32), sub_log2=args.sub)
     info = eng.index_info(ih)
     cap = N if args.cap is None else args.cap
     pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
@@ -248,6 +253,17 @@ def run_spx(args, world, rank, local):
     ms_max = max_over_ranks(ms, world, torch)
     clk = clocks.summary(t_host0, t_host1)
 
+    # per-kernel device times, live: CUDA events around each pass on the same stream
+    eng.set_phase_timing(True)
+    k_phase = max(1, min(args.steps, 10))
+    for _ in range(k_phase):
+        eng.join(ph, ih, pairs, counts, total, sync=False, stream=stream, plain=args.plain)
+    torch.cuda.synchronize()
+    ph_st = eng.stats(reset=True)
+    eng.set_phase_timing(False)
+    nt = max(ph_st["timed_joins"], 1)
+    phase_ms = {"resolve": ph_st["ms_resolve"] / nt, "scan": ph_st["ms_scan"] / nt, "emit": ph_st["ms_emit"] / nt}
+
     # end to end through the C ABI on pinned host buffers (H2D points, join, D2H pairs + counts)
     e2e = None
     if not args.no_e2e:
@@ -267,10 +283,16 @@ def run_spx(args, world, rank, local):
                "d2h_bytes_per_step": int(m * 8 + P * 8 + 8), "ms_per_step": sec * 1e3}
     clocks.stop()
 
-    idx_bytes = info["n_cells"] * 4 + info["n_entries"] * 16 + info["n_edge_refs"] * 16
-    alg_bytes = 8 * N + 8 * n_pairs + 8 * P + idx_bytes
+    idx_bytes = int(info["device_bytes"])
+    step_bytes = 8 * N + 8 * n_pairs + 8 * P + idx_bytes  # algorithmic bytes of one join
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    # dominant kernel: the resolve pass (reads every point once, writes the counts)
+    dom_ms = phase_ms["resolve"] if not args.plain else ms
+    dom_bytes = 8 * N + 8 * P + idx_bytes if not args.plain else step_bytes
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = args.traffic
+    if traffic is None and not args.plain and args.workload == "tess2000_100m" and args.grid == 0 and args.sub == 0:
+        traffic = RESOLVE_TRAFFIC_BYTES_PER_POINT * N
     out = None
     if rank == 0:
         cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(pts, v, o, args.cpu_budget)
@@ -280,8 +302,8 @@ def run_spx(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {
                 "workload": args.workload, "desc": desc, "points_per_gpu": N, "polygons": P,
-                "vertices": int(v.shape[0]), "pairs": int(n_pairs), "grid_log2": info["grid_log2"],
-                "fp32_filter": bool(args.fp32), "kernel": "plain two-pass" if args.plain else "fused single-pass",
+                "vertices": int(v.shape[0]), "pairs": int(n_pairs), "grid_log2": info["grid_log2"], "sub_log2": info["sub_log2"],
+                "fp32_filter": bool(args.fp32), "kernel": "plain two-pass" if args.plain else "resolve + scan + emit (cached two-pass Map)",
                 "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": int(info["device_bytes"]),
                 "l2": "inputs larger than L2 (points 8 B x N + pairs 8 B x N >> 129 MB); no flush",
                 "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
@@ -289,11 +311,16 @@ def run_spx(args, world, rank, local):
                 "parallelism": f"points sharded by rank, index replicated, dp{world}",
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
-                         "algorithmic_bytes_per_launch": int(alg_bytes)},
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel": "k_count<resolve> (join pass 1)" if not args.plain else "plain join (3 kernels)",
+                         "kernel_ms": dom_ms, "algorithmic_bytes_per_launch": int(dom_bytes),
+                         "step": {"algorithmic_bytes": int(step_bytes), "ms": ms,
+                                  "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                                  "frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
+                         "phase_ms": phase_ms},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * (3 if args.plain else 1),
+            "gpu_launches": args.steps * 3,  # resolve, scan, emit (plain: count, scan, write)
             "clocks": clk,
         }
         print(json.dumps(out), flush=True)
@@ -317,6 +344,9 @@ def main():
     ap.add_argument("--workload", default="tess2000_100m", choices=["tess2000_100m", "stars_1m"])
     ap.add_argument("--points", type=int, default=None, help="points per GPU (default: the workload's)")
     ap.add_argument("--grid", type=int, default=0, help="grid_log2 (0 = automatic)")
+    ap.add_argument("--sub", type=int, default=0, help="sub_log2 (0 = default, 3)")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture (reported as is)")
     ap.add_argument("--fp32", type=int, default=1)
     ap.add_argument("--plain", action="store_true", help="time the plain two-pass comparison kernels")
     ap.add_argument("--cap", type=int, default=None)

@@ -207,16 +207,29 @@ spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *coarse, uint32
                                int32_t *edges);
 void spx_host_index_free(spx_host_index *h);
 
-/* Counters accumulated by the kernels of this ctx since the last reset. */
+/* Counters accumulated by the kernels of this ctx since the last reset, and
+ * (with phase timing on) the device time of each pass, measured with CUDA
+ * events on the caller's stream (the time breakdown of §6.2). */
 typedef struct {
     uint64_t points_scanned;
-    uint64_t edge_tests;      /* straddling-edge tests that needed an orientation */
-    uint64_t fp32_escalations;/* of those, orientations redone in int64 because |d_f| <= E */
+    uint64_t edge_tests;       /* straddling-edge tests that needed an orientation */
+    uint64_t fp32_escalations; /* of those, orientations redone in int64 because |d_f| <= E */
     uint64_t pairs_emitted;
+    uint64_t timed_joins;      /* joins timed since the last reset */
+    uint64_t timed_aggregates; /* aggregates timed since the last reset */
+    double ms_resolve;         /* join pass 1: resolve every point (index lookups, exact tests, counts) */
+    double ms_scan;            /* join pass 2: scan of per-tile pair totals */
+    double ms_emit;            /* join pass 3: pairs written in point order */
+    double ms_aggregate;       /* count-only aggregate */
 } spx_stats_t;
 
 /* Read (synchronising the device) and optionally reset the counters. */
 spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset);
+
+/* Phase timing on (1) or off (0, the default).  While on, every join and
+ * aggregate records CUDA events around its passes and synchronises the stream
+ * after launching, to add the pass times to the counters. */
+spx_status spx_set_phase_timing(spx_ctx *ctx, int on);
 
 /* Release one handle (points, polygons or index).  An index must be freed
  * before the polygon set it was built from. */

@@ -67,6 +67,11 @@ struct spx_ctx {
     void *st_pts = nullptr, *st_pairs = nullptr, *st_counts = nullptr;
     size_t st_pts_b = 0, st_pairs_b = 0, st_counts_b = 0;
     cudaStream_t stream = nullptr;
+    // phase timing
+    bool timing = false;
+    cudaEvent_t ev[4] = {};
+    uint64_t timed_joins = 0, timed_aggs = 0;
+    double ms_resolve = 0, ms_scan = 0, ms_emit = 0, ms_agg = 0;
 };
 
 namespace {
@@ -176,9 +181,21 @@ spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_
     a.err = &ctx->aux->err;
     a.stats = ctx->aux->stats;
     a.fp32 = ix->fp32;
-    cudaError_t e = plain ? launch_join_plain(a, ctx->scratch, s) : launch_join(a, ctx->scratch, s);
+    const bool timed = ctx->timing && !plain;
+    cudaError_t e = plain ? launch_join_plain(a, ctx->scratch, s) : launch_join(a, ctx->scratch, s, timed ? ctx->ev : nullptr);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "join launch");
+    if (timed && pts->n) {
+        SPX_CUDA(cudaEventSynchronize(ctx->ev[3]), "join timing");
+        float t1 = 0, t2 = 0, t3 = 0;
+        cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
+        cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
+        cudaEventElapsedTime(&t3, ctx->ev[2], ctx->ev[3]);
+        ctx->ms_resolve += t1;
+        ctx->ms_scan += t2;
+        ctx->ms_emit += t3;
+        ctx->timed_joins++;
+    }
     if (n_pairs) {
         st = check_kernel_err(ctx, s);
         if (st != SPX_OK)
@@ -237,6 +254,9 @@ void spx_destroy(spx_ctx *ctx)
     cudaFree(ctx->st_counts);
     if (ctx->stream)
         cudaStreamDestroy(ctx->stream);
+    for (auto &e : ctx->ev)
+        if (e)
+            cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -431,9 +451,16 @@ spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint6
     spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, 16, s, "aggregate");
     if (st != SPX_OK)
         return st;
-    cudaError_t e = launch_aggregate(a, ctx->scratch, s);
+    cudaError_t e = launch_aggregate(a, ctx->scratch, s, ctx->timing ? ctx->ev : nullptr);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "aggregate launch");
+    if (ctx->timing && pts->n) {
+        SPX_CUDA(cudaEventSynchronize(ctx->ev[1]), "aggregate timing");
+        float t = 0;
+        cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
+        ctx->ms_agg += t;
+        ctx->timed_aggs++;
+    }
     return SPX_OK;
 }
 
@@ -547,9 +574,31 @@ spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset)
     out->edge_tests = v[kStatTests];
     out->fp32_escalations = v[kStatEscalations];
     out->pairs_emitted = v[kStatPairs];
-    if (reset)
+    out->timed_joins = ctx->timed_joins;
+    out->timed_aggregates = ctx->timed_aggs;
+    out->ms_resolve = ctx->ms_resolve;
+    out->ms_scan = ctx->ms_scan;
+    out->ms_emit = ctx->ms_emit;
+    out->ms_aggregate = ctx->ms_agg;
+    if (reset) {
         SPX_CUDA(cudaMemset(ctx->aux->stats, 0, sizeof(v)), "stats reset");
+        ctx->timed_joins = ctx->timed_aggs = 0;
+        ctx->ms_resolve = ctx->ms_scan = ctx->ms_emit = ctx->ms_agg = 0;
+    }
     return check_kernel_err(ctx, nullptr);
+}
+
+spx_status spx_set_phase_timing(spx_ctx *ctx, int on)
+{
+    if (!ctx)
+        return SPX_EINVAL;
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    if (on && !ctx->ev[0])
+        for (auto &e : ctx->ev)
+            SPX_CUDA(cudaEventCreate(&e), "event create");
+    ctx->timing = on != 0;
+    return SPX_OK;
 }
 
 spx_status spx_free(spx_ctx *ctx, uint64_t handle)

@@ -920,7 +920,7 @@ size_t plain_scratch_bytes(uint64_t n)
     return size_t(nb * 8 + 16);
 }
 
-cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s)
+cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
 {
     const uint64_t ntiles64 = (a.n + kTile - 1) / kTile;
     if (ntiles64 >= (1ull << 31))
@@ -948,12 +948,18 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s)
     }
     // pass 1: resolve every point, count per polygon and per tile
     const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
+    if (ev)
+        cudaEventRecord(ev[0], s);
     e = a.fp32 ? launch_count_kernel<true, true>(b, ntiles, use_hist, s)
                : launch_count_kernel<false, true>(b, ntiles, use_hist, s);
     if (e != cudaSuccess)
         return e;
+    if (ev)
+        cudaEventRecord(ev[1], s);
     // pass 2: tile offsets and the total
     k_scan<<<1, 1024, 0, s>>>(b.tile_tot, ntiles, a.total);
+    if (ev)
+        cudaEventRecord(ev[2], s);
     // pass 3: pairs in point order
     if (a.cap) {
         if (a.fp32)
@@ -961,10 +967,12 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s)
         else
             k_emit<false><<<ntiles, kThreads, 0, s>>>(b, b.tile_tot);
     }
+    if (ev)
+        cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s)
+cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
 {
     cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * (a.ix.P ? a.ix.P : 1), s);
     if (e != cudaSuccess || a.n == 0)
@@ -981,8 +989,13 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s)
     if (e != cudaSuccess)
         return e;
     const int use_hist = a.ix.P <= (uint32_t)kHistMax ? 1 : 0;
-    return a.fp32 ? launch_count_kernel<true, false>(b, ntiles, use_hist, s)
-                  : launch_count_kernel<false, false>(b, ntiles, use_hist, s);
+    if (ev)
+        cudaEventRecord(ev[0], s);
+    e = a.fp32 ? launch_count_kernel<true, false>(b, ntiles, use_hist, s)
+               : launch_count_kernel<false, false>(b, ntiles, use_hist, s);
+    if (ev)
+        cudaEventRecord(ev[1], s);
+    return e;
 }
 
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s)

@@ -46,11 +46,13 @@ struct JoinLaunch {
 size_t join_scratch_bytes(uint64_t n);
 size_t plain_scratch_bytes(uint64_t n);
 
-// scratch: device memory of join_scratch_bytes(n) bytes; zeroed inside.
-cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s);
+// scratch: device memory of join_scratch_bytes(n) bytes.  ev (may be null):
+// four events recorded before pass 1, after pass 1 (resolve), after pass 2
+// (scan) and after pass 3 (emit).
+cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s);
 // scratch: at least 16 bytes of device memory (zeroed inside).
-cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s);
+cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 int device_sm_count();
 

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "SPX_OK", -1: "SPX_EINVAL", -2: "SPX_ENOMEM", -3: "SPX_ECUDA"
 EXPORTS = [
     "spx_create", "spx_destroy", "spx_last_error", "spx_load_points", "spx_load_polygons", "spx_build_index",
     "spx_index_info_get", "spx_join", "spx_join_plain", "spx_aggregate", "spx_join_host", "spx_host_index_build",
-    "spx_host_index_copy", "spx_host_index_free", "spx_stats", "spx_free",
+    "spx_host_index_copy", "spx_host_index_free", "spx_stats", "spx_set_phase_timing", "spx_free",
 ]
 
 
@@ -45,7 +45,10 @@ class IndexInfo(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("points_scanned", C.c_uint64), ("edge_tests", C.c_uint64),
-                ("fp32_escalations", C.c_uint64), ("pairs_emitted", C.c_uint64)]
+                ("fp32_escalations", C.c_uint64), ("pairs_emitted", C.c_uint64),
+                ("timed_joins", C.c_uint64), ("timed_aggregates", C.c_uint64),
+                ("ms_resolve", C.c_double), ("ms_scan", C.c_double), ("ms_emit", C.c_double),
+                ("ms_aggregate", C.c_double)]
 
 
 _lib = None
@@ -77,6 +80,7 @@ def load(path: str = LIB_PATH):
         "spx_host_index_copy": ([V, V, V, V, V], I),
         "spx_host_index_free": ([V], None),
         "spx_stats": ([V, C.POINTER(Stats), I], I),
+        "spx_set_phase_timing": ([V, I], I),
         "spx_free": ([V, U64], I),
     }
     for name, (args, res) in sig.items():
@@ -218,6 +222,9 @@ class Engine:
             raise SpxError(st, f"join needs {n.value} pairs, capacity {cap}")
         self._check(st, "spx_join_host")
         return pairs[:n.value], counts[:n_polys], n.value
+
+    def set_phase_timing(self, on: bool):
+        self._check(self.lib.spx_set_phase_timing(self.ctx, 1 if on else 0), "spx_set_phase_timing")
 
     def stats(self, reset: bool = False) -> dict:
         s = Stats()
