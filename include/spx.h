@@ -164,6 +164,34 @@ spx_status spx_join_plain(spx_ctx *ctx, spx_points points, spx_index index, uint
                           uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream);
 
 /*
+ * Allocation-free variant of spx_join_plain (the paper has no counterpart; it
+ * exists for callers that cannot allocate device memory at call time: a
+ * process whose device memory is held entirely by another allocator, such as
+ * a framework's caching allocator, so cudaMalloc would fail; a latency-bound
+ * request loop that cannot afford an allocator call, which may block and
+ * synchronise the device; a deployment with a fixed device-memory budget
+ * audited up front).  Same join, same results as spx_join_plain, with its
+ * scratch in a fixed 512 KiB device array inside libspx instead of memory
+ * from cudaMalloc; the call itself allocates nothing (the points, polygons
+ * and index are loaded and built beforehand, and the caller passes the
+ * outputs: pairs_dev, cap, counts_dev, total_dev as in spx_join_plain).
+ *   - At most 16,777,216 points per call; a larger table is rejected with
+ *     SPX_EINVAL and a message stating the limit.
+ *   - Every GPU that loads libspx holds the 512 KiB array until the process
+ *     exits.  All calls share it, and it keeps the last call's contents (the
+ *     counting pass rewrites every value it later reads, so nothing needs
+ *     clearing): calls whose kernels overlap on the GPU (different streams,
+ *     different contexts in one process) race on it and corrupt each other's
+ *     results; serialise them.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Asynchronous on `stream`; no host out-parameter (read *total_dev).
+ */
+spx_status spx_join_plain_static(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev,
+                                 uint64_t cap, uint64_t *counts_dev, uint64_t *total_dev, void *stream);
+
+/*
  * Count aggregation without materialising the join (§5.2 "Spatial
  * Aggregations", the plan for point data): counts_dev[q] (uint64, P entries,
  * device) = number of points inside polygon q.

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -210,9 +211,81 @@ spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_
     return SPX_OK;
 }
 
+// Scratch of the allocation-free plain join (spx_join_plain_static): one
+// uint64 block total per 256-point block of the counting pass, 512 KiB in all.
+// It is a file-scope device array, so every GPU that loads this library holds
+// it until the process exits; every call shares it.
+constexpr uint64_t kStaticJoinMaxPoints = uint64_t(1) << 24;
+constexpr uint64_t kStaticJoinBlocks = kStaticJoinMaxPoints / 256;
+static __device__ __align__(256) unsigned long long g_static_join_scratch[kStaticJoinBlocks + 2];
+
+// Device address of g_static_join_scratch, resolved once per device (host
+// code cannot use the array's name as a device address).
+void *static_join_scratch(int device, cudaError_t &err)
+{
+    static std::mutex mu;
+    static void *addr[64] = {};
+    err = cudaSuccess;
+    if (device < 0 || device >= 64) {
+        err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_static_join_scratch);
+        if (err != cudaSuccess)
+            return nullptr;
+        addr[device] = p;
+    }
+    return addr[device];
+}
+
 } // namespace
 
 extern "C" {
+
+spx_status spx_join_plain_static(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev, uint64_t cap,
+                                 uint64_t *counts_dev, uint64_t *total_dev, void *stream)
+{
+    if (!ctx)
+        return SPX_EINVAL;
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    PointsObj *pts = lookup(ctx->points, points);
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!pts || !ix)
+        return fail(ctx, SPX_EINVAL, "join_plain_static: bad points or index handle");
+    if (pts->n > kStaticJoinMaxPoints)
+        return fail(ctx, SPX_EINVAL, "join_plain_static: the point table has " + std::to_string(pts->n) +
+                                         " points; the allocation-free join takes at most " +
+                                         std::to_string(kStaticJoinMaxPoints));
+    if (cap && !pairs_dev)
+        return fail(ctx, SPX_EINVAL, "join_plain_static: pairs_dev is NULL with cap > 0");
+    if ((reinterpret_cast<uintptr_t>(pairs_dev) & 7) || (reinterpret_cast<uintptr_t>(counts_dev) & 7) ||
+        (reinterpret_cast<uintptr_t>(total_dev) & 7))
+        return fail(ctx, SPX_EINVAL, "join_plain_static: output pointers must be 8-byte aligned");
+    cudaError_t e = cudaSuccess;
+    void *scratch = static_join_scratch(ctx->device, e);
+    if (!scratch)
+        return cuda_fail(ctx, e, "join_plain_static: cudaGetSymbolAddress of the static scratch");
+    JoinLaunch a{};
+    a.ix = ix->view;
+    a.pts = reinterpret_cast<const int2 *>(pts->dev);
+    a.n = pts->n;
+    a.pairs = reinterpret_cast<uint2 *>(pairs_dev);
+    a.cap = pairs_dev ? cap : 0;
+    a.counts = reinterpret_cast<unsigned long long *>(counts_dev);
+    a.total = reinterpret_cast<unsigned long long *>(total_dev);
+    a.err = &ctx->aux->err;
+    a.stats = ctx->aux->stats;
+    a.fp32 = 0;
+    // every block total is written by the counting pass before it is read: no clearing needed
+    e = launch_join_plain(a, scratch, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "join_plain_static launch");
+    return SPX_OK;
+}
 
 spx_status spx_create(int device, spx_ctx **out)
 {

@@ -23,6 +23,7 @@ EXPORTS = [
     "spx_create", "spx_destroy", "spx_last_error", "spx_load_points", "spx_load_polygons", "spx_build_index",
     "spx_index_info_get", "spx_join", "spx_join_plain", "spx_aggregate", "spx_join_host", "spx_host_index_build",
     "spx_host_index_copy", "spx_host_index_free", "spx_stats", "spx_set_phase_timing", "spx_free",
+    "spx_join_plain_static",
 ]
 
 
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH):
         "spx_host_index_free": ([V], None),
         "spx_stats": ([V, C.POINTER(Stats), I], I),
         "spx_set_phase_timing": ([V, I], I),
+        "spx_join_plain_static": ([V, U64, U64, V, U64, V, V, V], I),
         "spx_free": ([V, U64], I),
     }
     for name, (args, res) in sig.items():
@@ -205,6 +207,13 @@ class Engine:
             raise SpxError(st, f"join needs {n.value} pairs, capacity {cap}")
         self._check(st, "spx_join")
         return n.value if sync else None
+
+    def join_plain_static(self, points: int, index: int, pairs, counts, total, stream=None):
+        """spx_join_plain_static: the plain join with its scratch in libspx's
+        fixed device array (no allocation in the call); asynchronous."""
+        cap = 0 if pairs is None else pairs.shape[0]
+        self._check(self.lib.spx_join_plain_static(self.ctx, points, index, _dev_ptr(pairs), cap, _dev_ptr(counts),
+                                                   _dev_ptr(total), _stream(stream)), "spx_join_plain_static")
 
     def aggregate(self, points: int, index: int, counts, stream=None):
         self._check(self.lib.spx_aggregate(self.ctx, points, index, _dev_ptr(counts), _stream(stream)),
