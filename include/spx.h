@@ -156,6 +156,24 @@ spx_status spx_join(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *
                     uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream);
 
 /*
+ * Batched polygonal selection (§5.2 "Spatial Selection": the points inside a
+ * polygonal constraint; here the P polygons of the index are P independent
+ * query constraints answered in one pass over the points).  Output: for each
+ * query q, the ascending ids of the points inside it, at
+ * ids_dev[offsets_dev[q] .. offsets_dev[q+1]) (uint32 ids; offsets_dev holds
+ * P + 1 uint64, offsets_dev[P] = total).  ids past cap are not written.
+ * n_ids (host, may be NULL): if given, the call synchronises, writes the total
+ * and returns SPX_ECAPACITY if it exceeds cap.  At most 1024 query polygons
+ * per index (SPX_EINVAL otherwise).
+ * The first call with a given (points, index, ids_dev, cap, offsets_dev) runs
+ * the passes directly and then captures them into a CUDA graph; later calls
+ * with the same arguments replay that graph as one launch.  Graphs are
+ * dropped when their points or index are freed or the ctx scratch grows.
+ */
+spx_status spx_select(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *ids_dev, uint64_t cap,
+                      uint64_t *offsets_dev, uint64_t *n_ids, void *stream);
+
+/*
  * The same join through the plain comparison kernels: exact int64 orientation
  * only, one thread per point, a counting pass, a scan and a writing pass (the
  * two-pass Map of §5.1).  Same arguments and results as spx_join.

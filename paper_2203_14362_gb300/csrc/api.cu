@@ -12,6 +12,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <vector>
@@ -68,6 +69,9 @@ struct spx_ctx {
     void *st_pts = nullptr, *st_pairs = nullptr, *st_counts = nullptr;
     size_t st_pts_b = 0, st_pairs_b = 0, st_counts_b = 0;
     cudaStream_t stream = nullptr;
+    // batched selection: captured launch sequences, keyed by their arguments
+    std::map<std::tuple<uint64_t, uint64_t, uintptr_t, uint64_t, uintptr_t>, cudaGraphExec_t> select_graphs;
+    cudaStream_t capture_stream = nullptr;
     // phase timing
     bool timing = false;
     cudaEvent_t ev[4] = {};
@@ -128,6 +132,12 @@ spx_status ensure(spx_ctx *ctx, void **buf, size_t *have, size_t need, cudaStrea
         *have = 0;
     }
     size_t sz = need < 256 ? 256 : need;
+    if (buf == &ctx->scratch) {
+        // captured selections point at the old scratch
+        for (auto &kv : ctx->select_graphs)
+            cudaGraphExecDestroy(kv.second);
+        ctx->select_graphs.clear();
+    }
     cudaError_t e = cudaMalloc(buf, sz);
     if (e != cudaSuccess)
         return fail(ctx, SPX_ENOMEM, std::string(what) + ": cudaMalloc failed: " + cudaGetErrorString(e));
@@ -325,6 +335,10 @@ void spx_destroy(spx_ctx *ctx)
     cudaFree(ctx->st_pts);
     cudaFree(ctx->st_pairs);
     cudaFree(ctx->st_counts);
+    for (auto &kv : ctx->select_graphs)
+        cudaGraphExecDestroy(kv.second);
+    if (ctx->capture_stream)
+        cudaStreamDestroy(ctx->capture_stream);
     if (ctx->stream)
         cudaStreamDestroy(ctx->stream);
     for (auto &e : ctx->ev)
@@ -498,6 +512,82 @@ spx_status spx_join_plain(spx_ctx *ctx, spx_points points, spx_index index, uint
                           uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream)
 {
     return join_common(ctx, points, index, pairs_dev, cap, counts_dev, total_dev, n_pairs, stream, true);
+}
+
+spx_status spx_select(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *ids_dev, uint64_t cap,
+                      uint64_t *offsets_dev, uint64_t *n_ids, void *stream)
+{
+    if (!ctx)
+        return SPX_EINVAL;
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    PointsObj *pts = lookup(ctx->points, points);
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!pts || !ix)
+        return fail(ctx, SPX_EINVAL, "select: bad points or index handle");
+    if (!offsets_dev || (cap && !ids_dev))
+        return fail(ctx, SPX_EINVAL, "select: offsets_dev is NULL, or ids_dev is NULL with cap > 0");
+    if ((reinterpret_cast<uintptr_t>(offsets_dev) & 7) || (reinterpret_cast<uintptr_t>(ids_dev) & 3))
+        return fail(ctx, SPX_EINVAL, "select: misaligned output pointer");
+    if (ix->view.P > kSelectMaxQueries)
+        return fail(ctx, SPX_EINVAL, "select: an index of " + std::to_string(ix->view.P) +
+                                         " query polygons; batched selection takes at most " +
+                                         std::to_string(kSelectMaxQueries));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, select_scratch_bytes(pts->n, ix->view.P), s,
+                           "select");
+    if (st != SPX_OK)
+        return st;
+    JoinLaunch a{};
+    a.ix = ix->view;
+    a.pts = reinterpret_cast<const int2 *>(pts->dev);
+    a.n = pts->n;
+    a.err = &ctx->aux->err;
+    a.stats = ctx->aux->stats;
+    a.fp32 = ix->fp32;
+    unsigned long long *offs = reinterpret_cast<unsigned long long *>(offsets_dev);
+    const auto key = std::make_tuple(points, index, reinterpret_cast<uintptr_t>(ids_dev), cap,
+                                     reinterpret_cast<uintptr_t>(offsets_dev));
+    auto it = ctx->select_graphs.find(key);
+    if (it == ctx->select_graphs.end()) {
+        // first call with these arguments: run once directly (sets kernel attributes),
+        // then capture the whole sequence into a graph for the next calls
+        cudaError_t e = launch_select(a, ids_dev, cap, offs, ctx->scratch, s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "select launch");
+        if (!ctx->capture_stream)
+            SPX_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "capture stream");
+        SPX_CUDA(cudaStreamSynchronize(s), "select synchronize");
+        SPX_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed), "select capture");
+        e = launch_select(a, ids_dev, cap, offs, ctx->scratch, ctx->capture_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g)
+                cudaGraphDestroy(g);
+            return cuda_fail(ctx, e != cudaSuccess ? e : e2, "select capture");
+        }
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "select graph instantiate");
+        ctx->select_graphs[key] = ge;
+    } else {
+        SPX_CUDA(cudaGraphLaunch(it->second, s), "select graph launch");
+    }
+    if (n_ids) {
+        st = check_kernel_err(ctx, s);
+        if (st != SPX_OK)
+            return st;
+        unsigned long long t = 0;
+        SPX_CUDA(cudaMemcpy(&t, offs + ix->view.P, sizeof(t), cudaMemcpyDeviceToHost), "select total");
+        *n_ids = t;
+        if (t > cap)
+            return fail(ctx, SPX_ECAPACITY, "select: " + std::to_string(t) + " ids exceed capacity " +
+                                                std::to_string(cap));
+    }
+    return SPX_OK;
 }
 
 spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint64_t *counts_dev, void *stream)
@@ -686,6 +776,13 @@ spx_status spx_free(spx_ctx *ctx, uint64_t handle)
         if (!ix)
             return fail(ctx, SPX_EINVAL, "free: bad index handle");
         cudaDeviceSynchronize();
+        for (auto it = ctx->select_graphs.begin(); it != ctx->select_graphs.end();)
+            if (std::get<1>(it->first) == handle) {
+                cudaGraphExecDestroy(it->second);
+                it = ctx->select_graphs.erase(it);
+            } else {
+                ++it;
+            }
         cudaFree(ix->mem);
         PolysObj *pg = lookup(ctx->polys, ix->polys);
         if (pg)
@@ -707,6 +804,13 @@ spx_status spx_free(spx_ctx *ctx, uint64_t handle)
         if (!p)
             return fail(ctx, SPX_EINVAL, "free: bad points handle");
         cudaDeviceSynchronize();
+        for (auto it = ctx->select_graphs.begin(); it != ctx->select_graphs.end();)
+            if (std::get<0>(it->first) == handle) {
+                cudaGraphExecDestroy(it->second);
+                it = ctx->select_graphs.erase(it);
+            } else {
+                ++it;
+            }
         if (p->owned)
             cudaFree(p->dev);
         ctx->points.erase(handle);

@@ -814,6 +814,214 @@ __global__ void __launch_bounds__(1024) k_scan(unsigned long long *v, uint64_t n
         *total = s_carry;
 }
 
+// Device-wide exclusive scan for long arrays: per-chunk sums, a one-block scan
+// of the sums, then every chunk rescanned from its base.
+constexpr int kScanItems = 8;
+constexpr uint64_t kScanChunk = 1024 * kScanItems;
+
+__device__ __forceinline__ unsigned long long block_exclusive_scan_1024(unsigned long long x, unsigned long long &total,
+                                                                        unsigned long long *s_w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o)
+            inc += t;
+    }
+    if (lane == 31)
+        s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = s_w[lane];
+        unsigned long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o)
+                wi += t;
+        }
+        s_w[lane] = wi - w;
+        if (lane == 31)
+            s_w[32] = wi;
+    }
+    __syncthreads();
+    total = s_w[32];
+    const unsigned long long ex = s_w[warp] + inc - x;
+    __syncthreads();
+    return ex;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partials(const unsigned long long *v, uint64_t n,
+                                                        unsigned long long *part)
+{
+    __shared__ unsigned long long s_w[33];
+    const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        sum += (b0 + j < n) ? v[b0 + j] : 0ull;
+    unsigned long long total;
+    block_exclusive_scan_1024(sum, total, s_w);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(unsigned long long *v, uint64_t n,
+                                                     const unsigned long long *part_off)
+{
+    __shared__ unsigned long long s_w[33];
+    const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+    unsigned long long x[kScanItems], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        x[j] = (b0 + j < n) ? v[b0 + j] : 0ull;
+        sum += x[j];
+    }
+    unsigned long long total;
+    unsigned long long run = part_off[blockIdx.x] + block_exclusive_scan_1024(sum, total, s_w);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (b0 + j < n)
+            v[b0 + j] = run;
+        run += x[j];
+    }
+}
+
+// ------------------------------------------------------ batched selection
+// Selection of points by many query polygons at once (§5.2 "Spatial
+// Selection", one pass over the points for all queries): after the resolve
+// pass, each super-tile of kSuperTile points counts its points per query into
+// a query-major table; an exclusive scan of that table in query-major order
+// makes entry (q, s) the output position of super-tile s's first point of
+// query q; the emit kernel then writes every query's point ids in ascending
+// order.
+constexpr int kSuperTile = 32768;
+constexpr int kSelMaxQ = 1024;                      // queries per index for the shared-memory path
+constexpr int kSelWarpRange = kSuperTile / kWarps;  // points per warp of a super-tile
+
+// the queries of a point in several polygons after `after` (ascending walk),
+// or kResNone
+template <bool FP32>
+__device__ __forceinline__ uint32_t next_query(const IndexView &ix, int px, int py, uint32_t after, uint64_t keep)
+{
+    uint32_t best = kResNone;
+    point_emit<FP32>(ix, px, py, keep, [&](uint32_t q) {
+        if ((after == kResNone || q > after) && best == kResNone)
+            best = q;
+    });
+    return best;
+}
+
+template <bool FP32>
+__global__ void __launch_bounds__(kThreads) k_sel_count(JoinLaunch a, unsigned long long *table, uint32_t n_super)
+{
+    extern __shared__ uint32_t s_cnt[]; // P counters
+    const IndexView &ix = a.ix;
+    const uint64_t keep = policy_evict_last();
+    for (uint32_t q = threadIdx.x; q < ix.P; q += kThreads)
+        s_cnt[q] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * kSuperTile;
+    for (uint32_t j = threadIdx.x; j < (uint32_t)kSuperTile; j += kThreads) {
+        if (base + j >= a.n)
+            break;
+        const uint32_t r = __ldcg(a.res + base + j);
+        if (r == kResNone)
+            continue;
+        if (!(r & kResMulti)) {
+            atomicAdd(&s_cnt[r], 1u);
+        } else {
+            const int2 p = a.pts[base + j];
+            point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(&s_cnt[q], 1u); });
+        }
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < ix.P; q += kThreads)
+        table[(uint64_t)q * n_super + blockIdx.x] = s_cnt[q];
+}
+
+template <bool FP32>
+__global__ void __launch_bounds__(kThreads) k_sel_emit(JoinLaunch a, const unsigned long long *table, uint32_t n_super,
+                                                       uint32_t *ids, uint64_t cap)
+{
+    extern __shared__ unsigned long long s_run[]; // kWarps x P running positions
+    uint32_t *s_wc = reinterpret_cast<uint32_t *>(s_run + (size_t)kWarps * a.ix.P); // kWarps x P counts
+    const IndexView &ix = a.ix;
+    const uint32_t P = ix.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t keep = policy_evict_last();
+    for (uint32_t i = threadIdx.x; i < kWarps * P; i += kThreads)
+        s_wc[i] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * kSuperTile + (uint64_t)warp * kSelWarpRange;
+    // 1. every warp counts its range per query
+    for (uint32_t j = lane; j < (uint32_t)kSelWarpRange; j += 32) {
+        if (base + j >= a.n)
+            break;
+        const uint32_t r = __ldcg(a.res + base + j);
+        if (r == kResNone)
+            continue;
+        if (!(r & kResMulti)) {
+            atomicAdd(&s_wc[warp * P + r], 1u);
+        } else {
+            const int2 p = a.pts[base + j];
+            point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(&s_wc[warp * P + q], 1u); });
+        }
+    }
+    __syncthreads();
+    // 2. start positions per (warp, query)
+    for (uint32_t q = threadIdx.x; q < P; q += kThreads) {
+        unsigned long long pos = table[(uint64_t)q * n_super + blockIdx.x];
+        for (int w = 0; w < kWarps; ++w) {
+            s_run[w * P + q] = pos;
+            pos += s_wc[w * P + q];
+        }
+    }
+    __syncthreads();
+    // 3. every warp writes its range in point order; within 32 points, queries
+    //    are taken in ascending order and lanes in lane order
+    for (uint32_t j0 = 0; j0 < (uint32_t)kSelWarpRange; j0 += 32) {
+        if (base + j0 >= a.n)
+            break;
+        const uint64_t pid = base + j0 + lane;
+        const bool valid = pid < a.n;
+        const uint32_t r = valid ? __ldcg(a.res + pid) : kResNone;
+        const bool multi = r != kResNone && (r & kResMulti);
+        int2 p = make_int2(0, 0);
+        if (multi)
+            p = a.pts[pid];
+        uint32_t cur = multi ? (r & ~kResMulti) : r; // smallest query of the point, or kResNone
+        for (;;) {
+            const uint32_t qmin = __reduce_min_sync(kFull, cur);
+            if (qmin == kResNone)
+                break;
+            const bool mine = cur == qmin;
+            const uint32_t bl = __ballot_sync(kFull, mine);
+            const unsigned long long start = s_run[warp * P + qmin];
+            if (mine) {
+                const unsigned long long o = start + __popc(bl & lanemask_lt());
+                if (o < cap)
+                    ids[o] = (uint32_t)pid;
+                cur = multi ? next_query<FP32>(ix, p.x, p.y, qmin, keep) : kResNone;
+            }
+            __syncwarp();
+            if (lane == 0)
+                s_run[warp * P + qmin] = start + __popc(bl);
+            __syncwarp();
+        }
+    }
+}
+
+// offsets[q] = first position of query q (table entry (q, 0)), offsets[P] = total
+__global__ void k_sel_offsets(const unsigned long long *table, uint32_t n_super, uint32_t P,
+                              const unsigned long long *total, unsigned long long *offsets)
+{
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= P; q += gridDim.x * blockDim.x)
+        offsets[q] = q < P ? table[(uint64_t)q * n_super] : *total;
+}
+
 __global__ void __launch_bounds__(kPlainThreads) k_plain_write(JoinLaunch a, const unsigned long long *block_off)
 {
     __shared__ uint32_t s_w[(kPlainThreads / 32)];
@@ -893,6 +1101,26 @@ cudaError_t launch_count_kernel(const JoinLaunch &a, uint32_t ntiles, int use_hi
         return e;
     k_count<FP32, RESOLVE><<<persistent_grid(k_count<FP32, RESOLVE>, kThreads, smem, ntiles), kThreads, smem, s>>>(
         a, ntiles, use_hist);
+    return cudaGetLastError();
+}
+
+// Exclusive scan of n values in place; the total goes to *total.  part: at
+// least scan_partials(n) + 1 values of scratch.
+uint64_t scan_partials(uint64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
+
+cudaError_t launch_scan(unsigned long long *v, uint64_t n, unsigned long long *total, unsigned long long *part,
+                        cudaStream_t s)
+{
+    if (n <= 4 * kScanChunk) {
+        k_scan<<<1, 1024, 0, s>>>(v, n, total);
+        return cudaGetLastError();
+    }
+    const uint64_t nb = scan_partials(n);
+    if (nb >= (1ull << 31))
+        return cudaErrorInvalidValue;
+    k_scan_partials<<<(unsigned)nb, 1024, 0, s>>>(v, n, part);
+    k_scan<<<1, 1024, 0, s>>>(part, nb, total);
+    k_scan_apply<<<(unsigned)nb, 1024, 0, s>>>(v, n, part);
     return cudaGetLastError();
 }
 
@@ -996,6 +1224,74 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
     if (ev)
         cudaEventRecord(ev[1], s);
     return e;
+}
+
+size_t select_scratch_bytes(uint64_t n, uint32_t P)
+{
+    const uint64_t ntiles = (n + kTile - 1) / kTile;
+    const uint64_t n_super = (n + kSuperTile - 1) / kSuperTile;
+    const uint64_t tab = uint64_t(P) * n_super;
+    return size_t(((n * 4 + 15) & ~uint64_t(15)) + ntiles * 8 + 16 + tab * 8 + (scan_partials(tab) + 2) * 8 + 64);
+}
+
+cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
+                          void *scratch, cudaStream_t s)
+{
+    const uint64_t ntiles64 = (a.n + kTile - 1) / kTile;
+    const uint64_t n_super64 = (a.n + kSuperTile - 1) / kSuperTile;
+    if (ntiles64 >= (1ull << 31) || a.ix.P > (uint32_t)kSelMaxQ)
+        return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(a.pts) & 15)
+        return cudaErrorMisalignedAddress;
+    const uint32_t ntiles = uint32_t(ntiles64), n_super = uint32_t(n_super64), P = a.ix.P;
+    JoinLaunch b = a;
+    char *sc = static_cast<char *>(scratch);
+    b.res = reinterpret_cast<uint32_t *>(sc);
+    sc += (a.n * 4 + 15) & ~uint64_t(15);
+    b.tile_tot = reinterpret_cast<unsigned long long *>(sc);
+    sc += ntiles * 8;
+    b.tile_counter = reinterpret_cast<unsigned *>(sc);
+    sc += 16;
+    unsigned long long *table = reinterpret_cast<unsigned long long *>(sc);
+    sc += uint64_t(P) * n_super * 8;
+    unsigned long long *part = reinterpret_cast<unsigned long long *>(sc);
+    unsigned long long *total = part + scan_partials(uint64_t(P) * n_super) + 1;
+    b.counts = nullptr;
+    cudaError_t e = cudaMemsetAsync(b.tile_counter, 0, 16, s);
+    if (e != cudaSuccess)
+        return e;
+    if (ntiles == 0 || P == 0) {
+        return cudaMemsetAsync(offsets, 0, sizeof(unsigned long long) * (P + 1), s);
+    }
+    // pass 1: resolve every point once for all queries
+    e = a.fp32 ? launch_count_kernel<true, true>(b, ntiles, 0, s) : launch_count_kernel<false, true>(b, ntiles, 0, s);
+    if (e != cudaSuccess)
+        return e;
+    // pass 2: per (query, super-tile) counts, scanned in query-major order
+    const size_t sm_count = sizeof(uint32_t) * P;
+    if (a.fp32)
+        k_sel_count<true><<<n_super, kThreads, sm_count, s>>>(b, table, n_super);
+    else
+        k_sel_count<false><<<n_super, kThreads, sm_count, s>>>(b, table, n_super);
+    e = launch_scan(table, uint64_t(P) * n_super, total, part, s);
+    if (e != cudaSuccess)
+        return e;
+    k_sel_offsets<<<(P + 256) / 256, 256, 0, s>>>(table, n_super, P, total, offsets);
+    // pass 3: ids in ascending order per query
+    const size_t sm_emit = (sizeof(unsigned long long) + sizeof(uint32_t)) * size_t(kWarps) * P;
+    static bool done[2][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (a.fp32) {
+        if ((e = smem_opt_in(k_sel_emit<true>, (sizeof(unsigned long long) + 4) * kWarps * kSelMaxQ, done[1])) != cudaSuccess)
+            return e;
+        k_sel_emit<true><<<n_super, kThreads, sm_emit, s>>>(b, table, n_super, ids, cap);
+    } else {
+        if ((e = smem_opt_in(k_sel_emit<false>, (sizeof(unsigned long long) + 4) * kWarps * kSelMaxQ, done[0])) != cudaSuccess)
+            return e;
+        k_sel_emit<false><<<n_super, kThreads, sm_emit, s>>>(b, table, n_super, ids, cap);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s)

@@ -54,6 +54,14 @@ cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s
 // scratch: at least 16 bytes of device memory (zeroed inside).
 cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
+// Batched selection: per-query ascending point-id lists in ids (cap entries),
+// offsets[q] / offsets[P] (device, P + 1 values; offsets[P] = total).  At most
+// kSelMaxQ (1024) queries per index.  scratch: select_scratch_bytes(n, P).
+size_t select_scratch_bytes(uint64_t n, uint32_t P);
+cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
+                          void *scratch, cudaStream_t s);
+constexpr uint32_t kSelectMaxQueries = 1024;
+
 int device_sm_count();
 
 } // namespace spx

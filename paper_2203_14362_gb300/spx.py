@@ -23,7 +23,7 @@ EXPORTS = [
     "spx_create", "spx_destroy", "spx_last_error", "spx_load_points", "spx_load_polygons", "spx_build_index",
     "spx_index_info_get", "spx_join", "spx_join_plain", "spx_aggregate", "spx_join_host", "spx_host_index_build",
     "spx_host_index_copy", "spx_host_index_free", "spx_stats", "spx_set_phase_timing", "spx_free",
-    "spx_join_plain_static",
+    "spx_join_plain_static", "spx_select",
 ]
 
 
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
         "spx_stats": ([V, C.POINTER(Stats), I], I),
         "spx_set_phase_timing": ([V, I], I),
         "spx_join_plain_static": ([V, U64, U64, V, U64, V, V, V], I),
+        "spx_select": ([V, U64, U64, V, U64, V, P64, V], I),
         "spx_free": ([V, U64], I),
     }
     for name, (args, res) in sig.items():
@@ -206,6 +207,18 @@ class Engine:
         if st == SPX_ECAPACITY:
             raise SpxError(st, f"join needs {n.value} pairs, capacity {cap}")
         self._check(st, "spx_join")
+        return n.value if sync else None
+
+    def select(self, points: int, index: int, ids, offsets, sync: bool = True, stream=None):
+        """Batched selection: ids (int32/uint32 CUDA tensor, cap entries), offsets
+        (int64 CUDA tensor, P + 1 entries).  Returns the total when sync."""
+        cap = 0 if ids is None else ids.shape[0]
+        n = C.c_uint64()
+        st = self.lib.spx_select(self.ctx, points, index, _dev_ptr(ids), cap, _dev_ptr(offsets),
+                                 C.byref(n) if sync else None, _stream(stream))
+        if st == SPX_ECAPACITY:
+            raise SpxError(st, f"select needs {n.value} ids, capacity {cap}")
+        self._check(st, "spx_select")
         return n.value if sync else None
 
     def join_plain_static(self, points: int, index: int, pairs, counts, total, stream=None):
