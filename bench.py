@@ -56,6 +56,15 @@ def make_workload(name: str, n_override: int | None, rank: int):
         desc = (f"{n} mixture points (64 Gaussians, sigma 0.5-5% of box, 10% uniform) x 2000-cell tessellation "
                 f"(jittered quads, noisy edges, 52-2000 vertices/cell); pairs + counts")
         return pts, t.verts, t.ring_off, desc
+    if name == "select256_500m":
+        n = n_override or 500_000_000
+        seed = g.SEED_BASE + 3
+        mix = g.make_mixture(seed)
+        v, o = g.query_polygons(256, seed, mix)
+        pts = g.mixture_points(n, seed, mix, start=rank * n)
+        desc = (f"batched selection: {n} mixture points x 256 query polygons (lognormal 8-5000 vertices, "
+                f"concave, overlapping); per-query ascending id lists")
+        return pts, v, o, desc
     if name == "stars_1m":
         n = n_override or 1_000_000
         seed = g.SEED_BASE + 1
@@ -225,6 +234,8 @@ def run_spx(args, world, rank, local):
     gh = eng.load_polygons(v, o)
     ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32), sub_log2=args.sub)
     info = eng.index_info(ih)
+    if args.workload.startswith("select"):
+        return run_select_bench(args, world, rank, eng, ph, ih, info, dpts, pts, v, o, desc, clocks, torch)
     cap = N if args.cap is None else args.cap
     pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
     counts = torch.zeros(max(P, 1), dtype=torch.int64, device="cuda")
@@ -335,13 +346,71 @@ def run_spx(args, world, rank, local):
     return 0
 
 
+def run_select_bench(args, world, rank, eng, ph, ih, info, dpts, pts, v, o, desc, clocks, torch):
+    """Batched selection: one step = all query polygons answered in one pass."""
+    N, Q = pts.shape[0], int(o.shape[0] - 1)
+    offs = torch.zeros(Q + 1, dtype=torch.int64, device="cuda")
+    probe = torch.empty(1, dtype=torch.int32, device="cuda")
+    try:
+        total = eng.select(ph, ih, probe, offs)
+    except spx_error() as e:  # the two-call pattern: the first call reports the size
+        total = int(str(e).split("needs ")[1].split(" ")[0])
+    ids = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+    assert eng.select(ph, ih, ids, offs) == total
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        eng.select(ph, ih, ids, offs, sync=False, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        eng.select(ph, ih, ids, offs, sync=False, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, torch)
+    clk = clocks.summary(t_host0, t_host1)
+    clocks.stop()
+    peak, peak_kind = peaks()
+    alg = 8 * N + 4 * total + 8 * (Q + 1) + int(info["device_bytes"])
+    achieved = alg / (ms * 1e-3) / 1e9
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(pts, v, o, args.cpu_budget)
+        print(json.dumps({
+            "metric": METRIC, "value": world * N / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "points_per_gpu": N, "queries": Q,
+                       "vertices": int(v.shape[0]), "selected_ids": int(total), "grid_log2": info["grid_log2"],
+                       "sub_log2": info["sub_log2"], "point_query_evals_per_s": world * N * Q / (ms * 1e-3),
+                       "launch": "one CUDA graph per step (resolve, count table, scan, emit)",
+                       "index_build_ms": round(info["build_ms"], 1)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel": "whole selection step", "algorithmic_bytes_per_launch": int(alg)},
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps * 7, "clocks": clk,
+        }), flush=True)
+    eng.free(ih)
+    eng.close()
+    return 0
+
+
+def spx_error():
+    from paper_2203_14362_gb300 import spx
+    return spx.SpxError
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["spx", "reference"], default="spx")
-    ap.add_argument("--workload", default="tess2000_100m", choices=["tess2000_100m", "stars_1m"])
+    ap.add_argument("--workload", default="tess2000_100m", choices=["tess2000_100m", "stars_1m", "select256_500m"])
     ap.add_argument("--points", type=int, default=None, help="points per GPU (default: the workload's)")
     ap.add_argument("--grid", type=int, default=0, help="grid_log2 (0 = automatic)")
     ap.add_argument("--sub", type=int, default=0, help="sub_log2 (0 = default, 3)")

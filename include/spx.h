@@ -161,7 +161,8 @@ spx_status spx_join(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *
  * query constraints answered in one pass over the points).  Output: for each
  * query q, the ascending ids of the points inside it, at
  * ids_dev[offsets_dev[q] .. offsets_dev[q+1]) (uint32 ids; offsets_dev holds
- * P + 1 uint64, offsets_dev[P] = total).  ids past cap are not written.
+ * P + 1 uint64, offsets_dev[P] = total).  ids past cap are not written;
+ * when the total exceeds cap, only offsets_dev[P] is meaningful.
  * n_ids (host, may be NULL): if given, the call synchronises, writes the total
  * and returns SPX_ECAPACITY if it exceeds cap.  At most 1024 query polygons
  * per index (SPX_EINVAL otherwise).

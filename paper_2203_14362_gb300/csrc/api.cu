@@ -534,7 +534,7 @@ spx_status spx_select(spx_ctx *ctx, spx_points points, spx_index index, uint32_t
                                          " query polygons; batched selection takes at most " +
                                          std::to_string(kSelectMaxQueries));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, select_scratch_bytes(pts->n, ix->view.P), s,
+    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, select_scratch_bytes(pts->n, ix->view.P, cap), s,
                            "select");
     if (st != SPX_OK)
         return st;

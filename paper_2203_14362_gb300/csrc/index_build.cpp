@@ -492,9 +492,10 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
             out.fine[size_t(blk * FF + uint64_t(f))] = w;
         }
     }
-    // sentinels: the kernels read entries two at a time, and load fine word 0
+    // sentinels: the kernels read entries up to four at a time, and load fine word 0
     // and edge 0 in place of a missing one
-    out.entries.insert(out.entries.end(), {0u, 0u, 0u, kEntLast});
+    for (int k = 0; k < 4; ++k)
+        out.entries.insert(out.entries.end(), {0u, 0u, 0u, kEntLast});
     if (out.fine.empty())
         out.fine.push_back(0u);
     out.edges.insert(out.edges.end(), {0, 0, 0, 0});

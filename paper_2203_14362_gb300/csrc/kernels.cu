@@ -47,8 +47,22 @@ constexpr int kQueue = kTile / 2;           // list points compacted per tile (m
 constexpr int kPlainThreads = 256;          // threads per CTA of the plain kernels
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kPending = 0xffffffffu;
-constexpr uint32_t kResNone = 0xffffffffu;  // pass-1 result: in no polygon
-constexpr uint32_t kResMulti = 0x80000000u; // pass-1 result flag: in several polygons (low bits: the first)
+// Pass-1 result of a point (4 bytes):
+//   kResNone                            in no polygon
+//   q (bit 31 clear)                    in exactly polygon q
+//   kResMulti | kResCount | c<<20 | q   in c polygons (2 <= c <= 1022), the first q < 2^20
+//   kResMulti | q                       in several polygons, the first q (count not stored)
+constexpr uint32_t kResNone = 0xffffffffu;
+constexpr uint32_t kResMulti = 0x80000000u;
+constexpr uint32_t kResCount = 0x40000000u;
+
+__host__ __device__ constexpr uint32_t res_encode(uint32_t cnt, uint32_t first)
+{
+    return cnt == 0 ? kResNone
+                    : cnt == 1 ? first
+                               : (cnt <= 1022u && first < (1u << 20)) ? (kResMulti | kResCount | (cnt << 20) | first)
+                                                                      : (kResMulti | first);
+}
 constexpr int kHistMax = 11776;             // polygons counted in shared memory (46 KB)
 constexpr size_t kCountSmem = 3 * kTileBytes + kQueue * sizeof(uint2);
 
@@ -249,6 +263,60 @@ __device__ __forceinline__ uint32_t entry_in(const IndexView &ix, const uint4 &e
     return par;
 }
 
+// Calls f(polygon) for every polygon of the entry list starting at e that
+// contains (px, py), ascending.  Entries are taken two at a time: both
+// entries in one round trip, then the first four edges of each in another
+// (the entry array ends with sentinels, so reading two is in bounds).
+template <bool FP32, class F>
+__device__ __forceinline__ void walk_entries(const IndexView &ix, const uint4 *e, int px, int py, uint32_t &tests,
+                                             uint32_t &esc, uint64_t pol, F f)
+{
+    constexpr int B = 2;
+    for (bool more = true; more; e += B) {
+        uint4 en[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            en[k] = ld_idx(e + k, pol);
+        // entries of this list among the B: up to and including the first LAST
+        uint32_t live = 0;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            if (more)
+                live |= 1u << k;
+            if (more && (en[k].w & kEntLast))
+                more = false;
+        }
+        int4 v[B][4];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const uint32_t nk = ((live >> k) & 1u) && (en[k].w & kEntBoundary) ? min(en[k].z, 4u) : 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                v[k][j] = ld_idx(ix.edge + ((uint32_t)j < nk ? en[k].y + j : 0u), pol);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((uint32_t)j >= nk)
+                    v[k][j] = make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (((live >> k) & 1u) && entry_in<FP32>(ix, en[k], v[k], px, py, tests, esc, pol))
+                f(en[k].x);
+    }
+}
+
+// Calls f(polygon) for every polygon containing the in-box point (px, py),
+// ascending (only called for points with more than one match: their word is a list).
+template <bool FP32, class F>
+__device__ __forceinline__ void point_emit(const IndexView &ix, int px, int py, uint64_t pol, F f)
+{
+    uint32_t t = 0, s = 0;
+    const uint32_t w = resolve(ix, (uint32_t)px, (uint32_t)py, pol);
+    if ((w >> 30) != kCellList)
+        return;
+    walk_entries<FP32>(ix, ix.ent + (w & kPayloadMask), px, py, t, s, pol, f);
+}
+
 // Walk an entry list: number of polygons containing (px, py), smallest id.
 // Written so that the lanes of a warp stay converged around every load: the
 // common case (at most two entries, at most four edges each) issues all its
@@ -289,7 +357,7 @@ __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, 
     uint32_t c = in0 + in1;
     first = in0 ? en0.x : en1.x;
     if (two && !(en1.w & kEntLast)) {
-        // three or more polygons share this fine cell
+        // three or more polygons share this fine cell (rare)
         for (const uint4 *q = e + 2;; ++q) {
             const uint4 en = ld_idx(q, pol);
             if (!(en.w & kEntBoundary) || row_parity<FP32>(ix.edge + en.y, en.z, px, py, tests, esc, pol)) {
@@ -338,25 +406,6 @@ __device__ __forceinline__ uint32_t point_count(const IndexView &ix, int px, int
         return 1;
     }
     return walk_list<FP32>(ix, w & kPayloadMask, px, py, first, tests, esc, pol);
-}
-
-// Calls f(polygon) for every polygon containing the in-box point (px, py),
-// ascending (only called for points with more than one match: their word is a list).
-template <bool FP32, class F>
-__device__ __forceinline__ void point_emit(const IndexView &ix, int px, int py, uint64_t pol, F f)
-{
-    uint32_t t = 0, s = 0;
-    const uint32_t w = resolve(ix, (uint32_t)px, (uint32_t)py, pol);
-    if ((w >> 30) != kCellList)
-        return;
-    const uint4 *e = ix.ent + (w & kPayloadMask);
-    for (;;) {
-        const uint4 en = ld_idx(e++, pol);
-        if (!(en.w & kEntBoundary) || row_parity<FP32>(ix.edge + en.y, en.z, px, py, t, s, pol))
-            f(en.x);
-        if (en.w & kEntLast)
-            break;
-    }
 }
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v)
@@ -588,7 +637,7 @@ __global__ void __launch_bounds__(kThreads) k_count(JoinLaunch a, uint32_t ntile
             if (use_hist)
                 hist_add_warp(s_hist, cnt[i] == 1, first[i]);
             if (RESOLVE && loc < npts)
-                __stcg(a.res + base + loc, cnt[i] == 0 ? kResNone : (cnt[i] == 1 ? first[i] : (kResMulti | first[i])));
+                __stcg(a.res + base + loc, res_encode(cnt[i], first[i]));
             tsum += cnt[i];
             if (!cnt[i])
                 continue;
@@ -657,10 +706,14 @@ __global__ void __launch_bounds__(kThreads) k_emit(JoinLaunch a, const unsigned 
         res[i] = loc < npts ? __ldcs(a.res + base + loc) : kResNone;
         cnt[i] = res[i] == kResNone ? 0u : 1u;
         if (res[i] != kResNone && (res[i] & kResMulti)) {
-            // count again (rare): the point lies in several polygons
-            const int2 p = a.pts[base + loc];
-            uint32_t f = 0, t = 0, e = 0;
-            cnt[i] = point_count<FP32>(a.ix, p.x, p.y, f, t, e, keep);
+            // the point lies in several polygons: its count, stored or counted again
+            if (res[i] & kResCount) {
+                cnt[i] = (res[i] >> 20) & 0x3ffu;
+            } else {
+                const int2 p = a.pts[base + loc];
+                uint32_t f = 0, t = 0, e = 0;
+                cnt[i] = point_count<FP32>(a.ix, p.x, p.y, f, t, e, keep);
+            }
             multi = true;
         }
     }
@@ -891,84 +944,54 @@ __global__ void __launch_bounds__(1024) k_scan_apply(unsigned long long *v, uint
 
 // ------------------------------------------------------ batched selection
 // Selection of points by many query polygons at once (§5.2 "Spatial
-// Selection", one pass over the points for all queries): after the resolve
-// pass, each super-tile of kSuperTile points counts its points per query into
-// a query-major table; an exclusive scan of that table in query-major order
-// makes entry (q, s) the output position of super-tile s's first point of
-// query q; the emit kernel then writes every query's point ids in ascending
-// order.
+// Selection", one pass over the points for all queries).  The join runs once
+// and yields (point, query) pairs in point order; the pairs are then
+// partitioned by query, keeping point order: each super-tile of kSuperTile
+// pairs counts its pairs per query into a query-major table; an exclusive scan
+// of the table in query-major order makes entry (q, s) the output position of
+// super-tile s's first pair of query q; the emit kernel writes the point ids.
 constexpr int kSuperTile = 32768;
-constexpr int kSelMaxQ = 1024;                      // queries per index for the shared-memory path
-constexpr int kSelWarpRange = kSuperTile / kWarps;  // points per warp of a super-tile
+constexpr int kSelMaxQ = 1024;                      // queries per index (shared-memory counters)
+constexpr int kSelWarpRange = kSuperTile / kWarps;  // pairs per warp of a super-tile
 
-// the queries of a point in several polygons after `after` (ascending walk),
-// or kResNone
-template <bool FP32>
-__device__ __forceinline__ uint32_t next_query(const IndexView &ix, int px, int py, uint32_t after, uint64_t keep)
-{
-    uint32_t best = kResNone;
-    point_emit<FP32>(ix, px, py, keep, [&](uint32_t q) {
-        if ((after == kResNone || q > after) && best == kResNone)
-            best = q;
-    });
-    return best;
-}
-
-template <bool FP32>
-__global__ void __launch_bounds__(kThreads) k_sel_count(JoinLaunch a, unsigned long long *table, uint32_t n_super)
+__global__ void __launch_bounds__(kThreads) k_part_count(const uint2 *__restrict__ pairs,
+                                                         const unsigned long long *total, uint64_t cap, uint32_t P,
+                                                         unsigned long long *table, uint32_t n_super)
 {
     extern __shared__ uint32_t s_cnt[]; // P counters
-    const IndexView &ix = a.ix;
-    const uint64_t keep = policy_evict_last();
-    for (uint32_t q = threadIdx.x; q < ix.P; q += kThreads)
+    for (uint32_t q = threadIdx.x; q < P; q += kThreads)
         s_cnt[q] = 0;
     __syncthreads();
+    const unsigned long long n = min(*total, (unsigned long long)cap); // pairs past cap were not written
     const uint64_t base = (uint64_t)blockIdx.x * kSuperTile;
     for (uint32_t j = threadIdx.x; j < (uint32_t)kSuperTile; j += kThreads) {
-        if (base + j >= a.n)
-            break;
-        const uint32_t r = __ldcg(a.res + base + j);
-        if (r == kResNone)
-            continue;
-        if (!(r & kResMulti)) {
-            atomicAdd(&s_cnt[r], 1u);
-        } else {
-            const int2 p = a.pts[base + j];
-            point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(&s_cnt[q], 1u); });
-        }
+        const bool has = base + j < n;
+        const uint32_t q = has ? __ldcg(&pairs[base + j].y) : 0u;
+        hist_add_warp(s_cnt, has, q);
     }
     __syncthreads();
-    for (uint32_t q = threadIdx.x; q < ix.P; q += kThreads)
+    for (uint32_t q = threadIdx.x; q < P; q += kThreads)
         table[(uint64_t)q * n_super + blockIdx.x] = s_cnt[q];
 }
 
-template <bool FP32>
-__global__ void __launch_bounds__(kThreads) k_sel_emit(JoinLaunch a, const unsigned long long *table, uint32_t n_super,
-                                                       uint32_t *ids, uint64_t cap)
+__global__ void __launch_bounds__(kThreads) k_part_emit(const uint2 *__restrict__ pairs,
+                                                        const unsigned long long *total, uint32_t P,
+                                                        const unsigned long long *table, uint32_t n_super,
+                                                        uint32_t *ids, uint64_t cap)
 {
     extern __shared__ unsigned long long s_run[]; // kWarps x P running positions
-    uint32_t *s_wc = reinterpret_cast<uint32_t *>(s_run + (size_t)kWarps * a.ix.P); // kWarps x P counts
-    const IndexView &ix = a.ix;
-    const uint32_t P = ix.P;
+    uint32_t *s_wc = reinterpret_cast<uint32_t *>(s_run + (size_t)kWarps * P); // kWarps x P counts
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t keep = policy_evict_last();
     for (uint32_t i = threadIdx.x; i < kWarps * P; i += kThreads)
         s_wc[i] = 0;
     __syncthreads();
+    const unsigned long long n = min(*total, (unsigned long long)cap); // pairs past cap were not written
     const uint64_t base = (uint64_t)blockIdx.x * kSuperTile + (uint64_t)warp * kSelWarpRange;
     // 1. every warp counts its range per query
     for (uint32_t j = lane; j < (uint32_t)kSelWarpRange; j += 32) {
-        if (base + j >= a.n)
-            break;
-        const uint32_t r = __ldcg(a.res + base + j);
-        if (r == kResNone)
-            continue;
-        if (!(r & kResMulti)) {
-            atomicAdd(&s_wc[warp * P + r], 1u);
-        } else {
-            const int2 p = a.pts[base + j];
-            point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(&s_wc[warp * P + q], 1u); });
-        }
+        const bool has = base + j < n;
+        const uint32_t q = has ? __ldcg(&pairs[base + j].y) : 0u;
+        hist_add_warp(s_wc + warp * P, has, q);
     }
     __syncthreads();
     // 2. start positions per (warp, query)
@@ -980,37 +1003,24 @@ __global__ void __launch_bounds__(kThreads) k_sel_emit(JoinLaunch a, const unsig
         }
     }
     __syncthreads();
-    // 3. every warp writes its range in point order; within 32 points, queries
-    //    are taken in ascending order and lanes in lane order
+    // 3. every warp writes its range in pair (= point) order: lanes with the
+    //    same query take consecutive positions in lane order
     for (uint32_t j0 = 0; j0 < (uint32_t)kSelWarpRange; j0 += 32) {
-        if (base + j0 >= a.n)
+        if (base + j0 >= n)
             break;
-        const uint64_t pid = base + j0 + lane;
-        const bool valid = pid < a.n;
-        const uint32_t r = valid ? __ldcg(a.res + pid) : kResNone;
-        const bool multi = r != kResNone && (r & kResMulti);
-        int2 p = make_int2(0, 0);
-        if (multi)
-            p = a.pts[pid];
-        uint32_t cur = multi ? (r & ~kResMulti) : r; // smallest query of the point, or kResNone
-        for (;;) {
-            const uint32_t qmin = __reduce_min_sync(kFull, cur);
-            if (qmin == kResNone)
-                break;
-            const bool mine = cur == qmin;
-            const uint32_t bl = __ballot_sync(kFull, mine);
-            const unsigned long long start = s_run[warp * P + qmin];
-            if (mine) {
-                const unsigned long long o = start + __popc(bl & lanemask_lt());
-                if (o < cap)
-                    ids[o] = (uint32_t)pid;
-                cur = multi ? next_query<FP32>(ix, p.x, p.y, qmin, keep) : kResNone;
-            }
-            __syncwarp();
-            if (lane == 0)
-                s_run[warp * P + qmin] = start + __popc(bl);
-            __syncwarp();
+        const bool has = base + j0 + lane < n;
+        const uint2 pr = has ? __ldcg(&pairs[base + j0 + lane]) : make_uint2(0u, 0xffffffffu);
+        const uint32_t peers = __match_any_sync(kFull, pr.y);
+        const unsigned long long start = has ? s_run[warp * P + pr.y] : 0ull;
+        __syncwarp();
+        if (has) {
+            const unsigned long long o = start + __popc(peers & lanemask_lt());
+            if (o < cap)
+                ids[o] = pr.x;
+            if ((int)lane == __ffs(peers) - 1)
+                s_run[warp * P + pr.y] = start + __popc(peers);
         }
+        __syncwarp();
     }
 }
 
@@ -1226,71 +1236,58 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
     return e;
 }
 
-size_t select_scratch_bytes(uint64_t n, uint32_t P)
+size_t select_scratch_bytes(uint64_t n, uint32_t P, uint64_t cap)
 {
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
-    const uint64_t n_super = (n + kSuperTile - 1) / kSuperTile;
-    const uint64_t tab = uint64_t(P) * n_super;
-    return size_t(((n * 4 + 15) & ~uint64_t(15)) + ntiles * 8 + 16 + tab * 8 + (scan_partials(tab) + 2) * 8 + 64);
+    const uint64_t n_super = (cap + kSuperTile - 1) / kSuperTile;
+    const uint64_t tab = uint64_t(P) * (n_super ? n_super : 1);
+    return join_scratch_bytes(n) + 16 + cap * 8 + tab * 8 + (scan_partials(tab) + 2) * 8 + 64;
 }
 
 cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
                           void *scratch, cudaStream_t s)
 {
-    const uint64_t ntiles64 = (a.n + kTile - 1) / kTile;
-    const uint64_t n_super64 = (a.n + kSuperTile - 1) / kSuperTile;
-    if (ntiles64 >= (1ull << 31) || a.ix.P > (uint32_t)kSelMaxQ)
+    const uint32_t P = a.ix.P;
+    if (P > (uint32_t)kSelMaxQ)
         return cudaErrorInvalidValue;
-    if (reinterpret_cast<uintptr_t>(a.pts) & 15)
-        return cudaErrorMisalignedAddress;
-    const uint32_t ntiles = uint32_t(ntiles64), n_super = uint32_t(n_super64), P = a.ix.P;
-    JoinLaunch b = a;
+    const uint64_t n_super64 = (cap + kSuperTile - 1) / kSuperTile;
+    if (n_super64 >= (1ull << 31))
+        return cudaErrorInvalidValue;
+    const uint32_t n_super = uint32_t(n_super64 ? n_super64 : 1);
     char *sc = static_cast<char *>(scratch);
-    b.res = reinterpret_cast<uint32_t *>(sc);
-    sc += (a.n * 4 + 15) & ~uint64_t(15);
-    b.tile_tot = reinterpret_cast<unsigned long long *>(sc);
-    sc += ntiles * 8;
-    b.tile_counter = reinterpret_cast<unsigned *>(sc);
+    void *join_scratch = sc;
+    sc += (join_scratch_bytes(a.n) + 15) & ~size_t(15);
+    unsigned long long *total = reinterpret_cast<unsigned long long *>(sc);
     sc += 16;
+    uint2 *pairs = reinterpret_cast<uint2 *>(sc);
+    sc += cap * 8;
     unsigned long long *table = reinterpret_cast<unsigned long long *>(sc);
     sc += uint64_t(P) * n_super * 8;
     unsigned long long *part = reinterpret_cast<unsigned long long *>(sc);
-    unsigned long long *total = part + scan_partials(uint64_t(P) * n_super) + 1;
+    unsigned long long *tab_total = part + scan_partials(uint64_t(P) * n_super) + 1;
+    // 1. the join: (point, query) pairs in point order, and their total
+    JoinLaunch b = a;
+    b.pairs = pairs;
+    b.cap = cap;
     b.counts = nullptr;
-    cudaError_t e = cudaMemsetAsync(b.tile_counter, 0, 16, s);
+    b.total = total;
+    cudaError_t e = launch_join(b, join_scratch, s);
     if (e != cudaSuccess)
         return e;
-    if (ntiles == 0 || P == 0) {
-        return cudaMemsetAsync(offsets, 0, sizeof(unsigned long long) * (P + 1), s);
-    }
-    // pass 1: resolve every point once for all queries
-    e = a.fp32 ? launch_count_kernel<true, true>(b, ntiles, 0, s) : launch_count_kernel<false, true>(b, ntiles, 0, s);
-    if (e != cudaSuccess)
-        return e;
-    // pass 2: per (query, super-tile) counts, scanned in query-major order
-    const size_t sm_count = sizeof(uint32_t) * P;
-    if (a.fp32)
-        k_sel_count<true><<<n_super, kThreads, sm_count, s>>>(b, table, n_super);
-    else
-        k_sel_count<false><<<n_super, kThreads, sm_count, s>>>(b, table, n_super);
-    e = launch_scan(table, uint64_t(P) * n_super, total, part, s);
+    if (P == 0)
+        return cudaMemsetAsync(offsets, 0, sizeof(unsigned long long), s);
+    // 2. per (query, super-tile) counts of the pairs, scanned in query-major order
+    k_part_count<<<n_super, kThreads, sizeof(uint32_t) * P, s>>>(pairs, total, cap, P, table, n_super);
+    e = launch_scan(table, uint64_t(P) * n_super, tab_total, part, s);
     if (e != cudaSuccess)
         return e;
     k_sel_offsets<<<(P + 256) / 256, 256, 0, s>>>(table, n_super, P, total, offsets);
-    // pass 3: ids in ascending order per query
-    const size_t sm_emit = (sizeof(unsigned long long) + sizeof(uint32_t)) * size_t(kWarps) * P;
-    static bool done[2][64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (a.fp32) {
-        if ((e = smem_opt_in(k_sel_emit<true>, (sizeof(unsigned long long) + 4) * kWarps * kSelMaxQ, done[1])) != cudaSuccess)
-            return e;
-        k_sel_emit<true><<<n_super, kThreads, sm_emit, s>>>(b, table, n_super, ids, cap);
-    } else {
-        if ((e = smem_opt_in(k_sel_emit<false>, (sizeof(unsigned long long) + 4) * kWarps * kSelMaxQ, done[0])) != cudaSuccess)
-            return e;
-        k_sel_emit<false><<<n_super, kThreads, sm_emit, s>>>(b, table, n_super, ids, cap);
-    }
+    // 3. point ids, ascending per query
+    static bool done[64] = {};
+    if ((e = smem_opt_in(k_part_emit, (sizeof(unsigned long long) + 4) * kWarps * kSelMaxQ, done)) != cudaSuccess)
+        return e;
+    if (cap)
+        k_part_emit<<<n_super, kThreads, (sizeof(unsigned long long) + 4) * size_t(kWarps) * P, s>>>(
+            pairs, total, P, table, n_super, ids, cap);
     return cudaGetLastError();
 }
 

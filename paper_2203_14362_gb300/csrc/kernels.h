@@ -56,8 +56,8 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
 
 // Batched selection: per-query ascending point-id lists in ids (cap entries),
 // offsets[q] / offsets[P] (device, P + 1 values; offsets[P] = total).  At most
-// kSelMaxQ (1024) queries per index.  scratch: select_scratch_bytes(n, P).
-size_t select_scratch_bytes(uint64_t n, uint32_t P);
+// 1024 queries per index.  scratch: select_scratch_bytes(n, P, cap).
+size_t select_scratch_bytes(uint64_t n, uint32_t P, uint64_t cap);
 cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
                           void *scratch, cudaStream_t s);
 constexpr uint32_t kSelectMaxQueries = 1024;
