@@ -39,7 +39,7 @@ L2_BYTES = 129 * 1024 * 1024
 # the ncu capture summarised in profiles/k_count_resolve_tess2000_20m.md; only
 # valid for that kernel version, the default index (g = 11, sub = 3) and the
 # default workload.
-RESOLVE_TRAFFIC_BYTES_PER_POINT = (297.893376e6 + 59.560704e6) / 20e6
+RESOLVE_TRAFFIC_BYTES_PER_POINT = (295.875328e6 + 59.254784e6) / 20e6
 
 
 # ------------------------------------------------------------------ workloads
@@ -232,7 +232,15 @@ def run_spx(args, world, rank, local):
     dpts = torch.from_numpy(pts).cuda()
     ph = eng.load_points(dpts)
     gh = eng.load_polygons(v, o)
-    ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32), sub_log2=args.sub)
+    tune = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        params, trials, ih = eng.autotune(ph, gh, fp32_filter=bool(args.fp32))
+        tune = {"picked": [params["grid_log2"], params["sub_log2"]], "seconds": round(time.perf_counter() - t0, 2),
+                "trials": [[t["grid_log2"], t["sub_log2"], round(t["ms"], 4)] for t in trials],
+                "sample": "every (N / m)-th point, m = max(N / 100, min(N, 2^22)); count-only launches"}
+    else:
+        ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32), sub_log2=args.sub)
     info = eng.index_info(ih)
     if args.workload.startswith("select"):
         return run_select_bench(args, world, rank, eng, ph, ih, info, dpts, pts, v, o, desc, clocks, torch)
@@ -302,7 +310,8 @@ def run_spx(args, world, rank, local):
     dom_bytes = 8 * N + 8 * P + idx_bytes if not args.plain else step_bytes
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = args.traffic
-    if traffic is None and not args.plain and args.workload == "tess2000_100m" and args.grid == 0 and args.sub == 0:
+    if (traffic is None and RESOLVE_TRAFFIC_BYTES_PER_POINT and not args.plain and args.workload == "tess2000_100m"
+            and (info["grid_log2"], info["sub_log2"]) == (11, 3)):
         traffic = RESOLVE_TRAFFIC_BYTES_PER_POINT * N
     out = None
     if rank == 0:
@@ -320,6 +329,7 @@ def run_spx(args, world, rank, local):
                 "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
                 "fp32_escalation_fraction": st["fp32_escalations"] / max(st["edge_tests"], 1),
                 "parallelism": f"points sharded by rank, index replicated, dp{world}",
+                "autotune": tune,
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
@@ -417,6 +427,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture (reported as is)")
     ap.add_argument("--fp32", type=int, default=1)
+    ap.add_argument("--autotune", action="store_true", help="choose grid_log2 / sub_log2 with spx_autotune")
     ap.add_argument("--plain", action="store_true", help="time the plain two-pass comparison kernels")
     ap.add_argument("--cap", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")

@@ -138,6 +138,56 @@ typedef struct {
 
 spx_status spx_index_info_get(spx_ctx *ctx, spx_index index, spx_index_info *out);
 
+/* Autotuner settings.  Zero fields take the defaults. */
+typedef struct {
+    uint64_t sample_points; /* points of the sample; 0 = 1% of the table, but at least min(n, 2^22) */
+    int grid_min;           /* smallest grid_log2 tried (default 6) */
+    int grid_max;           /* largest grid_log2 tried (default 13) */
+    int reps;               /* timed launches per candidate, the fastest kept (default 5) */
+    int fp32_filter;        /* filter setting of every candidate and of the result: 1 (default) or 0 */
+    uint64_t max_index_bytes; /* skip candidates whose index would exceed this (default 4 GiB) */
+    int reserved[4];        /* must be zero */
+} spx_tune_params;
+
+/* One timed candidate. */
+typedef struct {
+    int grid_log2;
+    int sub_log2;
+    double ms;            /* fastest count-only launch over the sample */
+    double build_ms;      /* host build + upload of the candidate's index */
+    uint64_t device_bytes;
+} spx_tune_trial;
+
+/*
+ * Choose the index resolution by timing (§6 "Database Setup and Tuning": the
+ * paper fixes the cell size by a rule of thumb; §7 "Indexing Strategies and
+ * Tuning" leaves automatic tuning open).  A deterministic sample (every
+ * (n / m)-th point of `points`, m = the sample size) is copied once; then for
+ * candidate (grid_log2, sub_log2) pairs the index of `polys` is built and the
+ * count-only aggregate of the sample is timed (CUDA events on `stream`).
+ * Search: grid_log2 rises from grid_min at the largest allowed sub_log2 and
+ * stops after two candidates in a row that are not faster than the best; then
+ * sub_log2 1..3 is tried at the best grid_log2.  The per-polygon counts of
+ * every candidate are compared with the first: the resolution never changes a
+ * result, and a mismatch fails the call with SPX_EKERNEL.
+ *
+ *   tp          settings (may be NULL: all defaults).
+ *   best        receives the chosen grid_log2, sub_log2 and fp32_filter (reserved
+ *               fields zero), ready for spx_build_index.
+ *   trials      host array of max_trials records (may be NULL when max_trials
+ *               is 0); *n_trials (may be NULL) receives the number of
+ *               candidates timed, which can exceed max_trials (extra records
+ *               are dropped).
+ *   best_index  if not NULL, receives the chosen candidate's index (owned by
+ *               the ctx; free it with spx_free); other candidates are freed.
+ * Synchronises `stream`.  Needs device memory for the sample (8 B per point),
+ * one index at a time and P counters.  Errors: SPX_EINVAL (bad handle, bad
+ * settings, empty point table), SPX_ENOMEM, SPX_ECUDA, SPX_EKERNEL.
+ */
+spx_status spx_autotune(spx_ctx *ctx, spx_points points, spx_polys polys, const spx_tune_params *tp,
+                        spx_index_params *best, spx_tune_trial *trials, uint32_t max_trials, uint32_t *n_trials,
+                        spx_index *best_index, void *stream);
+
 /*
  * Polygon-point join (§5.2 "Spatial Joins", Polygon x Point), one pass over the
  * points.  Output: every (point_id, polygon_id) with the point inside the

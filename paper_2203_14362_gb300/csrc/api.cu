@@ -251,6 +251,80 @@ void *static_join_scratch(int device, cudaError_t &err)
     return addr[device];
 }
 
+// Build the index of polygon set `polys` with the checked parameters prm.  An
+// index of more than max_bytes device bytes is not uploaded: *out is then 0.
+spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_params &prm, spx_index *out,
+                            size_t max_bytes = SIZE_MAX)
+{
+    PolysObj *pg = lookup(ctx->polys, polys);
+    if (!pg)
+        return fail(ctx, SPX_EINVAL, "build_index: bad polygon handle");
+    const auto t0 = std::chrono::steady_clock::now();
+    const int g = prm.grid_log2 ? prm.grid_log2 : default_grid_log2(pg->xy.data(), pg->off.data(), pg->P);
+    const int sb = prm.sub_log2 ? prm.sub_log2 : kMaxSubLog2;
+    if (g < 1 || g > kMaxGridLog2 || sb < 1 || sb > kMaxSubLog2 || g + sb > kMaxFineLog2)
+        return fail(ctx, SPX_EINVAL, "build_index: grid_log2 must be in [1, 13] (0 = automatic), sub_log2 in "
+                                     "[1, 3] (0 = default), grid_log2 + sub_log2 <= 16");
+    HostIndex hi;
+    std::string err;
+    const int threads = std::max(1u, std::thread::hardware_concurrency());
+    if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, sb, threads, hi, err))
+        return fail(ctx, SPX_EINVAL, "build_index: " + err);
+    const size_t b_cell = hi.cell.size() * 4, b_fine = hi.fine.size() * 4, b_ent = hi.entries.size() * 4,
+                 b_edge = hi.edges.size() * 4;
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t total = up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + 256;
+    if (total > max_bytes) {
+        *out = 0;
+        return SPX_OK;
+    }
+    auto ix = std::make_unique<IndexObj>();
+    if (cudaMalloc(&ix->mem, total) != cudaSuccess)
+        return fail(ctx, SPX_ENOMEM, "build_index: cudaMalloc of " + std::to_string(total) + " bytes failed");
+    char *m = static_cast<char *>(ix->mem);
+    char *p_cell = m, *p_fine = p_cell + up(b_cell), *p_ent = p_fine + up(b_fine), *p_edge = p_ent + up(b_ent);
+    cudaError_t e = cudaMemcpy(p_cell, hi.cell.data(), b_cell, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b_fine)
+        e = cudaMemcpy(p_fine, hi.fine.data(), b_fine, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b_ent)
+        e = cudaMemcpy(p_ent, hi.entries.data(), b_ent, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b_edge)
+        e = cudaMemcpy(p_edge, hi.edges.data(), b_edge, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(ix->mem);
+        return cuda_fail(ctx, e, "build_index upload");
+    }
+    ix->polys = polys;
+    ix->fp32 = prm.fp32_filter ? 1 : 0;
+    ix->view.cell = reinterpret_cast<const uint32_t *>(p_cell);
+    ix->view.fine = reinterpret_cast<const uint32_t *>(p_fine);
+    ix->view.ent = reinterpret_cast<const uint4 *>(p_ent);
+    ix->view.edge = reinterpret_cast<const int4 *>(p_edge);
+    ix->view.sc = kBoxLog2 - g;
+    ix->view.gc = g;
+    ix->view.sf = kBoxLog2 - g - sb;
+    ix->view.sb = sb;
+    ix->view.P = pg->P;
+    spx_index_info &inf = ix->info;
+    inf.grid_log2 = g;
+    inf.sub_log2 = sb;
+    inf.n_polys = pg->P;
+    inf.n_cells = hi.cell.size();
+    inf.n_blocks = hi.n_blocks;
+    inf.n_entries = hi.entries.size() / 4;
+    inf.n_inside = hi.n_inside;
+    inf.n_mixed = hi.n_mixed;
+    inf.n_boundary = hi.n_boundary;
+    inf.n_edge_refs = hi.edges.size() / 4;
+    inf.device_bytes = total;
+    inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    pg->n_index++;
+    const uint64_t h = make_handle(ctx, kTagIndex);
+    ctx->indexes[h] = std::move(ix);
+    *out = h;
+    return SPX_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -418,9 +492,6 @@ spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params
         return fail(ctx, SPX_EINVAL, "build_index: null argument");
     ctx->err.clear();
     cudaSetDevice(ctx->device);
-    PolysObj *pg = lookup(ctx->polys, polys);
-    if (!pg)
-        return fail(ctx, SPX_EINVAL, "build_index: bad polygon handle");
     spx_index_params prm{};
     prm.fp32_filter = 1;
     if (params) {
@@ -429,65 +500,184 @@ spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params
             if (r)
                 return fail(ctx, SPX_EINVAL, "build_index: reserved fields must be zero");
     }
-    const auto t0 = std::chrono::steady_clock::now();
-    const int g = prm.grid_log2 ? prm.grid_log2 : default_grid_log2(pg->xy.data(), pg->off.data(), pg->P);
-    const int sb = prm.sub_log2 ? prm.sub_log2 : kMaxSubLog2;
-    if (g < 1 || g > kMaxGridLog2 || sb < 1 || sb > kMaxSubLog2 || g + sb > kMaxFineLog2)
-        return fail(ctx, SPX_EINVAL, "build_index: grid_log2 must be in [1, 13] (0 = automatic), sub_log2 in "
-                                     "[1, 3] (0 = default), grid_log2 + sub_log2 <= 16");
-    HostIndex hi;
-    std::string err;
-    const int threads = std::max(1u, std::thread::hardware_concurrency());
-    if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, sb, threads, hi, err))
-        return fail(ctx, SPX_EINVAL, "build_index: " + err);
-    const size_t b_cell = hi.cell.size() * 4, b_fine = hi.fine.size() * 4, b_ent = hi.entries.size() * 4,
-                 b_edge = hi.edges.size() * 4;
-    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-    const size_t total = up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + 256;
-    auto ix = std::make_unique<IndexObj>();
-    if (cudaMalloc(&ix->mem, total) != cudaSuccess)
-        return fail(ctx, SPX_ENOMEM, "build_index: cudaMalloc of " + std::to_string(total) + " bytes failed");
-    char *m = static_cast<char *>(ix->mem);
-    char *p_cell = m, *p_fine = p_cell + up(b_cell), *p_ent = p_fine + up(b_fine), *p_edge = p_ent + up(b_ent);
-    cudaError_t e = cudaMemcpy(p_cell, hi.cell.data(), b_cell, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && b_fine)
-        e = cudaMemcpy(p_fine, hi.fine.data(), b_fine, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && b_ent)
-        e = cudaMemcpy(p_ent, hi.entries.data(), b_ent, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && b_edge)
-        e = cudaMemcpy(p_edge, hi.edges.data(), b_edge, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(ix->mem);
-        return cuda_fail(ctx, e, "build_index upload");
+    return build_index_impl(ctx, polys, prm, out);
+}
+
+spx_status spx_autotune(spx_ctx *ctx, spx_points points, spx_polys polys, const spx_tune_params *tp,
+                        spx_index_params *best, spx_tune_trial *trials, uint32_t max_trials, uint32_t *n_trials,
+                        spx_index *best_index, void *stream)
+{
+    if (!ctx || !best || (max_trials && !trials))
+        return fail(ctx, SPX_EINVAL, "autotune: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    PointsObj *pts = lookup(ctx->points, points);
+    PolysObj *pg = lookup(ctx->polys, polys);
+    if (!pts || !pg)
+        return fail(ctx, SPX_EINVAL, "autotune: bad points or polygon handle");
+    if (pts->n == 0)
+        return fail(ctx, SPX_EINVAL, "autotune: the point table is empty");
+    spx_tune_params q{};
+    if (tp) {
+        q = *tp;
+        for (int r : q.reserved)
+            if (r)
+                return fail(ctx, SPX_EINVAL, "autotune: reserved fields must be zero");
+    } else {
+        q.fp32_filter = 1;
     }
-    ix->polys = polys;
-    ix->fp32 = prm.fp32_filter ? 1 : 0;
-    ix->view.cell = reinterpret_cast<const uint32_t *>(p_cell);
-    ix->view.fine = reinterpret_cast<const uint32_t *>(p_fine);
-    ix->view.ent = reinterpret_cast<const uint4 *>(p_ent);
-    ix->view.edge = reinterpret_cast<const int4 *>(p_edge);
-    ix->view.sc = kBoxLog2 - g;
-    ix->view.gc = g;
-    ix->view.sf = kBoxLog2 - g - sb;
-    ix->view.sb = sb;
-    ix->view.P = pg->P;
-    spx_index_info &inf = ix->info;
-    inf.grid_log2 = g;
-    inf.sub_log2 = sb;
-    inf.n_polys = pg->P;
-    inf.n_cells = hi.cell.size();
-    inf.n_blocks = hi.n_blocks;
-    inf.n_entries = hi.entries.size() / 4;
-    inf.n_inside = hi.n_inside;
-    inf.n_mixed = hi.n_mixed;
-    inf.n_boundary = hi.n_boundary;
-    inf.n_edge_refs = hi.edges.size() / 4;
-    inf.device_bytes = total;
-    inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    pg->n_index++;
-    const uint64_t h = make_handle(ctx, kTagIndex);
-    ctx->indexes[h] = std::move(ix);
-    *out = h;
+    const int gmin = q.grid_min ? q.grid_min : 6, gmax = q.grid_max ? q.grid_max : kMaxGridLog2;
+    const int reps = q.reps ? q.reps : 5;
+    const uint64_t max_bytes = q.max_index_bytes ? q.max_index_bytes : (uint64_t(4) << 30);
+    if (gmin < 1 || gmax > kMaxGridLog2 || gmin > gmax || reps < 1 || reps > 1000 ||
+        (q.fp32_filter != 0 && q.fp32_filter != 1))
+        return fail(ctx, SPX_EINVAL, "autotune: need 1 <= grid_min <= grid_max <= 13, 1 <= reps <= 1000, "
+                                     "fp32_filter 0 or 1");
+    uint64_t m = q.sample_points ? q.sample_points : std::max(pts->n / 100, std::min<uint64_t>(pts->n, 1u << 22));
+    if (m > pts->n)
+        m = pts->n;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint32_t P = pg->P;
+
+    // device memory of the tuner: sample | reference counts | candidate counts | counter words
+    const size_t b_sample = (m * 8 + 255) & ~size_t(255), b_counts = ((size_t(P) + 1) * 8 + 255) & ~size_t(255);
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, b_sample + 2 * b_counts + 256) != cudaSuccess)
+        return fail(ctx, SPX_ENOMEM, "autotune: cudaMalloc of the sample failed");
+    std::unique_ptr<void, decltype(&cudaFree)> mem_guard(mem, &cudaFree);
+    int2 *sample = static_cast<int2 *>(mem);
+    auto *ref = reinterpret_cast<unsigned long long *>(static_cast<char *>(mem) + b_sample);
+    auto *cur = reinterpret_cast<unsigned long long *>(static_cast<char *>(mem) + b_sample + b_counts);
+    void *words = static_cast<char *>(mem) + b_sample + 2 * b_counts;
+    SPX_CUDA(launch_gather_stride(reinterpret_cast<const int2 *>(pts->dev), pts->n, sample, m, s), "autotune sample");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SPX_CUDA(cudaEventCreate(&e0), "event create");
+    SPX_CUDA(cudaEventCreate(&e1), "event create");
+    std::unique_ptr<CUevent_st, decltype(&cudaEventDestroy)> g0(e0, &cudaEventDestroy), g1(e1, &cudaEventDestroy);
+
+    std::vector<spx_tune_trial> done;
+    std::vector<unsigned long long> h_ref(P ? P : 1), h_cur(P ? P : 1);
+    spx_index best_h = 0;
+    double best_ms = 0;
+    spx_index_params best_p{};
+    // time one candidate: 1 = timed, 0 = skipped (index too large or not allowed)
+    auto run = [&](int g, int sb, int &outcome) -> spx_status {
+        outcome = 0;
+        if (g < 1 || g > kMaxGridLog2 || sb < 1 || sb > kMaxSubLog2 || g + sb > kMaxFineLog2)
+            return SPX_OK;
+        for (const auto &t : done)
+            if (t.grid_log2 == g && t.sub_log2 == sb)
+                return SPX_OK;
+        spx_index_params prm{};
+        prm.grid_log2 = g;
+        prm.sub_log2 = sb;
+        prm.fp32_filter = q.fp32_filter;
+        spx_index h = 0;
+        spx_status st = build_index_impl(ctx, polys, prm, &h, max_bytes);
+        if (st != SPX_OK)
+            return st;
+        if (!h)
+            return SPX_OK;
+        IndexObj *ix = lookup(ctx->indexes, h);
+        JoinLaunch a{};
+        a.ix = ix->view;
+        a.pts = sample;
+        a.n = m;
+        a.counts = done.empty() ? ref : cur;
+        a.err = &ctx->aux->err;
+        a.stats = ctx->aux->stats;
+        a.fp32 = ix->fp32;
+        float best_t = 0;
+        cudaError_t e = cudaSuccess;
+        for (int r = 0; r <= reps && e == cudaSuccess; ++r) { // launch 0 warms the index into L2
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess)
+                e = launch_aggregate(a, words, s);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess)
+                e = cudaEventSynchronize(e1);
+            float t = 0;
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&t, e0, e1);
+            if (r == 1 || (r > 1 && t < best_t))
+                best_t = t;
+        }
+        if (e != cudaSuccess) {
+            spx_free(ctx, h);
+            return cuda_fail(ctx, e, "autotune launch");
+        }
+        st = check_kernel_err(ctx, s);
+        if (st == SPX_OK && !done.empty()) {
+            cudaError_t e2 = cudaMemcpy(h_cur.data(), cur, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost);
+            if (e2 != cudaSuccess)
+                st = cuda_fail(ctx, e2, "autotune counts");
+            else if (h_cur != h_ref)
+                st = fail(ctx, SPX_EKERNEL, "autotune: counts at grid_log2 " + std::to_string(g) + ", sub_log2 " +
+                                                std::to_string(sb) + " differ from the first candidate's");
+        } else if (st == SPX_OK) {
+            cudaError_t e2 = cudaMemcpy(h_ref.data(), ref, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost);
+            if (e2 != cudaSuccess)
+                st = cuda_fail(ctx, e2, "autotune counts");
+        }
+        if (st != SPX_OK) {
+            const std::string msg = ctx->err;
+            spx_free(ctx, h);
+            ctx->err = msg;
+            return st;
+        }
+        done.push_back({g, sb, double(best_t), ix->info.build_ms, ix->info.device_bytes});
+        outcome = 1;
+        if (!best_h || best_t < best_ms) {
+            if (best_h)
+                spx_free(ctx, best_h);
+            best_h = h;
+            best_ms = best_t;
+            best_p = prm;
+        } else {
+            spx_free(ctx, h);
+        }
+        return SPX_OK;
+    };
+    auto cleanup_fail = [&](spx_status st) {
+        const std::string msg = ctx->err;
+        if (best_h)
+            spx_free(ctx, best_h);
+        ctx->err = msg;
+        return st;
+    };
+    // 1. grid_log2 upwards at the largest sub_log2 allowed
+    int misses = 0;
+    for (int g = gmin; g <= gmax && misses < 2; ++g) {
+        const double before = best_h ? best_ms : 0;
+        const bool had = best_h != 0;
+        int outcome = 0;
+        spx_status st = run(g, std::min(kMaxSubLog2, kMaxFineLog2 - g), outcome);
+        if (st != SPX_OK)
+            return cleanup_fail(st);
+        if (!outcome)
+            continue;
+        misses = (had && !(best_ms < before)) ? misses + 1 : 0;
+    }
+    if (!best_h)
+        return fail(ctx, SPX_EINVAL, "autotune: every candidate's index exceeds max_index_bytes");
+    // 2. sub_log2 at the best grid_log2
+    const int gb = best_p.grid_log2;
+    for (int sb = 1; sb <= kMaxSubLog2; ++sb) {
+        int outcome = 0;
+        spx_status st = run(gb, sb, outcome);
+        if (st != SPX_OK)
+            return cleanup_fail(st);
+    }
+    *best = best_p;
+    if (n_trials)
+        *n_trials = uint32_t(done.size());
+    for (uint32_t i = 0; i < max_trials && i < done.size(); ++i)
+        trials[i] = done[i];
+    if (best_index)
+        *best_index = best_h;
+    else
+        spx_free(ctx, best_h);
     return SPX_OK;
 }
 

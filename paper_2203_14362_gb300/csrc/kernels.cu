@@ -26,6 +26,7 @@
 #include "kernels.h"
 #include "spx_internal.h"
 
+#include <algorithm>
 #include <climits>
 #include <cuda_runtime.h>
 
@@ -69,16 +70,6 @@ constexpr size_t kCountSmem = 3 * kTileBytes + kQueue * sizeof(uint2);
 constexpr unsigned kSpinLimit = 1u << 22;             // ~ seconds with the back-off below
 
 // ------------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
     uint32_t m;
@@ -1135,6 +1126,26 @@ cudaError_t launch_scan(unsigned long long *v, uint64_t n, unsigned long long *t
 }
 
 } // namespace
+
+// Deterministic sample for the tuner: dst[i] = src[i * stride], i < m.
+__global__ void __launch_bounds__(256) k_gather_stride(const int2 *__restrict__ src, uint64_t stride,
+                                                     int2 *__restrict__ dst, uint64_t m)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < m; i += (uint64_t)gridDim.x * 256)
+        dst[i] = src[i * stride];
+}
+
+cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_t m, cudaStream_t s)
+{
+    if (m == 0)
+        return cudaSuccess;
+    if (m > n)
+        return cudaErrorInvalidValue;
+    const uint64_t stride = n / m; // (m - 1) * stride < n
+    const uint64_t blocks = std::min<uint64_t>((m + 255) / 256, uint64_t(device_sm_count()) * 8);
+    k_gather_stride<<<unsigned(blocks), 256, 0, s>>>(src, stride, dst, m);
+    return cudaGetLastError();
+}
 
 int device_sm_count()
 {

@@ -62,6 +62,9 @@ cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsi
                           void *scratch, cudaStream_t s);
 constexpr uint32_t kSelectMaxQueries = 1024;
 
+// dst[i] = src[i * (n / m)] for i < m (m <= n): the tuner's deterministic sample.
+cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_t m, cudaStream_t s);
+
 int device_sm_count();
 
 } // namespace spx

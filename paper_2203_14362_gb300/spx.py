@@ -23,7 +23,7 @@ EXPORTS = [
     "spx_create", "spx_destroy", "spx_last_error", "spx_load_points", "spx_load_polygons", "spx_build_index",
     "spx_index_info_get", "spx_join", "spx_join_plain", "spx_aggregate", "spx_join_host", "spx_host_index_build",
     "spx_host_index_copy", "spx_host_index_free", "spx_stats", "spx_set_phase_timing", "spx_free",
-    "spx_join_plain_static", "spx_select",
+    "spx_join_plain_static", "spx_select", "spx_autotune",
 ]
 
 
@@ -42,6 +42,16 @@ class IndexInfo(C.Structure):
                 ("n_cells", C.c_uint64), ("n_blocks", C.c_uint64), ("n_entries", C.c_uint64),
                 ("n_inside", C.c_uint64), ("n_mixed", C.c_uint64), ("n_boundary", C.c_uint64),
                 ("n_edge_refs", C.c_uint64), ("device_bytes", C.c_uint64), ("build_ms", C.c_double)]
+
+
+class TuneParams(C.Structure):
+    _fields_ = [("sample_points", C.c_uint64), ("grid_min", C.c_int), ("grid_max", C.c_int), ("reps", C.c_int),
+                ("fp32_filter", C.c_int), ("max_index_bytes", C.c_uint64), ("reserved", C.c_int * 4)]
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("grid_log2", C.c_int), ("sub_log2", C.c_int), ("ms", C.c_double), ("build_ms", C.c_double),
+                ("device_bytes", C.c_uint64)]
 
 
 class Stats(C.Structure):
@@ -84,6 +94,8 @@ def load(path: str = LIB_PATH):
         "spx_set_phase_timing": ([V, I], I),
         "spx_join_plain_static": ([V, U64, U64, V, U64, V, V, V], I),
         "spx_select": ([V, U64, U64, V, U64, V, P64, V], I),
+        "spx_autotune": ([V, U64, U64, C.POINTER(TuneParams), C.POINTER(IndexParams), C.POINTER(TuneTrial), U32,
+                          C.POINTER(U32), P64, V], I),
         "spx_free": ([V, U64], I),
     }
     for name, (args, res) in sig.items():
@@ -185,6 +197,22 @@ class Engine:
         h = C.c_uint64()
         self._check(self.lib.spx_build_index(self.ctx, polys, C.byref(p), C.byref(h)), "spx_build_index")
         return h.value
+
+    def autotune(self, points: int, polys: int, sample_points: int = 0, grid_min: int = 0, grid_max: int = 0,
+                 reps: int = 0, fp32_filter: bool = True, max_index_bytes: int = 0, keep_index: bool = True,
+                 stream=None):
+        """spx_autotune: returns (params dict, list of trial dicts, index handle or None)."""
+        tp = TuneParams(sample_points, grid_min, grid_max, reps, 1 if fp32_filter else 0, max_index_bytes)
+        best = IndexParams()
+        trials = (TuneTrial * 64)()
+        n = C.c_uint32()
+        h = C.c_uint64()
+        self._check(self.lib.spx_autotune(self.ctx, points, polys, C.byref(tp), C.byref(best), trials, 64,
+                                          C.byref(n), C.byref(h) if keep_index else None, _stream(stream)),
+                    "spx_autotune")
+        params = {"grid_log2": best.grid_log2, "sub_log2": best.sub_log2, "fp32_filter": best.fp32_filter}
+        rows = [{f: getattr(trials[i], f) for f, _ in TuneTrial._fields_} for i in range(min(n.value, 64))]
+        return params, rows, (h.value if keep_index else None)
 
     def index_info(self, index: int) -> dict:
         inf = IndexInfo()
