@@ -40,6 +40,7 @@ L2_BYTES = 129 * 1024 * 1024
 # valid for that kernel version, the default index (g = 11, sub = 3) and the
 # default workload.
 RESOLVE_TRAFFIC_BYTES_PER_POINT = (295.875328e6 + 59.254784e6) / 20e6
+SERVE_SEED = 0x2203143620 + 4  # request indexes of the serving measurement
 
 
 # ------------------------------------------------------------------ workloads
@@ -52,7 +53,7 @@ def make_workload(name: str, n_override: int | None, rank: int):
         nx, ny = g.tessellation_shape(2000)
         t = g.quad_tessellation(nx, ny, seed, kmin=12, kmax=499)
         mix = g.make_mixture(seed)
-        pts = g.mixture_points(n, seed, mix, start=rank * n)
+        pts = g.mixture_points_parallel(n, seed, mix, start=rank * n)
         desc = (f"{n} mixture points (64 Gaussians, sigma 0.5-5% of box, 10% uniform) x 2000-cell tessellation "
                 f"(jittered quads, noisy edges, 52-2000 vertices/cell); pairs + counts")
         return pts, t.verts, t.ring_off, desc
@@ -61,10 +62,18 @@ def make_workload(name: str, n_override: int | None, rank: int):
         seed = g.SEED_BASE + 3
         mix = g.make_mixture(seed)
         v, o = g.query_polygons(256, seed, mix)
-        pts = g.mixture_points(n, seed, mix, start=rank * n)
+        pts = g.mixture_points_parallel(n, seed, mix, start=rank * n)
         desc = (f"batched selection: {n} mixture points x 256 query polygons (lognormal 8-5000 vertices, "
                 f"concave, overlapping); per-query ascending id lists")
         return pts, v, o, desc
+    if name == "serve_1b":
+        n = n_override or 1_000_000_000
+        seed = g.SEED_BASE + 4
+        mix = g.make_mixture(seed)
+        pts = g.mixture_points_parallel(n, seed, mix, start=rank * n)
+        desc = (f"serving: {n} resident mixture points; Poisson stream of 70% selections (1-64 query polygons) "
+                f"and 30% joins vs 500/1000/2500/5000-cell tessellations")
+        return pts, None, None, desc
     if name == "stars_1m":
         n = n_override or 1_000_000
         seed = g.SEED_BASE + 1
@@ -185,6 +194,10 @@ def run_reference(args, world, rank):
     from paper_2203_14362_gb300 import datagen as g
 
     sample = args.ref_sample
+    if args.workload == "serve_1b":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no serving runtime; "
+                          "run the reference arm on a join workload"}), flush=True)
+        return 0
     pts, v, o, desc = make_workload(args.workload, sample, 0)
     pr = oracle.Prepared(v, o)
     threads = oracle.default_threads()
@@ -226,11 +239,14 @@ def run_spx(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     clocks = ClockSampler(local)
     pts, v, o, desc = make_workload(args.workload, args.points, rank)
-    N, P = pts.shape[0], int(o.shape[0] - 1)
+    N = pts.shape[0]
 
     eng = spx.Engine(local)
     dpts = torch.from_numpy(pts).cuda()
     ph = eng.load_points(dpts)
+    if args.workload == "serve_1b":
+        return run_serve_bench(args, world, rank, eng, ph, dpts, N, desc, clocks, torch)
+    P = int(o.shape[0] - 1)
     gh = eng.load_polygons(v, o)
     tune = None
     if args.autotune:
@@ -302,6 +318,11 @@ def run_spx(args, world, rank, local):
                "d2h_bytes_per_step": int(m * 8 + P * 8 + 8), "ms_per_step": sec * 1e3}
     clocks.stop()
 
+    serving = None
+    if not args.no_serve and not args.plain:
+        serving = run_serving(eng, ph, N, SERVE_SEED, timed=args.serve_timed, warm=args.serve_warmup,
+                              burst=args.serve_burst)
+
     idx_bytes = int(info["device_bytes"])
     step_bytes = 8 * N + 8 * n_pairs + 8 * P + idx_bytes  # algorithmic bytes of one join
     peak, peak_kind = peaks()
@@ -343,6 +364,7 @@ def run_spx(args, world, rank, local):
             "e2e": e2e,
             "gpu_launches": args.steps * 3,  # resolve, scan, emit (plain: count, scan, write)
             "clocks": clk,
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
     eng.free(ih)
@@ -353,6 +375,143 @@ def run_spx(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+# -------------------------------------------------------------------- serving
+def serve_indexes(eng, seed: int, pool: int = 32):
+    """Prebuilt request indexes: 4 tessellations (joins) and a pool of query
+    polygon sets of 1-64 polygons (selections)."""
+    from paper_2203_14362_gb300 import datagen as g
+    from paper_2203_14362_gb300 import spx
+    out = []  # (kind, polys handle, index handle, polygons)
+    for k, cells in enumerate((500, 1000, 2500, 5000)):
+        nx, ny = g.tessellation_shape(cells)
+        t = g.quad_tessellation(nx, ny, seed + 100 + k)
+        gh = eng.load_polygons(t.verts, t.ring_off)
+        out.append((spx.SPX_REQ_JOIN, gh, eng.build_index(gh), cells))
+    mix = g.make_mixture(seed)
+    rng = np.random.default_rng(seed)
+    for k in range(pool):
+        q = int(rng.integers(1, 65))
+        v, o = g.query_polygons(q, seed + 200 + k, mix)
+        gh = eng.load_polygons(v, o)
+        out.append((spx.SPX_REQ_SELECT, gh, eng.build_index(gh), q))
+    return out
+
+
+def serve_stream(idx, n: int, seed: int):
+    """n requests: 70 % selections (uniform over the pool), 30 % joins."""
+    from paper_2203_14362_gb300 import spx
+    rng = np.random.default_rng(seed)
+    joins = [i for i, x in enumerate(idx) if x[0] == spx.SPX_REQ_JOIN]
+    sels = [i for i, x in enumerate(idx) if x[0] == spx.SPX_REQ_SELECT]
+    out = []
+    for _ in range(n):
+        pos = int(rng.choice(sels)) if rng.random() < 0.7 else int(rng.choice(joins))
+        out.append((idx[pos][0], pos))
+    return out
+
+
+def serve_run(srv, reqs, rate, warm: int, seed: int = 7):
+    """Submit reqs at Poisson arrivals of `rate` per second (None: all at once);
+    a collector waits for each result and releases it.  Latency = completion on
+    the device - submission, both on the server's clock."""
+    ids = [None] * len(reqs)
+    res = [None] * len(reqs)
+    ready = threading.Semaphore(0)
+
+    def collect():
+        for i in range(len(reqs)):
+            ready.acquire()
+            res[i] = srv.wait(ids[i], -1.0)
+            srv.release(ids[i])
+
+    th = threading.Thread(target=collect)
+    th.start()
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+    t0, t = time.perf_counter(), 0.0
+    for i, (kind, pos) in enumerate(reqs):
+        t += gaps[i]
+        d = t0 + t - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        ids[i] = srv.submit(kind, pos, tag=i)
+        ready.release()
+    th.join()
+    timed = res[warm:]
+    bad = sum(1 for r in timed if r["status"] != 0)
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in timed])
+    span = (max(r["t_done_ms"] for r in timed) - min(r["t_submit_ms"] for r in timed)) / 1e3
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "throughput_rps": len(timed) / span,
+            "mean_batch": float(np.mean([r["batch_size"] for r in timed])), "failed": bad}
+
+
+def run_serving(eng, ph, N: int, seed: int, timed: int, warm: int, burst: int):
+    """Capacity (a burst) and latency at 0.5 / 0.8 / 0.95 x capacity, for the
+    batching server and for the plain comparison (one request per launch)."""
+    from paper_2203_14362_gb300 import spx
+    t_build = time.perf_counter()
+    idx = serve_indexes(eng, seed)
+    build_s = time.perf_counter() - t_build
+    handles = [x[2] for x in idx]
+    out = {"points": N, "requests_timed": timed, "requests_warmup": warm, "burst": burst,
+           "mix": "70% selection (1-64 query polygons, pool of 32 prebuilt indexes), "
+                  "30% join vs 4 tessellations (500/1000/2500/5000 cells)",
+           "index_build_s": round(build_s, 1), "server": {"max_batch": 8, "slots": 2},
+           "latency": "device completion (stream callback) - submission, server clock", "rates": []}
+    arms = {"batched": dict(max_batch=8, slots=2), "plain": dict(plain=True)}
+    cap = {}
+    batches = 0
+    for name, kw in arms.items():
+        srv = spx.Server(eng, ph, handles, **kw)
+        serve_run(srv, serve_stream(idx, max(4, burst // 4), seed + 1), None, 0)  # warm-up
+        r = serve_run(srv, serve_stream(idx, burst, seed + 2), None, 0)
+        cap[name] = r["throughput_rps"]
+        srv.close()
+    out["capacity_rps"] = cap
+    for x in (0.5, 0.8, 0.95):
+        rate = x * cap["batched"]
+        row = {"x_capacity": x, "rate_rps": rate}
+        for name, kw in arms.items():
+            srv = spx.Server(eng, ph, handles, **kw)
+            row[name] = serve_run(srv, serve_stream(idx, warm + timed, seed + 10 + int(100 * x)), rate, warm)
+            batches += srv.stats()["batches"]
+            srv.close()
+        out["rates"].append(row)
+    for _, gh, ih, _ in idx:
+        eng.free(ih)
+        eng.free(gh)
+    out["value_gpts"] = cap["batched"] * N / 1e9
+    out["batches"] = batches
+    return out
+
+
+def run_serve_bench(args, world, rank, eng, ph, dpts, N, desc, clocks, torch):
+    """Serving at scale: one JSON line whose value is the batching server's
+    capacity in point evaluations per second (requests/s x resident points)."""
+    t_host0 = time.time()
+    sv = run_serving(eng, ph, N, SERVE_SEED, timed=args.serve_timed, warm=args.serve_warmup, burst=args.serve_burst)
+    t_host1 = time.time()
+    clk = clocks.summary(t_host0, t_host1)
+    clocks.stop()
+    cap = sv["capacity_rps"]["batched"]
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * sv["value_gpts"], "unit": UNIT, "n_gpus": world,
+            "steps": args.serve_timed, "warmup": args.serve_warmup, "ms_per_step": 1e3 / cap,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "points_per_gpu": N,
+                       "step": "one request at the batching server's capacity",
+                       "l2": "point table (8 B x N) larger than L2; no flush"},
+            "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": None, "clocks": clk, "serving": sv,
+        }), flush=True)
+    eng.free(ph)
+    eng.close()
+    del dpts
     return 0
 
 
@@ -420,7 +579,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["spx", "reference"], default="spx")
-    ap.add_argument("--workload", default="tess2000_100m", choices=["tess2000_100m", "stars_1m", "select256_500m"])
+    ap.add_argument("--workload", default="tess2000_100m",
+                    choices=["tess2000_100m", "stars_1m", "select256_500m", "serve_1b"])
     ap.add_argument("--points", type=int, default=None, help="points per GPU (default: the workload's)")
     ap.add_argument("--grid", type=int, default=0, help="grid_log2 (0 = automatic)")
     ap.add_argument("--sub", type=int, default=0, help="sub_log2 (0 = default, 3)")
@@ -435,6 +595,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement of the join workload")
+    ap.add_argument("--serve-timed", type=int, default=120, help="timed requests per arrival rate and arm")
+    ap.add_argument("--serve-warmup", type=int, default=20)
+    ap.add_argument("--serve-burst", type=int, default=48, help="requests of the capacity burst")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "spx":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -332,6 +332,119 @@ spx_status spx_set_phase_timing(spx_ctx *ctx, int on);
  * before the polygon set it was built from. */
 spx_status spx_free(spx_ctx *ctx, uint64_t handle);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * A server answers a stream of selection and join requests against one
+ * resident point table, on its own thread, with several requests in flight
+ * (§7 "Improving I/O Performance" names pipelining as future work; the paper's
+ * engine runs one query at a time).  Each batch goes through:
+ *   1. a count pass over the points (§5.1 Map, first pass) that yields the exact
+ *      size of every request's output,
+ *   2. admission: the outputs are allocated once the server's output budget
+ *      has room (device memory of results the caller still holds counts),
+ *   3. the write pass, then (selections) the stable partition into per-query
+ *      id lists.
+ * Continuous batching: whenever a slot is free, the requests waiting at that
+ * moment (up to max_batch, in arrival order) form one batch, and every pass
+ * reads the point table once for all of them (§5.2's one-pass batched
+ * selection, applied across requests).  Requests that arrive later join the
+ * next free slot; slots overlap on the device (one CUDA stream each).
+ * Results are byte-identical to spx_join / spx_select on the same index,
+ * whatever the batch composition.
+ *
+ * Thread safety: every spx_server_* call may come from any thread.  The ctx,
+ * the point table and the listed indexes must stay alive and unchanged until
+ * spx_server_destroy returns; the ctx may be used meanwhile (on its own
+ * thread) for anything but freeing them.
+ */
+typedef struct spx_server spx_server;
+
+typedef struct {
+    int max_batch;          /* requests per pass over the points, 1..8 (0 = 8; 1 = no batching) */
+    int slots;              /* batches in flight, 1..4 (0 = 2) */
+    int plain;              /* 1: comparison mode: each request alone (max_batch = slots = 1) through the
+                               plain kernels (int64 only, one thread per point, not persistent) */
+    int reserved0;          /* must be zero */
+    uint64_t output_budget; /* device bytes of outputs and temporaries held at once; 0 = half of the free
+                               device memory at creation.  A batch larger than the budget runs alone. */
+    int reserved[4];        /* must be zero */
+} spx_server_params;
+
+enum { SPX_REQ_SELECT = 1, SPX_REQ_JOIN = 2 };
+
+typedef struct {
+    int kind;       /* SPX_REQ_SELECT: per-query ascending point-id lists (at most 1024 polygons);
+                       SPX_REQ_JOIN: (point, polygon) pairs sorted by point then polygon, and counts */
+    uint32_t index; /* position of the request's index in the list given to spx_server_create */
+    uint64_t tag;   /* caller's value, returned in the result */
+} spx_request;
+
+typedef struct {
+    int status;                  /* SPX_OK, or this request's error */
+    int kind;
+    uint64_t tag;
+    uint64_t total;              /* pairs (join) or ids (selection) */
+    uint32_t n_polys;            /* polygons of the request's index */
+    uint32_t batch_size;         /* requests answered by the same passes */
+    const uint32_t *pairs_dev;   /* join: 2 * total uint32 (point id, polygon) pairs; else NULL */
+    const uint64_t *counts_dev;  /* join: n_polys counts; else NULL */
+    const uint32_t *ids_dev;     /* selection: total point ids, query-major, ascending per query; else NULL */
+    const uint64_t *offsets_dev; /* selection: n_polys + 1 list starts; else NULL */
+    double t_submit_ms;          /* server clock (ms since creation): submission */
+    double t_start_ms;           /* the batch's first launch */
+    double t_done_ms;            /* results complete on the device (stream callback) */
+} spx_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches;
+    uint64_t batched_requests;   /* sum of batch sizes */
+    uint64_t bytes_in_use;       /* outputs held (not yet released) plus temporaries */
+    uint64_t peak_bytes_in_use;
+    uint64_t admission_waits;    /* batches that waited for budget */
+} spx_server_stats_t;
+
+/*
+ * Create a server on ctx's device over `points` and the n_indexes indexes
+ * (requests name them by position).  params may be NULL (defaults).  Starts
+ * the server thread.  Errors: SPX_EINVAL (bad handle or parameter), SPX_ENOMEM,
+ * SPX_ECUDA.
+ */
+spx_status spx_server_create(spx_ctx *ctx, spx_points points, const spx_index *indexes, uint32_t n_indexes,
+                             const spx_server_params *params, spx_server **out);
+
+/* Queue one request; *req_id receives its id.  SPX_EINVAL for a bad kind or
+ * index position, or a selection index of more than 1024 polygons. */
+spx_status spx_server_submit(spx_server *srv, const spx_request *req, uint64_t *req_id);
+
+/* Result of a request: SPX_EBUSY while it is pending, SPX_EINVAL for an
+ * unknown (or released) id; otherwise fills *out and returns SPX_OK (the
+ * request's own status is out->status). */
+spx_status spx_server_poll(spx_server *srv, uint64_t req_id, spx_result *out);
+
+/* As spx_server_poll, waiting up to timeout_ms (< 0: without limit). */
+spx_status spx_server_wait(spx_server *srv, uint64_t req_id, double timeout_ms, spx_result *out);
+
+/* Give back a finished request's device buffers (its result pointers become
+ * invalid).  SPX_EBUSY while it is pending. */
+spx_status spx_server_release(spx_server *srv, uint64_t req_id);
+
+/* Copy a finished request's result to host memory (synchronous): a join's
+ * pairs (8 * total bytes) to `a` and counts (8 * n_polys) to `b`; a selection's
+ * ids (4 * total) to `a` and offsets (8 * (n_polys + 1)) to `b`.  a_bytes /
+ * b_bytes are the buffers' sizes: SPX_ECAPACITY if one is too small, nothing
+ * copied.  Either buffer may be NULL (skipped).  Must not run concurrently with
+ * spx_server_release of the same request.  SPX_EBUSY while pending. */
+spx_status spx_server_read(spx_server *srv, uint64_t req_id, void *a, uint64_t a_bytes, void *b, uint64_t b_bytes);
+
+spx_status spx_server_stats(spx_server *srv, spx_server_stats_t *out);
+
+/* Text of the last error of a server call (never NULL). */
+const char *spx_server_last_error(spx_server *srv);
+
+/* Finish every queued and running request, stop the thread and free every
+ * buffer, released or not.  Safe on NULL. */
+void spx_server_destroy(spx_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

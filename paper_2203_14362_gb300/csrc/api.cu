@@ -3,9 +3,11 @@
 // kernels.  Every step of the join runs in kernels.cu; this file only moves
 // bytes and checks arguments.
 #include "kernels.h"
+#include "server_internal.h"
 #include "spx.h"
 #include "spx_internal.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -270,10 +272,19 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     const int threads = std::max(1u, std::thread::hardware_concurrency());
     if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, sb, threads, hi, err))
         return fail(ctx, SPX_EINVAL, "build_index: " + err);
+    // cover bitmap: one bit per block of coarse cells, set when any of them is not empty
+    const int cg = std::min(g, kCoverLog2);
+    std::vector<uint32_t> cover(std::max<size_t>((size_t(1) << (2 * cg)) / 32, 1), 0u);
+    for (uint32_t cy = 0; cy < (1u << g); ++cy)
+        for (uint32_t cx = 0; cx < (1u << g); ++cx)
+            if ((hi.cell[(size_t(cy) << g) | cx] >> 30) != kCellEmpty) {
+                const uint32_t b = ((cy >> (g - cg)) << cg) | (cx >> (g - cg));
+                cover[b >> 5] |= 1u << (b & 31);
+            }
     const size_t b_cell = hi.cell.size() * 4, b_fine = hi.fine.size() * 4, b_ent = hi.entries.size() * 4,
-                 b_edge = hi.edges.size() * 4;
+                 b_edge = hi.edges.size() * 4, b_cover = cover.size() * 4;
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-    const size_t total = up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + 256;
+    const size_t total = up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + up(b_cover) + 256;
     if (total > max_bytes) {
         *out = 0;
         return SPX_OK;
@@ -282,8 +293,11 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     if (cudaMalloc(&ix->mem, total) != cudaSuccess)
         return fail(ctx, SPX_ENOMEM, "build_index: cudaMalloc of " + std::to_string(total) + " bytes failed");
     char *m = static_cast<char *>(ix->mem);
-    char *p_cell = m, *p_fine = p_cell + up(b_cell), *p_ent = p_fine + up(b_fine), *p_edge = p_ent + up(b_ent);
+    char *p_cell = m, *p_fine = p_cell + up(b_cell), *p_ent = p_fine + up(b_fine), *p_edge = p_ent + up(b_ent),
+         *p_cover = p_edge + up(b_edge);
     cudaError_t e = cudaMemcpy(p_cell, hi.cell.data(), b_cell, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p_cover, cover.data(), b_cover, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && b_fine)
         e = cudaMemcpy(p_fine, hi.fine.data(), b_fine, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && b_ent)
@@ -305,6 +319,9 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     ix->view.sf = kBoxLog2 - g - sb;
     ix->view.sb = sb;
     ix->view.P = pg->P;
+    ix->view.cover = reinterpret_cast<const uint32_t *>(p_cover);
+    ix->view.scv = kBoxLog2 - cg;
+    ix->view.cg = cg;
     spx_index_info &inf = ix->info;
     inf.grid_log2 = g;
     inf.sub_log2 = sb;
@@ -326,6 +343,32 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
 }
 
 } // namespace
+
+namespace spx {
+
+spx_status served_data(spx_ctx *ctx, spx_points points, const spx_index *indexes, uint32_t n, ServedData &out)
+{
+    PointsObj *pts = lookup(ctx->points, points);
+    if (!pts)
+        return fail(ctx, SPX_EINVAL, "server: bad points handle");
+    out.device = ctx->device;
+    out.pts = reinterpret_cast<const int2 *>(pts->dev);
+    out.n = pts->n;
+    out.ix.clear();
+    out.fp32.clear();
+    for (uint32_t i = 0; i < n; ++i) {
+        IndexObj *ix = lookup(ctx->indexes, indexes[i]);
+        if (!ix)
+            return fail(ctx, SPX_EINVAL, "server: bad index handle at position " + std::to_string(i));
+        out.ix.push_back(ix->view);
+        out.fp32.push_back(ix->fp32);
+    }
+    return SPX_OK;
+}
+
+spx_status ctx_error(spx_ctx *ctx, spx_status st, const std::string &msg) { return fail(ctx, st, msg); }
+
+} // namespace spx
 
 extern "C" {
 

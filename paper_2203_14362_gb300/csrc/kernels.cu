@@ -933,6 +933,171 @@ __global__ void __launch_bounds__(1024) k_scan_apply(unsigned long long *v, uint
     }
 }
 
+// ------------------------------------------------------ multi-request batches
+// Serving answers several requests, each with its own index, in one pass over
+// the points: the point table is read once per pass for the whole batch
+// instead of once per request (the one-pass batched selection of §5.2,
+// applied across requests).  Two passes, as in the Map of §5.1: the count pass
+// counts every request's pairs per tile of kMTile points, and its per-polygon
+// counts; the per-request tile totals are scanned; the emit pass counts again,
+// keeps each (request, point) result in shared memory, and writes every
+// request's pairs in (point, polygon) order from its tile's offset.  Tiles go
+// to CTAs round-robin; the output never depends on the schedule.
+constexpr int kMTile = 1024;               // points per tile
+constexpr int kMPerWarp = kMTile / kWarps; // consecutive points per warp
+constexpr size_t kMultiSmemHead = kMTile * sizeof(int2) + kWarps * kMaxBatch * (8 + 4);
+
+__device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Does the cover bitmap let (px, py) reach a non-empty coarse cell?  False for
+// points outside the box.
+__device__ __forceinline__ bool covered(const IndexView &ix, int px, int py)
+{
+    if ((unsigned)px >= kBox || (unsigned)py >= kBox)
+        return false;
+    const uint32_t b = (((uint32_t)py >> ix.scv) << ix.cg) | ((uint32_t)px >> ix.scv);
+    return (__ldg(ix.cover + (b >> 5)) >> (b & 31)) & 1u;
+}
+
+template <bool FP32, bool EMIT>
+__global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ MultiLaunch m,
+                                                    unsigned long long *tile_tot, uint32_t ntiles, int use_hist)
+{
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    int2 *s_pts = reinterpret_cast<int2 *>(s_raw);                                       // kMTile points
+    unsigned long long *s_woff = reinterpret_cast<unsigned long long *>(s_pts + kMTile); // kWarps x kMaxBatch
+    uint32_t *s_wtot = reinterpret_cast<uint32_t *>(s_woff + kWarps * kMaxBatch);        // kWarps x kMaxBatch
+    uint32_t *s_tail = s_wtot + kWarps * kMaxBatch; // emit: K x kMTile results; count: qbase[K] counters
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t keep = policy_evict_last();
+    const int K = m.K;
+    uint32_t tests = 0, esc = 0, scanned = 0, emitted = 0;
+    if (!EMIT && use_hist)
+        for (uint32_t i = threadIdx.x; i < m.qbase[K]; i += kThreads)
+            s_tail[i] = 0;
+    __syncthreads();
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t base = (uint64_t)t * kMTile;
+        const uint32_t npts = (uint32_t)min((uint64_t)kMTile, m.n - base);
+        for (uint32_t i = threadIdx.x; i < (uint32_t)kMTile; i += kThreads)
+            s_pts[i] = i < npts ? __ldcs(m.pts + base + i) : make_int2(-1, -1);
+        if (!EMIT && threadIdx.x == 0)
+            scanned += npts * (uint32_t)K;
+        __syncthreads();
+        // every request's count (and, in the emit pass, result) per point
+        for (int r = 0; r < K; ++r) {
+            const IndexView &ix = m.ix[r];
+            uint32_t *h = s_tail + m.qbase[r];
+            unsigned long long *cnt = m.counts[r];
+            uint32_t wsum = 0;
+            for (int k = 0; k < kMPerWarp; k += 32) {
+                const uint32_t i = warp * kMPerWarp + k + lane;
+                const int2 p = s_pts[i];
+                uint32_t first = 0, c = 0;
+                if (covered(ix, p.x, p.y))
+                    c = point_count<FP32>(ix, p.x, p.y, first, tests, esc, keep);
+                wsum += c;
+                if (EMIT) {
+                    s_tail[r * kMTile + i] = res_encode(c, first);
+                } else if (cnt && use_hist) {
+                    hist_add_warp(h, c == 1, first);
+                    if (c > 1)
+                        point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(h + q, 1u); });
+                } else if (cnt) {
+                    if (c == 1)
+                        atomicAdd(cnt + first, 1ull);
+                    else if (c > 1)
+                        point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(cnt + q, 1ull); });
+                }
+            }
+            wsum = warp_sum32(wsum);
+            if (lane == 0)
+                s_wtot[warp * kMaxBatch + r] = wsum;
+        }
+        __syncthreads();
+        if (!EMIT) {
+            // per-request tile totals (the next tile's staging waits for warp 0
+            // at its barrier, so s_wtot is read before it is rewritten)
+            if ((int)threadIdx.x < K) {
+                unsigned long long sum = 0;
+                for (int w = 0; w < kWarps; ++w)
+                    sum += s_wtot[w * kMaxBatch + threadIdx.x];
+                tile_tot[(uint64_t)threadIdx.x * ntiles + t] = sum;
+            }
+            continue;
+        }
+        // emit pass: start of every (warp, request) run of pairs
+        if ((int)threadIdx.x < K) {
+            const int r = threadIdx.x;
+            unsigned long long run = tile_tot[(uint64_t)r * ntiles + t];
+            for (int w = 0; w < kWarps; ++w) {
+                s_woff[w * kMaxBatch + r] = run;
+                run += s_wtot[w * kMaxBatch + r];
+            }
+        }
+        __syncthreads();
+        for (int r = 0; r < K; ++r) {
+            const IndexView &ix = m.ix[r];
+            uint2 *out = m.pairs[r];
+            const uint64_t cap = m.cap[r];
+            unsigned long long run = s_woff[warp * kMaxBatch + r];
+            for (int k = 0; k < kMPerWarp; k += 32) {
+                const uint32_t i = warp * kMPerWarp + k + lane;
+                const uint32_t res = s_tail[r * kMTile + i];
+                const int2 p = s_pts[i];
+                uint32_t c = res == kResNone ? 0u : !(res & kResMulti) ? 1u
+                             : (res & kResCount) ? ((res >> 20) & 0x3ffu) : 0xffffffffu;
+                if (c == 0xffffffffu) { // count not stored: count again
+                    uint32_t f = 0, t2 = 0, e2 = 0;
+                    c = point_count<FP32>(ix, p.x, p.y, f, t2, e2, keep);
+                }
+                uint32_t inc = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o)
+                        inc += v;
+                }
+                const uint32_t wtot = __shfl_sync(kFull, inc, 31);
+                unsigned long long o = run + inc - c;
+                const uint32_t pid = (uint32_t)(base + i);
+                if (c == 1) {
+                    if (o < cap)
+                        out[o] = make_uint2(pid, res);
+                } else if (c > 1) {
+                    point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) {
+                        if (o < cap)
+                            out[o] = make_uint2(pid, q);
+                        ++o;
+                    });
+                }
+                emitted += c;
+                run += wtot;
+            }
+        }
+        __syncthreads(); // s_pts, s_woff and s_tail are rewritten by the next tile
+    }
+    if (!EMIT && use_hist) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < m.qbase[K]; i += kThreads) {
+            const uint32_t v = s_tail[i];
+            if (!v)
+                continue;
+            int r = 0;
+            while (r + 1 < K && i >= m.qbase[r + 1])
+                ++r;
+            atomicAdd(m.counts[r] + (i - m.qbase[r]), (unsigned long long)v);
+        }
+    }
+    add_stats(m.stats, scanned, EMIT ? 0u : tests, EMIT ? 0u : esc, emitted);
+}
+
 // ------------------------------------------------------ batched selection
 // Selection of points by many query polygons at once (§5.2 "Spatial
 // Selection", one pass over the points for all queries).  The join runs once
@@ -1249,21 +1414,51 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
 
 size_t select_scratch_bytes(uint64_t n, uint32_t P, uint64_t cap)
 {
-    const uint64_t n_super = (cap + kSuperTile - 1) / kSuperTile;
-    const uint64_t tab = uint64_t(P) * (n_super ? n_super : 1);
-    return join_scratch_bytes(n) + 16 + cap * 8 + tab * 8 + (scan_partials(tab) + 2) * 8 + 64;
+    return ((join_scratch_bytes(n) + 15) & ~size_t(15)) + 16 + cap * 8 + partition_scratch_bytes(cap, P);
 }
 
-cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
-                          void *scratch, cudaStream_t s)
+size_t partition_scratch_bytes(uint64_t cap, uint32_t P)
 {
-    const uint32_t P = a.ix.P;
+    const uint64_t n_super = (cap + kSuperTile - 1) / kSuperTile;
+    const uint64_t tab = uint64_t(P) * (n_super ? n_super : 1);
+    return size_t(tab * 8 + (scan_partials(tab) + 2) * 8 + 64);
+}
+
+cudaError_t launch_partition(const uint2 *pairs, const unsigned long long *total, uint64_t cap, uint32_t P,
+                             uint32_t *ids, unsigned long long *offsets, void *scratch, cudaStream_t s)
+{
     if (P > (uint32_t)kSelMaxQ)
         return cudaErrorInvalidValue;
     const uint64_t n_super64 = (cap + kSuperTile - 1) / kSuperTile;
     if (n_super64 >= (1ull << 31))
         return cudaErrorInvalidValue;
+    if (P == 0)
+        return cudaMemsetAsync(offsets, 0, sizeof(unsigned long long), s);
     const uint32_t n_super = uint32_t(n_super64 ? n_super64 : 1);
+    unsigned long long *table = static_cast<unsigned long long *>(scratch);
+    unsigned long long *part = table + uint64_t(P) * n_super;
+    unsigned long long *tab_total = part + scan_partials(uint64_t(P) * n_super) + 1;
+    // per (query, super-tile) counts of the pairs, scanned in query-major order
+    k_part_count<<<n_super, kThreads, sizeof(uint32_t) * P, s>>>(pairs, total, cap, P, table, n_super);
+    cudaError_t e = launch_scan(table, uint64_t(P) * n_super, tab_total, part, s);
+    if (e != cudaSuccess)
+        return e;
+    k_sel_offsets<<<(P + 256) / 256, 256, 0, s>>>(table, n_super, P, total, offsets);
+    // point ids, ascending per query
+    static bool done[64] = {};
+    if ((e = smem_opt_in(k_part_emit, (sizeof(unsigned long long) + 4) * kWarps * kSelMaxQ, done)) != cudaSuccess)
+        return e;
+    if (cap)
+        k_part_emit<<<n_super, kThreads, (sizeof(unsigned long long) + 4) * size_t(kWarps) * P, s>>>(
+            pairs, total, P, table, n_super, ids, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
+                          void *scratch, cudaStream_t s)
+{
+    if (a.ix.P > (uint32_t)kSelMaxQ)
+        return cudaErrorInvalidValue;
     char *sc = static_cast<char *>(scratch);
     void *join_scratch = sc;
     sc += (join_scratch_bytes(a.n) + 15) & ~size_t(15);
@@ -1271,10 +1466,6 @@ cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsi
     sc += 16;
     uint2 *pairs = reinterpret_cast<uint2 *>(sc);
     sc += cap * 8;
-    unsigned long long *table = reinterpret_cast<unsigned long long *>(sc);
-    sc += uint64_t(P) * n_super * 8;
-    unsigned long long *part = reinterpret_cast<unsigned long long *>(sc);
-    unsigned long long *tab_total = part + scan_partials(uint64_t(P) * n_super) + 1;
     // 1. the join: (point, query) pairs in point order, and their total
     JoinLaunch b = a;
     b.pairs = pairs;
@@ -1284,22 +1475,8 @@ cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsi
     cudaError_t e = launch_join(b, join_scratch, s);
     if (e != cudaSuccess)
         return e;
-    if (P == 0)
-        return cudaMemsetAsync(offsets, 0, sizeof(unsigned long long), s);
-    // 2. per (query, super-tile) counts of the pairs, scanned in query-major order
-    k_part_count<<<n_super, kThreads, sizeof(uint32_t) * P, s>>>(pairs, total, cap, P, table, n_super);
-    e = launch_scan(table, uint64_t(P) * n_super, tab_total, part, s);
-    if (e != cudaSuccess)
-        return e;
-    k_sel_offsets<<<(P + 256) / 256, 256, 0, s>>>(table, n_super, P, total, offsets);
-    // 3. point ids, ascending per query
-    static bool done[64] = {};
-    if ((e = smem_opt_in(k_part_emit, (sizeof(unsigned long long) + 4) * kWarps * kSelMaxQ, done)) != cudaSuccess)
-        return e;
-    if (cap)
-        k_part_emit<<<n_super, kThreads, (sizeof(unsigned long long) + 4) * size_t(kWarps) * P, s>>>(
-            pairs, total, P, table, n_super, ids, cap);
-    return cudaGetLastError();
+    // 2. stable partition by query
+    return launch_partition(pairs, total, cap, a.ix.P, ids, offsets, sc, s);
 }
 
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s)
@@ -1322,6 +1499,126 @@ cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s
     k_plain_count<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
     k_scan<<<1, 1024, 0, s>>>(block, nb, a.total);
     k_plain_write<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ multi-request launchers
+namespace {
+uint64_t multi_ntiles(uint64_t n) { return (n + kMTile - 1) / kMTile; }
+uint64_t multi_part_words(uint64_t ntiles) { return scan_partials(ntiles) + 2; }
+} // namespace
+
+size_t multi_scratch_bytes(uint64_t n, int K)
+{
+    const uint64_t nt = multi_ntiles(n);
+    return size_t(K) * size_t(nt + multi_part_words(nt)) * 8 + 256;
+}
+
+static cudaError_t multi_check(const MultiLaunch &m)
+{
+    if (m.K < 1 || m.K > kMaxBatch)
+        return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(m.pts) & 7)
+        return cudaErrorMisalignedAddress;
+    if (multi_ntiles(m.n) >= (1ull << 31))
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+cudaError_t launch_multi_count(const MultiLaunch &m, void *scratch, cudaStream_t s)
+{
+    cudaError_t e = multi_check(m);
+    if (e != cudaSuccess)
+        return e;
+    for (int r = 0; r < m.K; ++r)
+        if (m.counts[r] && m.ix[r].P)
+            if ((e = cudaMemsetAsync(m.counts[r], 0, sizeof(unsigned long long) * m.ix[r].P, s)) != cudaSuccess)
+                return e;
+    const uint64_t nt = multi_ntiles(m.n);
+    if (nt == 0)
+        return cudaMemsetAsync(m.totals, 0, sizeof(unsigned long long) * m.K, s);
+    unsigned long long *tile_tot = static_cast<unsigned long long *>(scratch);
+    unsigned long long *part = tile_tot + uint64_t(m.K) * nt;
+    const int use_hist = m.qbase[m.K] <= kMultiHistMax ? 1 : 0;
+    const size_t smem = kMultiSmemHead + (use_hist ? sizeof(uint32_t) * m.qbase[m.K] : 0);
+    static bool done[2][64] = {};
+    if (m.fp32) {
+        if ((e = smem_opt_in(k_multi<true, false>, kMultiSmemHead + 4 * kMultiHistMax, done[0])) != cudaSuccess)
+            return e;
+        k_multi<true, false><<<persistent_grid(k_multi<true, false>, kThreads, smem, uint32_t(nt)), kThreads, smem,
+                               s>>>(m, tile_tot, uint32_t(nt), use_hist);
+    } else {
+        if ((e = smem_opt_in(k_multi<false, false>, kMultiSmemHead + 4 * kMultiHistMax, done[1])) != cudaSuccess)
+            return e;
+        k_multi<false, false><<<persistent_grid(k_multi<false, false>, kThreads, smem, uint32_t(nt)), kThreads,
+                                smem, s>>>(m, tile_tot, uint32_t(nt), use_hist);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    for (int r = 0; r < m.K; ++r)
+        if ((e = launch_scan(tile_tot + uint64_t(r) * nt, nt, m.totals + r, part + uint64_t(r) * multi_part_words(nt),
+                             s)) != cudaSuccess)
+            return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_multi_emit(const MultiLaunch &m, void *scratch, cudaStream_t s)
+{
+    cudaError_t e = multi_check(m);
+    if (e != cudaSuccess)
+        return e;
+    const uint64_t nt = multi_ntiles(m.n);
+    if (nt == 0)
+        return cudaSuccess;
+    unsigned long long *tile_tot = static_cast<unsigned long long *>(scratch);
+    const size_t smem = kMultiSmemHead + sizeof(uint32_t) * kMTile * m.K;
+    static bool done[2][64] = {};
+    const size_t smem_max = kMultiSmemHead + sizeof(uint32_t) * kMTile * kMaxBatch;
+    if (m.fp32) {
+        if ((e = smem_opt_in(k_multi<true, true>, smem_max, done[0])) != cudaSuccess)
+            return e;
+        k_multi<true, true><<<persistent_grid(k_multi<true, true>, kThreads, smem, uint32_t(nt)), kThreads, smem,
+                              s>>>(m, tile_tot, uint32_t(nt), 0);
+    } else {
+        if ((e = smem_opt_in(k_multi<false, true>, smem_max, done[1])) != cudaSuccess)
+            return e;
+        k_multi<false, true><<<persistent_grid(k_multi<false, true>, kThreads, smem, uint32_t(nt)), kThreads, smem,
+                               s>>>(m, tile_tot, uint32_t(nt), 0);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ plain path in two halves (serving comparison)
+size_t plain_split_scratch_bytes(uint64_t n)
+{
+    const uint64_t nb = (n + kPlainThreads - 1) / kPlainThreads;
+    return size_t(nb + scan_partials(nb) + 2) * 8 + 64;
+}
+
+cudaError_t launch_plain_count(const JoinLaunch &a, void *scratch, cudaStream_t s)
+{
+    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
+    if (nb >= (1ull << 31))
+        return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (a.counts && a.ix.P)
+        if ((e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.ix.P, s)) != cudaSuccess)
+            return e;
+    if (nb == 0)
+        return cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s);
+    unsigned long long *block = static_cast<unsigned long long *>(scratch);
+    k_plain_count<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    return launch_scan(block, nb, a.total, block + nb, s);
+}
+
+cudaError_t launch_plain_write(const JoinLaunch &a, void *scratch, cudaStream_t s)
+{
+    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
+    if (nb == 0)
+        return cudaSuccess;
+    k_plain_write<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, static_cast<const unsigned long long *>(scratch));
     return cudaGetLastError();
 }
 

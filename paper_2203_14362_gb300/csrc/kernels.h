@@ -16,7 +16,11 @@ struct IndexView {
     int sf;               // fine shift: 30 - g - sub
     int sb;               // sub
     uint32_t P;           // number of polygons
+    const uint32_t *cover; // 4^cg bits: cover cell holds a non-empty coarse cell
+    int scv;              // cover shift: 30 - cg
+    int cg;               // cover grid log2: min(g, kCoverLog2)
 };
+constexpr int kCoverLog2 = 8;
 
 // Device status word bits (ORed into the ctx's persistent error word).
 constexpr unsigned kErrTimeout = 1u;   // a bounded wait gave up
@@ -61,6 +65,49 @@ size_t select_scratch_bytes(uint64_t n, uint32_t P, uint64_t cap);
 cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
                           void *scratch, cudaStream_t s);
 constexpr uint32_t kSelectMaxQueries = 1024;
+
+// Stable partition of (point, query) pairs (point order) by query: ids[] gets
+// the point ids of query 0, then of query 1, ..., offsets[] (P + 1 values) the
+// list starts.  Reads min(*total, cap) pairs.  scratch: partition_scratch_bytes.
+size_t partition_scratch_bytes(uint64_t cap, uint32_t P);
+cudaError_t launch_partition(const uint2 *pairs, const unsigned long long *total, uint64_t cap, uint32_t P,
+                             uint32_t *ids, unsigned long long *offsets, void *scratch, cudaStream_t s);
+
+// Several requests, each with its own index, answered in one pass over the
+// points (serving).  At most kMaxBatch requests; their polygons together are
+// counted in shared memory when qbase[K] <= kMultiHistMax, else with global
+// atomics.
+constexpr int kMaxBatch = 8;
+constexpr uint32_t kMultiHistMax = 11776;
+
+struct MultiLaunch {
+    IndexView ix[kMaxBatch];
+    uint32_t qbase[kMaxBatch + 1];           // prefix sums of the requests' polygon counts
+    unsigned long long *counts[kMaxBatch];   // per request: P counters (or null); zeroed by the count launcher
+    uint2 *pairs[kMaxBatch];                 // per request: (point, polygon) pairs, point order (emit pass)
+    uint64_t cap[kMaxBatch];                 // capacity of pairs[r]
+    unsigned long long *totals;              // K device totals, written by the count launcher
+    const int2 *pts;
+    uint64_t n;
+    int K;
+    int fp32;
+    unsigned *err;
+    unsigned long long *stats;
+};
+
+// scratch of one batch (per-request tile totals / offsets and scan partials),
+// shared by the count and emit launches of that batch.
+size_t multi_scratch_bytes(uint64_t n, int K);
+// Pass 1 + scans: per-polygon counts and the K totals (m.totals).
+cudaError_t launch_multi_count(const MultiLaunch &m, void *scratch, cudaStream_t s);
+// Pass 2: every request's pairs in (point, polygon) order.
+cudaError_t launch_multi_emit(const MultiLaunch &m, void *scratch, cudaStream_t s);
+
+// The plain join (int64 only, one thread per point, not persistent) in two
+// halves: count + device-wide scan (a.total), then write.  Same scratch.
+size_t plain_split_scratch_bytes(uint64_t n);
+cudaError_t launch_plain_count(const JoinLaunch &a, void *scratch, cudaStream_t s);
+cudaError_t launch_plain_write(const JoinLaunch &a, void *scratch, cudaStream_t s);
 
 // dst[i] = src[i * (n / m)] for i < m (m <= n): the tuner's deterministic sample.
 cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_t m, cudaStream_t s);

@@ -164,6 +164,45 @@ def mixture_points(n: int, seed: int, mix: Mixture | None = None, start: int = 0
 
 
 # ---------------------------------------------------------------------- polygons
+def _mixture_chunk(args):
+    # worker of mixture_points_parallel: fill rows [lo, hi) of the shared table
+    from multiprocessing import shared_memory
+    name, n, seed, mix, start, lo, hi = args
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        out = np.ndarray((n, 2), dtype=np.int32, buffer=shm.buf)
+        out[lo:hi] = mixture_points(hi - lo, seed, mix, start + lo)
+        del out
+    finally:
+        shm.close()
+    return hi - lo
+
+
+def mixture_points_parallel(n: int, seed: int, mix: Mixture | None = None, start: int = 0,
+                            workers: int | None = None) -> np.ndarray:
+    """mixture_points(n, seed, mix, start), computed by a pool of spawned
+    processes over chunks of the index range.  Every point depends only on its
+    global index, so the result is the same array, byte for byte."""
+    import multiprocessing as mp
+    import os
+    from multiprocessing import shared_memory
+    mix = mix or make_mixture(seed)
+    workers = workers or min(32, os.cpu_count() or 1)
+    step = 1 << 23
+    if workers <= 1 or n <= step:
+        return mixture_points(n, seed, mix, start)
+    shm = shared_memory.SharedMemory(create=True, size=max(n * 8, 8))
+    try:
+        jobs = [(shm.name, n, seed, mix, start, lo, min(n, lo + step)) for lo in range(0, n, step)]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            done = sum(pool.imap_unordered(_mixture_chunk, jobs))
+        assert done == n
+        return np.ndarray((n, 2), dtype=np.int32, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
+
+
 def _rings(parts: list[np.ndarray]) -> tuple[np.ndarray, np.ndarray]:
     off = np.zeros(len(parts) + 1, dtype=np.uint64)
     off[1:] = np.cumsum([len(p) for p in parts])

@@ -24,7 +24,11 @@ EXPORTS = [
     "spx_index_info_get", "spx_join", "spx_join_plain", "spx_aggregate", "spx_join_host", "spx_host_index_build",
     "spx_host_index_copy", "spx_host_index_free", "spx_stats", "spx_set_phase_timing", "spx_free",
     "spx_join_plain_static", "spx_select", "spx_autotune",
+    "spx_server_create", "spx_server_submit", "spx_server_poll", "spx_server_wait", "spx_server_release",
+    "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
 ]
+
+SPX_REQ_SELECT, SPX_REQ_JOIN = 1, 2
 
 
 class SpxError(RuntimeError):
@@ -52,6 +56,28 @@ class TuneParams(C.Structure):
 class TuneTrial(C.Structure):
     _fields_ = [("grid_log2", C.c_int), ("sub_log2", C.c_int), ("ms", C.c_double), ("build_ms", C.c_double),
                 ("device_bytes", C.c_uint64)]
+
+
+class ServerParams(C.Structure):
+    _fields_ = [("max_batch", C.c_int), ("slots", C.c_int), ("plain", C.c_int), ("reserved0", C.c_int),
+                ("output_budget", C.c_uint64), ("reserved", C.c_int * 4)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("index", C.c_uint32), ("tag", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("kind", C.c_int), ("tag", C.c_uint64), ("total", C.c_uint64),
+                ("n_polys", C.c_uint32), ("batch_size", C.c_uint32), ("pairs_dev", C.c_void_p),
+                ("counts_dev", C.c_void_p), ("ids_dev", C.c_void_p), ("offsets_dev", C.c_void_p),
+                ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("batches", C.c_uint64), ("batched_requests", C.c_uint64), ("bytes_in_use", C.c_uint64),
+                ("peak_bytes_in_use", C.c_uint64), ("admission_waits", C.c_uint64)]
 
 
 class Stats(C.Structure):
@@ -96,6 +122,15 @@ def load(path: str = LIB_PATH):
         "spx_select": ([V, U64, U64, V, U64, V, P64, V], I),
         "spx_autotune": ([V, U64, U64, C.POINTER(TuneParams), C.POINTER(IndexParams), C.POINTER(TuneTrial), U32,
                           C.POINTER(U32), P64, V], I),
+        "spx_server_create": ([V, U64, V, U32, C.POINTER(ServerParams), C.POINTER(V)], I),
+        "spx_server_submit": ([V, C.POINTER(Request), P64], I),
+        "spx_server_poll": ([V, U64, C.POINTER(Result)], I),
+        "spx_server_wait": ([V, U64, C.c_double, C.POINTER(Result)], I),
+        "spx_server_release": ([V, U64], I),
+        "spx_server_read": ([V, U64, V, U64, V, U64], I),
+        "spx_server_stats": ([V, C.POINTER(ServerStats)], I),
+        "spx_server_last_error": ([V], C.c_char_p),
+        "spx_server_destroy": ([V], None),
         "spx_free": ([V, U64], I),
     }
     for name, (args, res) in sig.items():
@@ -280,6 +315,75 @@ class Engine:
         s = Stats()
         self._check(self.lib.spx_stats(self.ctx, C.byref(s), 1 if reset else 0), "spx_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+class Server:
+    """spx_server_*: a serving thread over one resident point table and a list
+    of indexes (requests name an index by its position in that list)."""
+
+    def __init__(self, eng: Engine, points: int, indexes, max_batch: int = 0, slots: int = 0, plain: bool = False,
+                 output_budget: int = 0):
+        self.lib = eng.lib
+        arr = (C.c_uint64 * max(len(indexes), 1))(*indexes)
+        prm = ServerParams(max_batch, slots, 1 if plain else 0, 0, output_budget)
+        h = C.c_void_p()
+        st = self.lib.spx_server_create(eng.ctx, points, arr, len(indexes), C.byref(prm), C.byref(h))
+        if st != SPX_OK:
+            raise SpxError(st, f"spx_server_create: {self.lib.spx_last_error(eng.ctx).decode()}")
+        self.h = h
+
+    def _check(self, st: int, what: str):
+        if st != SPX_OK:
+            raise SpxError(st, f"{what}: {self.lib.spx_server_last_error(self.h).decode()}")
+
+    def submit(self, kind: int, index: int, tag: int = 0) -> int:
+        rid = C.c_uint64()
+        self._check(self.lib.spx_server_submit(self.h, C.byref(Request(kind, index, tag)), C.byref(rid)),
+                    "spx_server_submit")
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: float = -1.0):
+        """Result dict, or None while the request is pending after timeout_ms."""
+        r = Result()
+        st = self.lib.spx_server_wait(self.h, rid, timeout_ms, C.byref(r))
+        if st == SPX_EBUSY:
+            return None
+        self._check(st, "spx_server_wait")
+        return {f: getattr(r, f) for f, _ in Result._fields_}
+
+    def poll(self, rid: int):
+        return self.wait(rid, 0.0)
+
+    def release(self, rid: int):
+        self._check(self.lib.spx_server_release(self.h, rid), "spx_server_release")
+
+    def read(self, rid: int, result: dict):
+        """Host copies of a finished result: (pairs (total, 2) uint32, counts) for
+        a join, (ids, offsets) for a selection."""
+        n, P = result["total"], result["n_polys"]
+        if result["kind"] == SPX_REQ_JOIN:
+            a, b = np.empty((n, 2), np.uint32), np.empty(P, np.uint64)
+        else:
+            a, b = np.empty(n, np.uint32), np.empty(P + 1, np.uint64)
+        self._check(self.lib.spx_server_read(self.h, rid, _np_ptr(a), a.nbytes, _np_ptr(b), b.nbytes),
+                    "spx_server_read")
+        return a, b
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self._check(self.lib.spx_server_stats(self.h, C.byref(s)), "spx_server_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.spx_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _stream(stream):

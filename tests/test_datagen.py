@@ -85,3 +85,12 @@ def test_tessellation_vertex_counts():
     t = g.quad_tessellation(5, 4, 3, kmin=12, kmax=499)
     nv = np.diff(t.ring_off)
     assert nv.min() >= 4 + 4 * 12 and nv.max() <= 4 + 4 * 499
+
+
+def test_mixture_points_parallel_is_identical():
+    mix = g.make_mixture(91)
+    n = (1 << 23) * 2 + 12345  # three chunks, the last ragged
+    a = g.mixture_points_parallel(n, 91, mix, start=777, workers=3)
+    b = g.mixture_points(n, 91, mix, start=777)
+    assert a.dtype == np.int32 and a.shape == (n, 2)
+    assert np.array_equal(a, b)
