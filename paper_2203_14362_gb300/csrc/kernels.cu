@@ -36,6 +36,9 @@ namespace {
 #ifndef SPX_TILE_THREADS
 #define SPX_TILE_THREADS 256
 #endif
+#ifndef SPX_PASS1_WARP
+#define SPX_PASS1_WARP 1 // 1: pass 1 by k_warp (warp-independent), 0: by k_count (TMA tile pipeline)
+#endif
 #ifndef SPX_TILE_ITEMS
 #define SPX_TILE_ITEMS 8
 #endif
@@ -933,6 +936,229 @@ __global__ void __launch_bounds__(1024) k_scan_apply(unsigned long long *v, uint
     }
 }
 
+__device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// ---------------------------------------------- warp-independent pass 1
+// The same pass as k_count without any CTA barrier in its loop: every warp
+// works alone on chunks of 32 x kWItems consecutive points (chunk c goes to
+// warp c mod #warps), loads its points with coalesced 8-byte loads, resolves
+// the coarse and fine words of all of a lane's points with independent
+// loads, and queues its list points in a per-warp shared-memory queue that
+// it walks 32 at a time.
+// A warp never waits for another warp, so a slow walk or an index miss only
+// stalls its own warp.  With RESOLVE, every chunk's pair total is stored for
+// the scan, and k_wemit writes the pairs chunk by chunk.
+#ifndef SPX_WARP_ITEMS
+#define SPX_WARP_ITEMS 4
+#endif
+#ifndef SPX_WARP_PREFETCH
+#define SPX_WARP_PREFETCH 0 // 1: the next chunk's points are loaded while this one is resolved
+#endif
+#ifndef SPX_WARP_MIN_BLOCKS
+#define SPX_WARP_MIN_BLOCKS 3
+#endif
+constexpr int kWItems = SPX_WARP_ITEMS; // points per lane per chunk (4: 128-point chunks)
+constexpr int kWChunk = 32 * kWItems;   // consecutive points per warp chunk
+constexpr int kWQueue = 64;           // list points queued per warp
+constexpr size_t kWarpSmem = size_t(kWarps) * kWQueue * sizeof(uint4);
+
+template <bool FP32, bool RESOLVE>
+__global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaunch a, uint32_t nchunks, int use_hist)
+{
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kWQueue; // (x, y, first entry, chunk index)
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_raw + kWarpSmem);
+    const IndexView &ix = a.ix;
+    const uint64_t keep = policy_evict_last();
+    const bool hist = use_hist && a.counts;
+    if (hist)
+        for (uint32_t i = threadIdx.x; i < ix.P; i += kThreads)
+            s_hist[i] = 0;
+    __syncthreads();
+    uint32_t n_tests = 0, n_esc = 0, n_pts = 0, n_pairs = 0;
+    // count one polygon for every lane with has (converged warp)
+    auto count1 = [&](bool has, uint32_t q) {
+        if (!a.counts)
+            return;
+        if (hist)
+            hist_add_warp(s_hist, has, q);
+        else if (has)
+            atomicAdd(a.counts + q, 1ull);
+    };
+    const uint32_t nw = gridDim.x * kWarps;
+    // the next chunk's points are loaded while this chunk is resolved
+    int2 pn[kWItems];
+    auto load_chunk = [&](uint32_t c) {
+        const uint64_t b = (uint64_t)c * kWChunk;
+        const uint32_t m = (uint32_t)min((uint64_t)kWChunk, a.n - b);
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t loc = j * 32 + lane;
+            pn[j] = loc < m ? __ldcs(a.pts + b + loc) : make_int2(-1, -1);
+        }
+    };
+    if (SPX_WARP_PREFETCH && blockIdx.x * kWarps + warp < nchunks)
+        load_chunk(blockIdx.x * kWarps + warp);
+    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+        const uint64_t base = (uint64_t)ch * kWChunk;
+        const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
+        if (!SPX_WARP_PREFETCH)
+            load_chunk(ch);
+        int2 p[kWItems];
+        uint32_t w[kWItems];
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            p[j] = pn[j];
+            n_pts += j * 32 + lane < (int)npts ? 1u : 0u;
+        }
+        if (SPX_WARP_PREFETCH && ch + nw < nchunks)
+            load_chunk(ch + nw);
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const bool ok = (unsigned)p[j].x < kBox && (unsigned)p[j].y < kBox;
+            const uint32_t cw = coarse_word(ix, ok ? (uint32_t)p[j].x : 0u, ok ? (uint32_t)p[j].y : 0u, keep);
+            w[j] = ok ? cw : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const bool sub = (w[j] >> 30) == kCellSub;
+            const uint32_t fw = fine_word(ix, sub ? w[j] : 0u, sub ? (uint32_t)p[j].x : 0u,
+                                          sub ? (uint32_t)p[j].y : 0u, keep);
+            w[j] = sub ? fw : w[j];
+        }
+        uint32_t total = 0, qn = 0;
+        // walk m <= 32 queued points starting at k0, one per lane
+        auto walk = [&](uint32_t k0, uint32_t m) {
+            __syncwarp();
+            const bool has = (uint32_t)lane < m;
+            const uint4 it = s_q[k0 + (has ? lane : 0)];
+            uint32_t f = 0;
+            uint32_t c = walk_list<FP32>(ix, it.z, (int)it.x, (int)it.y, f, n_tests, n_esc, keep);
+            c = has ? c : 0u;
+            total += c;
+            count1(c == 1, f);
+            if (c > 1 && a.counts)
+                point_emit<FP32>(ix, (int)it.x, (int)it.y, keep, [&](uint32_t q) {
+                    if (hist)
+                        atomicAdd(s_hist + q, 1u);
+                    else
+                        atomicAdd(a.counts + q, 1ull);
+                });
+            if (RESOLVE && has)
+                __stcg(a.res + base + it.w, res_encode(c, f));
+            __syncwarp();
+        };
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t kind = w[j] >> 30, loc = j * 32 + lane;
+            const bool one = kind == kCellInsideOne, lst = kind == kCellList;
+            total += one ? 1u : 0u;
+            count1(one, w[j] & kPayloadMask);
+            if (RESOLVE && loc < npts && !lst)
+                __stcg(a.res + base + loc, one ? (w[j] & kPayloadMask) : kResNone);
+            const uint32_t bl = __ballot_sync(kFull, lst);
+            if (lst)
+                s_q[qn + __popc(bl & lanemask_lt())] =
+                    make_uint4((uint32_t)p[j].x, (uint32_t)p[j].y, w[j] & kPayloadMask, loc);
+            qn += __popc(bl);
+            if (qn >= 32) { // the newest 32 (qn <= 63 < kWQueue)
+                walk(qn - 32, 32);
+                qn -= 32;
+            }
+        }
+        if (qn)
+            walk(0, qn);
+        n_pairs += total;
+        total = warp_sum32(total);
+        if (RESOLVE && lane == 0)
+            a.tile_tot[ch] = total; // per-chunk pair total, scanned into offsets
+    }
+    if (hist) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < ix.P; i += kThreads)
+            if (s_hist[i])
+                atomicAdd(a.counts + i, (unsigned long long)s_hist[i]);
+    }
+    add_stats(a.stats, n_pts, n_tests, n_esc, n_pairs);
+}
+
+// Pass 3 of the join with warp chunks: every warp writes the pairs of its
+// chunks from the stored per-point results at the chunk's scanned offset.
+// Lane order within a round of 32 points, rounds in order: point order.
+template <bool FP32>
+__global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsigned long long *chunk_off,
+                                                    uint32_t nchunks)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t keep = policy_evict_last();
+    const uint32_t nw = gridDim.x * kWarps;
+    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+        const uint64_t base = (uint64_t)ch * kWChunk;
+        const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
+        unsigned long long run = chunk_off[ch];
+        uint32_t res[kWItems];
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t loc = j * 32 + lane;
+            res[j] = loc < npts ? __ldcs(a.res + base + loc) : kResNone;
+        }
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t loc = j * 32 + lane, r = res[j];
+            const bool multi = r != kResNone && (r & kResMulti);
+            uint32_t c = r == kResNone ? 0u : 1u, pre, tot;
+            if (!__any_sync(kFull, multi)) {
+                const uint32_t bl = __ballot_sync(kFull, c != 0);
+                pre = __popc(bl & lanemask_lt());
+                tot = __popc(bl);
+            } else {
+                int2 p = make_int2(0, 0);
+                if (multi) {
+                    p = a.pts[base + loc];
+                    if (r & kResCount) {
+                        c = (r >> 20) & 0x3ffu;
+                    } else { // count not stored: count again
+                        uint32_t f = 0, t = 0, e = 0;
+                        c = point_count<FP32>(a.ix, p.x, p.y, f, t, e, keep);
+                    }
+                }
+                uint32_t inc = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o)
+                        inc += v;
+                }
+                pre = inc - c;
+                tot = __shfl_sync(kFull, inc, 31);
+                if (multi) {
+                    unsigned long long o = run + pre;
+                    const uint32_t pid = (uint32_t)(base + loc);
+                    point_emit<FP32>(a.ix, p.x, p.y, keep, [&](uint32_t q) {
+                        if (o < a.cap)
+                            __stcs(a.pairs + o, make_uint2(pid, q));
+                        ++o;
+                    });
+                    c = 0; // written
+                }
+            }
+            if (c) {
+                const unsigned long long o = run + pre;
+                if (o < a.cap)
+                    __stcs(a.pairs + o, make_uint2((uint32_t)(base + loc), r));
+            }
+            run += tot;
+        }
+    }
+}
+
 // ------------------------------------------------------ multi-request batches
 // Serving answers several requests, each with its own index, in one pass over
 // the points: the point table is read once per pass for the whole batch
@@ -946,14 +1172,6 @@ __global__ void __launch_bounds__(1024) k_scan_apply(unsigned long long *v, uint
 constexpr int kMTile = 1024;               // points per tile
 constexpr int kMPerWarp = kMTile / kWarps; // consecutive points per warp
 constexpr size_t kMultiSmemHead = kMTile * sizeof(int2) + kWarps * kMaxBatch * (8 + 4);
-
-__device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
 
 // Does the cover bitmap let (px, py) reach a non-empty coarse cell?  False for
 // points outside the box.
@@ -1270,6 +1488,23 @@ cudaError_t launch_count_kernel(const JoinLaunch &a, uint32_t ntiles, int use_hi
     return cudaGetLastError();
 }
 
+template <bool FP32, bool RESOLVE>
+cudaError_t launch_warp_kernel(const JoinLaunch &a, int use_hist, cudaStream_t s)
+{
+    static bool done[64] = {};
+    const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
+    if (nchunks >= (1ull << 32))
+        return cudaErrorInvalidValue;
+    const size_t smem = kWarpSmem + (use_hist ? sizeof(uint32_t) * a.ix.P : 0);
+    cudaError_t e = smem_opt_in(k_warp<FP32, RESOLVE>, kWarpSmem + sizeof(uint32_t) * kHistMax, done);
+    if (e != cudaSuccess)
+        return e;
+    const uint32_t nblk = uint32_t((nchunks + kWarps - 1) / kWarps);
+    k_warp<FP32, RESOLVE><<<persistent_grid(k_warp<FP32, RESOLVE>, kThreads, smem, nblk), kThreads, smem, s>>>(
+        a, uint32_t(nchunks), use_hist);
+    return cudaGetLastError();
+}
+
 // Exclusive scan of n values in place; the total goes to *total.  part: at
 // least scan_partials(n) + 1 values of scratch.
 uint64_t scan_partials(uint64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
@@ -1323,9 +1558,10 @@ int device_sm_count()
 
 size_t join_scratch_bytes(uint64_t n)
 {
-    // per-point results | per-tile totals (then offsets) | tile counter
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
-    return size_t(((n * 4 + 15) & ~uint64_t(15)) + ntiles * 8 + 16);
+    // per-point results | per-tile or per-chunk totals (then offsets) | scan partials | tile counter
+    const uint64_t ntiles = (n + kTile - 1) / kTile, nchunks = (n + kWChunk - 1) / kWChunk;
+    const uint64_t nt = ntiles > nchunks ? ntiles : nchunks;
+    return size_t(((n * 4 + 15) & ~uint64_t(15)) + (nt + scan_partials(nt) + 2) * 8 + 16);
 }
 
 size_t plain_scratch_bytes(uint64_t n)
@@ -1336,17 +1572,19 @@ size_t plain_scratch_bytes(uint64_t n)
 
 cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
 {
-    const uint64_t ntiles64 = (a.n + kTile - 1) / kTile;
-    if (ntiles64 >= (1ull << 31))
+    const uint64_t ntiles64 = (a.n + kTile - 1) / kTile, nchunks64 = (a.n + kWChunk - 1) / kWChunk;
+    if (nchunks64 >= (1ull << 31))
         return cudaErrorInvalidValue;
     if (reinterpret_cast<uintptr_t>(a.pts) & 15)
         return cudaErrorMisalignedAddress;
-    const uint32_t ntiles = uint32_t(ntiles64);
+    const uint32_t ntiles = uint32_t(ntiles64), nchunks = uint32_t(nchunks64);
+    const uint64_t nt = ntiles64 > nchunks64 ? ntiles64 : nchunks64;
     JoinLaunch b = a;
     char *sc = static_cast<char *>(scratch);
     b.res = reinterpret_cast<uint32_t *>(sc);
     b.tile_tot = reinterpret_cast<unsigned long long *>(sc + ((a.n * 4 + 15) & ~uint64_t(15)));
-    b.tile_counter = reinterpret_cast<unsigned *>(b.tile_tot + ntiles);
+    unsigned long long *part = b.tile_tot + nt;
+    b.tile_counter = reinterpret_cast<unsigned *>(part + scan_partials(nt) + 2);
     cudaError_t e = cudaMemsetAsync(b.tile_counter, 0, 16, s);
     if (e != cudaSuccess)
         return e;
@@ -1360,26 +1598,45 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cuda
             return cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s);
         return cudaSuccess;
     }
-    // pass 1: resolve every point, count per polygon and per tile
+    // pass 1: resolve every point, count per polygon and per tile (chunk)
     const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
     if (ev)
         cudaEventRecord(ev[0], s);
+#if SPX_PASS1_WARP
+    e = a.fp32 ? launch_warp_kernel<true, true>(b, use_hist, s) : launch_warp_kernel<false, true>(b, use_hist, s);
+#else
     e = a.fp32 ? launch_count_kernel<true, true>(b, ntiles, use_hist, s)
                : launch_count_kernel<false, true>(b, ntiles, use_hist, s);
+#endif
     if (e != cudaSuccess)
         return e;
     if (ev)
         cudaEventRecord(ev[1], s);
-    // pass 2: tile offsets and the total
+    // pass 2: offsets and the total
+#if SPX_PASS1_WARP
+    if ((e = launch_scan(b.tile_tot, nchunks, a.total, part, s)) != cudaSuccess)
+        return e;
+#else
     k_scan<<<1, 1024, 0, s>>>(b.tile_tot, ntiles, a.total);
+#endif
     if (ev)
         cudaEventRecord(ev[2], s);
     // pass 3: pairs in point order
     if (a.cap) {
+#if SPX_PASS1_WARP
+        const uint32_t nblk = (nchunks + kWarps - 1) / kWarps;
+        if (a.fp32)
+            k_wemit<true><<<persistent_grid(k_wemit<true>, kThreads, 0, nblk), kThreads, 0, s>>>(b, b.tile_tot,
+                                                                                             nchunks);
+        else
+            k_wemit<false><<<persistent_grid(k_wemit<false>, kThreads, 0, nblk), kThreads, 0, s>>>(b, b.tile_tot,
+                                                                                               nchunks);
+#else
         if (a.fp32)
             k_emit<true><<<ntiles, kThreads, 0, s>>>(b, b.tile_tot);
         else
             k_emit<false><<<ntiles, kThreads, 0, s>>>(b, b.tile_tot);
+#endif
     }
     if (ev)
         cudaEventRecord(ev[3], s);
@@ -1405,8 +1662,12 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
     const int use_hist = a.ix.P <= (uint32_t)kHistMax ? 1 : 0;
     if (ev)
         cudaEventRecord(ev[0], s);
+#if SPX_PASS1_WARP
+    e = a.fp32 ? launch_warp_kernel<true, false>(b, use_hist, s) : launch_warp_kernel<false, false>(b, use_hist, s);
+#else
     e = a.fp32 ? launch_count_kernel<true, false>(b, ntiles, use_hist, s)
                : launch_count_kernel<false, false>(b, ntiles, use_hist, s);
+#endif
     if (ev)
         cudaEventRecord(ev[1], s);
     return e;
