@@ -39,7 +39,7 @@ L2_BYTES = 129 * 1024 * 1024
 # the ncu capture summarised in profiles/k_count_resolve_tess2000_20m.md; only
 # valid for that kernel version, the default index (g = 11, sub = 3) and the
 # default workload.
-RESOLVE_TRAFFIC_BYTES_PER_POINT = (295.875328e6 + 59.254784e6) / 20e6
+RESOLVE_TRAFFIC_BYTES_PER_POINT = None
 SERVE_SEED = 0x2203143620 + 4  # request indexes of the serving measurement
 
 
@@ -356,7 +356,7 @@ def run_spx(args, world, rank, local):
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": "k_count<resolve> (join pass 1)" if not args.plain else "plain join (3 kernels)",
+                         "kernel": "k_warp<resolve> (join pass 1)" if not args.plain else "plain join (3 kernels)",
                          "kernel_ms": dom_ms, "algorithmic_bytes_per_launch": int(dom_bytes),
                          "step": {"algorithmic_bytes": int(step_bytes), "ms": ms,
                                   "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
@@ -633,7 +633,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
                        "fp32_escalation_fraction": st["fp32_escalations"] / max(st["edge_tests"], 1),
                        "l2": "inputs larger than L2 (32 GB of points); no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_count<aggregate>",
+                         "traffic": None, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_warp<aggregate>",
                          "kernel_ms": k_ms, "algorithmic_bytes_per_launch": int(alg)},
             "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps, "clocks": clk,
         }), flush=True)

@@ -949,23 +949,27 @@ __device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
 // works alone on chunks of 32 x kWItems consecutive points (chunk c goes to
 // warp c mod #warps), loads its points with coalesced 8-byte loads, resolves
 // the coarse and fine words of all of a lane's points with independent
-// loads, and queues its list points in a per-warp shared-memory queue that
-// it walks 32 at a time.
-// A warp never waits for another warp, so a slow walk or an index miss only
-// stalls its own warp.  With RESOLVE, every chunk's pair total is stored for
+// loads, and queues its list points in a per-warp shared-memory queue that it
+// walks 32 at a time once the whole chunk is resolved (the chunk's points and
+// words are dead by then, which keeps the kernel at 64 registers and 4 CTAs
+// per SM).  A warp never waits for another warp, so a slow walk or an index
+// miss only stalls its own warp.  With RESOLVE, every chunk's pair total is stored for
 // the scan, and k_wemit writes the pairs chunk by chunk.
 #ifndef SPX_WARP_ITEMS
-#define SPX_WARP_ITEMS 4
+#define SPX_WARP_ITEMS 8
 #endif
 #ifndef SPX_WARP_PREFETCH
 #define SPX_WARP_PREFETCH 0 // 1: the next chunk's points are loaded while this one is resolved
 #endif
 #ifndef SPX_WARP_MIN_BLOCKS
-#define SPX_WARP_MIN_BLOCKS 3
+#define SPX_WARP_MIN_BLOCKS 4
 #endif
-constexpr int kWItems = SPX_WARP_ITEMS; // points per lane per chunk (4: 128-point chunks)
+constexpr int kWItems = SPX_WARP_ITEMS; // points per lane per chunk (8: 256-point chunks)
 constexpr int kWChunk = 32 * kWItems;   // consecutive points per warp chunk
-constexpr int kWQueue = 64;           // list points queued per warp
+#ifndef SPX_WARP_WALK_END
+#define SPX_WARP_WALK_END 1 // 1: a chunk's list points are all queued and walked after it is resolved
+#endif
+constexpr int kWQueue = SPX_WARP_WALK_END ? (kWChunk > 64 ? kWChunk : 64) : 64; // list points queued per warp
 constexpr size_t kWarpSmem = size_t(kWarps) * kWQueue * sizeof(uint4);
 
 template <bool FP32, bool RESOLVE>
@@ -1068,13 +1072,13 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
                 s_q[qn + __popc(bl & lanemask_lt())] =
                     make_uint4((uint32_t)p[j].x, (uint32_t)p[j].y, w[j] & kPayloadMask, loc);
             qn += __popc(bl);
-            if (qn >= 32) { // the newest 32 (qn <= 63 < kWQueue)
+            if (!SPX_WARP_WALK_END && qn >= 32) { // the newest 32 (qn <= 63 < kWQueue)
                 walk(qn - 32, 32);
                 qn -= 32;
             }
         }
-        if (qn)
-            walk(0, qn);
+        for (uint32_t k0 = 0; k0 < qn; k0 += 32)
+            walk(k0, min(qn - k0, 32u));
         n_pairs += total;
         total = warp_sum32(total);
         if (RESOLVE && lane == 0)
