@@ -269,11 +269,14 @@ spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint6
 
 /*
  * End-to-end join on host buffers: copies the n points at xy_host to the
- * device, joins them against the index, and copies pairs and counts back.
- * pairs_host holds cap pairs (2*cap uint32), counts_host P uint64 (may be
- * NULL); *n_pairs receives the total (SPX_ECAPACITY if above cap).  Device
- * staging buffers are owned by the ctx and reused.  Pinned host memory makes
- * the copies faster.  Synchronous.
+ * device, joins them against the index, and returns pairs and counts in host
+ * memory.  pairs_host holds cap pairs (2*cap uint32), counts_host P uint64 (may
+ * be NULL); *n_pairs receives the total (SPX_ECAPACITY if above cap; the first
+ * cap pairs are written).  The table is processed in slices of 2^23 points so
+ * that the copy of a slice to the device, the join of the previous slice and
+ * the copy of the pairs of the one before back to the host overlap (the copies
+ * run on the copy engines).  Device staging buffers are owned by the ctx and
+ * reused.  Pinned host memory makes the copies faster.  Synchronous.
  */
 spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_index index, uint32_t *pairs_host,
                          uint64_t cap, uint64_t *counts_host, uint64_t *n_pairs);

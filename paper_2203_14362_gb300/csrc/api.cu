@@ -71,6 +71,12 @@ struct spx_ctx {
     void *st_pts = nullptr, *st_pairs = nullptr, *st_counts = nullptr;
     size_t st_pts_b = 0, st_pairs_b = 0, st_counts_b = 0;
     cudaStream_t stream = nullptr;
+    // spx_join_host: copy-in, emit and copy-out streams, three events per
+    // slice, pinned (base, total) words per slice
+    cudaStream_t in_stream = nullptr, emit_stream = nullptr, out_stream = nullptr;
+    std::vector<cudaEvent_t> slice_ev;
+    unsigned long long *slice_words = nullptr;
+    size_t slice_words_n = 0;
     // batched selection: captured launch sequences, keyed by their arguments
     std::map<std::tuple<uint64_t, uint64_t, uintptr_t, uint64_t, uintptr_t>, cudaGraphExec_t> select_graphs;
     cudaStream_t capture_stream = nullptr;
@@ -456,6 +462,15 @@ void spx_destroy(spx_ctx *ctx)
         cudaGraphExecDestroy(kv.second);
     if (ctx->capture_stream)
         cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->in_stream)
+        cudaStreamDestroy(ctx->in_stream);
+    if (ctx->emit_stream)
+        cudaStreamDestroy(ctx->emit_stream);
+    if (ctx->out_stream)
+        cudaStreamDestroy(ctx->out_stream);
+    cudaFreeHost(ctx->slice_words);
+    for (auto e : ctx->slice_ev)
+        cudaEventDestroy(e);
     if (ctx->stream)
         cudaStreamDestroy(ctx->stream);
     for (auto &e : ctx->ev)
@@ -873,39 +888,113 @@ spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_i
     if (n >= (1ull << 32))
         return fail(ctx, SPX_EINVAL, "join_host: n must be < 2^32");
     cudaStream_t s = ctx->stream;
+    for (cudaStream_t *p : {&ctx->in_stream, &ctx->emit_stream, &ctx->out_stream})
+        if (!*p)
+            SPX_CUDA(cudaStreamCreateWithFlags(p, cudaStreamNonBlocking), "join_host stream");
+    // Slices of kSlice points flow through four streams: copy-in of slice
+    // k + 1 (in_stream), resolve of slice k (stream), emit of slice k - 1 into
+    // device staging (emit_stream) and copy-out of the slice before
+    // (out_stream).  Slice k's pairs start at base[k] = base[k - 1] +
+    // total[k - 1], computed on the device; the host reads (base[k], total[k])
+    // to size the slice's copy-out.  Both copy directions run on the copy
+    // engines, beside the kernels.
+    constexpr uint64_t kSlice = uint64_t(1) << 23;
+    const uint64_t n_slices = (n + kSlice - 1) / kSlice;
+    const uint64_t cpts = join_chunk_points(), nchunks = (n + cpts - 1) / cpts;
+    const size_t b_res = ((n * 4 + 15) & ~uint64_t(15)), words = nchunks + join_part_words(kSlice) + 2 * n_slices + 2;
     spx_status st;
     if ((st = ensure(ctx, &ctx->st_pts, &ctx->st_pts_b, n * 8 + 16, s, "join_host")) != SPX_OK ||
         (st = ensure(ctx, &ctx->st_pairs, &ctx->st_pairs_b, cap * 8 + 16, s, "join_host")) != SPX_OK ||
         (st = ensure(ctx, &ctx->st_counts, &ctx->st_counts_b, size_t(ix->view.P) * 8 + 16, s, "join_host")) != SPX_OK ||
-        (st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, join_scratch_bytes(n), s, "join_host")) != SPX_OK)
+        (st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, b_res + words * 8, s, "join_host")) != SPX_OK)
         return st;
-    if (n)
-        SPX_CUDA(cudaMemcpyAsync(ctx->st_pts, xy_host, n * 8, cudaMemcpyHostToDevice, s), "join_host H2D");
-    JoinLaunch a{};
-    a.ix = ix->view;
-    a.pts = reinterpret_cast<const int2 *>(ctx->st_pts);
-    a.n = n;
-    a.pairs = reinterpret_cast<uint2 *>(ctx->st_pairs);
-    a.cap = cap;
-    a.counts = reinterpret_cast<unsigned long long *>(ctx->st_counts);
-    a.total = &ctx->aux->total;
-    a.err = &ctx->aux->err;
-    a.stats = ctx->aux->stats;
-    a.fp32 = ix->fp32;
-    cudaError_t e = launch_join(a, ctx->scratch, s);
-    if (e != cudaSuccess)
-        return cuda_fail(ctx, e, "join_host launch");
-    unsigned long long t = 0;
-    SPX_CUDA(cudaMemcpyAsync(&t, &ctx->aux->total, sizeof(t), cudaMemcpyDeviceToHost, s), "join_host total");
+    while (ctx->slice_ev.size() < 3 * n_slices + 1) {
+        cudaEvent_t e = nullptr;
+        SPX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "join_host event");
+        ctx->slice_ev.push_back(e);
+    }
+    if (ctx->slice_words_n < 2 * n_slices + 2) {
+        cudaFreeHost(ctx->slice_words);
+        ctx->slice_words = nullptr;
+        ctx->slice_words_n = 0;
+        SPX_CUDA(cudaMallocHost(reinterpret_cast<void **>(&ctx->slice_words), (2 * n_slices + 2) * 8),
+                 "join_host pinned words");
+        ctx->slice_words_n = 2 * n_slices + 2;
+    }
+    cudaEvent_t *ev_in = ctx->slice_ev.data(), *ev_res = ev_in + n_slices, *ev_emit = ev_res + n_slices;
+    uint32_t *res = static_cast<uint32_t *>(ctx->scratch);
+    unsigned long long *chunk_tot = reinterpret_cast<unsigned long long *>(static_cast<char *>(ctx->scratch) + b_res);
+    unsigned long long *part = chunk_tot + nchunks;
+    unsigned long long *bt = part + join_part_words(kSlice); // (base[k], total[k]) pairs, then base[n_slices]
+    SPX_CUDA(cudaMemsetAsync(bt, 0, 8, s), "join_host base");
+    if (ix->view.P)
+        SPX_CUDA(cudaMemsetAsync(ctx->st_counts, 0, size_t(ix->view.P) * 8, s), "join_host counts");
+    for (uint64_t k = 0; k < n_slices; ++k) {
+        const uint64_t lo = k * kSlice, m = n - lo < kSlice ? n - lo : kSlice;
+        SPX_CUDA(cudaMemcpyAsync(static_cast<char *>(ctx->st_pts) + lo * 8, xy_host + 2 * lo, m * 8,
+                                 cudaMemcpyHostToDevice, ctx->in_stream),
+                 "join_host H2D");
+        SPX_CUDA(cudaEventRecord(ev_in[k], ctx->in_stream), "join_host event");
+    }
+    for (uint64_t k = 0; k < n_slices; ++k) {
+        const uint64_t lo = k * kSlice, m = n - lo < kSlice ? n - lo : kSlice;
+        JoinLaunch a{};
+        a.ix = ix->view;
+        a.pts = reinterpret_cast<const int2 *>(static_cast<char *>(ctx->st_pts) + lo * 8);
+        a.n = m;
+        a.pairs = reinterpret_cast<uint2 *>(ctx->st_pairs);
+        a.cap = cap;
+        a.counts = reinterpret_cast<unsigned long long *>(ctx->st_counts);
+        a.res = res + lo;
+        a.tile_tot = chunk_tot + lo / cpts;
+        a.total = bt + 2 * k + 1;
+        a.err = &ctx->aux->err;
+        a.stats = ctx->aux->stats;
+        a.fp32 = ix->fp32;
+        a.pid0 = uint32_t(lo);
+        a.keep_counts = 1;
+        a.pair_base = bt + 2 * k;
+        // resolve slice k once its points are in; base[k + 1]; (base, total) to the host
+        cudaError_t e = cudaStreamWaitEvent(s, ev_in[k], 0);
+        if (e == cudaSuccess)
+            e = launch_join_resolve(a, part, s);
+        if (e == cudaSuccess)
+            e = launch_sum_u64(bt + 2 * k + 2, bt + 2 * k, bt + 2 * k + 1, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->slice_words + 2 * k, bt + 2 * k, 16, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_res[k], s);
+        // emit slice k into the device staging buffer
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(ctx->emit_stream, ev_res[k], 0);
+        if (e == cudaSuccess)
+            e = launch_join_emit(a, ctx->emit_stream);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_emit[k], ctx->emit_stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "join_host launch");
+    }
+    // copy-out, slice by slice, as soon as each slice's size is known
+    uint64_t t = 0;
+    for (uint64_t k = 0; k < n_slices; ++k) {
+        SPX_CUDA(cudaEventSynchronize(ev_res[k]), "join_host slice size");
+        const uint64_t b0 = ctx->slice_words[2 * k], tk = ctx->slice_words[2 * k + 1];
+        t = b0 + tk;
+        const uint64_t hi = t < cap ? t : cap;
+        SPX_CUDA(cudaStreamWaitEvent(ctx->out_stream, ev_emit[k], 0), "join_host wait");
+        if (b0 < hi)
+            SPX_CUDA(cudaMemcpyAsync(pairs_host + 2 * b0, static_cast<char *>(ctx->st_pairs) + b0 * 8, (hi - b0) * 8,
+                                     cudaMemcpyDeviceToHost, ctx->out_stream),
+                     "join_host D2H");
+    }
+    cudaEvent_t ev_done = ctx->slice_ev[3 * n_slices];
+    SPX_CUDA(cudaEventRecord(ev_done, ctx->out_stream), "join_host event");
+    SPX_CUDA(cudaStreamWaitEvent(s, ev_done, 0), "join_host wait");
     if (counts_host && ix->view.P)
         SPX_CUDA(cudaMemcpyAsync(counts_host, ctx->st_counts, size_t(ix->view.P) * 8, cudaMemcpyDeviceToHost, s),
                  "join_host counts D2H");
     if ((st = check_kernel_err(ctx, s)) != SPX_OK)
         return st;
-    const uint64_t m = t < cap ? t : cap;
-    if (m)
-        SPX_CUDA(cudaMemcpyAsync(pairs_host, ctx->st_pairs, m * 8, cudaMemcpyDeviceToHost, s), "join_host D2H");
-    SPX_CUDA(cudaStreamSynchronize(s), "join_host sync");
     *n_pairs = t;
     if (t > cap)
         return fail(ctx, SPX_ECAPACITY, "join_host: " + std::to_string(t) + " pairs exceed capacity");

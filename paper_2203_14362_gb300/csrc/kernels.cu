@@ -15,14 +15,15 @@
 // from FP32 when |d_f| > 2^-21 (|t1| + |t2|) (forward error bound of the FP32
 // evaluation with a factor-2 margin), else from an exact int64 recomputation.
 //
-// The fused kernel is persistent: each CTA claims 2048-point tiles in order,
-// and TMA bulk-copies the NEXT tile's points into shared memory (mbarrier
-// completion) while it works on the current one.  Within a tile every thread
-// resolves 8 points with independent loads; the few points whose fine cell
-// holds an entry list are compacted into a shared-memory queue and walked by
-// all threads together, so the edge loops run converged.  The join then scans
-// the per-point match counts, gets the tile's output offset by decoupled
-// look-back and writes the pairs in point order.
+// The join is a cached two-pass Map (§5.1).  Pass 1 (k_warp) is persistent
+// and barrier-free: every warp takes its own 256-point chunks, resolves the
+// coarse and fine words of all its points with independent loads, queues the
+// few points whose fine cell holds an entry list in a per-warp shared-memory
+// queue and walks them 32 at a time, so the edge loops run converged; it
+// stores a 4-byte result per point and a pair total per chunk.  A device-wide
+// scan turns the totals into offsets, and pass 3 (k_wemit) writes each
+// chunk's pairs in point order.  The count aggregate is pass 1 alone.  Serving
+// batches (k_multi) and the selection partition (k_part_*) follow.
 #include "kernels.h"
 #include "spx_internal.h"
 
@@ -36,21 +37,10 @@ namespace {
 #ifndef SPX_TILE_THREADS
 #define SPX_TILE_THREADS 256
 #endif
-#ifndef SPX_PASS1_WARP
-#define SPX_PASS1_WARP 1 // 1: pass 1 by k_warp (warp-independent), 0: by k_count (TMA tile pipeline)
-#endif
-#ifndef SPX_TILE_ITEMS
-#define SPX_TILE_ITEMS 8
-#endif
-constexpr int kThreads = SPX_TILE_THREADS;  // threads per CTA of the tile kernel
+constexpr int kThreads = SPX_TILE_THREADS;  // threads per CTA of the persistent kernels
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = SPX_TILE_ITEMS;      // points per thread per tile
-constexpr int kTile = kThreads * kItems;    // points per tile
-constexpr uint32_t kTileBytes = kTile * 8;  // bytes of points per tile
-constexpr int kQueue = kTile / 2;           // list points compacted per tile (more are walked in place)
 constexpr int kPlainThreads = 256;          // threads per CTA of the plain kernels
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr uint32_t kPending = 0xffffffffu;
 // Pass-1 result of a point (4 bytes):
 //   kResNone                            in no polygon
 //   q (bit 31 clear)                    in exactly polygon q
@@ -68,9 +58,7 @@ __host__ __device__ constexpr uint32_t res_encode(uint32_t cnt, uint32_t first)
                                                                       : (kResMulti | first);
 }
 constexpr int kHistMax = 11776;             // polygons counted in shared memory (46 KB)
-constexpr size_t kCountSmem = 3 * kTileBytes + kQueue * sizeof(uint2);
 
-constexpr unsigned kSpinLimit = 1u << 22;             // ~ seconds with the back-off below
 
 // ------------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t lanemask_lt()
@@ -79,42 +67,12 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(smem_u32(bar)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
 // L2 eviction policies: the index stays resident (evict_last) while the
 // streamed points pass through (evict_first).
 __device__ __forceinline__ uint64_t policy_evict_last()
 {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_first()
-{
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 __device__ __forceinline__ uint32_t ld_idx(const uint32_t *p, uint64_t pol)
@@ -141,15 +99,6 @@ __device__ __forceinline__ int4 ld_idx(const int4 *p, uint64_t pol)
 }
 // 1-D bulk copy global -> shared (TMA), completion counted on `bar`.
 // dst, src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
 // ------------------------------------------------------------- the predicate
 // sign of d = (bx-ax)(py-ay) - (by-ay)(px-ax)
 template <bool FP32>
@@ -422,371 +371,6 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t pt
     }
 }
 
-// ------------------------------------------------------------ tile kernels
-// Both kernels are persistent: CTAs claim kTile-point tiles in order from an
-// atomic counter and TMA bulk-copy each tile's points into a ring of shared-
-// memory buffers (mbarrier completion) one tile ahead.  Per tile, every worker
-// thread resolves kItems points with independent loads; points whose fine
-// cell holds a list are compacted into a shared-memory queue and walked by
-// all workers (dynamic assignment).
-
-// worker-only barrier (named barrier 1): the join's flush warp never joins it
-template <int N>
-__device__ __forceinline__ void workers_sync()
-{
-    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// bounded wait for phase `parity` of an mbarrier; on expiry sets `code` in err
-__device__ __forceinline__ void mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err, unsigned code)
-{
-    unsigned spins = 0;
-    while (!mbar_try_wait(bar, parity)) {
-        if (++spins > kSpinLimit) {
-            atomicOr(err, code);
-            return;
-        }
-        __nanosleep(20);
-    }
-}
-
-// Copy of tile t into ring buffer dst: TMA for the 16-byte part, a plain
-// store for an odd last point.  Completes on `bar`.
-__device__ __forceinline__ void issue_tile(const JoinLaunch &a, uint32_t t, int2 *dst, uint64_t *bar)
-{
-    const uint64_t base = (uint64_t)t * kTile;
-    const uint64_t rem = a.n - base;
-    const uint32_t np = rem < (uint64_t)kTile ? (uint32_t)rem : (uint32_t)kTile;
-    const uint32_t bytes = (np & ~1u) * 8u;
-    if (np & 1u)
-        dst[np - 1] = a.pts[base + np - 1];
-    if (bytes) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(bar, bytes);
-        tma_load_1d(dst, a.pts + base, bytes, bar, policy_evict_first());
-    } else {
-        mbar_arrive(bar);
-    }
-}
-
-// Resolve, queue and walk one tile: cnt[i] / first[i] of the point at
-// tile location i * kThreads + wtid.  SYNC is the barrier among the workers.
-template <bool FP32, class SYNC>
-__device__ __forceinline__ void eval_tile(const IndexView &ix, const int2 *tb, uint32_t npts, uint2 *s_q,
-                                          uint32_t *s_qn, uint32_t *s_qj, uint32_t (&cnt)[kItems],
-                                          uint32_t (&first)[kItems], uint32_t &n_tests, uint32_t &n_esc,
-                                          uint32_t &n_pts, uint64_t keep, int wtid, SYNC sync)
-{
-    const int lane = wtid & 31;
-    // every lane loads (from cell 0 / fine word 0 when it has nothing to look
-    // up) and keeps or drops the result, so the warp stays converged
-    uint32_t w[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const uint32_t loc = i * kThreads + wtid;
-        const int2 p = tb[loc < npts ? loc : 0u];
-        const bool ok = loc < npts && (unsigned)p.x < kBox && (unsigned)p.y < kBox;
-        n_pts += loc < npts ? 1u : 0u;
-        const uint32_t px = ok ? (uint32_t)p.x : 0u, py = ok ? (uint32_t)p.y : 0u;
-        const uint32_t cw = coarse_word(ix, px, py, keep);
-        w[i] = ok ? cw : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const bool sub = (w[i] >> 30) == kCellSub;
-        const int2 p = tb[sub ? i * kThreads + wtid : 0u];
-        const uint32_t fw = fine_word(ix, sub ? w[i] : 0u, sub ? (uint32_t)p.x : 0u, sub ? (uint32_t)p.y : 0u, keep);
-        w[i] = sub ? fw : w[i];
-    }
-    // one INSIDE polygon: done; a list: into the queue
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const uint32_t kind = w[i] >> 30;
-        cnt[i] = kind == kCellInsideOne ? 1u : 0u;
-        first[i] = w[i] & kPayloadMask;
-        const bool is_list = kind == kCellList;
-        const uint32_t bl = __ballot_sync(kFull, is_list);
-        if (bl) {
-            const int leader = __ffs(bl) - 1;
-            uint32_t slot0 = 0;
-            if (lane == leader)
-                slot0 = atomicAdd(s_qn, (uint32_t)__popc(bl));
-            slot0 = __shfl_sync(kFull, slot0, leader);
-            if (is_list) {
-                const uint32_t slot = slot0 + __popc(bl & lanemask_lt());
-                const uint32_t loc = i * kThreads + wtid;
-                if (slot < (uint32_t)kQueue) {
-                    s_q[slot] = make_uint2(loc, w[i] & kPayloadMask);
-                    cnt[i] = kPending;
-                    first[i] = slot;
-                } else {
-                    const int2 p = tb[loc];
-                    uint32_t f = 0;
-                    cnt[i] = walk_list<FP32>(ix, w[i] & kPayloadMask, p.x, p.y, f, n_tests, n_esc, keep);
-                    first[i] = f;
-                }
-            }
-        }
-    }
-    sync();
-    {
-        // warp-synchronous: a warp takes 32 queued points at a time, one per lane
-        const uint32_t qn = min(*s_qn, (uint32_t)kQueue);
-        for (;;) {
-            uint32_t j0 = 0;
-            if (lane == 0)
-                j0 = atomicAdd(s_qj, 32u);
-            j0 = __shfl_sync(kFull, j0, 0);
-            if (j0 >= qn)
-                break;
-            const uint32_t j = j0 + lane;
-            const bool has = j < qn;
-            const uint2 it = s_q[has ? j : j0];
-            const int2 p = tb[it.x];
-            uint32_t f = 0;
-            const uint32_t c = walk_list<FP32>(ix, it.y, p.x, p.y, f, n_tests, n_esc, keep);
-            __syncwarp();
-            if (has)
-                s_q[j] = make_uint2(c, f);
-            __syncwarp();
-        }
-    }
-    sync();
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        if (cnt[i] == kPending) {
-            const uint2 r = s_q[first[i]];
-            cnt[i] = r.x;
-            first[i] = r.y;
-        }
-    }
-}
-
-// ------------------------------------------------- count / resolve (pass 1)
-// Counts only (the aggregation plan that never materialises the join, §5.2):
-// per-polygon counts in a shared-memory histogram.  With RESOLVE, the same
-// pass is also the first pass of the join (the counting pass of the two-pass
-// Map, §5.1): it stores every point's result (none / its polygon / "several",
-// 4 bytes) and every tile's pair total, so the writing pass needs no index
-// lookups.  Three buffers: one worked on, one arriving, one spare.
-template <bool FP32, bool RESOLVE>
-__global__ void __launch_bounds__(kThreads) k_count(JoinLaunch a, uint32_t ntiles, int use_hist)
-{
-    constexpr int R = 3;
-    extern __shared__ __align__(128) unsigned char dsm[];
-    int2 *s_buf = reinterpret_cast<int2 *>(dsm);
-    uint2 *s_q = reinterpret_cast<uint2 *>(dsm + R * kTileBytes);
-    uint32_t *s_hist = reinterpret_cast<uint32_t *>(dsm + R * kTileBytes + kQueue * sizeof(uint2));
-    __shared__ __align__(8) uint64_t s_full[R];
-    __shared__ uint32_t s_tile[R];
-    __shared__ uint32_t s_qn, s_qj;
-    __shared__ uint32_t s_wsum[kWarps];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const IndexView &ix = a.ix;
-    const uint64_t keep = policy_evict_last();
-    if (use_hist)
-        for (uint32_t i = tid; i < ix.P; i += kThreads)
-            s_hist[i] = 0;
-    auto claim = [&](int b) {
-        const uint32_t nt = atomicAdd(a.tile_counter, 1u);
-        s_tile[b] = nt;
-        if (nt < ntiles)
-            issue_tile(a, nt, s_buf + b * kTile, &s_full[b]);
-    };
-    if (tid == 0) {
-        for (int b = 0; b < R; ++b)
-            mbar_init(&s_full[b], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_qn = 0;
-        s_qj = 0;
-        claim(0);
-    }
-    __syncthreads();
-    uint32_t n_tests = 0, n_esc = 0, n_pts = 0, n_pairs = 0;
-    auto sync = [] { __syncthreads(); };
-    for (uint32_t k = 0;; ++k) {
-        const int b = int(k % R);
-        const uint32_t tile = s_tile[b];
-        if (tile >= ntiles)
-            break;
-        if (tid == 0)
-            claim(int((k + 1) % R)); // that buffer's tile (k-2) ended with a barrier
-        mbar_wait(&s_full[b], (k / R) & 1u, a.err, kErrCopy);
-        const int2 *tb = s_buf + b * kTile;
-        const uint64_t base = (uint64_t)tile * kTile;
-        const uint64_t rem = a.n - base;
-        const uint32_t npts = rem < (uint64_t)kTile ? (uint32_t)rem : (uint32_t)kTile;
-        uint32_t cnt[kItems], first[kItems];
-        eval_tile<FP32>(ix, tb, npts, s_q, &s_qn, &s_qj, cnt, first, n_tests, n_esc, n_pts, keep, tid, sync);
-        uint32_t tsum = 0;
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const uint32_t loc = i * kThreads + tid;
-            if (use_hist)
-                hist_add_warp(s_hist, cnt[i] == 1, first[i]);
-            if (RESOLVE && loc < npts)
-                __stcg(a.res + base + loc, res_encode(cnt[i], first[i]));
-            tsum += cnt[i];
-            if (!cnt[i])
-                continue;
-            n_pairs += cnt[i];
-            if (cnt[i] == 1) {
-                if (!use_hist && a.counts)
-                    atomicAdd(a.counts + first[i], 1ull);
-            } else if (a.counts) {
-                const int2 p = tb[loc];
-                point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) {
-                    if (use_hist)
-                        atomicAdd(&s_hist[q], 1u);
-                    else
-                        atomicAdd(a.counts + q, 1ull);
-                });
-            }
-        }
-        if (RESOLVE) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                tsum += __shfl_xor_sync(kFull, tsum, o);
-            if (lane == 0)
-                s_wsum[warp] = tsum;
-        }
-        if (tid == 0) {
-            s_qn = 0;
-            s_qj = 0;
-        }
-        __syncthreads(); // buffer b, the queue and the warp sums are complete
-        if (RESOLVE && tid == 0) {
-            unsigned long long t = 0;
-            for (int w = 0; w < kWarps; ++w)
-                t += s_wsum[w];
-            a.tile_tot[tile] = t;
-        }
-    }
-    add_stats(a.stats, n_pts, n_tests, n_esc, n_pairs);
-    if (use_hist && a.counts) {
-        __syncthreads();
-        for (uint32_t i = tid; i < ix.P; i += kThreads)
-            if (s_hist[i])
-                atomicAdd(a.counts + i, (unsigned long long)s_hist[i]);
-    }
-}
-
-// ------------------------------------------------------ write pairs (pass 3)
-// One tile per CTA: the tile's results (4 bytes per point) are read, a ballot
-// scan gives every point's place in the tile's output, and the pairs go to
-// tile_off[tile] + place, in point order.  A point in several polygons is
-// walked again to emit all of them, ascending.
-template <bool FP32>
-__global__ void __launch_bounds__(kThreads) k_emit(JoinLaunch a, const unsigned long long *tile_off)
-{
-    __shared__ uint32_t s_off[kItems * kWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t tile = blockIdx.x;
-    const uint64_t base = (uint64_t)tile * kTile;
-    const uint64_t rem = a.n - base;
-    const uint32_t npts = rem < (uint64_t)kTile ? (uint32_t)rem : (uint32_t)kTile;
-    const uint64_t keep = policy_evict_last();
-    uint32_t res[kItems], cnt[kItems];
-    bool multi = false;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const uint32_t loc = i * kThreads + tid;
-        res[i] = loc < npts ? __ldcs(a.res + base + loc) : kResNone;
-        cnt[i] = res[i] == kResNone ? 0u : 1u;
-        if (res[i] != kResNone && (res[i] & kResMulti)) {
-            // the point lies in several polygons: its count, stored or counted again
-            if (res[i] & kResCount) {
-                cnt[i] = (res[i] >> 20) & 0x3ffu;
-            } else {
-                const int2 p = a.pts[base + loc];
-                uint32_t f = 0, t = 0, e = 0;
-                cnt[i] = point_count<FP32>(a.ix, p.x, p.y, f, t, e, keep);
-            }
-            multi = true;
-        }
-    }
-    multi = __any_sync(kFull, multi);
-    uint32_t pre[kItems];
-    if (!multi) {
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const uint32_t bl = __ballot_sync(kFull, cnt[i] != 0);
-            pre[i] = __popc(bl & lanemask_lt());
-            if (lane == 0)
-                s_off[i * kWarps + warp] = __popc(bl);
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            uint32_t inc = cnt[i];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, inc, o);
-                if (lane >= o)
-                    inc += t;
-            }
-            pre[i] = inc - cnt[i];
-            if (lane == 31)
-                s_off[i * kWarps + warp] = inc;
-        }
-    }
-    __syncthreads();
-    if (warp == 0) {
-        // exclusive scan of the kItems x kWarps row totals, VPL per lane
-        constexpr int VPL = (kItems * kWarps + 31) / 32;
-        static_assert(kItems * kWarps <= 32 * VPL && VPL <= 4, "row totals per lane");
-        uint32_t v[VPL], lsum = 0;
-#pragma unroll
-        for (int j = 0; j < VPL; ++j) {
-            const int r = lane * VPL + j;
-            v[j] = r < kItems * kWarps ? s_off[r] : 0u;
-            lsum += v[j];
-        }
-        uint32_t inc = lsum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o)
-                inc += t;
-        }
-        uint32_t run = inc - lsum;
-#pragma unroll
-        for (int j = 0; j < VPL; ++j) {
-            const int r = lane * VPL + j;
-            if (r < kItems * kWarps)
-                s_off[r] = run;
-            run += v[j];
-        }
-    }
-    __syncthreads();
-    const unsigned long long tbase = tile_off[tile];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        if (!cnt[i])
-            continue;
-        const uint32_t loc = i * kThreads + tid;
-        const uint32_t pid = (uint32_t)(base + loc);
-        unsigned long long o = tbase + s_off[i * kWarps + warp] + pre[i];
-        if (!(res[i] & kResMulti)) {
-            if (o < a.cap)
-                __stcs(a.pairs + o, make_uint2(pid, res[i]));
-        } else {
-            const int2 p = a.pts[base + loc];
-            point_emit<FP32>(a.ix, p.x, p.y, keep, [&](uint32_t q) {
-                if (o < a.cap)
-                    __stcs(a.pairs + o, make_uint2(pid, q));
-                ++o;
-            });
-        }
-    }
-}
-
 // ------------------------------------------------------- plain comparison join
 // Exact int64 only; one thread per point; pass 1 counts per 256-point block,
 // a one-block scan makes block offsets, pass 2 recounts and writes.  Counts by
@@ -945,8 +529,11 @@ __device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
 }
 
 // ---------------------------------------------- warp-independent pass 1
-// The same pass as k_count without any CTA barrier in its loop: every warp
-// works alone on chunks of 32 x kWItems consecutive points (chunk c goes to
+// Pass 1 of the join (the counting pass of the two-pass Map, §5.1; with
+// RESOLVE it also stores every point's 4-byte result: none / its polygon /
+// "several" with their count) and, without RESOLVE, the count-only
+// aggregation that never materialises the join (§5.2).  No CTA barrier in
+// its loop: every warp works alone on chunks of 32 x kWItems consecutive points (chunk c goes to
 // warp c mod #warps), loads its points with coalesced 8-byte loads, resolves
 // the coarse and fine words of all of a lane's points with independent
 // loads, and queues its list points in a per-warp shared-memory queue that it
@@ -958,18 +545,12 @@ __device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
 #ifndef SPX_WARP_ITEMS
 #define SPX_WARP_ITEMS 8
 #endif
-#ifndef SPX_WARP_PREFETCH
-#define SPX_WARP_PREFETCH 0 // 1: the next chunk's points are loaded while this one is resolved
-#endif
 #ifndef SPX_WARP_MIN_BLOCKS
 #define SPX_WARP_MIN_BLOCKS 4
 #endif
 constexpr int kWItems = SPX_WARP_ITEMS; // points per lane per chunk (8: 256-point chunks)
 constexpr int kWChunk = 32 * kWItems;   // consecutive points per warp chunk
-#ifndef SPX_WARP_WALK_END
-#define SPX_WARP_WALK_END 1 // 1: a chunk's list points are all queued and walked after it is resolved
-#endif
-constexpr int kWQueue = SPX_WARP_WALK_END ? (kWChunk > 64 ? kWChunk : 64) : 64; // list points queued per warp
+constexpr int kWQueue = kWChunk;        // list points queued per warp: a whole chunk
 constexpr size_t kWarpSmem = size_t(kWarps) * kWQueue * sizeof(uint4);
 
 template <bool FP32, bool RESOLVE>
@@ -997,33 +578,17 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
             atomicAdd(a.counts + q, 1ull);
     };
     const uint32_t nw = gridDim.x * kWarps;
-    // the next chunk's points are loaded while this chunk is resolved
-    int2 pn[kWItems];
-    auto load_chunk = [&](uint32_t c) {
-        const uint64_t b = (uint64_t)c * kWChunk;
-        const uint32_t m = (uint32_t)min((uint64_t)kWChunk, a.n - b);
-#pragma unroll
-        for (int j = 0; j < kWItems; ++j) {
-            const uint32_t loc = j * 32 + lane;
-            pn[j] = loc < m ? __ldcs(a.pts + b + loc) : make_int2(-1, -1);
-        }
-    };
-    if (SPX_WARP_PREFETCH && blockIdx.x * kWarps + warp < nchunks)
-        load_chunk(blockIdx.x * kWarps + warp);
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
         const uint64_t base = (uint64_t)ch * kWChunk;
         const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
-        if (!SPX_WARP_PREFETCH)
-            load_chunk(ch);
         int2 p[kWItems];
         uint32_t w[kWItems];
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
-            p[j] = pn[j];
-            n_pts += j * 32 + lane < (int)npts ? 1u : 0u;
+            const uint32_t loc = j * 32 + lane;
+            p[j] = loc < npts ? __ldcs(a.pts + base + loc) : make_int2(-1, -1);
+            n_pts += loc < npts ? 1u : 0u;
         }
-        if (SPX_WARP_PREFETCH && ch + nw < nchunks)
-            load_chunk(ch + nw);
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             const bool ok = (unsigned)p[j].x < kBox && (unsigned)p[j].y < kBox;
@@ -1072,10 +637,6 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
                 s_q[qn + __popc(bl & lanemask_lt())] =
                     make_uint4((uint32_t)p[j].x, (uint32_t)p[j].y, w[j] & kPayloadMask, loc);
             qn += __popc(bl);
-            if (!SPX_WARP_WALK_END && qn >= 32) { // the newest 32 (qn <= 63 < kWQueue)
-                walk(qn - 32, 32);
-                qn -= 32;
-            }
         }
         for (uint32_t k0 = 0; k0 < qn; k0 += 32)
             walk(k0, min(qn - k0, 32u));
@@ -1106,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
         const uint64_t base = (uint64_t)ch * kWChunk;
         const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
-        unsigned long long run = chunk_off[ch];
+        unsigned long long run = chunk_off[ch] + (a.pair_base ? *a.pair_base : 0ull);
         uint32_t res[kWItems];
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
@@ -1144,7 +705,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
                 tot = __shfl_sync(kFull, inc, 31);
                 if (multi) {
                     unsigned long long o = run + pre;
-                    const uint32_t pid = (uint32_t)(base + loc);
+                    const uint32_t pid = a.pid0 + (uint32_t)(base + loc);
                     point_emit<FP32>(a.ix, p.x, p.y, keep, [&](uint32_t q) {
                         if (o < a.cap)
                             __stcs(a.pairs + o, make_uint2(pid, q));
@@ -1156,7 +717,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
             if (c) {
                 const unsigned long long o = run + pre;
                 if (o < a.cap)
-                    __stcs(a.pairs + o, make_uint2((uint32_t)(base + loc), r));
+                    __stcs(a.pairs + o, make_uint2(a.pid0 + (uint32_t)(base + loc), r));
             }
             run += tot;
         }
@@ -1480,19 +1041,6 @@ int persistent_grid(K kernel, int threads, size_t smem, uint32_t ntiles)
 }
 
 template <bool FP32, bool RESOLVE>
-cudaError_t launch_count_kernel(const JoinLaunch &a, uint32_t ntiles, int use_hist, cudaStream_t s)
-{
-    static bool done[64] = {};
-    const size_t smem = kCountSmem + (use_hist ? sizeof(uint32_t) * a.ix.P : 0);
-    cudaError_t e = smem_opt_in(k_count<FP32, RESOLVE>, kCountSmem + sizeof(uint32_t) * kHistMax, done);
-    if (e != cudaSuccess)
-        return e;
-    k_count<FP32, RESOLVE><<<persistent_grid(k_count<FP32, RESOLVE>, kThreads, smem, ntiles), kThreads, smem, s>>>(
-        a, ntiles, use_hist);
-    return cudaGetLastError();
-}
-
-template <bool FP32, bool RESOLVE>
 cudaError_t launch_warp_kernel(const JoinLaunch &a, int use_hist, cudaStream_t s)
 {
     static bool done[64] = {};
@@ -1551,6 +1099,51 @@ cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_
     return cudaGetLastError();
 }
 
+uint32_t join_chunk_points() { return kWChunk; }
+uint64_t join_part_words(uint64_t n) { return scan_partials((n + kWChunk - 1) / kWChunk) + 2; }
+
+cudaError_t launch_join_resolve(const JoinLaunch &a, unsigned long long *part, cudaStream_t s)
+{
+    const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
+    if (nchunks >= (1ull << 31))
+        return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(a.pts) & 15)
+        return cudaErrorMisalignedAddress;
+    if (nchunks == 0)
+        return a.total ? cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s) : cudaSuccess;
+    const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
+    cudaError_t e =
+        a.fp32 ? launch_warp_kernel<true, true>(a, use_hist, s) : launch_warp_kernel<false, true>(a, use_hist, s);
+    if (e != cudaSuccess)
+        return e;
+    return launch_scan(a.tile_tot, nchunks, a.total, part, s);
+}
+
+cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s)
+{
+    const uint32_t nchunks = uint32_t((a.n + kWChunk - 1) / kWChunk);
+    if (nchunks == 0 || a.cap == 0)
+        return cudaSuccess;
+    const uint32_t nblk = (nchunks + kWarps - 1) / kWarps;
+    if (a.fp32)
+        k_wemit<true><<<persistent_grid(k_wemit<true>, kThreads, 0, nblk), kThreads, 0, s>>>(a, a.tile_tot, nchunks);
+    else
+        k_wemit<false><<<persistent_grid(k_wemit<false>, kThreads, 0, nblk), kThreads, 0, s>>>(a, a.tile_tot, nchunks);
+    return cudaGetLastError();
+}
+
+__global__ void k_sum_u64(unsigned long long *dst, const unsigned long long *x, const unsigned long long *y)
+{
+    *dst = *x + *y;
+}
+
+cudaError_t launch_sum_u64(unsigned long long *dst, const unsigned long long *x, const unsigned long long *y,
+                           cudaStream_t s)
+{
+    k_sum_u64<<<1, 1, 0, s>>>(dst, x, y);
+    return cudaGetLastError();
+}
+
 int device_sm_count()
 {
     int dev = 0;
@@ -1562,10 +1155,9 @@ int device_sm_count()
 
 size_t join_scratch_bytes(uint64_t n)
 {
-    // per-point results | per-tile or per-chunk totals (then offsets) | scan partials | tile counter
-    const uint64_t ntiles = (n + kTile - 1) / kTile, nchunks = (n + kWChunk - 1) / kWChunk;
-    const uint64_t nt = ntiles > nchunks ? ntiles : nchunks;
-    return size_t(((n * 4 + 15) & ~uint64_t(15)) + (nt + scan_partials(nt) + 2) * 8 + 16);
+    // per-point results | per-chunk totals (then offsets) | scan partials
+    const uint64_t nchunks = (n + kWChunk - 1) / kWChunk;
+    return size_t(((n * 4 + 15) & ~uint64_t(15)) + (nchunks + join_part_words(n)) * 8 + 16);
 }
 
 size_t plain_scratch_bytes(uint64_t n)
@@ -1576,102 +1168,53 @@ size_t plain_scratch_bytes(uint64_t n)
 
 cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
 {
-    const uint64_t ntiles64 = (a.n + kTile - 1) / kTile, nchunks64 = (a.n + kWChunk - 1) / kWChunk;
-    if (nchunks64 >= (1ull << 31))
+    if ((a.n + kWChunk - 1) / kWChunk >= (1ull << 31))
         return cudaErrorInvalidValue;
-    if (reinterpret_cast<uintptr_t>(a.pts) & 15)
-        return cudaErrorMisalignedAddress;
-    const uint32_t ntiles = uint32_t(ntiles64), nchunks = uint32_t(nchunks64);
-    const uint64_t nt = ntiles64 > nchunks64 ? ntiles64 : nchunks64;
     JoinLaunch b = a;
     char *sc = static_cast<char *>(scratch);
     b.res = reinterpret_cast<uint32_t *>(sc);
     b.tile_tot = reinterpret_cast<unsigned long long *>(sc + ((a.n * 4 + 15) & ~uint64_t(15)));
-    unsigned long long *part = b.tile_tot + nt;
-    b.tile_counter = reinterpret_cast<unsigned *>(part + scan_partials(nt) + 2);
-    cudaError_t e = cudaMemsetAsync(b.tile_counter, 0, 16, s);
-    if (e != cudaSuccess)
-        return e;
-    if (a.counts && a.ix.P) {
-        e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.ix.P, s);
-        if (e != cudaSuccess)
+    unsigned long long *part = b.tile_tot + (a.n + kWChunk - 1) / kWChunk;
+    cudaError_t e;
+    if (a.counts && a.ix.P && !a.keep_counts)
+        if ((e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.ix.P, s)) != cudaSuccess)
             return e;
-    }
-    if (ntiles == 0) {
-        if (a.total)
-            return cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s);
-        return cudaSuccess;
-    }
-    // pass 1: resolve every point, count per polygon and per tile (chunk)
-    const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
+    if (a.n == 0)
+        return a.total ? cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s) : cudaSuccess;
+    // passes 1 and 2: resolve every point (counts per polygon, per-point
+    // results, per-chunk totals), then the offsets and the total
     if (ev)
         cudaEventRecord(ev[0], s);
-#if SPX_PASS1_WARP
+    const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
     e = a.fp32 ? launch_warp_kernel<true, true>(b, use_hist, s) : launch_warp_kernel<false, true>(b, use_hist, s);
-#else
-    e = a.fp32 ? launch_count_kernel<true, true>(b, ntiles, use_hist, s)
-               : launch_count_kernel<false, true>(b, ntiles, use_hist, s);
-#endif
     if (e != cudaSuccess)
         return e;
     if (ev)
         cudaEventRecord(ev[1], s);
-    // pass 2: offsets and the total
-#if SPX_PASS1_WARP
-    if ((e = launch_scan(b.tile_tot, nchunks, a.total, part, s)) != cudaSuccess)
+    if ((e = launch_scan(b.tile_tot, (a.n + kWChunk - 1) / kWChunk, a.total, part, s)) != cudaSuccess)
         return e;
-#else
-    k_scan<<<1, 1024, 0, s>>>(b.tile_tot, ntiles, a.total);
-#endif
     if (ev)
         cudaEventRecord(ev[2], s);
     // pass 3: pairs in point order
-    if (a.cap) {
-#if SPX_PASS1_WARP
-        const uint32_t nblk = (nchunks + kWarps - 1) / kWarps;
-        if (a.fp32)
-            k_wemit<true><<<persistent_grid(k_wemit<true>, kThreads, 0, nblk), kThreads, 0, s>>>(b, b.tile_tot,
-                                                                                             nchunks);
-        else
-            k_wemit<false><<<persistent_grid(k_wemit<false>, kThreads, 0, nblk), kThreads, 0, s>>>(b, b.tile_tot,
-                                                                                               nchunks);
-#else
-        if (a.fp32)
-            k_emit<true><<<ntiles, kThreads, 0, s>>>(b, b.tile_tot);
-        else
-            k_emit<false><<<ntiles, kThreads, 0, s>>>(b, b.tile_tot);
-#endif
-    }
+    if ((e = launch_join_emit(b, s)) != cudaSuccess)
+        return e;
     if (ev)
         cudaEventRecord(ev[3], s);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
 {
+    (void)scratch;
     cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * (a.ix.P ? a.ix.P : 1), s);
     if (e != cudaSuccess || a.n == 0)
         return e;
     if (reinterpret_cast<uintptr_t>(a.pts) & 15)
         return cudaErrorMisalignedAddress;
-    const uint64_t ntiles64 = (a.n + kTile - 1) / kTile;
-    if (ntiles64 >= (1ull << 31))
-        return cudaErrorInvalidValue;
-    const uint32_t ntiles = uint32_t(ntiles64);
-    JoinLaunch b = a;
-    b.tile_counter = reinterpret_cast<unsigned *>(scratch);
-    e = cudaMemsetAsync(scratch, 0, 16, s);
-    if (e != cudaSuccess)
-        return e;
     const int use_hist = a.ix.P <= (uint32_t)kHistMax ? 1 : 0;
     if (ev)
         cudaEventRecord(ev[0], s);
-#if SPX_PASS1_WARP
-    e = a.fp32 ? launch_warp_kernel<true, false>(b, use_hist, s) : launch_warp_kernel<false, false>(b, use_hist, s);
-#else
-    e = a.fp32 ? launch_count_kernel<true, false>(b, ntiles, use_hist, s)
-               : launch_count_kernel<false, false>(b, ntiles, use_hist, s);
-#endif
+    e = a.fp32 ? launch_warp_kernel<true, false>(a, use_hist, s) : launch_warp_kernel<false, false>(a, use_hist, s);
     if (ev)
         cudaEventRecord(ev[1], s);
     return e;

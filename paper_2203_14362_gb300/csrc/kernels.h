@@ -39,11 +39,16 @@ struct JoinLaunch {
     unsigned long long *counts;   // P entries or null; zeroed by the launcher
     unsigned long long *total;    // device total or null
     uint32_t *res;                // join pass 1 -> 3: per-point result (scratch)
-    unsigned long long *tile_tot; // join: per-tile pair totals, then offsets (scratch)
-    unsigned *tile_counter;       // tile claims (scratch)
+    unsigned long long *tile_tot; // join: per-chunk pair totals, then offsets (scratch)
     unsigned *err;                // persistent error word
     unsigned long long *stats;    // kStatCount counters
     int fp32;
+    // chunked joins (a slice of a larger table): point ids are pid0 + row;
+    // pair offsets start at *pair_base (device, null: 0); keep_counts: counts
+    // are not zeroed (they accumulate over the slices)
+    uint32_t pid0;
+    int keep_counts;
+    const unsigned long long *pair_base;
 };
 
 // Scratch bytes the join needs for n points (per-point results, tile totals, counter).
@@ -55,7 +60,7 @@ size_t plain_scratch_bytes(uint64_t n);
 // (scan) and after pass 3 (emit).
 cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s);
-// scratch: at least 16 bytes of device memory (zeroed inside).
+// scratch: unused (may be null).
 cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // Batched selection: per-query ascending point-id lists in ids (cap entries),
@@ -108,6 +113,20 @@ cudaError_t launch_multi_emit(const MultiLaunch &m, void *scratch, cudaStream_t 
 size_t plain_split_scratch_bytes(uint64_t n);
 cudaError_t launch_plain_count(const JoinLaunch &a, void *scratch, cudaStream_t s);
 cudaError_t launch_plain_write(const JoinLaunch &a, void *scratch, cudaStream_t s);
+
+// The join's passes as separate launches, for callers that pipeline slices of
+// a table: a.res (4 B per point) and a.tile_tot (one u64 per
+// join_chunk_points() points) are given by the caller.  resolve = pass 1 and
+// the scan (*a.total = the slice's pair total; part: join_part_words(n) u64);
+// emit = pass 3.
+uint32_t join_chunk_points();
+uint64_t join_part_words(uint64_t n);
+cudaError_t launch_join_resolve(const JoinLaunch &a, unsigned long long *part, cudaStream_t s);
+cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s);
+
+// *dst = *x + *y (one thread; sliced joins chain their pair offsets).
+cudaError_t launch_sum_u64(unsigned long long *dst, const unsigned long long *x, const unsigned long long *y,
+                           cudaStream_t s);
 
 // dst[i] = src[i * (n / m)] for i < m (m <= n): the tuner's deterministic sample.
 cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_t m, cudaStream_t s);

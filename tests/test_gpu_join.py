@@ -188,6 +188,40 @@ def test_join_host_end_to_end(eng):
     eng.free(gh)
 
 
+@pytest.mark.parametrize("pinned", [False, True])
+def test_join_host_slices(eng, pinned):
+    # three 2^23-point slices, the last one ragged, overlapping polygons (a
+    # point can have several pairs, so slice offsets do not follow point ids)
+    mix = g.make_mixture(g.SEED_BASE + 60)
+    pts = g.mixture_points((1 << 24) + 123_457, g.SEED_BASE + 60, mix)
+    v, o = g.query_polygons(40, g.SEED_BASE + 60, mix, r_med=0.05, r_clip=(0.01, 0.2))
+    ref = oracle.Prepared(v, o)
+    want_p, want_c = ref.join(pts)
+    ref.close()
+    assert want_p.shape[0] > 0 and np.any(np.bincount(want_p[:, 0].astype(np.int64)) > 1)
+    gh = eng.load_polygons(v, o)
+    ih = eng.build_index(gh)
+    P = o.shape[0] - 1
+    cap = want_p.shape[0] + 5
+    if pinned:
+        hp = torch.empty((cap, 2), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        hx = torch.empty(pts.shape, dtype=torch.int32, pin_memory=True).numpy()
+        hx[:] = pts
+    else:
+        hp, hx = None, pts
+    p, c, n = eng.join_host(hx, ih, cap=cap, n_polys=P, pairs_out=hp)
+    assert n == want_p.shape[0] and np.array_equal(p, want_p) and np.array_equal(c, want_c)
+    # a capacity that runs out in the middle slice: the first cap pairs, then the error
+    small = want_p.shape[0] // 2
+    buf = np.zeros((small, 2), np.uint32)
+    with pytest.raises(spx.SpxError) as ei:
+        eng.join_host(hx, ih, cap=small, n_polys=P, pairs_out=buf)
+    assert ei.value.status == spx.SPX_ECAPACITY
+    assert np.array_equal(buf, want_p[:small])
+    eng.free(ih)
+    eng.free(gh)
+
+
 def test_bad_arguments(eng):
     with pytest.raises(spx.SpxError):
         eng.load_points(np.array([[1 << 30, 0]], np.int32))
