@@ -607,10 +607,12 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
         auto walk = [&](uint32_t k0, uint32_t m) {
             __syncwarp();
             const bool has = (uint32_t)lane < m;
-            const uint4 it = s_q[k0 + (has ? lane : 0)];
-            uint32_t f = 0;
-            uint32_t c = walk_list<FP32>(ix, it.z, (int)it.x, (int)it.y, f, n_tests, n_esc, keep);
+            const uint4 it = s_q[k0 + (has ? lane : 0)]; // idle lanes repeat lane 0's walk, uncounted
+            uint32_t f = 0, t_l = 0, e_l = 0;
+            uint32_t c = walk_list<FP32>(ix, it.z, (int)it.x, (int)it.y, f, t_l, e_l, keep);
             c = has ? c : 0u;
+            n_tests += has ? t_l : 0u;
+            n_esc += has ? e_l : 0u;
             total += c;
             count1(c == 1, f);
             if (c > 1 && a.counts)
@@ -729,14 +731,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
 // the points: the point table is read once per pass for the whole batch
 // instead of once per request (the one-pass batched selection of §5.2,
 // applied across requests).  Two passes, as in the Map of §5.1: the count pass
-// counts every request's pairs per tile of kMTile points, and its per-polygon
-// counts; the per-request tile totals are scanned; the emit pass counts again,
-// keeps each (request, point) result in shared memory, and writes every
-// request's pairs in (point, polygon) order from its tile's offset.  Tiles go
-// to CTAs round-robin; the output never depends on the schedule.
-constexpr int kMTile = 1024;               // points per tile
-constexpr int kMPerWarp = kMTile / kWarps; // consecutive points per warp
-constexpr size_t kMultiSmemHead = kMTile * sizeof(int2) + kWarps * kMaxBatch * (8 + 4);
+// counts every request's pairs per warp chunk (and the join requests'
+// per-polygon counts); the per-request chunk totals are scanned; the emit pass
+// resolves again and writes every request's pairs in (point, polygon) order
+// from its chunk's offset.  As in k_warp, every warp works alone on its
+// chunks (loaded once for all requests) and walks list points from a
+// per-warp queue; the output never depends on the schedule.
+constexpr uint32_t kMPending = 0xffffffffu; // a list point whose walk is queued
+#ifndef SPX_MULTI_ITEMS
+#define SPX_MULTI_ITEMS 4
+#endif
+constexpr int kMItems = SPX_MULTI_ITEMS;                      // points per lane per chunk
+constexpr int kMChunk = 32 * kMItems;                         // consecutive points per warp chunk
+constexpr size_t kMultiSmem = size_t(kWarps) * kMChunk * sizeof(uint4); // per-warp queues
 
 // Does the cover bitmap let (px, py) reach a non-empty coarse cell?  False for
 // points outside the box.
@@ -750,97 +757,122 @@ __device__ __forceinline__ bool covered(const IndexView &ix, int px, int py)
 
 template <bool FP32, bool EMIT>
 __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ MultiLaunch m,
-                                                    unsigned long long *tile_tot, uint32_t ntiles, int use_hist)
+                                                    unsigned long long *chunk_tot, uint32_t nchunks, int use_hist)
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
-    int2 *s_pts = reinterpret_cast<int2 *>(s_raw);                                       // kMTile points
-    unsigned long long *s_woff = reinterpret_cast<unsigned long long *>(s_pts + kMTile); // kWarps x kMaxBatch
-    uint32_t *s_wtot = reinterpret_cast<uint32_t *>(s_woff + kWarps * kMaxBatch);        // kWarps x kMaxBatch
-    uint32_t *s_tail = s_wtot + kWarps * kMaxBatch; // emit: K x kMTile results; count: qbase[K] counters
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kMChunk; // (x, y, first entry) -> (count, first)
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_raw + kMultiSmem); // count pass: qbase[K] counters
     const uint64_t keep = policy_evict_last();
     const int K = m.K;
     uint32_t tests = 0, esc = 0, scanned = 0, emitted = 0;
     if (!EMIT && use_hist)
         for (uint32_t i = threadIdx.x; i < m.qbase[K]; i += kThreads)
-            s_tail[i] = 0;
+            s_hist[i] = 0;
     __syncthreads();
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t base = (uint64_t)t * kMTile;
-        const uint32_t npts = (uint32_t)min((uint64_t)kMTile, m.n - base);
-        for (uint32_t i = threadIdx.x; i < (uint32_t)kMTile; i += kThreads)
-            s_pts[i] = i < npts ? __ldcs(m.pts + base + i) : make_int2(-1, -1);
-        if (!EMIT && threadIdx.x == 0)
-            scanned += npts * (uint32_t)K;
-        __syncthreads();
-        // every request's count (and, in the emit pass, result) per point
+    const uint32_t nw = gridDim.x * kWarps;
+    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+        const uint64_t base = (uint64_t)ch * kMChunk;
+        const uint32_t npts = (uint32_t)min((uint64_t)kMChunk, m.n - base);
+        int2 p[kMItems];
+#pragma unroll
+        for (int j = 0; j < kMItems; ++j) {
+            const uint32_t loc = j * 32 + lane;
+            p[j] = loc < npts ? __ldcs(m.pts + base + loc) : make_int2(-1, -1);
+            if (!EMIT)
+                scanned += loc < npts ? (uint32_t)K : 0u;
+        }
         for (int r = 0; r < K; ++r) {
             const IndexView &ix = m.ix[r];
-            uint32_t *h = s_tail + m.qbase[r];
-            unsigned long long *cnt = m.counts[r];
-            uint32_t wsum = 0;
-            for (int k = 0; k < kMPerWarp; k += 32) {
-                const uint32_t i = warp * kMPerWarp + k + lane;
-                const int2 p = s_pts[i];
-                uint32_t first = 0, c = 0;
-                if (covered(ix, p.x, p.y))
-                    c = point_count<FP32>(ix, p.x, p.y, first, tests, esc, keep);
-                wsum += c;
-                if (EMIT) {
-                    s_tail[r * kMTile + i] = res_encode(c, first);
-                } else if (cnt && use_hist) {
-                    hist_add_warp(h, c == 1, first);
-                    if (c > 1)
-                        point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(h + q, 1u); });
-                } else if (cnt) {
-                    if (c == 1)
-                        atomicAdd(cnt + first, 1ull);
-                    else if (c > 1)
-                        point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(cnt + q, 1ull); });
+            uint32_t c[kMItems], f[kMItems];
+#pragma unroll
+            for (int j = 0; j < kMItems; ++j) {
+                const bool ok = covered(ix, p[j].x, p[j].y);
+                const uint32_t cw = coarse_word(ix, ok ? (uint32_t)p[j].x : 0u, ok ? (uint32_t)p[j].y : 0u, keep);
+                f[j] = ok ? cw : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < kMItems; ++j) {
+                const bool sub = (f[j] >> 30) == kCellSub;
+                const uint32_t fw = fine_word(ix, sub ? f[j] : 0u, sub ? (uint32_t)p[j].x : 0u,
+                                              sub ? (uint32_t)p[j].y : 0u, keep);
+                f[j] = sub ? fw : f[j];
+            }
+            // one INSIDE polygon: done; a list: queued
+            uint32_t qn = 0;
+#pragma unroll
+            for (int j = 0; j < kMItems; ++j) {
+                const uint32_t kind = f[j] >> 30;
+                const bool lst = kind == kCellList;
+                c[j] = kind == kCellInsideOne ? 1u : 0u;
+                const uint32_t bl = __ballot_sync(kFull, lst);
+                if (lst) {
+                    const uint32_t slot = qn + __popc(bl & lanemask_lt());
+                    s_q[slot] = make_uint4((uint32_t)p[j].x, (uint32_t)p[j].y, f[j] & kPayloadMask, 0u);
+                    c[j] = kMPending;
+                    f[j] = slot;
+                } else {
+                    f[j] &= kPayloadMask;
                 }
+                qn += __popc(bl);
             }
-            wsum = warp_sum32(wsum);
-            if (lane == 0)
-                s_wtot[warp * kMaxBatch + r] = wsum;
-        }
-        __syncthreads();
-        if (!EMIT) {
-            // per-request tile totals (the next tile's staging waits for warp 0
-            // at its barrier, so s_wtot is read before it is rewritten)
-            if ((int)threadIdx.x < K) {
-                unsigned long long sum = 0;
-                for (int w = 0; w < kWarps; ++w)
-                    sum += s_wtot[w * kMaxBatch + threadIdx.x];
-                tile_tot[(uint64_t)threadIdx.x * ntiles + t] = sum;
+            __syncwarp();
+            for (uint32_t k0 = 0; k0 < qn; k0 += 32) {
+                const bool has = k0 + lane < qn;
+                const uint4 it = s_q[has ? k0 + lane : k0]; // idle lanes repeat the first walk, uncounted
+                uint32_t fq = 0, t_l = 0, e_l = 0;
+                const uint32_t cq = walk_list<FP32>(ix, it.z, (int)it.x, (int)it.y, fq, t_l, e_l, keep);
+                if (!EMIT && has) {
+                    tests += t_l;
+                    esc += e_l;
+                }
+                __syncwarp();
+                if (has)
+                    s_q[k0 + lane] = make_uint4(cq, fq, 0u, 0u);
+                __syncwarp();
             }
-            continue;
-        }
-        // emit pass: start of every (warp, request) run of pairs
-        if ((int)threadIdx.x < K) {
-            const int r = threadIdx.x;
-            unsigned long long run = tile_tot[(uint64_t)r * ntiles + t];
-            for (int w = 0; w < kWarps; ++w) {
-                s_woff[w * kMaxBatch + r] = run;
-                run += s_wtot[w * kMaxBatch + r];
+#pragma unroll
+            for (int j = 0; j < kMItems; ++j)
+                if (c[j] == kMPending) {
+                    const uint4 q = s_q[f[j]];
+                    c[j] = q.x;
+                    f[j] = q.y;
+                }
+            __syncwarp(); // s_q is rewritten for the next request
+            unsigned long long *cnt = m.counts[r];
+            if (!EMIT) {
+                uint32_t total = 0;
+                uint32_t *h = s_hist + m.qbase[r];
+#pragma unroll
+                for (int j = 0; j < kMItems; ++j) {
+                    total += c[j];
+                    if (!cnt)
+                        continue;
+                    if (use_hist)
+                        hist_add_warp(h, c[j] == 1, f[j]);
+                    else if (c[j] == 1)
+                        atomicAdd(cnt + f[j], 1ull);
+                    if (c[j] > 1)
+                        point_emit<FP32>(ix, p[j].x, p[j].y, keep, [&](uint32_t q) {
+                            if (use_hist)
+                                atomicAdd(h + q, 1u);
+                            else
+                                atomicAdd(cnt + q, 1ull);
+                        });
+                }
+                total = warp_sum32(total);
+                if (lane == 0)
+                    chunk_tot[(uint64_t)r * nchunks + ch] = total;
+                continue;
             }
-        }
-        __syncthreads();
-        for (int r = 0; r < K; ++r) {
-            const IndexView &ix = m.ix[r];
+            // emit: pairs of request r in point order from the chunk's offset
             uint2 *out = m.pairs[r];
             const uint64_t cap = m.cap[r];
-            unsigned long long run = s_woff[warp * kMaxBatch + r];
-            for (int k = 0; k < kMPerWarp; k += 32) {
-                const uint32_t i = warp * kMPerWarp + k + lane;
-                const uint32_t res = s_tail[r * kMTile + i];
-                const int2 p = s_pts[i];
-                uint32_t c = res == kResNone ? 0u : !(res & kResMulti) ? 1u
-                             : (res & kResCount) ? ((res >> 20) & 0x3ffu) : 0xffffffffu;
-                if (c == 0xffffffffu) { // count not stored: count again
-                    uint32_t f = 0, t2 = 0, e2 = 0;
-                    c = point_count<FP32>(ix, p.x, p.y, f, t2, e2, keep);
-                }
-                uint32_t inc = c;
+            unsigned long long run = chunk_tot[(uint64_t)r * nchunks + ch];
+#pragma unroll
+            for (int j = 0; j < kMItems; ++j) {
+                const uint32_t loc = j * 32 + lane, cj = c[j];
+                uint32_t inc = cj;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t v = __shfl_up_sync(kFull, inc, o);
@@ -848,28 +880,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
                         inc += v;
                 }
                 const uint32_t wtot = __shfl_sync(kFull, inc, 31);
-                unsigned long long o = run + inc - c;
-                const uint32_t pid = (uint32_t)(base + i);
-                if (c == 1) {
+                unsigned long long o = run + inc - cj;
+                const uint32_t pid = (uint32_t)(base + loc);
+                if (cj == 1) {
                     if (o < cap)
-                        out[o] = make_uint2(pid, res);
-                } else if (c > 1) {
-                    point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) {
+                        out[o] = make_uint2(pid, f[j]);
+                } else if (cj > 1) {
+                    point_emit<FP32>(ix, p[j].x, p[j].y, keep, [&](uint32_t q) {
                         if (o < cap)
                             out[o] = make_uint2(pid, q);
                         ++o;
                     });
                 }
-                emitted += c;
+                emitted += cj;
                 run += wtot;
             }
         }
-        __syncthreads(); // s_pts, s_woff and s_tail are rewritten by the next tile
     }
     if (!EMIT && use_hist) {
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < m.qbase[K]; i += kThreads) {
-            const uint32_t v = s_tail[i];
+            const uint32_t v = s_hist[i];
             if (!v)
                 continue;
             int r = 0;
@@ -878,7 +909,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
             atomicAdd(m.counts[r] + (i - m.qbase[r]), (unsigned long long)v);
         }
     }
-    add_stats(m.stats, scanned, EMIT ? 0u : tests, EMIT ? 0u : esc, emitted);
+    add_stats(m.stats, scanned, tests, esc, emitted);
 }
 
 // ------------------------------------------------------ batched selection
@@ -1312,7 +1343,7 @@ cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s
 
 // ------------------------------------------------------ multi-request launchers
 namespace {
-uint64_t multi_ntiles(uint64_t n) { return (n + kMTile - 1) / kMTile; }
+uint64_t multi_ntiles(uint64_t n) { return (n + kMChunk - 1) / kMChunk; }
 uint64_t multi_part_words(uint64_t ntiles) { return scan_partials(ntiles) + 2; }
 } // namespace
 
@@ -1348,17 +1379,17 @@ cudaError_t launch_multi_count(const MultiLaunch &m, void *scratch, cudaStream_t
     unsigned long long *tile_tot = static_cast<unsigned long long *>(scratch);
     unsigned long long *part = tile_tot + uint64_t(m.K) * nt;
     const int use_hist = m.qbase[m.K] <= kMultiHistMax ? 1 : 0;
-    const size_t smem = kMultiSmemHead + (use_hist ? sizeof(uint32_t) * m.qbase[m.K] : 0);
+    const size_t smem = kMultiSmem + (use_hist ? sizeof(uint32_t) * m.qbase[m.K] : 0);
     static bool done[2][64] = {};
     if (m.fp32) {
-        if ((e = smem_opt_in(k_multi<true, false>, kMultiSmemHead + 4 * kMultiHistMax, done[0])) != cudaSuccess)
+        if ((e = smem_opt_in(k_multi<true, false>, kMultiSmem + 4 * kMultiHistMax, done[0])) != cudaSuccess)
             return e;
-        k_multi<true, false><<<persistent_grid(k_multi<true, false>, kThreads, smem, uint32_t(nt)), kThreads, smem,
+        k_multi<true, false><<<persistent_grid(k_multi<true, false>, kThreads, smem, uint32_t((nt + kWarps - 1) / kWarps)), kThreads, smem,
                                s>>>(m, tile_tot, uint32_t(nt), use_hist);
     } else {
-        if ((e = smem_opt_in(k_multi<false, false>, kMultiSmemHead + 4 * kMultiHistMax, done[1])) != cudaSuccess)
+        if ((e = smem_opt_in(k_multi<false, false>, kMultiSmem + 4 * kMultiHistMax, done[1])) != cudaSuccess)
             return e;
-        k_multi<false, false><<<persistent_grid(k_multi<false, false>, kThreads, smem, uint32_t(nt)), kThreads,
+        k_multi<false, false><<<persistent_grid(k_multi<false, false>, kThreads, smem, uint32_t((nt + kWarps - 1) / kWarps)), kThreads,
                                 smem, s>>>(m, tile_tot, uint32_t(nt), use_hist);
     }
     if ((e = cudaGetLastError()) != cudaSuccess)
@@ -1379,18 +1410,18 @@ cudaError_t launch_multi_emit(const MultiLaunch &m, void *scratch, cudaStream_t 
     if (nt == 0)
         return cudaSuccess;
     unsigned long long *tile_tot = static_cast<unsigned long long *>(scratch);
-    const size_t smem = kMultiSmemHead + sizeof(uint32_t) * kMTile * m.K;
+    const size_t smem = kMultiSmem;
     static bool done[2][64] = {};
-    const size_t smem_max = kMultiSmemHead + sizeof(uint32_t) * kMTile * kMaxBatch;
+    const size_t smem_max = kMultiSmem;
     if (m.fp32) {
         if ((e = smem_opt_in(k_multi<true, true>, smem_max, done[0])) != cudaSuccess)
             return e;
-        k_multi<true, true><<<persistent_grid(k_multi<true, true>, kThreads, smem, uint32_t(nt)), kThreads, smem,
+        k_multi<true, true><<<persistent_grid(k_multi<true, true>, kThreads, smem, uint32_t((nt + kWarps - 1) / kWarps)), kThreads, smem,
                               s>>>(m, tile_tot, uint32_t(nt), 0);
     } else {
         if ((e = smem_opt_in(k_multi<false, true>, smem_max, done[1])) != cudaSuccess)
             return e;
-        k_multi<false, true><<<persistent_grid(k_multi<false, true>, kThreads, smem, uint32_t(nt)), kThreads, smem,
+        k_multi<false, true><<<persistent_grid(k_multi<false, true>, kThreads, smem, uint32_t((nt + kWarps - 1) / kWarps)), kThreads, smem,
                                s>>>(m, tile_tot, uint32_t(nt), 0);
     }
     return cudaGetLastError();

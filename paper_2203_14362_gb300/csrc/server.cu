@@ -72,8 +72,9 @@ struct spx_server {
     cudaStream_t release_stream = nullptr;
     std::vector<std::unique_ptr<Slot>> slots;
     std::thread worker;
-    std::mutex mu;
-    std::condition_variable cv;      // wakes the worker
+    std::mutex mu;                   // server state (the worker holds it across CUDA calls)
+    std::mutex cv_mu;                // wake-ups only: never held across a CUDA call
+    std::condition_variable cv;      // wakes the worker (with cv_mu)
     std::condition_variable cv_done; // wakes waiters
     std::deque<Req *> queue;
     std::map<uint64_t, std::unique_ptr<Req>> reqs;
@@ -85,6 +86,15 @@ struct spx_server {
     std::atomic<int> events{0};
 
     double now_ms() const { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
+    // count an event that may let the worker progress and wake it
+    void signal()
+    {
+        {
+            std::lock_guard<std::mutex> lk(cv_mu);
+            events.fetch_add(1);
+        }
+        cv.notify_all();
+    }
     void run();
     void start_batch(Slot &sl);
     void counted(Slot &sl);
@@ -97,18 +107,16 @@ namespace {
 
 void CUDART_CB on_stream_point(void *p)
 {
-    // Runs on a CUDA thread: no CUDA calls here.  The server mutex is taken so
-    // that the worker cannot miss the wake-up between its check and its wait
-    // (the worker makes no blocking CUDA call while it holds the mutex).
+    // Runs on CUDA's host-function thread: no CUDA calls here, and never the
+    // server mutex -- the worker holds that across CUDA calls, some of which
+    // (lazy module loading on a kernel's first launch, for one) can wait for
+    // pending host functions.  The slot's flag is atomic; the wake-up goes
+    // through cv_mu, which nobody holds across a CUDA call.
     Slot *sl = static_cast<Slot *>(p);
     spx_server *srv = sl->srv;
-    {
-        std::lock_guard<std::mutex> lk(srv->mu);
-        sl->t_cb.store(srv->now_ms());
-        sl->flag.fetch_add(1);
-        srv->events.fetch_add(1);
-    }
-    srv->cv.notify_all();
+    sl->t_cb.store(srv->now_ms());
+    sl->flag.fetch_add(1);
+    srv->signal();
 }
 
 size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -384,8 +392,10 @@ void spx_server::written(Slot &sl)
 void spx_server::run()
 {
     cudaSetDevice(data.device);
-    std::unique_lock<std::mutex> lk(mu);
     for (;;) {
+        // events seen before this pass: any later one ends the wait below
+        const int ev0 = events.load();
+        std::unique_lock<std::mutex> lk(mu);
         bool progress = false;
         for (auto &up : slots) {
             Slot &sl = *up;
@@ -413,9 +423,10 @@ void spx_server::run()
             if (idle)
                 break;
         }
+        lk.unlock();
         if (!progress) {
-            const int ev = events.load();
-            cv.wait_for(lk, std::chrono::microseconds(500), [&] { return events.load() != ev; });
+            std::unique_lock<std::mutex> lw(cv_mu);
+            cv.wait_for(lw, std::chrono::milliseconds(50), [&] { return events.load() != ev0; });
         }
     }
 }
@@ -539,8 +550,7 @@ spx_status spx_server_submit(spx_server *srv, const spx_request *req, uint64_t *
     *req_id = r->id;
     srv->reqs[r->id] = std::move(r);
     srv->st.submitted++;
-    srv->events.fetch_add(1);
-    srv->cv.notify_all();
+    srv->signal();
     return SPX_OK;
 }
 
@@ -657,8 +667,7 @@ spx_status spx_server_release(spx_server *srv, uint64_t req_id)
     pool_free(r->counts, srv->release_stream);
     srv->used -= r->out_bytes + r->counts_bytes;
     srv->reqs.erase(it);
-    srv->events.fetch_add(1); // a batch may be waiting for budget
-    srv->cv.notify_all();
+    srv->signal(); // a batch may be waiting for budget
     return SPX_OK;
 }
 
@@ -689,9 +698,8 @@ void spx_server_destroy(spx_server *srv)
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->stopping = true;
-        srv->events.fetch_add(1);
     }
-    srv->cv.notify_all();
+    srv->signal();
     if (srv->worker.joinable())
         srv->worker.join();
     cudaSetDevice(srv->data.device);
