@@ -35,11 +35,11 @@ if ROOT not in sys.path:
 METRIC = "billion points joined/sec and % HBM roofline; serving p50/p99 ms vs plain kernel"
 UNIT = "Gpoints/s"
 L2_BYTES = 129 * 1024 * 1024
-# DRAM bytes (read + write) per point of the dominant kernel (join pass 1) from
-# the ncu capture summarised in profiles/k_count_resolve_tess2000_20m.md; only
-# valid for that kernel version, the default index (g = 11, sub = 3) and the
-# default workload.
-RESOLVE_TRAFFIC_BYTES_PER_POINT = None
+# DRAM bytes (read + write) per point of the dominant kernel (join pass 1,
+# k_warp) from one ncu capture of a 20M-point run of the default workload,
+# scaled per point; only valid for that kernel version, the default index
+# (g = 11, sub = 3) and the default workload.
+RESOLVE_TRAFFIC_BYTES_PER_POINT = (298.410496e6 + 62.456576e6) / 20e6
 SERVE_SEED = 0x2203143620 + 4  # request indexes of the serving measurement
 
 
