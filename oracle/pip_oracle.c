@@ -285,6 +285,11 @@ static void *fast_worker(void *arg)
     const oracle_t *o = j->o;
     for (uint64_t i = j->lo; i < j->hi; ++i) {
         int32_t px = j->pts[2 * i], py = j->pts[2 * i + 1];
+        /* every vertex lies in [0, 2^30]^2 and the half-open rule leaves the
+         * box's right and top sides outside, so a point outside [0, 2^30)^2 is
+         * in no polygon (and has no bucket) */
+        if (px < 0 || py < 0 || px >= (1 << ORACLE_BOX_LOG2) || py >= (1 << ORACLE_BOX_LOG2))
+            continue;
         uint64_t k = (uint64_t)(py >> o->bucket_log2) * o->nb + (uint64_t)(px >> o->bucket_log2);
         for (uint64_t m = o->bucket_off[k]; m < o->bucket_off[k + 1]; ++m) { /* (s3) */
             uint32_t q = o->bucket_poly[m];

@@ -305,6 +305,25 @@ def test_pure_equals_fast(olib):
             assert np.array_equal(cp, cf)
 
 
+def test_points_outside_the_box(olib):
+    # vertices lie in [0, 2^30]^2: a point outside [0, 2^30)^2 is in no polygon
+    # (the box's right and top sides are outside under the half-open rule);
+    # the pure mode tests every edge, the fast mode must agree
+    box = 1 << 30
+    v = np.array([[0, 0], [box, 0], [box, box], [0, box]], np.int32)
+    o = np.array([0, 4], np.uint64)
+    pts = np.array([[5, 5], [-1, 5], [5, -1], [box, 5], [5, box], [-(1 << 31), 7], [(1 << 31) - 1, 0],
+                    [(1 << 31) - 1, (1 << 31) - 1], [box - 1, box - 1], [0, 0]], np.int32)
+    t = g.quad_tessellation(4, 3, 9, kmin=2, kmax=20)
+    for vv, oo in ((v, o), (t.verts, t.ring_off)):
+        pp, cp = oracle.join_pure(pts, vv, oo, olib)
+        pr = oracle.Prepared(vv, oo, olib)
+        pf, cf = pr.join(pts, threads=2)
+        pr.close()
+        assert np.array_equal(pp, pf) and np.array_equal(cp, cf)
+        assert sorted(set(pp[:, 0].tolist())) == [0, 8, 9]  # only the three points inside the box
+
+
 def test_metamorphic_translation_reversal_rotation(olib):
     rng = np.random.default_rng(17)
     mix = g.make_mixture(12)
