@@ -563,6 +563,19 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     # properties that hold at any size: the tessellation covers the box, so
     # every point lies in exactly one cell
     assert int(counts.sum().item()) == N, "sum of counts != number of points"
+    cluster = None
+    ph_run = ph
+    if args.cluster:
+        # one-off: a copy grouped by grid cell (load time, outside the timed steps)
+        t0 = time.perf_counter()
+        ph_run = eng.cluster_points(ph, args.cluster)
+        cl_s = time.perf_counter() - t0
+        c2 = torch.zeros(P, dtype=torch.int64, device="cuda")
+        eng.aggregate(ph_run, ih, c2, stream=stream)
+        torch.cuda.synchronize()
+        assert torch.equal(c2, counts), "clustered counts differ from the row-order counts"
+        cluster = {"grid_log2": args.cluster, "seconds": round(cl_s, 3),
+                   "check": "counts on the clustered copy == counts on the row-order table"}
     # the first points' counts against the oracle
     m = min(head.shape[0], 2_000_000)
     ph_head = eng.load_points(dpts[:m])
@@ -574,7 +587,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     assert np.array_equal(c_head.cpu().numpy().view(np.uint64), ref), "prefix counts differ from the oracle"
     eng.free(ph_head)
     for _ in range(args.warmup):
-        eng.aggregate(ph, ih, counts, stream=stream)
+        eng.aggregate(ph_run, ih, counts, stream=stream)
     torch.cuda.synchronize()
     eng.stats(reset=True)
     barrier(world)
@@ -583,7 +596,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     t_host0 = time.time()
     e0.record(stream)
     for _ in range(args.steps):
-        eng.aggregate(ph, ih, counts, stream=stream)
+        eng.aggregate(ph_run, ih, counts, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     t_host1 = time.time()
@@ -594,7 +607,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     clk = clocks.summary(t_host0, t_host1)
     eng.set_phase_timing(True)
     for _ in range(max(1, min(args.steps, 5))):
-        eng.aggregate(ph, ih, counts, stream=stream)
+        eng.aggregate(ph_run, ih, counts, stream=stream)
     torch.cuda.synchronize()
     ph_st = eng.stats(reset=True)
     eng.set_phase_timing(False)
@@ -626,7 +639,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
                        "points_per_gpu": N, "polygons": P, "vertices": int(v.shape[0]),
                        "grid_log2": info["grid_log2"], "sub_log2": info["sub_log2"],
                        "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": idx_bytes,
-                       "generation_s": round(gen_s, 1), "autotune": tune,
+                       "generation_s": round(gen_s, 1), "autotune": tune, "clustered_table": cluster,
                        "checks": "sum(counts) == N; counts of the first %d points == oracle" % m,
                        "counting": "global atomics (P > shared-memory histogram)" if P > 11776 else "shared memory",
                        "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
@@ -640,6 +653,8 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     pr.close()
     eng.free(ih)
     eng.free(gh)
+    if ph_run != ph:
+        eng.free(ph_run)
     eng.free(ph)
     eng.close()
     del dpts
@@ -719,6 +734,8 @@ def main():
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture (reported as is)")
     ap.add_argument("--fp32", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="choose grid_log2 / sub_log2 with spx_autotune")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="count_4b: aggregate over a copy clustered by the cells of a 2^G grid (0: row order)")
     ap.add_argument("--plain", action="store_true", help="time the plain two-pass comparison kernels")
     ap.add_argument("--cap", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")

@@ -84,6 +84,27 @@ const char *spx_last_error(const spx_ctx *ctx);
 spx_status spx_load_points(spx_ctx *ctx, const int32_t *xy, uint64_t n, int xy_is_device, spx_points *out);
 
 /*
+ * Cell-clustered copy of a point table (§5.3 "Grid-based index filtering":
+ * SPADE stores its data as a clustered grid, each cell the block of data that
+ * falls into it).  *out receives a new, owned table with the same n points
+ * grouped by the cells of a 2^grid_log2 x 2^grid_log2 grid over the box
+ * (row-major cell order, points outside the box last; the order within a cell
+ * is unspecified).  Consecutive points then share index cells, so a pass over
+ * the copy reads the index from cache.  Only spx_aggregate takes a clustered
+ * table -- per-polygon counts do not depend on the order of the points; the
+ * join, the selection and the server reject it with SPX_EINVAL (their outputs
+ * are keyed by row).  grid_log2 in [1, 12], 0 = 12.  Device memory: 8 B per
+ * point for the copy, plus 8 B per cell while it is built.  Synchronises the
+ * ctx's stream.  Errors: SPX_EINVAL, SPX_ENOMEM, SPX_ECUDA.
+ */
+spx_status spx_cluster_points(spx_ctx *ctx, spx_points points, int grid_log2, spx_points *out);
+
+/* Device address of a point table (valid while the handle lives), its number
+ * of points, and its clustering grid (0: row order).  Any pointer may be NULL. */
+spx_status spx_points_info(spx_ctx *ctx, spx_points points, const int32_t **xy_dev, uint64_t *n, int *cluster_log2);
+
+/*
+ * Load a polygon set from host memory/*
  * Load a polygon set from host memory (§4.2, polygons are the constraint
  * canvases of selections and joins).  Polygon q is the implicitly closed ring
  * xy[2*ring_off[q] .. 2*ring_off[q+1]) of int32 (x, y) vertices, 0 <= x, y <=

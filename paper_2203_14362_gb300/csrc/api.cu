@@ -30,6 +30,7 @@ struct PointsObj {
     int32_t *dev = nullptr;
     uint64_t n = 0;
     bool owned = false;
+    int cluster_log2 = 0; // > 0: a cell-clustered copy (point order is not row order)
 };
 
 struct PolysObj {
@@ -179,6 +180,8 @@ spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_
     IndexObj *ix = lookup(ctx->indexes, index);
     if (!pts || !ix)
         return fail(ctx, SPX_EINVAL, "join: bad points or index handle");
+    if (pts->cluster_log2)
+        return fail(ctx, SPX_EINVAL, "join: a cell-clustered point table has no row order; use spx_aggregate");
     if (cap && !pairs_dev)
         return fail(ctx, SPX_EINVAL, "join: pairs_dev is NULL with cap > 0");
     if ((reinterpret_cast<uintptr_t>(pairs_dev) & 7) || (reinterpret_cast<uintptr_t>(counts_dev) & 7) ||
@@ -357,6 +360,8 @@ spx_status served_data(spx_ctx *ctx, spx_points points, const spx_index *indexes
     PointsObj *pts = lookup(ctx->points, points);
     if (!pts)
         return fail(ctx, SPX_EINVAL, "server: bad points handle");
+    if (pts->cluster_log2)
+        return fail(ctx, SPX_EINVAL, "server: a cell-clustered point table has no row order");
     out.device = ctx->device;
     out.pts = reinterpret_cast<const int2 *>(pts->dev);
     out.n = pts->n;
@@ -389,6 +394,8 @@ spx_status spx_join_plain_static(spx_ctx *ctx, spx_points points, spx_index inde
     IndexObj *ix = lookup(ctx->indexes, index);
     if (!pts || !ix)
         return fail(ctx, SPX_EINVAL, "join_plain_static: bad points or index handle");
+    if (pts->cluster_log2)
+        return fail(ctx, SPX_EINVAL, "join_plain_static: a cell-clustered point table has no row order");
     if (pts->n > kStaticJoinMaxPoints)
         return fail(ctx, SPX_EINVAL, "join_plain_static: the point table has " + std::to_string(pts->n) +
                                          " points; the allocation-free join takes at most " +
@@ -512,6 +519,62 @@ spx_status spx_load_points(spx_ctx *ctx, const int32_t *xy, uint64_t n, int xy_i
     const uint64_t h = make_handle(ctx, kTagPoints);
     ctx->points[h] = std::move(p);
     *out = h;
+    return SPX_OK;
+}
+
+spx_status spx_cluster_points(spx_ctx *ctx, spx_points points, int grid_log2, spx_points *out)
+{
+    if (!ctx || !out)
+        return fail(ctx, SPX_EINVAL, "cluster_points: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    PointsObj *src = lookup(ctx->points, points);
+    if (!src)
+        return fail(ctx, SPX_EINVAL, "cluster_points: bad points handle");
+    const int c = grid_log2 ? grid_log2 : 12;
+    if (c < 1 || c > 12)
+        return fail(ctx, SPX_EINVAL, "cluster_points: grid_log2 must be in [1, 12] (0 = 12)");
+    auto p = std::make_unique<PointsObj>();
+    p->n = src->n;
+    p->owned = true;
+    p->cluster_log2 = c;
+    void *d = nullptr, *scratch = nullptr;
+    if (cudaMalloc(&d, src->n ? src->n * 8 : 16) != cudaSuccess)
+        return fail(ctx, SPX_ENOMEM, "cluster_points: cudaMalloc of the copy failed");
+    if (cudaMalloc(&scratch, cluster_scratch_bytes(c)) != cudaSuccess) {
+        cudaFree(d);
+        return fail(ctx, SPX_ENOMEM, "cluster_points: cudaMalloc of the cell counters failed");
+    }
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = launch_cluster(reinterpret_cast<const int2 *>(src->dev), src->n, c, scratch,
+                                   static_cast<int2 *>(d), s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(ctx, e, "cluster_points");
+    }
+    p->dev = static_cast<int32_t *>(d);
+    const uint64_t h = make_handle(ctx, kTagPoints);
+    ctx->points[h] = std::move(p);
+    *out = h;
+    return SPX_OK;
+}
+
+spx_status spx_points_info(spx_ctx *ctx, spx_points points, const int32_t **xy_dev, uint64_t *n, int *cluster_log2)
+{
+    if (!ctx)
+        return SPX_EINVAL;
+    PointsObj *p = lookup(ctx->points, points);
+    if (!p)
+        return fail(ctx, SPX_EINVAL, "points_info: bad points handle");
+    if (xy_dev)
+        *xy_dev = p->dev;
+    if (n)
+        *n = p->n;
+    if (cluster_log2)
+        *cluster_log2 = p->cluster_log2;
     return SPX_OK;
 }
 
@@ -773,6 +836,8 @@ spx_status spx_select(spx_ctx *ctx, spx_points points, spx_index index, uint32_t
     IndexObj *ix = lookup(ctx->indexes, index);
     if (!pts || !ix)
         return fail(ctx, SPX_EINVAL, "select: bad points or index handle");
+    if (pts->cluster_log2)
+        return fail(ctx, SPX_EINVAL, "select: a cell-clustered point table has no row order; use spx_aggregate");
     if (!offsets_dev || (cap && !ids_dev))
         return fail(ctx, SPX_EINVAL, "select: offsets_dev is NULL, or ids_dev is NULL with cap > 0");
     if ((reinterpret_cast<uintptr_t>(offsets_dev) & 7) || (reinterpret_cast<uintptr_t>(ids_dev) & 3))

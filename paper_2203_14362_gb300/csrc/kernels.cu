@@ -333,6 +333,18 @@ __device__ __forceinline__ void hist_add_warp(uint32_t *h, bool has, uint32_t q)
     }
 }
 
+// Global counter update for one item of every lane of a converged warp (lanes
+// with has = false add nothing): one atomic per distinct polygon of the warp,
+// so a clustered table's lanes do not serialise on the same counter.
+__device__ __forceinline__ void global_add_warp(unsigned long long *cnt, bool has, uint32_t q)
+{
+    if (!__ballot_sync(kFull, has))
+        return;
+    const uint32_t peers = __match_any_sync(kFull, has ? q : 0xffffffffu);
+    if (has && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+        atomicAdd(cnt + q, (unsigned long long)__popc(peers));
+}
+
 // Whole predicate for one point (plain kernels, overflow path).
 template <bool FP32>
 __device__ __forceinline__ uint32_t point_count(const IndexView &ix, int px, int py, uint32_t &first,
@@ -574,8 +586,8 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
             return;
         if (hist)
             hist_add_warp(s_hist, has, q);
-        else if (has)
-            atomicAdd(a.counts + q, 1ull);
+        else
+            global_add_warp(a.counts, has, q);
     };
     const uint32_t nw = gridDim.x * kWarps;
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
@@ -850,8 +862,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
                         continue;
                     if (use_hist)
                         hist_add_warp(h, c[j] == 1, f[j]);
-                    else if (c[j] == 1)
-                        atomicAdd(cnt + f[j], 1ull);
+                    else
+                        global_add_warp(cnt, c[j] == 1, f[j]);
                     if (c[j] > 1)
                         point_emit<FP32>(ix, p[j].x, p[j].y, keep, [&](uint32_t q) {
                             if (use_hist)
@@ -1127,6 +1139,81 @@ cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_
     const uint64_t stride = n / m; // (m - 1) * stride < n
     const uint64_t blocks = std::min<uint64_t>((m + 255) / 256, uint64_t(device_sm_count()) * 8);
     k_gather_stride<<<unsigned(blocks), 256, 0, s>>>(src, stride, dst, m);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ clustered point table
+// Counting sort of a point table by grid cell (row-major cells of a 2^c x 2^c
+// grid; points outside the box go to one last bin).  Lanes of a warp with the
+// same key share one atomic.
+__device__ __forceinline__ uint32_t cell_key(int2 p, int c)
+{
+    if ((unsigned)p.x >= kBox || (unsigned)p.y >= kBox)
+        return 1u << (2 * c);
+    const int sh = kBoxLog2 - c;
+    return (((uint32_t)p.y >> sh) << c) | ((uint32_t)p.x >> sh);
+}
+
+__global__ void __launch_bounds__(256) k_cell_hist(const int2 *__restrict__ pts, uint64_t n, int c,
+                                                 unsigned long long *cnt)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * 256;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * 256 + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint64_t i = i0 + (threadIdx.x & 31);
+        const bool has = i < n;
+        const uint32_t key = has ? cell_key(__ldcs(pts + i), c) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(kFull, key);
+        if (has && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+            atomicAdd(cnt + key, (unsigned long long)__popc(peers));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cell_scatter(const int2 *__restrict__ pts, uint64_t n, int c,
+                                                    unsigned long long *cursor, int2 *__restrict__ out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * 256;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * 256 + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        const bool has = i < n;
+        const int2 p = has ? __ldcs(pts + i) : make_int2(-1, -1);
+        const uint32_t key = has ? cell_key(p, c) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(kFull, key);
+        const int leader = __ffs(peers) - 1;
+        unsigned long long base = 0;
+        if (has && lane == leader)
+            base = atomicAdd(cursor + key, (unsigned long long)__popc(peers));
+        base = __shfl_sync(kFull, base, leader);
+        if (has)
+            out[base + __popc(peers & lanemask_lt())] = p;
+    }
+}
+
+size_t cluster_scratch_bytes(int c)
+{
+    const uint64_t bins = (uint64_t(1) << (2 * c)) + 1;
+    return size_t(bins + scan_partials(bins) + 2) * 8 + 64;
+}
+
+cudaError_t launch_cluster(const int2 *pts, uint64_t n, int c, void *scratch, int2 *out, cudaStream_t s)
+{
+    if (c < 1 || c > 12)
+        return cudaErrorInvalidValue;
+    if (n == 0)
+        return cudaSuccess;
+    const uint64_t bins = (uint64_t(1) << (2 * c)) + 1;
+    unsigned long long *cnt = static_cast<unsigned long long *>(scratch);
+    unsigned long long *part = cnt + bins;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, bins * 8, s);
+    if (e != cudaSuccess)
+        return e;
+    const unsigned grid = unsigned(std::min<uint64_t>((n + 255) / 256, uint64_t(device_sm_count()) * 16));
+    k_cell_hist<<<grid, 256, 0, s>>>(pts, n, c, cnt);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    if ((e = launch_scan(cnt, bins, nullptr, part, s)) != cudaSuccess) // cnt: cell starts (cursors)
+        return e;
+    k_cell_scatter<<<grid, 256, 0, s>>>(pts, n, c, cnt, out);
     return cudaGetLastError();
 }
 

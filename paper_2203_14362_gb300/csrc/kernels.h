@@ -128,6 +128,12 @@ cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s);
 cudaError_t launch_sum_u64(unsigned long long *dst, const unsigned long long *x, const unsigned long long *y,
                            cudaStream_t s);
 
+// Copy of n points grouped by the cells of a 2^c x 2^c grid (row-major cells,
+// points outside the box last; order within a cell unspecified), c in 1..12.
+// scratch: cluster_scratch_bytes(c).
+size_t cluster_scratch_bytes(int c);
+cudaError_t launch_cluster(const int2 *pts, uint64_t n, int c, void *scratch, int2 *out, cudaStream_t s);
+
 // dst[i] = src[i * (n / m)] for i < m (m <= n): the tuner's deterministic sample.
 cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_t m, cudaStream_t s);
 

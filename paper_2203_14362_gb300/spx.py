@@ -26,6 +26,7 @@ EXPORTS = [
     "spx_join_plain_static", "spx_select", "spx_autotune",
     "spx_server_create", "spx_server_submit", "spx_server_poll", "spx_server_wait", "spx_server_release",
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
+    "spx_cluster_points", "spx_points_info",
 ]
 
 SPX_REQ_SELECT, SPX_REQ_JOIN = 1, 2
@@ -131,6 +132,8 @@ def load(path: str = LIB_PATH):
         "spx_server_stats": ([V, C.POINTER(ServerStats)], I),
         "spx_server_last_error": ([V], C.c_char_p),
         "spx_server_destroy": ([V], None),
+        "spx_cluster_points": ([V, U64, I, P64], I),
+        "spx_points_info": ([V, U64, C.POINTER(V), P64, C.POINTER(I)], I),
         "spx_free": ([V, U64], I),
     }
     for name, (args, res) in sig.items():
@@ -218,6 +221,19 @@ class Engine:
             self._check(self.lib.spx_load_points(self.ctx, _dev_ptr(xy), xy.shape[0], 1, C.byref(h)),
                         "spx_load_points")
         return h.value
+
+    def cluster_points(self, points: int, grid_log2: int = 0) -> int:
+        """spx_cluster_points: a cell-clustered copy (aggregate only)."""
+        h = C.c_uint64()
+        self._check(self.lib.spx_cluster_points(self.ctx, points, grid_log2, C.byref(h)), "spx_cluster_points")
+        return h.value
+
+    def points_info(self, points: int) -> dict:
+        """Device address, size and clustering grid of a point table."""
+        ptr, n, c = C.c_void_p(), C.c_uint64(), C.c_int()
+        self._check(self.lib.spx_points_info(self.ctx, points, C.byref(ptr), C.byref(n), C.byref(c)),
+                    "spx_points_info")
+        return {"ptr": ptr.value or 0, "n": n.value, "cluster_log2": c.value}
 
     def load_polygons(self, verts: np.ndarray, ring_off: np.ndarray) -> int:
         xy = np.ascontiguousarray(verts, dtype=np.int32)
