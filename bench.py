@@ -565,6 +565,8 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     assert int(counts.sum().item()) == N, "sum of counts != number of points"
     cluster = None
     ph_run = ph
+    if args.cluster < 0:
+        args.cluster = 12
     if args.cluster:
         # one-off: a copy grouped by grid cell (load time, outside the timed steps)
         t0 = time.perf_counter()
@@ -734,8 +736,9 @@ def main():
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture (reported as is)")
     ap.add_argument("--fp32", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="choose grid_log2 / sub_log2 with spx_autotune")
-    ap.add_argument("--cluster", type=int, default=0,
-                    help="count_4b: aggregate over a copy clustered by the cells of a 2^G grid (0: row order)")
+    ap.add_argument("--cluster", type=int, default=-1,
+                    help="count_4b: aggregate over a copy clustered by the cells of a 2^G grid "
+                         "(-1: G = 12, the default; 0: the table in row order)")
     ap.add_argument("--plain", action="store_true", help="time the plain two-pass comparison kernels")
     ap.add_argument("--cap", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
