@@ -53,7 +53,7 @@ def make_workload(name: str, n_override: int | None, rank: int):
         nx, ny = g.tessellation_shape(2000)
         t = g.quad_tessellation(nx, ny, seed, kmin=12, kmax=499)
         mix = g.make_mixture(seed)
-        pts = g.mixture_points_parallel(n, seed, mix, start=rank * n)
+        pts = g.mixture_points_parallel(n, seed, mix, start=shard_start(rank, n))
         desc = (f"{n} mixture points (64 Gaussians, sigma 0.5-5% of box, 10% uniform) x 2000-cell tessellation "
                 f"(jittered quads, noisy edges, 52-2000 vertices/cell); pairs + counts")
         return pts, t.verts, t.ring_off, desc
@@ -62,7 +62,7 @@ def make_workload(name: str, n_override: int | None, rank: int):
         seed = g.SEED_BASE + 3
         mix = g.make_mixture(seed)
         v, o = g.query_polygons(256, seed, mix)
-        pts = g.mixture_points_parallel(n, seed, mix, start=rank * n)
+        pts = g.mixture_points_parallel(n, seed, mix, start=shard_start(rank, n))
         desc = (f"batched selection: {n} mixture points x 256 query polygons (lognormal 8-5000 vertices, "
                 f"concave, overlapping); per-query ascending id lists")
         return pts, v, o, desc
@@ -70,7 +70,7 @@ def make_workload(name: str, n_override: int | None, rank: int):
         n = n_override or 1_000_000_000
         seed = g.SEED_BASE + 4
         mix = g.make_mixture(seed)
-        pts = g.mixture_points_parallel(n, seed, mix, start=rank * n)
+        pts = g.mixture_points_parallel(n, seed, mix, start=shard_start(rank, n))
         desc = (f"serving: {n} resident mixture points; Poisson stream of 70% selections (1-64 query polygons) "
                 f"and 30% joins vs 500/1000/2500/5000-cell tessellations")
         return pts, None, None, desc
@@ -155,13 +155,45 @@ def dist_setup():
     return world, rank, local
 
 
+def dist_init(world: int, local: int, torch):
+    """One process per GPU (NCCL); gloo where there is no GPU (tests)."""
+    if world == 1:
+        return
+    import torch.distributed as dist
+    if dist.is_initialized():
+        return
+    if torch.cuda.is_available():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group("gloo")
+
+
+def _dist_device():
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def max_over_ranks(x: float, world: int, torch):
     if world == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_dist_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_counts_over_ranks(counts, world: int):
+    """Per-polygon counts of the whole table: each rank joins its own range of
+    points, so the counts are summed over ranks (the path's one exchange)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(counts, op=dist.ReduceOp.SUM)
+    return counts
+
+
+def shard_start(rank: int, n_per_rank: int) -> int:
+    """First global point index of a rank's range (weak scaling)."""
+    return rank * n_per_rank
 
 
 def barrier(world: int):
@@ -234,9 +266,7 @@ def run_spx(args, world, rank, local):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist_init(world, local, torch)
     clocks = ClockSampler(local)
     if args.workload == "count_4b":
         return run_count_bench(args, world, rank, local, clocks, torch)
@@ -281,6 +311,7 @@ def run_spx(args, world, rank, local):
     e0.record(stream)
     for _ in range(args.steps):
         eng.join(ph, ih, pairs, counts, total, sync=False, stream=stream, plain=args.plain)
+        sum_counts_over_ranks(counts, world)
     e1.record(stream)
     torch.cuda.synchronize()
     t_host1 = time.time()
@@ -538,7 +569,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     head = None
     for lo in range(0, N, chunk):
         hi = min(N, lo + chunk)
-        c = g.mixture_points_parallel(hi - lo, seed, mix, start=rank * N + lo)
+        c = g.mixture_points_parallel(hi - lo, seed, mix, start=shard_start(rank, N) + lo)
         if head is None:
             head = c[:min(c.shape[0], 20_000_000)].copy()
         dpts[lo:hi].copy_(torch.from_numpy(c))
@@ -599,6 +630,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     e0.record(stream)
     for _ in range(args.steps):
         eng.aggregate(ph_run, ih, counts, stream=stream)
+        sum_counts_over_ranks(counts, world)
     e1.record(stream)
     torch.cuda.synchronize()
     t_host1 = time.time()
