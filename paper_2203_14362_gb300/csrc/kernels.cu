@@ -670,12 +670,21 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
 
 // Pass 3 of the join with warp chunks: every warp writes the pairs of its
 // chunks from the stored per-point results at the chunk's scanned offset.
-// Lane order within a round of 32 points, rounds in order: point order.
+// Lane order within a round of 32 points, rounds in order: point order.  A
+// point in one polygon is written at once; a point in several is queued with
+// its offset, and the warp walks its queue 32 points at a time afterwards (all
+// lanes busy, as in pass 1) to write their pairs.
+constexpr size_t kEmitSmem = size_t(kWarps) * kWChunk * (sizeof(uint4) + sizeof(unsigned long long));
+
 template <bool FP32>
 __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsigned long long *chunk_off,
-                                                    uint32_t nchunks)
+                                                       uint32_t nchunks)
 {
+    extern __shared__ __align__(16) unsigned char s_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kWChunk; // (x, y, point id)
+    unsigned long long *s_o =
+        reinterpret_cast<unsigned long long *>(s_raw + size_t(kWarps) * kWChunk * sizeof(uint4)) + warp * kWChunk;
     const uint64_t keep = policy_evict_last();
     const uint32_t nw = gridDim.x * kWarps;
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
@@ -688,9 +697,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
             const uint32_t loc = j * 32 + lane;
             res[j] = loc < npts ? __ldcs(a.res + base + loc) : kResNone;
         }
+        uint32_t qn = 0;
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             const uint32_t loc = j * 32 + lane, r = res[j];
+            const uint32_t pid = a.pid0 + (uint32_t)(base + loc);
             const bool multi = r != kResNone && (r & kResMulti);
             uint32_t c = r == kResNone ? 0u : 1u, pre, tot;
             if (!__any_sync(kFull, multi)) {
@@ -717,24 +728,35 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
                 }
                 pre = inc - c;
                 tot = __shfl_sync(kFull, inc, 31);
+                const uint32_t bl = __ballot_sync(kFull, multi);
                 if (multi) {
-                    unsigned long long o = run + pre;
-                    const uint32_t pid = a.pid0 + (uint32_t)(base + loc);
-                    point_emit<FP32>(a.ix, p.x, p.y, keep, [&](uint32_t q) {
-                        if (o < a.cap)
-                            __stcs(a.pairs + o, make_uint2(pid, q));
-                        ++o;
-                    });
-                    c = 0; // written
+                    const uint32_t slot = qn + __popc(bl & lanemask_lt());
+                    s_q[slot] = make_uint4((uint32_t)p.x, (uint32_t)p.y, pid, 0u);
+                    s_o[slot] = run + pre;
+                    c = 0; // written from the queue
                 }
+                qn += __popc(bl);
             }
             if (c) {
                 const unsigned long long o = run + pre;
                 if (o < a.cap)
-                    __stcs(a.pairs + o, make_uint2(a.pid0 + (uint32_t)(base + loc), r));
+                    __stcs(a.pairs + o, make_uint2(pid, r));
             }
             run += tot;
         }
+        __syncwarp();
+        for (uint32_t k0 = 0; k0 < qn; k0 += 32) {
+            if (k0 + lane < qn) {
+                const uint4 it = s_q[k0 + lane];
+                unsigned long long o = s_o[k0 + lane];
+                point_emit<FP32>(a.ix, (int)it.x, (int)it.y, keep, [&](uint32_t q) {
+                    if (o < a.cap)
+                        __stcs(a.pairs + o, make_uint2(it.z, q));
+                    ++o;
+                });
+            }
+        }
+        __syncwarp(); // the queue is rewritten by the next chunk
     }
 }
 
@@ -1243,10 +1265,19 @@ cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s)
     if (nchunks == 0 || a.cap == 0)
         return cudaSuccess;
     const uint32_t nblk = (nchunks + kWarps - 1) / kWarps;
-    if (a.fp32)
-        k_wemit<true><<<persistent_grid(k_wemit<true>, kThreads, 0, nblk), kThreads, 0, s>>>(a, a.tile_tot, nchunks);
-    else
-        k_wemit<false><<<persistent_grid(k_wemit<false>, kThreads, 0, nblk), kThreads, 0, s>>>(a, a.tile_tot, nchunks);
+    static bool done[2][64] = {};
+    cudaError_t e;
+    if (a.fp32) {
+        if ((e = smem_opt_in(k_wemit<true>, kEmitSmem, done[0])) != cudaSuccess)
+            return e;
+        k_wemit<true><<<persistent_grid(k_wemit<true>, kThreads, kEmitSmem, nblk), kThreads, kEmitSmem, s>>>(
+            a, a.tile_tot, nchunks);
+    } else {
+        if ((e = smem_opt_in(k_wemit<false>, kEmitSmem, done[1])) != cudaSuccess)
+            return e;
+        k_wemit<false><<<persistent_grid(k_wemit<false>, kThreads, kEmitSmem, nblk), kThreads, kEmitSmem, s>>>(
+            a, a.tile_tot, nchunks);
+    }
     return cudaGetLastError();
 }
 
