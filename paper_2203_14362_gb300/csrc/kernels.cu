@@ -777,7 +777,7 @@ constexpr uint32_t kMPending = 0xffffffffu; // a list point whose walk is queued
 #endif
 constexpr int kMItems = SPX_MULTI_ITEMS;                      // points per lane per chunk
 constexpr int kMChunk = 32 * kMItems;                         // consecutive points per warp chunk
-constexpr size_t kMultiSmem = size_t(kWarps) * kMChunk * sizeof(uint4); // per-warp queues
+constexpr size_t kMultiSmem = size_t(kWarps) * kMChunk * (sizeof(uint4) + sizeof(unsigned long long)); // queues
 
 // Does the cover bitmap let (px, py) reach a non-empty coarse cell?  False for
 // points outside the box.
@@ -796,6 +796,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kMChunk; // (x, y, first entry) -> (count, first)
+    unsigned long long *s_o = // emit pass: output offsets of queued points
+        reinterpret_cast<unsigned long long *>(s_raw + size_t(kWarps) * kMChunk * sizeof(uint4)) + warp * kMChunk;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_raw + kMultiSmem); // count pass: qbase[K] counters
     const uint64_t keep = policy_evict_last();
     const int K = m.K;
@@ -899,10 +901,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
                     chunk_tot[(uint64_t)r * nchunks + ch] = total;
                 continue;
             }
-            // emit: pairs of request r in point order from the chunk's offset
+            // emit: pairs of request r in point order from the chunk's offset;
+            // points in several polygons are queued and walked 32 at a time
             uint2 *out = m.pairs[r];
             const uint64_t cap = m.cap[r];
             unsigned long long run = chunk_tot[(uint64_t)r * nchunks + ch];
+            uint32_t mq = 0;
 #pragma unroll
             for (int j = 0; j < kMItems; ++j) {
                 const uint32_t loc = j * 32 + lane, cj = c[j];
@@ -914,21 +918,33 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
                         inc += v;
                 }
                 const uint32_t wtot = __shfl_sync(kFull, inc, 31);
-                unsigned long long o = run + inc - cj;
+                const unsigned long long o = run + inc - cj;
                 const uint32_t pid = (uint32_t)(base + loc);
-                if (cj == 1) {
-                    if (o < cap)
-                        out[o] = make_uint2(pid, f[j]);
-                } else if (cj > 1) {
-                    point_emit<FP32>(ix, p[j].x, p[j].y, keep, [&](uint32_t q) {
-                        if (o < cap)
-                            out[o] = make_uint2(pid, q);
-                        ++o;
-                    });
+                if (cj == 1 && o < cap)
+                    out[o] = make_uint2(pid, f[j]);
+                const uint32_t bl = __ballot_sync(kFull, cj > 1);
+                if (cj > 1) {
+                    const uint32_t slot = mq + __popc(bl & lanemask_lt());
+                    s_q[slot] = make_uint4((uint32_t)p[j].x, (uint32_t)p[j].y, pid, 0u);
+                    s_o[slot] = o;
                 }
+                mq += __popc(bl);
                 emitted += cj;
                 run += wtot;
             }
+            __syncwarp();
+            for (uint32_t k0 = 0; k0 < mq; k0 += 32) {
+                if (k0 + lane < mq) {
+                    const uint4 it = s_q[k0 + lane];
+                    unsigned long long o = s_o[k0 + lane];
+                    point_emit<FP32>(ix, (int)it.x, (int)it.y, keep, [&](uint32_t q) {
+                        if (o < cap)
+                            out[o] = make_uint2(it.z, q);
+                        ++o;
+                    });
+                }
+            }
+            __syncwarp(); // s_q is rewritten for the next request
         }
     }
     if (!EMIT && use_hist) {
