@@ -191,6 +191,16 @@ def sum_counts_over_ranks(counts, world: int):
     return counts
 
 
+def join_launches(n: int, plain: bool) -> int:
+    """Kernels one spx_join launches: pass 1, the scan (one kernel up to 32768
+    values, else three), pass 3 (256-point chunks; plain: 256-point blocks and
+    the one-block scan)."""
+    if plain:
+        return 3
+    chunks = (n + 255) // 256
+    return 2 + (1 if chunks <= 4 * 8192 else 3)
+
+
 def shard_start(rank: int, n_per_rank: int) -> int:
     """First global point index of a rank's range (weak scaling)."""
     return rank * n_per_rank
@@ -395,7 +405,7 @@ def run_spx(args, world, rank, local):
                          "phase_ms": phase_ms},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * 3,  # resolve, scan, emit (plain: count, scan, write)
+            "gpu_launches": args.steps * join_launches(N, args.plain),
             "clocks": clk,
             "serving": serving,
         }
@@ -540,7 +550,10 @@ def run_serve_bench(args, world, rank, eng, ph, dpts, N, desc, clocks, torch):
                        "step": "one request at the batching server's capacity",
                        "l2": "point table (8 B x N) larger than L2; no flush"},
             "roofline": None, "cpu_baseline": None, "e2e": None,
-            "gpu_launches": None, "clocks": clk, "serving": sv,
+            # two batch-kernel launches (count, emit) per batch of the timed runs;
+            # scans and selection partitions add more
+            "gpu_launches": 2 * sv["batches"], "gpu_launches_note": "lower bound: k_multi launches only",
+            "clocks": clk, "serving": sv,
         }), flush=True)
     eng.free(ph)
     eng.close()
@@ -741,7 +754,10 @@ def run_select_bench(args, world, rank, eng, ph, ih, info, dpts, pts, v, o, desc
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
                          "kernel": "whole selection step", "algorithmic_bytes_per_launch": int(alg)},
-            "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps * 7, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": None, "clocks": clk,
+            # the join, then the partition: count table, its scan, offsets, emit
+            "gpu_launches": args.steps * (join_launches(N, False) + 3 +
+                                          (1 if Q * max(1, -(-total // 32768)) <= 4 * 8192 else 3)),
         }), flush=True)
     eng.free(ih)
     eng.close()

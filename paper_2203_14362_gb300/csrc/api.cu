@@ -21,6 +21,10 @@
 
 using namespace spx;
 
+#ifndef SPX_HOST_SLICE_LOG2
+#define SPX_HOST_SLICE_LOG2 23 // points per slice of spx_join_host (a multiple of the join's chunk)
+#endif
+
 namespace {
 
 enum : uint64_t { kTagPoints = 1, kTagPolys = 2, kTagIndex = 3 };
@@ -963,7 +967,7 @@ spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_i
     // total[k - 1], computed on the device; the host reads (base[k], total[k])
     // to size the slice's copy-out.  Both copy directions run on the copy
     // engines, beside the kernels.
-    constexpr uint64_t kSlice = uint64_t(1) << 23;
+    constexpr uint64_t kSlice = uint64_t(1) << SPX_HOST_SLICE_LOG2;
     const uint64_t n_slices = (n + kSlice - 1) / kSlice;
     const uint64_t cpts = join_chunk_points(), nchunks = (n + cpts - 1) / cpts;
     const size_t b_res = ((n * 4 + 15) & ~uint64_t(15)), words = nchunks + join_part_words(kSlice) + 2 * n_slices + 2;
