@@ -658,6 +658,25 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     torch.cuda.synchronize()
     ph_st = eng.stats(reset=True)
     eng.set_phase_timing(False)
+    # end to end from host memory: the table in pinned host memory, streamed
+    # through the device every step (host-to-device copies inside the timing)
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty((N, 2), dtype=torch.int32, pin_memory=True)
+        hx.copy_(dpts)
+        hxn = hx.numpy()
+        hc = np.zeros(P, np.uint64)
+        eng.aggregate_host(hxn, ih, P, counts_out=hc)
+        assert np.array_equal(hc, counts.cpu().numpy().view(np.uint64)), "streamed counts differ"
+        k_e2e = max(1, min(args.steps, args.e2e_steps))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            eng.aggregate_host(hxn, ih, P, counts_out=hc)
+        sec = max_over_ranks((time.perf_counter() - t0) / k_e2e, world, torch)
+        e2e = {"value": world * N / sec / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
+               "d2h_bytes_per_step": int(P * 8), "ms_per_step": sec * 1e3,
+               "path": "spx_aggregate_host: the row-order table streamed from pinned host memory"}
+        del hx, hxn
     clocks.stop()
     k_ms = ph_st["ms_aggregate"] / max(ph_st["timed_aggregates"], 1)
     idx_bytes = int(info["device_bytes"])
@@ -695,7 +714,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_warp<aggregate>",
                          "kernel_ms": k_ms, "algorithmic_bytes_per_launch": int(alg)},
-            "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
         }), flush=True)
     pr.close()
     eng.free(ih)

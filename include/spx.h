@@ -303,6 +303,30 @@ spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_i
                          uint64_t cap, uint64_t *counts_host, uint64_t *n_pairs);
 
 /*
+ * Count aggregation over a point table in host memory (§5.2 "Spatial
+ * Aggregations" over a table that need not fit in device memory, §5.3
+ * "Out-of-Core Queries"): the n points at xy_host stream through four device
+ * slots of one slice each (the copy of a slice overlaps the counting of the
+ * slices before it); counts_host receives P uint64.  Device memory does not
+ * grow with n.  Synchronous.  Errors: SPX_EINVAL, SPX_ENOMEM, SPX_ECUDA.
+ */
+spx_status spx_aggregate_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_index index, uint64_t *counts_host);
+
+/*
+ * How spx_join_host moves a host table (§5.3 out-of-core queries; §7 names
+ * pipelining as future work): mode 1 stages the whole table and the pairs in
+ * device memory; mode 2 streams the table through four device slots and has
+ * the kernels write the pairs straight into pairs_host (the device must be able
+ * to write it: pinned memory, or pageable memory on a system whose GPU uses the
+ * host page tables; else spx_join_host returns SPX_EINVAL), so device memory
+ * does not grow with n; mode 0 (the default) stages when the table, its
+ * results and the pairs fit in half the free device memory, else streams.
+ * slice_log2: points per slice, 16..26 (0: 2^23).  Applies to later calls on
+ * this ctx (spx_aggregate_host always streams and uses the same slice size).
+ */
+spx_status spx_set_host_streaming(spx_ctx *ctx, int mode, int slice_log2);
+
+/*
  * Host-only build of the same grid index, for inspection (no device, no ctx):
  * the index build runs on the host, so its output can be checked without a
  * GPU.  spx_host_index_build builds it (grid_log2 0 = automatic, sub_log2 0 =

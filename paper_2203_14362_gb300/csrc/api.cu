@@ -82,6 +82,8 @@ struct spx_ctx {
     std::vector<cudaEvent_t> slice_ev;
     unsigned long long *slice_words = nullptr;
     size_t slice_words_n = 0;
+    int host_mode = 0;                          // 0 automatic, 1 staged, 2 streamed
+    int host_slice_log2 = SPX_HOST_SLICE_LOG2;  // points per slice
     // batched selection: captured launch sequences, keyed by their arguments
     std::map<std::tuple<uint64_t, uint64_t, uintptr_t, uint64_t, uintptr_t>, cudaGraphExec_t> select_graphs;
     cudaStream_t capture_stream = nullptr;
@@ -944,22 +946,10 @@ spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint6
     return SPX_OK;
 }
 
-spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_index index, uint32_t *pairs_host,
-                         uint64_t cap, uint64_t *counts_host, uint64_t *n_pairs)
+static spx_status join_host_staged(spx_ctx *ctx, IndexObj *ix, const int32_t *xy_host, uint64_t n, uint32_t *pairs_host,
+                                   uint64_t cap, uint64_t *counts_host, uint64_t *n_pairs, uint64_t kSlice)
 {
-    if (!ctx || (!xy_host && n) || (!pairs_host && cap) || !n_pairs)
-        return fail(ctx, SPX_EINVAL, "join_host: null argument");
-    ctx->err.clear();
-    cudaSetDevice(ctx->device);
-    IndexObj *ix = lookup(ctx->indexes, index);
-    if (!ix)
-        return fail(ctx, SPX_EINVAL, "join_host: bad index handle");
-    if (n >= (1ull << 32))
-        return fail(ctx, SPX_EINVAL, "join_host: n must be < 2^32");
     cudaStream_t s = ctx->stream;
-    for (cudaStream_t *p : {&ctx->in_stream, &ctx->emit_stream, &ctx->out_stream})
-        if (!*p)
-            SPX_CUDA(cudaStreamCreateWithFlags(p, cudaStreamNonBlocking), "join_host stream");
     // Slices of kSlice points flow through four streams: copy-in of slice
     // k + 1 (in_stream), resolve of slice k (stream), emit of slice k - 1 into
     // device staging (emit_stream) and copy-out of the slice before
@@ -967,7 +957,6 @@ spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_i
     // total[k - 1], computed on the device; the host reads (base[k], total[k])
     // to size the slice's copy-out.  Both copy directions run on the copy
     // engines, beside the kernels.
-    constexpr uint64_t kSlice = uint64_t(1) << SPX_HOST_SLICE_LOG2;
     const uint64_t n_slices = (n + kSlice - 1) / kSlice;
     const uint64_t cpts = join_chunk_points(), nchunks = (n + cpts - 1) / cpts;
     const size_t b_res = ((n * 4 + 15) & ~uint64_t(15)), words = nchunks + join_part_words(kSlice) + 2 * n_slices + 2;
@@ -1067,6 +1056,229 @@ spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_i
     *n_pairs = t;
     if (t > cap)
         return fail(ctx, SPX_ECAPACITY, "join_host: " + std::to_string(t) + " pairs exceed capacity");
+    return SPX_OK;
+}
+
+// Can kernels of this device write host memory at p directly (pinned and
+// mapped at the same address, managed, or pageable memory that the device
+// reaches through the host page tables)?
+static bool device_reaches_host(int device, const void *p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) == cudaSuccess) {
+        if ((at.type == cudaMemoryTypeHost && at.devicePointer == p) || at.type == cudaMemoryTypeManaged)
+            return true;
+    } else {
+        cudaGetLastError();
+    }
+    int pageable = 0;
+    cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+    return pageable == 1;
+}
+
+constexpr uint64_t kRing = 4; // device slots of a streamed host table
+
+// Tables larger than device memory (§5.3 "Out-of-Core Queries"): the points
+// cycle through kRing device slots of kSlice points (the copy of slice k + 4
+// waits until slice k is emitted), and the pairs go straight into pairs_host,
+// which the device writes through the host link.  Device memory does not grow
+// with n.
+static spx_status join_host_streamed(spx_ctx *ctx, IndexObj *ix, const int32_t *xy_host, uint64_t n,
+                                     uint32_t *pairs_host, uint64_t cap, uint64_t *counts_host, uint64_t *n_pairs,
+                                     uint64_t kSlice)
+{
+    cudaStream_t s = ctx->stream;
+    const uint64_t n_slices = (n + kSlice - 1) / kSlice;
+    const uint64_t cpts = join_chunk_points(), slice_chunks = (kSlice + cpts - 1) / cpts;
+    const size_t b_pts = kSlice * 8, b_res = kSlice * 4, b_tot = slice_chunks * 8;
+    const size_t words = join_part_words(kSlice) + 2 * n_slices + 2;
+    spx_status st;
+    if ((st = ensure(ctx, &ctx->st_counts, &ctx->st_counts_b, size_t(ix->view.P) * 8 + 16, s, "join_host")) != SPX_OK ||
+        (st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, kRing * (b_pts + b_res + b_tot) + words * 8 + 256, s,
+                     "join_host")) != SPX_OK)
+        return st;
+    while (ctx->slice_ev.size() < 3 * n_slices + 1) {
+        cudaEvent_t e = nullptr;
+        SPX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "join_host event");
+        ctx->slice_ev.push_back(e);
+    }
+    cudaEvent_t *ev_in = ctx->slice_ev.data(), *ev_res = ev_in + n_slices, *ev_emit = ev_res + n_slices;
+    char *m0 = static_cast<char *>(ctx->scratch);
+    char *ring_pts = m0, *ring_res = m0 + kRing * b_pts, *ring_tot = ring_res + kRing * b_res;
+    unsigned long long *part = reinterpret_cast<unsigned long long *>(ring_tot + kRing * b_tot);
+    unsigned long long *bt = part + join_part_words(kSlice); // (base[k], total[k]) pairs, then base[n_slices]
+    SPX_CUDA(cudaMemsetAsync(bt, 0, 8, s), "join_host base");
+    if (ix->view.P)
+        SPX_CUDA(cudaMemsetAsync(ctx->st_counts, 0, size_t(ix->view.P) * 8, s), "join_host counts");
+    // the first copy waits for the zeroing above (the ring may hold a previous call's data)
+    cudaEvent_t ev_start = ctx->slice_ev[3 * n_slices];
+    SPX_CUDA(cudaEventRecord(ev_start, s), "join_host event");
+    SPX_CUDA(cudaStreamWaitEvent(ctx->in_stream, ev_start, 0), "join_host wait");
+    for (uint64_t k = 0; k < n_slices; ++k) {
+        const uint64_t slot = k % kRing, lo = k * kSlice, m = n - lo < kSlice ? n - lo : kSlice;
+        cudaError_t e = cudaSuccess;
+        if (k >= kRing)
+            e = cudaStreamWaitEvent(ctx->in_stream, ev_emit[k - kRing], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ring_pts + slot * b_pts, xy_host + 2 * lo, m * 8, cudaMemcpyHostToDevice,
+                                ctx->in_stream);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_in[k], ctx->in_stream);
+        JoinLaunch a{};
+        a.ix = ix->view;
+        a.pts = reinterpret_cast<const int2 *>(ring_pts + slot * b_pts);
+        a.n = m;
+        a.pairs = reinterpret_cast<uint2 *>(pairs_host);
+        a.cap = cap;
+        a.counts = reinterpret_cast<unsigned long long *>(ctx->st_counts);
+        a.res = reinterpret_cast<uint32_t *>(ring_res + slot * b_res);
+        a.tile_tot = reinterpret_cast<unsigned long long *>(ring_tot + slot * b_tot);
+        a.total = bt + 2 * k + 1;
+        a.err = &ctx->aux->err;
+        a.stats = ctx->aux->stats;
+        a.fp32 = ix->fp32;
+        a.pid0 = uint32_t(lo);
+        a.keep_counts = 1;
+        a.pair_base = bt + 2 * k;
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, ev_in[k], 0);
+        if (e == cudaSuccess)
+            e = launch_join_resolve(a, part, s);
+        if (e == cudaSuccess)
+            e = launch_sum_u64(bt + 2 * k + 2, bt + 2 * k, bt + 2 * k + 1, s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_res[k], s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(ctx->emit_stream, ev_res[k], 0);
+        if (e == cudaSuccess)
+            e = launch_join_emit(a, ctx->emit_stream);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_emit[k], ctx->emit_stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "join_host launch");
+    }
+    cudaEvent_t ev_done = ctx->slice_ev[3 * n_slices];
+    SPX_CUDA(cudaEventRecord(ev_done, ctx->emit_stream), "join_host event");
+    SPX_CUDA(cudaStreamWaitEvent(s, ev_done, 0), "join_host wait");
+    unsigned long long t = 0;
+    SPX_CUDA(cudaMemcpyAsync(&t, bt + 2 * n_slices, sizeof(t), cudaMemcpyDeviceToHost, s), "join_host total");
+    if (counts_host && ix->view.P)
+        SPX_CUDA(cudaMemcpyAsync(counts_host, ctx->st_counts, size_t(ix->view.P) * 8, cudaMemcpyDeviceToHost, s),
+                 "join_host counts D2H");
+    if ((st = check_kernel_err(ctx, s)) != SPX_OK)
+        return st;
+    *n_pairs = t;
+    if (t > cap)
+        return fail(ctx, SPX_ECAPACITY, "join_host: " + std::to_string(t) + " pairs exceed capacity");
+    return SPX_OK;
+}
+
+spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_index index, uint32_t *pairs_host,
+                         uint64_t cap, uint64_t *counts_host, uint64_t *n_pairs)
+{
+    if (!ctx || (!xy_host && n) || (!pairs_host && cap) || !n_pairs)
+        return fail(ctx, SPX_EINVAL, "join_host: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!ix)
+        return fail(ctx, SPX_EINVAL, "join_host: bad index handle");
+    if (n >= (1ull << 32))
+        return fail(ctx, SPX_EINVAL, "join_host: n must be < 2^32");
+    for (cudaStream_t *p : {&ctx->in_stream, &ctx->emit_stream, &ctx->out_stream})
+        if (!*p)
+            SPX_CUDA(cudaStreamCreateWithFlags(p, cudaStreamNonBlocking), "join_host stream");
+    const uint64_t slice = uint64_t(1) << ctx->host_slice_log2;
+    const bool reach = cap == 0 || device_reaches_host(ctx->device, pairs_host);
+    int mode = ctx->host_mode;
+    if (mode == 0) {
+        // staged when the table, its results and the pairs fit in half the free device memory
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        const uint64_t staged = n * 8 + n * 4 + cap * 8 + (uint64_t(1) << 26);
+        mode = (staged <= fr / 2 || !reach) ? 1 : 2;
+    }
+    if (mode == 2 && !reach)
+        return fail(ctx, SPX_EINVAL, "join_host: streaming needs pairs_host that the device can write "
+                                     "(pinned memory, or a system whose GPU uses the host page tables)");
+    return mode == 1 ? join_host_staged(ctx, ix, xy_host, n, pairs_host, cap, counts_host, n_pairs, slice)
+                     : join_host_streamed(ctx, ix, xy_host, n, pairs_host, cap, counts_host, n_pairs, slice);
+}
+
+spx_status spx_aggregate_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_index index, uint64_t *counts_host)
+{
+    if (!ctx || (!xy_host && n) || !counts_host)
+        return fail(ctx, SPX_EINVAL, "aggregate_host: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!ix)
+        return fail(ctx, SPX_EINVAL, "aggregate_host: bad index handle");
+    cudaStream_t s = ctx->stream;
+    if (!ctx->in_stream)
+        SPX_CUDA(cudaStreamCreateWithFlags(&ctx->in_stream, cudaStreamNonBlocking), "aggregate_host stream");
+    // the points cycle through kRing device slots; counts accumulate on the device
+    const uint64_t kSlice = uint64_t(1) << ctx->host_slice_log2, n_slices = (n + kSlice - 1) / kSlice;
+    const size_t b_pts = kSlice * 8;
+    spx_status st;
+    if ((st = ensure(ctx, &ctx->st_counts, &ctx->st_counts_b, size_t(ix->view.P) * 8 + 16, s, "aggregate_host")) !=
+            SPX_OK ||
+        (st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, kRing * b_pts + 256, s, "aggregate_host")) != SPX_OK)
+        return st;
+    while (ctx->slice_ev.size() < 2 * n_slices + 1) {
+        cudaEvent_t e = nullptr;
+        SPX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "aggregate_host event");
+        ctx->slice_ev.push_back(e);
+    }
+    cudaEvent_t *ev_in = ctx->slice_ev.data(), *ev_agg = ev_in + n_slices;
+    char *ring = static_cast<char *>(ctx->scratch);
+    unsigned long long *counts = reinterpret_cast<unsigned long long *>(ctx->st_counts);
+    if (ix->view.P)
+        SPX_CUDA(cudaMemsetAsync(counts, 0, size_t(ix->view.P) * 8, s), "aggregate_host counts");
+    cudaEvent_t ev_start = ctx->slice_ev[2 * n_slices];
+    SPX_CUDA(cudaEventRecord(ev_start, s), "aggregate_host event");
+    SPX_CUDA(cudaStreamWaitEvent(ctx->in_stream, ev_start, 0), "aggregate_host wait");
+    for (uint64_t k = 0; k < n_slices; ++k) {
+        const uint64_t slot = k % kRing, lo = k * kSlice, m = n - lo < kSlice ? n - lo : kSlice;
+        cudaError_t e = cudaSuccess;
+        if (k >= kRing)
+            e = cudaStreamWaitEvent(ctx->in_stream, ev_agg[k - kRing], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ring + slot * b_pts, xy_host + 2 * lo, m * 8, cudaMemcpyHostToDevice, ctx->in_stream);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_in[k], ctx->in_stream);
+        JoinLaunch a{};
+        a.ix = ix->view;
+        a.pts = reinterpret_cast<const int2 *>(ring + slot * b_pts);
+        a.n = m;
+        a.counts = counts;
+        a.err = &ctx->aux->err;
+        a.stats = ctx->aux->stats;
+        a.fp32 = ix->fp32;
+        a.keep_counts = 1;
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, ev_in[k], 0);
+        if (e == cudaSuccess)
+            e = launch_aggregate(a, nullptr, s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_agg[k], s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "aggregate_host launch");
+    }
+    if (ix->view.P)
+        SPX_CUDA(cudaMemcpyAsync(counts_host, counts, size_t(ix->view.P) * 8, cudaMemcpyDeviceToHost, s),
+                 "aggregate_host counts D2H");
+    return check_kernel_err(ctx, s);
+}
+
+spx_status spx_set_host_streaming(spx_ctx *ctx, int mode, int slice_log2)
+{
+    if (!ctx)
+        return SPX_EINVAL;
+    if (mode < 0 || mode > 2 || (slice_log2 && (slice_log2 < 16 || slice_log2 > 26)))
+        return fail(ctx, SPX_EINVAL, "set_host_streaming: mode 0..2, slice_log2 0 or 16..26");
+    ctx->host_mode = mode;
+    ctx->host_slice_log2 = slice_log2 ? slice_log2 : SPX_HOST_SLICE_LOG2;
     return SPX_OK;
 }
 

@@ -1371,7 +1371,9 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cuda
 cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
 {
     (void)scratch;
-    cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * (a.ix.P ? a.ix.P : 1), s);
+    cudaError_t e = cudaSuccess;
+    if (!a.keep_counts)
+        e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * (a.ix.P ? a.ix.P : 1), s);
     if (e != cudaSuccess || a.n == 0)
         return e;
     if (reinterpret_cast<uintptr_t>(a.pts) & 15)

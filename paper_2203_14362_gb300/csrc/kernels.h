@@ -60,7 +60,8 @@ size_t plain_scratch_bytes(uint64_t n);
 // (scan) and after pass 3 (emit).
 cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s);
-// scratch: unused (may be null).
+// scratch: unused (may be null).  a.keep_counts: add to the counts instead of
+// zeroing them first.
 cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // Batched selection: per-query ascending point-id lists in ids (cap entries),

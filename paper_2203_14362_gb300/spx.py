@@ -26,7 +26,7 @@ EXPORTS = [
     "spx_join_plain_static", "spx_select", "spx_autotune",
     "spx_server_create", "spx_server_submit", "spx_server_poll", "spx_server_wait", "spx_server_release",
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
-    "spx_cluster_points", "spx_points_info",
+    "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
 ]
 
 SPX_REQ_SELECT, SPX_REQ_JOIN = 1, 2
@@ -133,6 +133,8 @@ def load(path: str = LIB_PATH):
         "spx_server_last_error": ([V], C.c_char_p),
         "spx_server_destroy": ([V], None),
         "spx_cluster_points": ([V, U64, I, P64], I),
+        "spx_aggregate_host": ([V, V, U64, U64, V], I),
+        "spx_set_host_streaming": ([V, I, I], I),
         "spx_points_info": ([V, U64, C.POINTER(V), P64, C.POINTER(I)], I),
         "spx_free": ([V, U64], I),
     }
@@ -323,6 +325,17 @@ class Engine:
             raise SpxError(st, f"join needs {n.value} pairs, capacity {cap}")
         self._check(st, "spx_join_host")
         return pairs[:n.value], counts[:n_polys], n.value
+
+    def aggregate_host(self, xy: np.ndarray, index: int, n_polys: int, counts_out=None):
+        """Count-only aggregation over a host table, streamed through the device."""
+        a = np.ascontiguousarray(xy, dtype=np.int32)
+        counts = counts_out if counts_out is not None else np.zeros(max(n_polys, 1), np.uint64)
+        self._check(self.lib.spx_aggregate_host(self.ctx, _np_ptr(a), a.shape[0], index, _np_ptr(counts)),
+                    "spx_aggregate_host")
+        return counts[:n_polys]
+
+    def set_host_streaming(self, mode: int = 0, slice_log2: int = 0):
+        self._check(self.lib.spx_set_host_streaming(self.ctx, mode, slice_log2), "spx_set_host_streaming")
 
     def set_phase_timing(self, on: bool):
         self._check(self.lib.spx_set_phase_timing(self.ctx, 1 if on else 0), "spx_set_phase_timing")
