@@ -321,8 +321,8 @@ spx_status spx_aggregate_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, 
  * host page tables; else spx_join_host returns SPX_EINVAL), so device memory
  * does not grow with n; mode 0 (the default) stages when the table, its
  * results and the pairs fit in half the free device memory, else streams.
- * slice_log2: points per slice, 16..26 (0: 2^23).  Applies to later calls on
- * this ctx (spx_aggregate_host always streams and uses the same slice size).
+ * slice_log2: points per slice, 16..26 (0: 2^23 for the join, 2^25 for
+ * spx_aggregate_host, which always streams).  Applies to later calls on this ctx.
  */
 spx_status spx_set_host_streaming(spx_ctx *ctx, int mode, int slice_log2);
 

@@ -84,6 +84,7 @@ struct spx_ctx {
     size_t slice_words_n = 0;
     int host_mode = 0;                          // 0 automatic, 1 staged, 2 streamed
     int host_slice_log2 = SPX_HOST_SLICE_LOG2;  // points per slice
+    bool host_slice_set = false;                // set by the caller (else the aggregate takes 2^25)
     // batched selection: captured launch sequences, keyed by their arguments
     std::map<std::tuple<uint64_t, uint64_t, uintptr_t, uint64_t, uintptr_t>, cudaGraphExec_t> select_graphs;
     cudaStream_t capture_stream = nullptr;
@@ -1217,8 +1218,11 @@ spx_status spx_aggregate_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, 
     cudaStream_t s = ctx->stream;
     if (!ctx->in_stream)
         SPX_CUDA(cudaStreamCreateWithFlags(&ctx->in_stream, cudaStreamNonBlocking), "aggregate_host stream");
-    // the points cycle through kRing device slots; counts accumulate on the device
-    const uint64_t kSlice = uint64_t(1) << ctx->host_slice_log2, n_slices = (n + kSlice - 1) / kSlice;
+    // the points cycle through kRing device slots; counts accumulate on the
+    // device.  Without a slice size from the caller, 2^25 points: the count
+    // pass has no output to overlap, so larger slices cut the per-slice cost.
+    const uint64_t kSlice = uint64_t(1) << (ctx->host_slice_set ? ctx->host_slice_log2 : 25);
+    const uint64_t n_slices = (n + kSlice - 1) / kSlice;
     const size_t b_pts = kSlice * 8;
     spx_status st;
     if ((st = ensure(ctx, &ctx->st_counts, &ctx->st_counts_b, size_t(ix->view.P) * 8 + 16, s, "aggregate_host")) !=
@@ -1279,6 +1283,7 @@ spx_status spx_set_host_streaming(spx_ctx *ctx, int mode, int slice_log2)
         return fail(ctx, SPX_EINVAL, "set_host_streaming: mode 0..2, slice_log2 0 or 16..26");
     ctx->host_mode = mode;
     ctx->host_slice_log2 = slice_log2 ? slice_log2 : SPX_HOST_SLICE_LOG2;
+    ctx->host_slice_set = slice_log2 != 0;
     return SPX_OK;
 }
 
