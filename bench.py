@@ -39,7 +39,7 @@ L2_BYTES = 129 * 1024 * 1024
 # k_warp) from one ncu capture of a 20M-point run of the default workload,
 # scaled per point; only valid for that kernel version, the default index
 # (g = 11, sub = 3) and the default workload.
-RESOLVE_TRAFFIC_BYTES_PER_POINT = (298.410496e6 + 62.456576e6) / 20e6
+RESOLVE_TRAFFIC_BYTES_PER_POINT = (298.491648e6 + 62.491904e6) / 20e6
 SERVE_SEED = 0x2203143620 + 4  # request indexes of the serving measurement
 
 

@@ -715,6 +715,7 @@ spx_status spx_autotune(spx_ctx *ctx, spx_points points, spx_polys polys, const 
         a.err = &ctx->aux->err;
         a.stats = ctx->aux->stats;
         a.fp32 = ix->fp32;
+        a.clustered = pts->cluster_log2 ? 1 : 0; // the strided sample keeps the table's order
         float best_t = 0;
         cudaError_t e = cudaSuccess;
         for (int r = 0; r <= reps && e == cudaSuccess; ++r) { // launch 0 warms the index into L2
@@ -930,6 +931,7 @@ spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint6
     a.err = &ctx->aux->err;
     a.stats = ctx->aux->stats;
     a.fp32 = ix->fp32;
+    a.clustered = pts->cluster_log2 ? 1 : 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, 16, s, "aggregate");
     if (st != SPX_OK)

@@ -565,7 +565,7 @@ constexpr int kWChunk = 32 * kWItems;   // consecutive points per warp chunk
 constexpr int kWQueue = kWChunk;        // list points queued per warp: a whole chunk
 constexpr size_t kWarpSmem = size_t(kWarps) * kWQueue * sizeof(uint4);
 
-template <bool FP32, bool RESOLVE>
+template <bool FP32, bool RESOLVE, bool CLUSTERED>
 __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaunch a, uint32_t nchunks, int use_hist)
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -584,10 +584,12 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
     auto count1 = [&](bool has, uint32_t q) {
         if (!a.counts)
             return;
-        if (hist)
-            hist_add_warp(s_hist, has, q);
-        else
+        if (!hist)
             global_add_warp(a.counts, has, q);
+        else if (CLUSTERED) // lanes mostly share a counter: one atomic per distinct polygon
+            hist_add_warp(s_hist, has, q);
+        else if (has) // lanes mostly hit different counters: one atomic each, no vote
+            atomicAdd(s_hist + q, 1u);
     };
     const uint32_t nw = gridDim.x * kWarps;
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
@@ -610,9 +612,8 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             const bool sub = (w[j] >> 30) == kCellSub;
-            const uint32_t fw = fine_word(ix, sub ? w[j] : 0u, sub ? (uint32_t)p[j].x : 0u,
-                                          sub ? (uint32_t)p[j].y : 0u, keep);
-            w[j] = sub ? fw : w[j];
+            if (sub)
+                w[j] = fine_word(ix, w[j], (uint32_t)p[j].x, (uint32_t)p[j].y, keep);
         }
         uint32_t total = 0, qn = 0;
         // walk m <= 32 queued points starting at k0, one per lane
@@ -1121,7 +1122,7 @@ int persistent_grid(K kernel, int threads, size_t smem, uint32_t ntiles)
     return grid;
 }
 
-template <bool FP32, bool RESOLVE>
+template <bool FP32, bool RESOLVE, bool CLUSTERED = false>
 cudaError_t launch_warp_kernel(const JoinLaunch &a, int use_hist, cudaStream_t s)
 {
     static bool done[64] = {};
@@ -1129,12 +1130,12 @@ cudaError_t launch_warp_kernel(const JoinLaunch &a, int use_hist, cudaStream_t s
     if (nchunks >= (1ull << 32))
         return cudaErrorInvalidValue;
     const size_t smem = kWarpSmem + (use_hist ? sizeof(uint32_t) * a.ix.P : 0);
-    cudaError_t e = smem_opt_in(k_warp<FP32, RESOLVE>, kWarpSmem + sizeof(uint32_t) * kHistMax, done);
+    auto kern = k_warp<FP32, RESOLVE, CLUSTERED>;
+    cudaError_t e = smem_opt_in(kern, kWarpSmem + sizeof(uint32_t) * kHistMax, done);
     if (e != cudaSuccess)
         return e;
     const uint32_t nblk = uint32_t((nchunks + kWarps - 1) / kWarps);
-    k_warp<FP32, RESOLVE><<<persistent_grid(k_warp<FP32, RESOLVE>, kThreads, smem, nblk), kThreads, smem, s>>>(
-        a, uint32_t(nchunks), use_hist);
+    kern<<<persistent_grid(kern, kThreads, smem, nblk), kThreads, smem, s>>>(a, uint32_t(nchunks), use_hist);
     return cudaGetLastError();
 }
 
@@ -1381,7 +1382,11 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
     const int use_hist = a.ix.P <= (uint32_t)kHistMax ? 1 : 0;
     if (ev)
         cudaEventRecord(ev[0], s);
-    e = a.fp32 ? launch_warp_kernel<true, false>(a, use_hist, s) : launch_warp_kernel<false, false>(a, use_hist, s);
+    if (a.clustered)
+        e = a.fp32 ? launch_warp_kernel<true, false, true>(a, use_hist, s)
+                   : launch_warp_kernel<false, false, true>(a, use_hist, s);
+    else
+        e = a.fp32 ? launch_warp_kernel<true, false>(a, use_hist, s) : launch_warp_kernel<false, false>(a, use_hist, s);
     if (ev)
         cudaEventRecord(ev[1], s);
     return e;

@@ -49,6 +49,7 @@ struct JoinLaunch {
     uint32_t pid0;
     int keep_counts;
     const unsigned long long *pair_base;
+    int clustered;  // the points are grouped by cell: lanes of a warp mostly share a polygon
 };
 
 // Scratch bytes the join needs for n points (per-point results, tile totals, counter).
