@@ -885,10 +885,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
                     total += c[j];
                     if (!cnt)
                         continue;
-                    if (use_hist)
-                        hist_add_warp(h, c[j] == 1, f[j]);
-                    else
+                    if (!use_hist) // served tables are in row order: lanes rarely share a counter
                         global_add_warp(cnt, c[j] == 1, f[j]);
+                    else if (c[j] == 1)
+                        atomicAdd(h + f[j], 1u);
                     if (c[j] > 1)
                         point_emit<FP32>(ix, p[j].x, p[j].y, keep, [&](uint32_t q) {
                             if (use_hist)
