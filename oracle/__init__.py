@@ -6,7 +6,8 @@ shares no code with the CUDA path.  The arithmetic lives in `pip_oracle.c`
 (plain C, exact int64); this module compiles it with gcc and marshals numpy
 arrays.  See the header of `pip_oracle.c` for the definition it computes
 (SPADE §5.2 selection / join / aggregation, §4.3 exact boundary tests, §7
-intersection = containment for points).
+intersection = containment for points), and of the distance join with disks
+(§5.2 "Distance-Based Queries": distance(p, c) <= r, exact in int64).
 
 Every function here is pinned by tests against facts that do not come from the
 oracle itself (brute force with an independent formulation, closed forms for
@@ -60,6 +61,8 @@ def _bind(lib):
     lib.oracle_free.restype = None
     lib.oracle_join_fast.argtypes = [P, P, C.c_uint64, P, C.c_uint64, P, C.c_int]
     lib.oracle_join_fast.restype = C.c_uint64
+    lib.oracle_disk_join.argtypes = [P, C.c_uint64, P, P, C.c_uint32, P, C.c_uint64, P]
+    lib.oracle_disk_join.restype = C.c_uint64
     return lib
 
 
@@ -99,6 +102,23 @@ def join_pure(points, verts, ring_off, lib=None):
     pairs = np.zeros((max(total, 1), 2), dtype=np.uint32)
     lib.oracle_join_pure(_ptr(pts), pts.shape[0], _ptr(xy), _ptr(off), P, _ptr(pairs), total, _ptr(counts))
     return pairs[:total], counts[:P]
+
+
+def disk_join(points, centers, radii, lib=None):
+    """Distance join (SPADE §5.2 "Distance-Based Queries"): pairs (M, 2) uint32
+    (point id, disk id) with (px - cx)^2 + (py - cy)^2 <= r^2, sorted, and
+    counts (Q,) uint64.  Every disk is tested for every point."""
+    lib = lib or load()
+    pts = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 2)
+    cxy = np.ascontiguousarray(centers, dtype=np.int32).reshape(-1, 2)
+    r = np.ascontiguousarray(radii, dtype=np.int32).reshape(-1)
+    Q = cxy.shape[0]
+    assert r.shape[0] == Q and (Q == 0 or (r.min() >= 0 and r.max() < (1 << 30)))
+    counts = np.zeros(max(Q, 1), dtype=np.uint64)
+    total = lib.oracle_disk_join(_ptr(pts), pts.shape[0], _ptr(cxy), _ptr(r), Q, None, 0, _ptr(counts))
+    pairs = np.zeros((max(total, 1), 2), dtype=np.uint32)
+    lib.oracle_disk_join(_ptr(pts), pts.shape[0], _ptr(cxy), _ptr(r), Q, _ptr(pairs), total, _ptr(counts))
+    return pairs[:total], counts[:Q]
 
 
 class Prepared:

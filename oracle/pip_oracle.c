@@ -355,3 +355,41 @@ uint64_t oracle_join_fast(const oracle_t *o, const int32_t *pts, uint64_t n, uin
     free(th);
     return total;
 }
+
+
+/*
+ * Distance join of points with disks (SPADE §4.2 "Canvases for Distance-Based
+ * Queries" and §5.2 "Distance-Based Queries": a point lies within distance r
+ * of a centre c iff distance(p, c) <= r).  With integer coordinates the test is
+ * exact in int64: (px - cx)^2 + (py - cy)^2 <= r^2 (|differences| < 2^31, so
+ * each square is below 2^62; radii are below 2^30, so r^2 < 2^60 and the sum
+ * of two squares that exceeds r^2 is detected before it could overflow).
+ * Pairs (point id, disk id) in lexicographic order; counts[q] per disk.
+ * Every disk is tested for every point: the definition, written out.
+ */
+uint64_t oracle_disk_join(const int32_t *pts, uint64_t n, const int32_t *cxy, const int32_t *r, uint32_t Q,
+                          uint32_t *pairs, uint64_t cap, uint64_t *counts)
+{
+    uint64_t total = 0;
+    for (uint32_t q = 0; q < Q; ++q)
+        counts[q] = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const int64_t px = pts[2 * i], py = pts[2 * i + 1];
+        for (uint32_t q = 0; q < Q; ++q) {
+            const int64_t dx = px - cxy[2 * q], dy = py - cxy[2 * q + 1], rr = (int64_t)r[q] * r[q];
+            const int64_t dx2 = dx * dx;
+            if (dx2 > rr)
+                continue;
+            if (dx2 + dy * dy > rr)
+                continue;
+            if (pairs && total < cap) {
+                pairs[2 * total] = (uint32_t)i;
+                pairs[2 * total + 1] = q;
+            }
+            counts[q]++;
+            total++;
+        }
+    }
+    return total;
+}
+
