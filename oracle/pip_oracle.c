@@ -375,6 +375,9 @@ uint64_t oracle_disk_join(const int32_t *pts, uint64_t n, const int32_t *cxy, co
         counts[q] = 0;
     for (uint64_t i = 0; i < n; ++i) {
         const int64_t px = pts[2 * i], py = pts[2 * i + 1];
+        /* the points' domain is [0, 2^30)^2; a point outside it is in no disk */
+        if (px < 0 || py < 0 || px >= (1 << ORACLE_BOX_LOG2) || py >= (1 << ORACLE_BOX_LOG2))
+            continue;
         for (uint32_t q = 0; q < Q; ++q) {
             const int64_t dx = px - cxy[2 * q], dy = py - cxy[2 * q + 1], rr = (int64_t)r[q] * r[q];
             const int64_t dx2 = dx * dx;

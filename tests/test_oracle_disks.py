@@ -55,6 +55,13 @@ def test_zero_radius_and_far_points(olib):
     assert counts.tolist() == [1, 3]
 
 
+def test_points_outside_the_domain(olib):
+    # points lie in [0, 2^30)^2; one outside is in no disk, even a disk around it
+    pts = np.array([[-1, 0], [0, -3], [1 << 30, 5], [0, 0], [2, 0]], np.int32)
+    pairs, counts = oracle.disk_join(pts, np.array([[0, 0]], np.int32), np.array([5], np.int32), olib)
+    assert pairs[:, 0].tolist() == [3, 4] and counts.tolist() == [2]
+
+
 def test_translation_invariance_and_order(olib):
     rng = np.random.default_rng(5)
     pts = rng.integers(1 << 20, 1 << 21, size=(20_000, 2)).astype(np.int32)
