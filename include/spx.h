@@ -140,6 +140,24 @@ typedef struct {
  */
 spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params *params, spx_index *out);
 
+/*
+ * Index of a set of disks for distance queries (§4.2 "Canvases for
+ * Distance-Based Queries": a distance constraint around a point is a disk;
+ * §5.2 "Distance-Based Queries": the pairs whose distance is <= r, one radius
+ * per disk as in the paper's second distance join).  Disk q has centre
+ * (cxy[2q], cxy[2q+1]) in [0, 2^30]^2 and radius r[q] in [0, 2^30); a point p
+ * (in [0, 2^30)^2) is within it iff (px-cx)^2 + (py-cy)^2 <= r^2, decided
+ * exactly.  The index is a 2^grid_log2 grid (0: about eight cells across the
+ * median diameter); a cell wholly inside a disk needs no test.  The returned
+ * index serves spx_join (pairs (point id, disk id) in that order, counts per
+ * disk), spx_select (per-disk ascending point-id lists, at most 1024 disks)
+ * and spx_aggregate; the other calls refuse it.  Host input, copied.
+ * Errors: SPX_EINVAL (a centre or radius out of range, a grid too fine for the
+ * number of entries), SPX_ENOMEM, SPX_ECUDA.
+ */
+spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t *r, uint32_t Q, int grid_log2,
+                                spx_index *out);
+
 /* Sizes of a built index. */
 typedef struct {
     int grid_log2;

@@ -17,7 +17,7 @@ LIB = os.path.join(PKG, "libspx.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels.cu", "api.cu", "server.cu"]
-CPP_SOURCES = ["index_build.cpp"]
+CPP_SOURCES = ["index_build.cpp", "disk_index.cpp"]
 
 
 def nvcc() -> str:

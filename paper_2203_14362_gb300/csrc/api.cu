@@ -46,6 +46,8 @@ struct PolysObj {
 
 struct IndexObj {
     uint64_t polys = 0;
+    int kind = 0;        // 0: polygons (view), 1: disks (dview)
+    DiskView dview{};
     IndexView view{};
     int fp32 = 1;
     void *mem = nullptr; // one allocation: cells | entries | edges
@@ -176,6 +178,44 @@ spx_status check_kernel_err(spx_ctx *ctx, cudaStream_t s)
     return SPX_OK;
 }
 
+// The distance join (a disk index): same contract as the polygon join.
+spx_status disk_join_common(spx_ctx *ctx, PointsObj *pts, IndexObj *ix, uint32_t *pairs_dev, uint64_t cap,
+                            uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream)
+{
+    if (cap && !pairs_dev)
+        return fail(ctx, SPX_EINVAL, "join: pairs_dev is NULL with cap > 0");
+    if ((reinterpret_cast<uintptr_t>(pairs_dev) & 7) || (reinterpret_cast<uintptr_t>(counts_dev) & 7) ||
+        (reinterpret_cast<uintptr_t>(total_dev) & 7))
+        return fail(ctx, SPX_EINVAL, "join: output pointers must be 8-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, disk_scratch_bytes(pts->n), s, "join");
+    if (st != SPX_OK)
+        return st;
+    DiskLaunch a{};
+    a.dv = ix->dview;
+    a.pts = reinterpret_cast<const int2 *>(pts->dev);
+    a.n = pts->n;
+    a.pairs = reinterpret_cast<uint2 *>(pairs_dev);
+    a.cap = pairs_dev ? cap : 0;
+    a.counts = reinterpret_cast<unsigned long long *>(counts_dev);
+    a.total = total_dev ? reinterpret_cast<unsigned long long *>(total_dev) : (n_pairs ? &ctx->aux->total : nullptr);
+    a.stats = ctx->aux->stats;
+    cudaError_t e = launch_disk_join(a, ctx->scratch, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "join launch");
+    if (n_pairs) {
+        if ((st = check_kernel_err(ctx, s)) != SPX_OK)
+            return st;
+        unsigned long long t = 0;
+        SPX_CUDA(cudaMemcpy(&t, a.total, sizeof(t), cudaMemcpyDeviceToHost), "read total");
+        *n_pairs = t;
+        if (t > cap)
+            return fail(ctx, SPX_ECAPACITY, "join: " + std::to_string(t) + " pairs exceed capacity " +
+                                                std::to_string(cap));
+    }
+    return SPX_OK;
+}
+
 spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev, uint64_t cap,
                        uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream, bool plain)
 {
@@ -189,6 +229,8 @@ spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_
         return fail(ctx, SPX_EINVAL, "join: bad points or index handle");
     if (pts->cluster_log2)
         return fail(ctx, SPX_EINVAL, "join: a cell-clustered point table has no row order; use spx_aggregate");
+    if (ix->kind == 1)
+        return disk_join_common(ctx, pts, ix, pairs_dev, cap, counts_dev, total_dev, n_pairs, stream);
     if (cap && !pairs_dev)
         return fail(ctx, SPX_EINVAL, "join: pairs_dev is NULL with cap > 0");
     if ((reinterpret_cast<uintptr_t>(pairs_dev) & 7) || (reinterpret_cast<uintptr_t>(counts_dev) & 7) ||
@@ -376,8 +418,9 @@ spx_status served_data(spx_ctx *ctx, spx_points points, const spx_index *indexes
     out.fp32.clear();
     for (uint32_t i = 0; i < n; ++i) {
         IndexObj *ix = lookup(ctx->indexes, indexes[i]);
-        if (!ix)
-            return fail(ctx, SPX_EINVAL, "server: bad index handle at position " + std::to_string(i));
+        if (!ix || ix->kind != 0)
+            return fail(ctx, SPX_EINVAL, "server: bad index handle at position " + std::to_string(i) +
+                                             " (polygon indexes only)");
         out.ix.push_back(ix->view);
         out.fp32.push_back(ix->fp32);
     }
@@ -403,6 +446,8 @@ spx_status spx_join_plain_static(spx_ctx *ctx, spx_points points, spx_index inde
         return fail(ctx, SPX_EINVAL, "join_plain_static: bad points or index handle");
     if (pts->cluster_log2)
         return fail(ctx, SPX_EINVAL, "join_plain_static: a cell-clustered point table has no row order");
+    if (ix->kind != 0)
+        return fail(ctx, SPX_EINVAL, "join_plain_static: needs a polygon index");
     if (pts->n > kStaticJoinMaxPoints)
         return fail(ctx, SPX_EINVAL, "join_plain_static: the point table has " + std::to_string(pts->n) +
                                          " points; the allocation-free join takes at most " +
@@ -810,6 +855,68 @@ spx_status spx_autotune(spx_ctx *ctx, spx_points points, spx_polys polys, const 
     return SPX_OK;
 }
 
+spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t *r, uint32_t Q, int grid_log2,
+                                spx_index *out)
+{
+    if (!ctx || !out || (Q && (!cxy || !r)))
+        return fail(ctx, SPX_EINVAL, "build_disk_index: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    if (Q >= (1u << 30))
+        return fail(ctx, SPX_EINVAL, "build_disk_index: Q must be < 2^30");
+    for (uint32_t q = 0; q < Q; ++q) {
+        if (cxy[2 * q] < 0 || cxy[2 * q] > int32_t(kBox) || cxy[2 * q + 1] < 0 || cxy[2 * q + 1] > int32_t(kBox))
+            return fail(ctx, SPX_EINVAL, "build_disk_index: centre " + std::to_string(q) + " outside [0, 2^30]^2");
+        if (r[q] < 0 || r[q] >= int32_t(kBox))
+            return fail(ctx, SPX_EINVAL, "build_disk_index: radius " + std::to_string(q) + " outside [0, 2^30)");
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const int g = grid_log2 ? grid_log2 : default_disk_grid_log2(r, Q);
+    HostDiskIndex hd;
+    std::string err;
+    if (!build_disk_index(cxy, r, Q, g, hd, err))
+        return fail(ctx, SPX_EINVAL, "build_disk_index: " + err);
+    std::vector<int4> disks(std::max<uint32_t>(Q, 1));
+    for (uint32_t q = 0; q < Q; ++q)
+        disks[q] = make_int4(cxy[2 * q], cxy[2 * q + 1], r[q], 0);
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t b_cell = hd.cell.size() * 4, b_ent = hd.entries.size() * 4, b_disk = disks.size() * sizeof(int4);
+    const size_t total = up(b_cell) + up(b_ent) + up(b_disk);
+    auto ix = std::make_unique<IndexObj>();
+    if (cudaMalloc(&ix->mem, total) != cudaSuccess)
+        return fail(ctx, SPX_ENOMEM, "build_disk_index: cudaMalloc failed");
+    char *m = static_cast<char *>(ix->mem), *p_ent = m + up(b_cell), *p_disk = p_ent + up(b_ent);
+    cudaError_t e = cudaMemcpy(m, hd.cell.data(), b_cell, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p_ent, hd.entries.data(), b_ent, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p_disk, disks.data(), b_disk, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(ix->mem);
+        return cuda_fail(ctx, e, "build_disk_index upload");
+    }
+    ix->kind = 1;
+    ix->dview.cell = reinterpret_cast<const uint32_t *>(m);
+    ix->dview.ent = reinterpret_cast<const uint32_t *>(p_ent);
+    ix->dview.disk = reinterpret_cast<const int4 *>(p_disk);
+    ix->dview.sc = kBoxLog2 - g;
+    ix->dview.g = g;
+    ix->dview.Q = Q;
+    spx_index_info &inf = ix->info;
+    inf.grid_log2 = g;
+    inf.n_polys = Q;
+    inf.n_cells = hd.cell.size();
+    inf.n_entries = hd.entries.size();
+    inf.n_inside = hd.n_inside;
+    inf.n_boundary = hd.n_boundary;
+    inf.device_bytes = total;
+    inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const uint64_t h = make_handle(ctx, kTagIndex);
+    ctx->indexes[h] = std::move(ix);
+    *out = h;
+    return SPX_OK;
+}
+
 spx_status spx_index_info_get(spx_ctx *ctx, spx_index index, spx_index_info *out)
 {
     if (!ctx || !out)
@@ -850,11 +957,39 @@ spx_status spx_select(spx_ctx *ctx, spx_points points, spx_index index, uint32_t
         return fail(ctx, SPX_EINVAL, "select: offsets_dev is NULL, or ids_dev is NULL with cap > 0");
     if ((reinterpret_cast<uintptr_t>(offsets_dev) & 7) || (reinterpret_cast<uintptr_t>(ids_dev) & 3))
         return fail(ctx, SPX_EINVAL, "select: misaligned output pointer");
-    if (ix->view.P > kSelectMaxQueries)
-        return fail(ctx, SPX_EINVAL, "select: an index of " + std::to_string(ix->view.P) +
-                                         " query polygons; batched selection takes at most " +
+    const uint32_t PQ = ix->kind == 1 ? ix->dview.Q : ix->view.P;
+    if (PQ > kSelectMaxQueries)
+        return fail(ctx, SPX_EINVAL, "select: an index of " + std::to_string(PQ) +
+                                         " queries; batched selection takes at most " +
                                          std::to_string(kSelectMaxQueries));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (ix->kind == 1) {
+        // distance selection: points within r of each centre, ascending per disk
+        spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, disk_select_scratch_bytes(pts->n, PQ, cap), s,
+                               "select");
+        if (st != SPX_OK)
+            return st;
+        DiskLaunch a{};
+        a.dv = ix->dview;
+        a.pts = reinterpret_cast<const int2 *>(pts->dev);
+        a.n = pts->n;
+        a.stats = ctx->aux->stats;
+        unsigned long long *offs = reinterpret_cast<unsigned long long *>(offsets_dev);
+        cudaError_t e = launch_disk_select(a, ids_dev, cap, offs, ctx->scratch, s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "select launch");
+        if (n_ids) {
+            if ((st = check_kernel_err(ctx, s)) != SPX_OK)
+                return st;
+            unsigned long long t = 0;
+            SPX_CUDA(cudaMemcpy(&t, offs + PQ, sizeof(t), cudaMemcpyDeviceToHost), "select total");
+            *n_ids = t;
+            if (t > cap)
+                return fail(ctx, SPX_ECAPACITY, "select: " + std::to_string(t) + " ids exceed capacity " +
+                                                    std::to_string(cap));
+        }
+        return SPX_OK;
+    }
     spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, select_scratch_bytes(pts->n, ix->view.P, cap), s,
                            "select");
     if (st != SPX_OK)
@@ -923,6 +1058,16 @@ spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint6
         return fail(ctx, SPX_EINVAL, "aggregate: bad points or index handle");
     if (reinterpret_cast<uintptr_t>(counts_dev) & 7)
         return fail(ctx, SPX_EINVAL, "aggregate: counts_dev must be 8-byte aligned");
+    if (ix->kind == 1) {
+        DiskLaunch d{};
+        d.dv = ix->dview;
+        d.pts = reinterpret_cast<const int2 *>(pts->dev);
+        d.n = pts->n;
+        d.counts = reinterpret_cast<unsigned long long *>(counts_dev);
+        d.stats = ctx->aux->stats;
+        cudaError_t e = launch_disk_aggregate(d, reinterpret_cast<cudaStream_t>(stream));
+        return e == cudaSuccess ? SPX_OK : cuda_fail(ctx, e, "aggregate launch");
+    }
     JoinLaunch a{};
     a.ix = ix->view;
     a.pts = reinterpret_cast<const int2 *>(pts->dev);
@@ -1184,8 +1329,8 @@ spx_status spx_join_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, spx_i
     ctx->err.clear();
     cudaSetDevice(ctx->device);
     IndexObj *ix = lookup(ctx->indexes, index);
-    if (!ix)
-        return fail(ctx, SPX_EINVAL, "join_host: bad index handle");
+    if (!ix || ix->kind != 0)
+        return fail(ctx, SPX_EINVAL, "join_host: bad index handle (a polygon index is needed)");
     if (n >= (1ull << 32))
         return fail(ctx, SPX_EINVAL, "join_host: n must be < 2^32");
     for (cudaStream_t *p : {&ctx->in_stream, &ctx->emit_stream, &ctx->out_stream})
@@ -1215,8 +1360,8 @@ spx_status spx_aggregate_host(spx_ctx *ctx, const int32_t *xy_host, uint64_t n, 
     ctx->err.clear();
     cudaSetDevice(ctx->device);
     IndexObj *ix = lookup(ctx->indexes, index);
-    if (!ix)
-        return fail(ctx, SPX_EINVAL, "aggregate_host: bad index handle");
+    if (!ix || ix->kind != 0)
+        return fail(ctx, SPX_EINVAL, "aggregate_host: bad index handle (a polygon index is needed)");
     cudaStream_t s = ctx->stream;
     if (!ctx->in_stream)
         SPX_CUDA(cudaStreamCreateWithFlags(&ctx->in_stream, cudaStreamNonBlocking), "aggregate_host stream");

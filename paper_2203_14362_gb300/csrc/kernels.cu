@@ -1181,6 +1181,141 @@ cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ distance queries (disks)
+// A point is within distance r of a centre c iff (px-cx)^2 + (py-cy)^2 <= r^2,
+// exact in int64 (differences < 2^31; r < 2^30; the x term is compared with
+// r^2 before the sum, so the sum cannot overflow).  One thread per point, as
+// the plain join: the disks' grid cell, then INSIDE entries count at once and
+// BOUNDARY entries take the exact test; lists are in disk order.
+__device__ __forceinline__ bool in_disk(const int4 &d, int px, int py)
+{
+    const long long dx = (long long)px - d.x, dy = (long long)py - d.y, rr = (long long)d.z * d.z;
+    const long long dx2 = dx * dx;
+    return dx2 <= rr && dx2 + dy * dy <= rr;
+}
+
+template <class F>
+__device__ __forceinline__ uint32_t disk_walk(const DiskView &d, int px, int py, uint32_t &first, uint32_t &tests,
+                                              uint64_t pol, F f)
+{
+    if ((unsigned)px >= kBox || (unsigned)py >= kBox)
+        return 0;
+    const uint32_t w = ld_idx(d.cell + ((((uint32_t)py >> d.sc) << d.g) | ((uint32_t)px >> d.sc)), pol);
+    const uint32_t kind = w >> 30;
+    if (kind == kCellInsideOne) {
+        first = w & kPayloadMask;
+        f(first);
+        return 1;
+    }
+    if (kind != kCellList)
+        return 0;
+    const uint32_t *e = d.ent + (w & kPayloadMask);
+    const uint32_t n = ld_idx(e, pol);
+    uint32_t c = 0;
+    for (uint32_t k = 1; k <= n; ++k) {
+        const uint32_t en = ld_idx(e + k, pol), q = en >> 1;
+        bool in = true;
+        if (en & 1u) {
+            ++tests;
+            in = in_disk(__ldg(d.disk + q), px, py);
+        }
+        if (in) {
+            if (!c)
+                first = q;
+            ++c;
+            f(q);
+        }
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(kPlainThreads) k_disk_count(DiskLaunch a, unsigned long long *block_cnt)
+{
+    __shared__ uint32_t s_w[kPlainThreads / 32];
+    const uint64_t idx = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
+    const uint64_t keep = policy_evict_last();
+    uint32_t c = 0, first = 0, tests = 0;
+    if (idx < a.n) {
+        const int2 p = a.pts[idx];
+        c = disk_walk(a.dv, p.x, p.y, first, tests, keep, [](uint32_t) {});
+    }
+    const uint32_t s = warp_sum32(c);
+    if ((threadIdx.x & 31) == 0)
+        s_w[threadIdx.x >> 5] = s;
+    add_stats(a.stats, idx < a.n ? 1u : 0u, tests, 0u, c);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < kPlainThreads / 32; ++w)
+            b += s_w[w];
+        block_cnt[blockIdx.x] = b;
+    }
+}
+
+__global__ void __launch_bounds__(kPlainThreads) k_disk_write(DiskLaunch a, const unsigned long long *block_off)
+{
+    __shared__ uint32_t s_w[kPlainThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t idx = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
+    const uint64_t keep = policy_evict_last();
+    uint32_t c = 0, first = 0, tests = 0;
+    int2 p = make_int2(-1, -1);
+    if (idx < a.n) {
+        p = a.pts[idx];
+        c = disk_walk(a.dv, p.x, p.y, first, tests, keep, [](uint32_t) {});
+    }
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o)
+            inc += v;
+    }
+    if (lane == 31)
+        s_w[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w)
+        wpre += s_w[w];
+    unsigned long long o = block_off[blockIdx.x] + wpre + inc - c;
+    if (a.counts)
+        global_add_warp(a.counts, c == 1, first);
+    if (c >= 1) {
+        const uint32_t pid = (uint32_t)idx;
+        if (c == 1) {
+            if (o < a.cap)
+                a.pairs[o] = make_uint2(pid, first);
+        } else {
+            uint32_t f2 = 0, t2 = 0;
+            disk_walk(a.dv, p.x, p.y, f2, t2, keep, [&](uint32_t q) {
+                if (o < a.cap)
+                    a.pairs[o] = make_uint2(pid, q);
+                ++o;
+                if (a.counts)
+                    atomicAdd(a.counts + q, 1ull);
+            });
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPlainThreads) k_disk_agg(DiskLaunch a)
+{
+    const uint64_t idx = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
+    const uint64_t keep = policy_evict_last();
+    uint32_t c = 0, first = 0, tests = 0;
+    int2 p = make_int2(-1, -1);
+    if (idx < a.n) {
+        p = a.pts[idx];
+        c = disk_walk(a.dv, p.x, p.y, first, tests, keep, [](uint32_t) {});
+    }
+    global_add_warp(a.counts, c == 1, first);
+    if (c > 1) {
+        uint32_t f2 = 0, t2 = 0;
+        disk_walk(a.dv, p.x, p.y, f2, t2, keep, [&](uint32_t q) { atomicAdd(a.counts + q, 1ull); });
+    }
+    add_stats(a.stats, idx < a.n ? 1u : 0u, tests, 0u, c);
+}
+
 // ------------------------------------------------------ clustered point table
 // Counting sort of a point table by grid cell (row-major cells of a 2^c x 2^c
 // grid; points outside the box go to one last bin).  Lanes of a warp with the
@@ -1600,6 +1735,70 @@ cudaError_t launch_plain_write(const JoinLaunch &a, void *scratch, cudaStream_t 
         return cudaSuccess;
     k_plain_write<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, static_cast<const unsigned long long *>(scratch));
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------ distance-query launchers
+size_t disk_scratch_bytes(uint64_t n) { return plain_split_scratch_bytes(n); }
+
+cudaError_t launch_disk_join(const DiskLaunch &a, void *scratch, cudaStream_t s)
+{
+    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
+    if (nb >= (1ull << 31))
+        return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (a.counts && a.dv.Q)
+        if ((e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.dv.Q, s)) != cudaSuccess)
+            return e;
+    if (nb == 0)
+        return a.total ? cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s) : cudaSuccess;
+    unsigned long long *block = static_cast<unsigned long long *>(scratch);
+    k_disk_count<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    if ((e = launch_scan(block, nb, a.total, block + nb, s)) != cudaSuccess)
+        return e;
+    k_disk_write<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_disk_aggregate(const DiskLaunch &a, cudaStream_t s)
+{
+    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
+    if (nb >= (1ull << 31))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * (a.dv.Q ? a.dv.Q : 1), s);
+    if (e != cudaSuccess || nb == 0)
+        return e;
+    k_disk_agg<<<(unsigned)nb, kPlainThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+size_t disk_select_scratch_bytes(uint64_t n, uint32_t Q, uint64_t cap)
+{
+    return ((disk_scratch_bytes(n) + 15) & ~size_t(15)) + 16 + cap * 8 + partition_scratch_bytes(cap, Q);
+}
+
+cudaError_t launch_disk_select(const DiskLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
+                               void *scratch, cudaStream_t s)
+{
+    if (a.dv.Q > (uint32_t)kSelMaxQ)
+        return cudaErrorInvalidValue;
+    char *sc = static_cast<char *>(scratch);
+    void *join_scratch = sc;
+    sc += (disk_scratch_bytes(a.n) + 15) & ~size_t(15);
+    unsigned long long *total = reinterpret_cast<unsigned long long *>(sc);
+    sc += 16;
+    uint2 *pairs = reinterpret_cast<uint2 *>(sc);
+    sc += cap * 8;
+    DiskLaunch b = a;
+    b.pairs = pairs;
+    b.cap = cap;
+    b.counts = nullptr;
+    b.total = total;
+    cudaError_t e = launch_disk_join(b, join_scratch, s);
+    if (e != cudaSuccess)
+        return e;
+    return launch_partition(pairs, total, cap, a.dv.Q, ids, offsets, sc, s);
 }
 
 } // namespace spx

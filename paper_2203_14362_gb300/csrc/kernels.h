@@ -22,6 +22,41 @@ struct IndexView {
 };
 constexpr int kCoverLog2 = 8;
 
+// A grid index of disks (distance queries): cell words as the coarse level of
+// IndexView; lists in ent (n, then n words disk << 1 | boundary); disks as
+// (cx, cy, r, 0).
+struct DiskView {
+    const uint32_t *cell;
+    const uint32_t *ent;
+    const int4 *disk;
+    int sc; // 30 - g
+    int g;
+    uint32_t Q;
+};
+
+struct DiskLaunch {
+    DiskView dv;
+    const int2 *pts;
+    uint64_t n;
+    uint2 *pairs; // may be null when cap == 0
+    uint64_t cap;
+    unsigned long long *counts; // Q entries or null; zeroed by the launchers
+    unsigned long long *total;  // device total or null
+    unsigned long long *stats;
+};
+
+// Distance join: pairs (point, disk) with distance <= r, in (point, disk)
+// order, counts, total.  scratch: disk_scratch_bytes(n).
+size_t disk_scratch_bytes(uint64_t n);
+cudaError_t launch_disk_join(const DiskLaunch &a, void *scratch, cudaStream_t s);
+// Counts only.
+cudaError_t launch_disk_aggregate(const DiskLaunch &a, cudaStream_t s);
+// Per-disk ascending point-id lists (the selection); scratch:
+// disk_select_scratch_bytes(n, Q, cap).
+size_t disk_select_scratch_bytes(uint64_t n, uint32_t Q, uint64_t cap);
+cudaError_t launch_disk_select(const DiskLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
+                               void *scratch, cudaStream_t s);
+
 // Device status word bits (ORed into the ctx's persistent error word).
 constexpr unsigned kErrTimeout = 1u;   // a bounded wait gave up
 constexpr unsigned kErrInternal = 2u;  // an internal consistency check failed

@@ -57,6 +57,18 @@ struct HostIndex {
     uint64_t n_boundary = 0;         // (fine cell, polygon) pairs that need the exact test
 };
 
+// Grid index of Q disks (centre, radius): cell words as in HostIndex's coarse
+// level (empty / INSIDE one disk / list), lists in `entries`.
+struct HostDiskIndex {
+    int grid_log2 = 0;
+    uint32_t n_disks = 0;
+    std::vector<uint32_t> cell;     // 4^g words
+    std::vector<uint32_t> entries;  // per list: n, then n words (disk << 1 | boundary)
+    uint64_t n_inside = 0, n_boundary = 0;
+};
+bool build_disk_index(const int32_t *cxy, const int32_t *r, uint32_t Q, int g, HostDiskIndex &out, std::string &err);
+int default_disk_grid_log2(const int32_t *r, uint32_t Q);
+
 // Build the index of P rings (xy: interleaved int32 pairs, ring_off: P + 1
 // offsets in vertices) with 2^grid_log2 coarse cells per side, each mixed
 // cell split into 2^sub_log2 x 2^sub_log2 fine cells.  Returns false and sets

@@ -27,6 +27,7 @@ EXPORTS = [
     "spx_server_create", "spx_server_submit", "spx_server_poll", "spx_server_wait", "spx_server_release",
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
     "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
+    "spx_build_disk_index",
 ]
 
 SPX_REQ_SELECT, SPX_REQ_JOIN = 1, 2
@@ -133,6 +134,7 @@ def load(path: str = LIB_PATH):
         "spx_server_last_error": ([V], C.c_char_p),
         "spx_server_destroy": ([V], None),
         "spx_cluster_points": ([V, U64, I, P64], I),
+        "spx_build_disk_index": ([V, V, V, U32, I, P64], I),
         "spx_aggregate_host": ([V, V, U64, U64, V], I),
         "spx_set_host_streaming": ([V, I, I], I),
         "spx_points_info": ([V, U64, C.POINTER(V), P64, C.POINTER(I)], I),
@@ -266,6 +268,16 @@ class Engine:
         params = {"grid_log2": best.grid_log2, "sub_log2": best.sub_log2, "fp32_filter": best.fp32_filter}
         rows = [{f: getattr(trials[i], f) for f, _ in TuneTrial._fields_} for i in range(min(n.value, 64))]
         return params, rows, (h.value if keep_index else None)
+
+    def build_disk_index(self, centers: np.ndarray, radii: np.ndarray, grid_log2: int = 0) -> int:
+        """spx_build_disk_index: an index of disks for distance joins / selections."""
+        c = np.ascontiguousarray(centers, dtype=np.int32).reshape(-1, 2)
+        r = np.ascontiguousarray(radii, dtype=np.int32).reshape(-1)
+        assert c.shape[0] == r.shape[0]
+        h = C.c_uint64()
+        self._check(self.lib.spx_build_disk_index(self.ctx, _np_ptr(c), _np_ptr(r), c.shape[0], grid_log2,
+                                                  C.byref(h)), "spx_build_disk_index")
+        return h.value
 
     def index_info(self, index: int) -> dict:
         inf = IndexInfo()
