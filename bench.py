@@ -66,6 +66,17 @@ def make_workload(name: str, n_override: int | None, rank: int):
         desc = (f"batched selection: {n} mixture points x 256 query polygons (lognormal 8-5000 vertices, "
                 f"concave, overlapping); per-query ascending id lists")
         return pts, v, o, desc
+    if name == "dist1024_100m":
+        n = n_override or 100_000_000
+        seed = g.SEED_BASE + 6
+        mix = g.make_mixture(seed)
+        pts = g.mixture_points_parallel(n, seed, mix, start=shard_start(rank, n))
+        centers = g.mixture_points(1024, seed + 1, mix)
+        rng = np.random.default_rng(seed)
+        radii = np.clip(np.exp(rng.normal(np.log(0.001 * (1 << 30)), 0.8, 1024)), 1e4, 2e7).astype(np.int32)
+        desc = (f"distance join: {n} mixture points x 1024 disks (centres from the point mixture, radius "
+                f"lognormal, median 0.1% of the box); pairs (point, disk) with distance <= r + counts")
+        return pts, centers, radii, desc
     if name == "serve_1b":
         n = n_override or 1_000_000_000
         seed = g.SEED_BASE + 4
@@ -228,6 +239,19 @@ def cpu_baseline(pts, verts, ring_off, budget_s: float = 12.0, chunk: int = 1_00
             "sample": f"first {done} points of the same table (pairs + counts, fast oracle, {el:.1f} s)"}
 
 
+def disk_cpu_baseline(pts, centers, radii, budget_s: float = 12.0, chunk: int = 200_000):
+    """The oracle's distance join (every disk for every point) on the first points."""
+    import oracle
+    done, t0 = 0, time.perf_counter()
+    while done < pts.shape[0] and time.perf_counter() - t0 < budget_s:
+        m = min(chunk, pts.shape[0] - done)
+        oracle.disk_join(pts[done:done + m], centers, radii)
+        done += m
+    el = time.perf_counter() - t0
+    return {"value": done / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} points (distance join, brute force over all disks, {el:.1f} s)"}
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args, world, rank):
     if rank != 0:
@@ -241,16 +265,24 @@ def run_reference(args, world, rank):
                           "workloads; this workload reports its oracle sample in cpu_baseline"}), flush=True)
         return 0
     pts, v, o, desc = make_workload(args.workload, sample, 0)
-    pr = oracle.Prepared(v, o)
-    threads = oracle.default_threads()
+    if args.workload.startswith("dist"):
+        threads = 1
+
+        def step():
+            oracle.disk_join(pts, v, o)
+    else:
+        pr = oracle.Prepared(v, o)
+        threads = oracle.default_threads()
+
+        def step():
+            pr.join(pts, threads=threads)
     for _ in range(max(args.warmup, 0)):
-        pr.join(pts, threads=threads)
+        step()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        pr.join(pts, threads=threads)
+        step()
         times.append(time.perf_counter() - t0)
-    pr.close()
     sec = sum(times) / len(times)
     val = sample / sec / 1e9
     line = {
@@ -258,7 +290,7 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "sample_points_per_step": sample,
-                   "polygons": int(o.shape[0] - 1), "vertices": int(v.shape[0])},
+                   "polygons": int(v.shape[0]) if args.workload.startswith("dist") else int(o.shape[0] - 1)},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"first {sample} points of the workload per step (pairs + counts, fast oracle)"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -288,10 +320,13 @@ def run_spx(args, world, rank, local):
     ph = eng.load_points(dpts)
     if args.workload == "serve_1b":
         return run_serve_bench(args, world, rank, eng, ph, dpts, N, desc, clocks, torch)
-    P = int(o.shape[0] - 1)
-    gh = eng.load_polygons(v, o)
+    dist = args.workload.startswith("dist")
+    P = int(v.shape[0]) if dist else int(o.shape[0] - 1)
+    gh = None if dist else eng.load_polygons(v, o)
     tune = None
-    if args.autotune:
+    if dist:
+        ih = eng.build_disk_index(v, o, args.grid)
+    elif args.autotune:
         t0 = time.perf_counter()
         params, trials, ih = eng.autotune(ph, gh, fp32_filter=bool(args.fp32))
         tune = {"picked": [params["grid_log2"], params["sub_log2"]], "seconds": round(time.perf_counter() - t0, 2),
@@ -306,7 +341,14 @@ def run_spx(args, world, rank, local):
     pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
     counts = torch.zeros(max(P, 1), dtype=torch.int64, device="cuda")
     total = torch.zeros(1, dtype=torch.int64, device="cuda")
-    n_pairs = eng.join(ph, ih, pairs, counts, total, sync=True, plain=args.plain)
+    try:
+        n_pairs = eng.join(ph, ih, pairs, counts, total, sync=True, plain=args.plain)
+    except spx.SpxError as e:  # the two-call pattern: the first call reports the size
+        if e.status != spx.SPX_ECAPACITY:
+            raise
+        cap = int(str(e).split("needs ")[1].split(" ")[0])
+        pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+        n_pairs = eng.join(ph, ih, pairs, counts, total, sync=True, plain=args.plain)
     assert int(counts.sum().item()) == n_pairs
 
     stream = torch.cuda.current_stream()
@@ -344,7 +386,7 @@ def run_spx(args, world, rank, local):
 
     # end to end through the C ABI on pinned host buffers (H2D points, join, D2H pairs + counts)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not dist:  # spx_join_host takes polygon indexes
         hx = torch.empty((N, 2), dtype=torch.int32, pin_memory=True)
         hx.numpy()[:] = pts
         hp = torch.empty((cap, 2), dtype=torch.int32, pin_memory=True)
@@ -362,16 +404,18 @@ def run_spx(args, world, rank, local):
     clocks.stop()
 
     serving = None
-    if not args.no_serve and not args.plain:
+    if not args.no_serve and not args.plain and not dist:
         serving = run_serving(eng, ph, N, SERVE_SEED, timed=args.serve_timed, warm=args.serve_warmup,
                               burst=args.serve_burst)
 
     idx_bytes = int(info["device_bytes"])
     step_bytes = 8 * N + 8 * n_pairs + 8 * P + idx_bytes  # algorithmic bytes of one join
     peak, peak_kind = peaks()
-    # dominant kernel: the resolve pass (reads every point once, writes the counts)
-    dom_ms = phase_ms["resolve"] if not args.plain else ms
-    dom_bytes = 8 * N + 8 * P + idx_bytes if not args.plain else step_bytes
+    # dominant kernel: the resolve pass (reads every point once, writes the counts);
+    # the distance join has no phase timing: its whole step
+    whole = args.plain or dist
+    dom_ms = ms if whole else phase_ms["resolve"]
+    dom_bytes = step_bytes if whole else 8 * N + 8 * P + idx_bytes
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = args.traffic
     if (traffic is None and RESOLVE_TRAFFIC_BYTES_PER_POINT and not args.plain and args.workload == "tess2000_100m"
@@ -379,15 +423,19 @@ def run_spx(args, world, rank, local):
         traffic = RESOLVE_TRAFFIC_BYTES_PER_POINT * N
     out = None
     if rank == 0:
-        cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(pts, v, o, args.cpu_budget)
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = disk_cpu_baseline(pts, v, o, args.cpu_budget) if dist else cpu_baseline(pts, v, o, args.cpu_budget)
         out = {
             "metric": METRIC, "value": world * N / (ms_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {
                 "workload": args.workload, "desc": desc, "points_per_gpu": N, "polygons": P,
-                "vertices": int(v.shape[0]), "pairs": int(n_pairs), "grid_log2": info["grid_log2"], "sub_log2": info["sub_log2"],
-                "fp32_filter": bool(args.fp32), "kernel": "plain two-pass" if args.plain else "resolve + scan + emit (cached two-pass Map)",
+                "vertices": 0 if dist else int(v.shape[0]), "pairs": int(n_pairs), "grid_log2": info["grid_log2"],
+                "sub_log2": info["sub_log2"], "fp32_filter": bool(args.fp32),
+                "kernel": ("distance join: count, scan, write (one thread per point)" if dist else
+                           "plain two-pass" if args.plain else "resolve (k_warp) + scan + emit (k_wemit): cached two-pass Map"),
                 "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": int(info["device_bytes"]),
                 "l2": "inputs larger than L2 (points 8 B x N + pairs 8 B x N >> 129 MB); no flush",
                 "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
@@ -397,7 +445,8 @@ def run_spx(args, world, rank, local):
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": "k_warp<resolve> (join pass 1)" if not args.plain else "plain join (3 kernels)",
+                         "kernel": ("disk join (3 kernels)" if dist else "plain join (3 kernels)" if args.plain
+                                    else "k_warp<resolve> (join pass 1)"),
                          "kernel_ms": dom_ms, "algorithmic_bytes_per_launch": int(dom_bytes),
                          "step": {"algorithmic_bytes": int(step_bytes), "ms": ms,
                                   "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
@@ -405,13 +454,14 @@ def run_spx(args, world, rank, local):
                          "phase_ms": phase_ms},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * join_launches(N, args.plain),
+            "gpu_launches": args.steps * join_launches(N, args.plain or dist),
             "clocks": clk,
             "serving": serving,
         }
         print(json.dumps(out), flush=True)
     eng.free(ih)
-    eng.free(gh)
+    if gh is not None:
+        eng.free(gh)
     eng.free(ph)
     eng.close()
     del dpts
@@ -795,7 +845,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["spx", "reference"], default="spx")
     ap.add_argument("--workload", default="tess2000_100m",
-                    choices=["tess2000_100m", "stars_1m", "select256_500m", "serve_1b", "count_4b"])
+                    choices=["tess2000_100m", "stars_1m", "select256_500m", "serve_1b", "count_4b", "dist1024_100m"])
     ap.add_argument("--points", type=int, default=None, help="points per GPU (default: the workload's)")
     ap.add_argument("--grid", type=int, default=0, help="grid_log2 (0 = automatic)")
     ap.add_argument("--sub", type=int, default=0, help="sub_log2 (0 = default, 3)")
