@@ -411,9 +411,8 @@ def run_spx(args, world, rank, local):
     idx_bytes = int(info["device_bytes"])
     step_bytes = 8 * N + 8 * n_pairs + 8 * P + idx_bytes  # algorithmic bytes of one join
     peak, peak_kind = peaks()
-    # dominant kernel: the resolve pass (reads every point once, writes the counts);
-    # the distance join has no phase timing: its whole step
-    whole = args.plain or dist
+    # dominant kernel: the resolve pass (reads every point once, writes the counts)
+    whole = args.plain
     dom_ms = ms if whole else phase_ms["resolve"]
     dom_bytes = step_bytes if whole else 8 * N + 8 * P + idx_bytes
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
@@ -434,7 +433,7 @@ def run_spx(args, world, rank, local):
                 "workload": args.workload, "desc": desc, "points_per_gpu": N, "polygons": P,
                 "vertices": 0 if dist else int(v.shape[0]), "pairs": int(n_pairs), "grid_log2": info["grid_log2"],
                 "sub_log2": info["sub_log2"], "fp32_filter": bool(args.fp32),
-                "kernel": ("distance join: count, scan, write (one thread per point)" if dist else
+                "kernel": ("distance join: resolve (k_dwarp) + scan + emit (k_dwemit)" if dist else
                            "plain two-pass" if args.plain else "resolve (k_warp) + scan + emit (k_wemit): cached two-pass Map"),
                 "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": int(info["device_bytes"]),
                 "l2": "inputs larger than L2 (points 8 B x N + pairs 8 B x N >> 129 MB); no flush",
@@ -445,8 +444,8 @@ def run_spx(args, world, rank, local):
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": ("disk join (3 kernels)" if dist else "plain join (3 kernels)" if args.plain
-                                    else "k_warp<resolve> (join pass 1)"),
+                         "kernel": ("k_dwarp<resolve> (distance join pass 1)" if dist else "plain join (3 kernels)"
+                                    if args.plain else "k_warp<resolve> (join pass 1)"),
                          "kernel_ms": dom_ms, "algorithmic_bytes_per_launch": int(dom_bytes),
                          "step": {"algorithmic_bytes": int(step_bytes), "ms": ms,
                                   "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
@@ -454,7 +453,7 @@ def run_spx(args, world, rank, local):
                          "phase_ms": phase_ms},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * join_launches(N, args.plain or dist),
+            "gpu_launches": args.steps * join_launches(N, args.plain),
             "clocks": clk,
             "serving": serving,
         }

@@ -178,6 +178,37 @@ spx_status check_kernel_err(spx_ctx *ctx, cudaStream_t s)
     return SPX_OK;
 }
 
+// Cover bitmap of a 2^g x 2^g grid of cell words: one bit per block of
+// cells of a 2^cg x 2^cg grid (cg = min(g, kCoverLog2)), set when any cell of
+// the block is not empty.
+std::vector<uint32_t> cover_bitmap(const std::vector<uint32_t> &cell, int g)
+{
+    const int cg = std::min(g, kCoverLog2);
+    std::vector<uint32_t> cover(std::max<size_t>((size_t(1) << (2 * cg)) / 32, 1), 0u);
+    for (uint32_t cy = 0; cy < (1u << g); ++cy)
+        for (uint32_t cx = 0; cx < (1u << g); ++cx)
+            if ((cell[(size_t(cy) << g) | cx] >> 30) != kCellEmpty) {
+                const uint32_t b = ((cy >> (g - cg)) << cg) | (cx >> (g - cg));
+                cover[b >> 5] |= 1u << (b & 31);
+            }
+    return cover;
+}
+
+// Adds the phases of the join just launched (events ev[0..3]) to the totals.
+spx_status add_phase_times(spx_ctx *ctx)
+{
+    SPX_CUDA(cudaEventSynchronize(ctx->ev[3]), "join timing");
+    float t1 = 0, t2 = 0, t3 = 0;
+    cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&t3, ctx->ev[2], ctx->ev[3]);
+    ctx->ms_resolve += t1;
+    ctx->ms_scan += t2;
+    ctx->ms_emit += t3;
+    ctx->timed_joins++;
+    return SPX_OK;
+}
+
 // The distance join (a disk index): same contract as the polygon join.
 spx_status disk_join_common(spx_ctx *ctx, PointsObj *pts, IndexObj *ix, uint32_t *pairs_dev, uint64_t cap,
                             uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream)
@@ -200,9 +231,12 @@ spx_status disk_join_common(spx_ctx *ctx, PointsObj *pts, IndexObj *ix, uint32_t
     a.counts = reinterpret_cast<unsigned long long *>(counts_dev);
     a.total = total_dev ? reinterpret_cast<unsigned long long *>(total_dev) : (n_pairs ? &ctx->aux->total : nullptr);
     a.stats = ctx->aux->stats;
-    cudaError_t e = launch_disk_join(a, ctx->scratch, s);
+    const bool timed = ctx->timing;
+    cudaError_t e = launch_disk_join(a, ctx->scratch, s, timed ? ctx->ev : nullptr);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "join launch");
+    if (timed && pts->n && (st = add_phase_times(ctx)) != SPX_OK)
+        return st;
     if (n_pairs) {
         if ((st = check_kernel_err(ctx, s)) != SPX_OK)
             return st;
@@ -256,17 +290,8 @@ spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_
     cudaError_t e = plain ? launch_join_plain(a, ctx->scratch, s) : launch_join(a, ctx->scratch, s, timed ? ctx->ev : nullptr);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "join launch");
-    if (timed && pts->n) {
-        SPX_CUDA(cudaEventSynchronize(ctx->ev[3]), "join timing");
-        float t1 = 0, t2 = 0, t3 = 0;
-        cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
-        cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
-        cudaEventElapsedTime(&t3, ctx->ev[2], ctx->ev[3]);
-        ctx->ms_resolve += t1;
-        ctx->ms_scan += t2;
-        ctx->ms_emit += t3;
-        ctx->timed_joins++;
-    }
+    if (timed && pts->n && (st = add_phase_times(ctx)) != SPX_OK)
+        return st;
     if (n_pairs) {
         st = check_kernel_err(ctx, s);
         if (st != SPX_OK)
@@ -330,15 +355,8 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     const int threads = std::max(1u, std::thread::hardware_concurrency());
     if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, sb, threads, hi, err))
         return fail(ctx, SPX_EINVAL, "build_index: " + err);
-    // cover bitmap: one bit per block of coarse cells, set when any of them is not empty
     const int cg = std::min(g, kCoverLog2);
-    std::vector<uint32_t> cover(std::max<size_t>((size_t(1) << (2 * cg)) / 32, 1), 0u);
-    for (uint32_t cy = 0; cy < (1u << g); ++cy)
-        for (uint32_t cx = 0; cx < (1u << g); ++cx)
-            if ((hi.cell[(size_t(cy) << g) | cx] >> 30) != kCellEmpty) {
-                const uint32_t b = ((cy >> (g - cg)) << cg) | (cx >> (g - cg));
-                cover[b >> 5] |= 1u << (b & 31);
-            }
+    const std::vector<uint32_t> cover = cover_bitmap(hi.cell, g);
     const size_t b_cell = hi.cell.size() * 4, b_fine = hi.fine.size() * 4, b_ent = hi.entries.size() * 4,
                  b_edge = hi.edges.size() * 4, b_cover = cover.size() * 4;
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
@@ -879,18 +897,23 @@ spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t 
     std::vector<int4> disks(std::max<uint32_t>(Q, 1));
     for (uint32_t q = 0; q < Q; ++q)
         disks[q] = make_int4(cxy[2 * q], cxy[2 * q + 1], r[q], 0);
+    const std::vector<uint32_t> cover = cover_bitmap(hd.cell, g);
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-    const size_t b_cell = hd.cell.size() * 4, b_ent = hd.entries.size() * 4, b_disk = disks.size() * sizeof(int4);
-    const size_t total = up(b_cell) + up(b_ent) + up(b_disk);
+    const size_t b_cell = hd.cell.size() * 4, b_ent = hd.entries.size() * 4, b_disk = disks.size() * sizeof(int4),
+                 b_cover = cover.size() * 4;
+    const size_t total = up(b_cell) + up(b_ent) + up(b_disk) + up(b_cover);
     auto ix = std::make_unique<IndexObj>();
     if (cudaMalloc(&ix->mem, total) != cudaSuccess)
         return fail(ctx, SPX_ENOMEM, "build_disk_index: cudaMalloc failed");
-    char *m = static_cast<char *>(ix->mem), *p_ent = m + up(b_cell), *p_disk = p_ent + up(b_ent);
+    char *m = static_cast<char *>(ix->mem), *p_ent = m + up(b_cell), *p_disk = p_ent + up(b_ent),
+         *p_cover = p_disk + up(b_disk);
     cudaError_t e = cudaMemcpy(m, hd.cell.data(), b_cell, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(p_ent, hd.entries.data(), b_ent, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(p_disk, disks.data(), b_disk, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p_cover, cover.data(), b_cover, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(ix->mem);
         return cuda_fail(ctx, e, "build_disk_index upload");
@@ -899,8 +922,11 @@ spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t 
     ix->dview.cell = reinterpret_cast<const uint32_t *>(m);
     ix->dview.ent = reinterpret_cast<const uint32_t *>(p_ent);
     ix->dview.disk = reinterpret_cast<const int4 *>(p_disk);
+    ix->dview.cover = reinterpret_cast<const uint32_t *>(p_cover);
     ix->dview.sc = kBoxLog2 - g;
     ix->dview.g = g;
+    ix->dview.cg = std::min(g, kCoverLog2);
+    ix->dview.scv = kBoxLog2 - ix->dview.cg;
     ix->dview.Q = Q;
     spx_index_info &inf = ix->info;
     inf.grid_log2 = g;

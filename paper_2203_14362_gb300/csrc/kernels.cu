@@ -1184,9 +1184,9 @@ cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_
 // ------------------------------------------------------ distance queries (disks)
 // A point is within distance r of a centre c iff (px-cx)^2 + (py-cy)^2 <= r^2,
 // exact in int64 (differences < 2^31; r < 2^30; the x term is compared with
-// r^2 before the sum, so the sum cannot overflow).  One thread per point, as
-// the plain join: the disks' grid cell, then INSIDE entries count at once and
-// BOUNDARY entries take the exact test; lists are in disk order.
+// r^2 before the sum, so the sum cannot overflow).  A point reads the word of
+// its cell in the disks' grid; INSIDE entries count at once and BOUNDARY
+// entries take the exact test; lists are in disk order.
 __device__ __forceinline__ bool in_disk(const int4 &d, int px, int py)
 {
     const long long dx = (long long)px - d.x, dy = (long long)py - d.y, rr = (long long)d.z * d.z;
@@ -1229,91 +1229,262 @@ __device__ __forceinline__ uint32_t disk_walk(const DiskView &d, int px, int py,
     return c;
 }
 
-__global__ void __launch_bounds__(kPlainThreads) k_disk_count(DiskLaunch a, unsigned long long *block_cnt)
-{
-    __shared__ uint32_t s_w[kPlainThreads / 32];
-    const uint64_t idx = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
-    const uint64_t keep = policy_evict_last();
-    uint32_t c = 0, first = 0, tests = 0;
-    if (idx < a.n) {
-        const int2 p = a.pts[idx];
-        c = disk_walk(a.dv, p.x, p.y, first, tests, keep, [](uint32_t) {});
-    }
-    const uint32_t s = warp_sum32(c);
-    if ((threadIdx.x & 31) == 0)
-        s_w[threadIdx.x >> 5] = s;
-    add_stats(a.stats, idx < a.n ? 1u : 0u, tests, 0u, c);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long b = 0;
-        for (int w = 0; w < kPlainThreads / 32; ++w)
-            b += s_w[w];
-        block_cnt[blockIdx.x] = b;
-    }
-}
+// Distance join with warp chunks (the design of k_warp / k_wemit): pass 1
+// resolves every point once: the cover bitmap (in shared memory) sends the
+// points of blocks without any disk away without an index read; the others
+// read their cell word, and the points of list cells are queued in shared
+// memory.  The queue carries over from chunk to chunk and the warp walks it
+// in full rounds of 32 (one chain of dependent loads per 32 list points); a
+// walked point adds its pairs to its own chunk's total (zeroed before the
+// launch).  It stores a 4-byte result per point and a pair total per
+// 256-point chunk, and counts per disk (in shared memory when Q <=
+// kHistMax); pass 3 writes the pairs from the results.
+constexpr uint32_t kDiskCoverWords = 1u << (2 * kCoverLog2 - 5); // cover bitmap in shared memory
+constexpr int kDQueue = kWChunk + 32; // a chunk's points plus a partial round
+constexpr size_t kDWarpSmem = size_t(kWarps) * kDQueue * sizeof(uint4);
 
-__global__ void __launch_bounds__(kPlainThreads) k_disk_write(DiskLaunch a, const unsigned long long *block_off)
+template <bool RESOLVE>
+__global__ void __launch_bounds__(kThreads, 4) k_dwarp(DiskLaunch a, unsigned long long *chunk_tot, uint32_t *res,
+                                                       uint32_t nchunks, int use_hist)
 {
-    __shared__ uint32_t s_w[kPlainThreads / 32];
+    extern __shared__ __align__(16) unsigned char s_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t idx = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
+    uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kDQueue; // (x, y, list offset, point index)
+    uint32_t *s_cov = reinterpret_cast<uint32_t *>(s_raw + kDWarpSmem);
+    uint32_t *s_hist = s_cov + kDiskCoverWords;
+    const DiskView &d = a.dv;
     const uint64_t keep = policy_evict_last();
-    uint32_t c = 0, first = 0, tests = 0;
-    int2 p = make_int2(-1, -1);
-    if (idx < a.n) {
-        p = a.pts[idx];
-        c = disk_walk(a.dv, p.x, p.y, first, tests, keep, [](uint32_t) {});
-    }
-    uint32_t inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o)
-            inc += v;
-    }
-    if (lane == 31)
-        s_w[warp] = inc;
+    const bool hist = use_hist && a.counts;
+    const uint32_t ncov = max(1u, (1u << (2 * d.cg)) >> 5);
+    for (uint32_t i = threadIdx.x; i < ncov; i += kThreads)
+        s_cov[i] = __ldg(d.cover + i);
+    if (hist)
+        for (uint32_t i = threadIdx.x; i < d.Q; i += kThreads)
+            s_hist[i] = 0;
     __syncthreads();
-    uint32_t wpre = 0;
-    for (int w = 0; w < warp; ++w)
-        wpre += s_w[w];
-    unsigned long long o = block_off[blockIdx.x] + wpre + inc - c;
-    if (a.counts)
-        global_add_warp(a.counts, c == 1, first);
-    if (c >= 1) {
-        const uint32_t pid = (uint32_t)idx;
-        if (c == 1) {
-            if (o < a.cap)
-                a.pairs[o] = make_uint2(pid, first);
-        } else {
-            uint32_t f2 = 0, t2 = 0;
-            disk_walk(a.dv, p.x, p.y, f2, t2, keep, [&](uint32_t q) {
-                if (o < a.cap)
-                    a.pairs[o] = make_uint2(pid, q);
-                ++o;
-                if (a.counts)
-                    atomicAdd(a.counts + q, 1ull);
-            });
+    // count one disk for every lane with has (converged warp)
+    auto count1 = [&](bool has, uint32_t q) {
+        if (!a.counts)
+            return;
+        if (!hist)
+            global_add_warp(a.counts, has, q);
+        else if (has)
+            atomicAdd(s_hist + q, 1u);
+    };
+    uint32_t n_tests = 0, n_pts = 0, n_pairs = 0;
+    // walk queued list points [k0, k0 + m), m <= 32, one per lane; their pairs
+    // are added to their chunk's total
+    auto walk = [&](uint32_t k0, uint32_t m) {
+        const bool has = (uint32_t)lane < m;
+        const uint4 it = s_q[k0 + (has ? lane : 0)]; // idle lanes repeat lane 0's walk, uncounted
+        const uint32_t *e = d.ent + it.z;
+        const uint32_t n = ld_idx(e, keep);
+        uint32_t c = 0, f = 0, t_l = 0;
+        for (uint32_t k = 1; k <= n; ++k) {
+            const uint32_t en = ld_idx(e + k, keep), q = en >> 1;
+            bool in = true;
+            if (en & 1u) {
+                ++t_l;
+                in = in_disk(__ldg(d.disk + q), (int)it.x, (int)it.y);
+            }
+            if (in) {
+                if (!c)
+                    f = q;
+                else if (has && a.counts) // the first disk is counted with the warp below
+                    hist ? (void)atomicAdd(s_hist + q, 1u) : (void)atomicAdd(a.counts + q, 1ull);
+                ++c;
+            }
+        }
+        c = has ? c : 0u;
+        n_tests += has ? t_l : 0u;
+        n_pairs += c;
+        count1(c >= 1, f);
+        if (RESOLVE && has) {
+            __stcg(res + it.w, res_encode(c, f));
+            if (c)
+                atomicAdd(chunk_tot + it.w / kWChunk, (unsigned long long)c);
+        }
+        __syncwarp();
+    };
+    const uint32_t nw = gridDim.x * kWarps;
+    uint32_t qn = 0; // queued list points, < 32 between chunks
+    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+        const uint64_t base = (uint64_t)ch * kWChunk;
+        const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
+        int2 p[kWItems];
+        uint32_t w[kWItems];
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t loc = j * 32 + lane;
+            p[j] = loc < npts ? __ldcs(a.pts + base + loc) : make_int2(-1, -1);
+            n_pts += loc < npts ? 1u : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            // points outside the box or in a block of empty cells read no cell word
+            const uint32_t px = (uint32_t)p[j].x, py = (uint32_t)p[j].y;
+            const uint32_t b = (((py & (kBox - 1)) >> d.scv) << d.cg) | ((px & (kBox - 1)) >> d.scv);
+            const bool ok = px < kBox && py < kBox && ((s_cov[b >> 5] >> (b & 31)) & 1u);
+            w[j] = ok ? ld_idx(d.cell + ((((py & (kBox - 1)) >> d.sc) << d.g) | ((px & (kBox - 1)) >> d.sc)), keep)
+                      : 0u;
+        }
+        uint32_t total = 0;
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t kind = w[j] >> 30, loc = j * 32 + lane;
+            const bool one = kind == kCellInsideOne, lst = kind == kCellList;
+            total += one ? 1u : 0u;
+            count1(one, w[j] & kPayloadMask);
+            if (RESOLVE && loc < npts && !lst)
+                __stcg(res + base + loc, one ? (w[j] & kPayloadMask) : kResNone);
+            const uint32_t bl = __ballot_sync(kFull, lst);
+            if (lst)
+                s_q[qn + __popc(bl & lanemask_lt())] =
+                    make_uint4((uint32_t)p[j].x, (uint32_t)p[j].y, w[j] & kPayloadMask, (uint32_t)(base + loc));
+            qn += __popc(bl);
+        }
+        n_pairs += total;
+        total = warp_sum32(total);
+        if (RESOLVE && lane == 0 && total)
+            atomicAdd(chunk_tot + ch, (unsigned long long)total);
+        __syncwarp();
+        if (qn >= 32) {
+            uint32_t k0 = 0;
+            for (; qn - k0 >= 32; k0 += 32)
+                walk(k0, 32);
+            // move the partial round (< 32, from k0 >= 32) to the front
+            const uint32_t rem = qn - k0;
+            const uint4 it = (uint32_t)lane < rem ? s_q[k0 + lane] : make_uint4(0, 0, 0, 0);
+            __syncwarp();
+            if ((uint32_t)lane < rem)
+                s_q[lane] = it;
+            qn = rem;
+            __syncwarp();
         }
     }
+    __syncwarp();
+    if (qn)
+        walk(0, qn);
+    if (hist) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < d.Q; i += kThreads)
+            if (s_hist[i])
+                atomicAdd(a.counts + i, (unsigned long long)s_hist[i]);
+    }
+    add_stats(a.stats, n_pts, n_tests, 0u, n_pairs);
 }
 
-__global__ void __launch_bounds__(kPlainThreads) k_disk_agg(DiskLaunch a)
+// Pass 3 of the distance join: as k_wemit, a point in one disk is written at
+// once and a point in several is queued with its offset.  Such points are
+// rare, so the queue carries over from chunk to chunk and the warp walks it
+// only in full rounds of 32 (and what is left at the end): a pair's place
+// comes from its offset, not from when it is written.
+constexpr size_t kDEmitSmem = size_t(kWarps) * kDQueue * (sizeof(uint4) + sizeof(unsigned long long));
+
+__global__ void __launch_bounds__(kThreads, 4) k_dwemit(DiskLaunch a, const unsigned long long *chunk_off,
+                                                        const uint32_t *res_in, uint32_t nchunks)
 {
-    const uint64_t idx = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kDQueue; // (x, y, point id)
+    unsigned long long *s_o =
+        reinterpret_cast<unsigned long long *>(s_raw + size_t(kWarps) * kDQueue * sizeof(uint4)) + warp * kDQueue;
     const uint64_t keep = policy_evict_last();
-    uint32_t c = 0, first = 0, tests = 0;
-    int2 p = make_int2(-1, -1);
-    if (idx < a.n) {
-        p = a.pts[idx];
-        c = disk_walk(a.dv, p.x, p.y, first, tests, keep, [](uint32_t) {});
+    // walk queued points [k0, k0 + m), m <= 32, one per lane
+    auto walk = [&](uint32_t k0, uint32_t m) {
+        if ((uint32_t)lane < m) {
+            const uint4 it = s_q[k0 + lane];
+            unsigned long long o = s_o[k0 + lane];
+            uint32_t f = 0, t = 0;
+            disk_walk(a.dv, (int)it.x, (int)it.y, f, t, keep, [&](uint32_t q) {
+                if (o < a.cap)
+                    __stcs(a.pairs + o, make_uint2(it.z, q));
+                ++o;
+            });
+        }
+    };
+    uint32_t qn = 0; // queued points, < 32 between chunks
+    const uint32_t nw = gridDim.x * kWarps;
+    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+        const uint64_t base = (uint64_t)ch * kWChunk;
+        const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
+        unsigned long long run = chunk_off[ch];
+        uint32_t res[kWItems];
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t loc = j * 32 + lane;
+            res[j] = loc < npts ? __ldcs(res_in + base + loc) : kResNone;
+        }
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t loc = j * 32 + lane, r = res[j];
+            const uint32_t pid = (uint32_t)(base + loc);
+            const bool multi = r != kResNone && (r & kResMulti);
+            uint32_t c = r == kResNone ? 0u : 1u, pre, tot;
+            if (!__any_sync(kFull, multi)) {
+                const uint32_t bl = __ballot_sync(kFull, c != 0);
+                pre = __popc(bl & lanemask_lt());
+                tot = __popc(bl);
+            } else {
+                int2 p = make_int2(0, 0);
+                if (multi) {
+                    p = a.pts[base + loc];
+                    if (r & kResCount) {
+                        c = (r >> 20) & 0x3ffu;
+                    } else { // count not stored: count again
+                        uint32_t f = 0, t = 0;
+                        c = disk_walk(a.dv, p.x, p.y, f, t, keep, [](uint32_t) {});
+                    }
+                }
+                uint32_t inc = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o)
+                        inc += v;
+                }
+                pre = inc - c;
+                tot = __shfl_sync(kFull, inc, 31);
+                const uint32_t bl = __ballot_sync(kFull, multi);
+                if (multi) {
+                    const uint32_t slot = qn + __popc(bl & lanemask_lt());
+                    s_q[slot] = make_uint4((uint32_t)p.x, (uint32_t)p.y, pid, 0u);
+                    s_o[slot] = run + pre;
+                    c = 0; // written from the queue
+                }
+                qn += __popc(bl);
+            }
+            if (c) {
+                const unsigned long long o = run + pre;
+                if (o < a.cap)
+                    __stcs(a.pairs + o, make_uint2(pid, r));
+            }
+            run += tot;
+        }
+        __syncwarp();
+        if (qn >= 32) {
+            uint32_t k0 = 0;
+            for (; qn - k0 >= 32; k0 += 32)
+                walk(k0, 32);
+            // move the partial round (< 32, from k0 >= 32) to the front
+            const uint32_t rem = qn - k0;
+            uint4 it = make_uint4(0, 0, 0, 0);
+            unsigned long long o = 0;
+            if ((uint32_t)lane < rem) {
+                it = s_q[k0 + lane];
+                o = s_o[k0 + lane];
+            }
+            __syncwarp();
+            if ((uint32_t)lane < rem) {
+                s_q[lane] = it;
+                s_o[lane] = o;
+            }
+            qn = rem;
+            __syncwarp();
+        }
     }
-    global_add_warp(a.counts, c == 1, first);
-    if (c > 1) {
-        uint32_t f2 = 0, t2 = 0;
-        disk_walk(a.dv, p.x, p.y, f2, t2, keep, [&](uint32_t q) { atomicAdd(a.counts + q, 1ull); });
-    }
-    add_stats(a.stats, idx < a.n ? 1u : 0u, tests, 0u, c);
+    __syncwarp();
+    walk(0, qn);
 }
 
 // ------------------------------------------------------ clustered point table
@@ -1738,39 +1909,76 @@ cudaError_t launch_plain_write(const JoinLaunch &a, void *scratch, cudaStream_t 
 }
 
 // ------------------------------------------------------ distance-query launchers
-size_t disk_scratch_bytes(uint64_t n) { return plain_split_scratch_bytes(n); }
-
-cudaError_t launch_disk_join(const DiskLaunch &a, void *scratch, cudaStream_t s)
+template <bool RESOLVE>
+cudaError_t launch_dwarp(const DiskLaunch &a, unsigned long long *tot, uint32_t *res, uint32_t nchunks,
+                         cudaStream_t s)
 {
-    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
-    if (nb >= (1ull << 31))
+    static bool done[64] = {};
+    const int use_hist = a.counts && a.dv.Q <= (uint32_t)kHistMax;
+    const size_t fixed = kDWarpSmem + sizeof(uint32_t) * kDiskCoverWords;
+    const size_t smem = fixed + (use_hist ? sizeof(uint32_t) * a.dv.Q : 0);
+    auto kern = k_dwarp<RESOLVE>;
+    cudaError_t e = smem_opt_in(kern, fixed + sizeof(uint32_t) * kHistMax, done);
+    if (e != cudaSuccess)
+        return e;
+    const uint32_t nblk = (nchunks + kWarps - 1) / kWarps;
+    kern<<<persistent_grid(kern, kThreads, smem, nblk), kThreads, smem, s>>>(a, tot, res, nchunks, use_hist);
+    return cudaGetLastError();
+}
+
+// The polygon join's scratch layout: per-point results | per-chunk totals
+// (then offsets) | scan partials.
+size_t disk_scratch_bytes(uint64_t n) { return join_scratch_bytes(n); }
+
+cudaError_t launch_disk_join(const DiskLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
+{
+    const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
+    if (nchunks >= (1ull << 31))
         return cudaErrorInvalidValue;
     cudaError_t e;
     if (a.counts && a.dv.Q)
         if ((e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.dv.Q, s)) != cudaSuccess)
             return e;
-    if (nb == 0)
+    if (nchunks == 0)
         return a.total ? cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s) : cudaSuccess;
-    unsigned long long *block = static_cast<unsigned long long *>(scratch);
-    k_disk_count<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
-    if ((e = cudaGetLastError()) != cudaSuccess)
+    char *sc = static_cast<char *>(scratch);
+    uint32_t *res = reinterpret_cast<uint32_t *>(sc);
+    unsigned long long *tot = reinterpret_cast<unsigned long long *>(sc + ((a.n * 4 + 15) & ~uint64_t(15)));
+    unsigned long long *part = tot + nchunks;
+    const uint32_t nblk = uint32_t((nchunks + kWarps - 1) / kWarps);
+    if (ev)
+        cudaEventRecord(ev[0], s);
+    if ((e = cudaMemsetAsync(tot, 0, nchunks * sizeof(unsigned long long), s)) != cudaSuccess)
         return e;
-    if ((e = launch_scan(block, nb, a.total, block + nb, s)) != cudaSuccess)
+    if ((e = launch_dwarp<true>(a, tot, res, uint32_t(nchunks), s)) != cudaSuccess)
         return e;
-    k_disk_write<<<(unsigned)nb, kPlainThreads, 0, s>>>(a, block);
+    if (ev)
+        cudaEventRecord(ev[1], s);
+    if ((e = launch_scan(tot, nchunks, a.total, part, s)) != cudaSuccess)
+        return e;
+    if (ev)
+        cudaEventRecord(ev[2], s);
+    if (a.cap) {
+        static bool done[64] = {};
+        if ((e = smem_opt_in(k_dwemit, kDEmitSmem, done)) != cudaSuccess)
+            return e;
+        k_dwemit<<<persistent_grid(k_dwemit, kThreads, kDEmitSmem, nblk), kThreads, kDEmitSmem, s>>>(
+            a, tot, res, uint32_t(nchunks));
+    }
+    if (ev)
+        cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_disk_aggregate(const DiskLaunch &a, cudaStream_t s)
 {
-    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
-    if (nb >= (1ull << 31))
+    const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
+    if (nchunks >= (1ull << 31))
         return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * (a.dv.Q ? a.dv.Q : 1), s);
-    if (e != cudaSuccess || nb == 0)
+    if (e != cudaSuccess || nchunks == 0)
         return e;
-    k_disk_agg<<<(unsigned)nb, kPlainThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_dwarp<false>(a, nullptr, nullptr, uint32_t(nchunks), s);
 }
 
 size_t disk_select_scratch_bytes(uint64_t n, uint32_t Q, uint64_t cap)
@@ -1795,7 +2003,7 @@ cudaError_t launch_disk_select(const DiskLaunch &a, uint32_t *ids, uint64_t cap,
     b.cap = cap;
     b.counts = nullptr;
     b.total = total;
-    cudaError_t e = launch_disk_join(b, join_scratch, s);
+    cudaError_t e = launch_disk_join(b, join_scratch, s, nullptr);
     if (e != cudaSuccess)
         return e;
     return launch_partition(pairs, total, cap, a.dv.Q, ids, offsets, sc, s);

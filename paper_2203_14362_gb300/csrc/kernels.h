@@ -24,14 +24,18 @@ constexpr int kCoverLog2 = 8;
 
 // A grid index of disks (distance queries): cell words as the coarse level of
 // IndexView; lists in ent (n, then n words disk << 1 | boundary); disks as
-// (cx, cy, r, 0).
+// (cx, cy, r, 0); the cover bitmap as in IndexView (4^cg bits, at least one
+// word).
 struct DiskView {
     const uint32_t *cell;
     const uint32_t *ent;
     const int4 *disk;
+    const uint32_t *cover;
     int sc; // 30 - g
     int g;
     uint32_t Q;
+    int scv; // 30 - cg
+    int cg;  // min(g, kCoverLog2)
 };
 
 struct DiskLaunch {
@@ -46,9 +50,10 @@ struct DiskLaunch {
 };
 
 // Distance join: pairs (point, disk) with distance <= r, in (point, disk)
-// order, counts, total.  scratch: disk_scratch_bytes(n).
+// order, counts, total.  scratch: disk_scratch_bytes(n).  ev (or null): four
+// events recorded before pass 1, before the scan, before pass 3 and after it.
 size_t disk_scratch_bytes(uint64_t n);
-cudaError_t launch_disk_join(const DiskLaunch &a, void *scratch, cudaStream_t s);
+cudaError_t launch_disk_join(const DiskLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev);
 // Counts only.
 cudaError_t launch_disk_aggregate(const DiskLaunch &a, cudaStream_t s);
 // Per-disk ascending point-id lists (the selection); scratch:
