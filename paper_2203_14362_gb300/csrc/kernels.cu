@@ -1235,8 +1235,8 @@ __device__ __forceinline__ uint32_t disk_walk(const DiskView &d, int px, int py,
 // read their cell word, and the points of list cells are queued in shared
 // memory.  The queue carries over from chunk to chunk and the warp walks it
 // in full rounds of 32 (one chain of dependent loads per 32 list points); a
-// walked point adds its pairs to its own chunk's total (zeroed before the
-// launch).  It stores a 4-byte result per point and a pair total per
+// walked point adds its pairs to its own chunk's total (stored by lane 0
+// before any of the chunk's points is walked).  It stores a 4-byte result per point and a pair total per
 // 256-point chunk, and counts per disk (in shared memory when Q <=
 // kHistMax); pass 3 writes the pairs from the results.
 constexpr uint32_t kDiskCoverWords = 1u << (2 * kCoverLog2 - 5); // cover bitmap in shared memory
@@ -1345,8 +1345,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_dwarp(DiskLaunch a, unsigned lo
         }
         n_pairs += total;
         total = warp_sum32(total);
-        if (RESOLVE && lane == 0 && total)
-            atomicAdd(chunk_tot + ch, (unsigned long long)total);
+        if (RESOLVE && lane == 0)
+            chunk_tot[ch] = total; // the chunk's pair total so far; its queued points add theirs
         __syncwarp();
         if (qn >= 32) {
             uint32_t k0 = 0;
@@ -1948,8 +1948,6 @@ cudaError_t launch_disk_join(const DiskLaunch &a, void *scratch, cudaStream_t s,
     const uint32_t nblk = uint32_t((nchunks + kWarps - 1) / kWarps);
     if (ev)
         cudaEventRecord(ev[0], s);
-    if ((e = cudaMemsetAsync(tot, 0, nchunks * sizeof(unsigned long long), s)) != cudaSuccess)
-        return e;
     if ((e = launch_dwarp<true>(a, tot, res, uint32_t(nchunks), s)) != cudaSuccess)
         return e;
     if (ev)
