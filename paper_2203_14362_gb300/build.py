@@ -51,13 +51,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if not force and not _stale([]):
         return LIB
     nv = nvcc()
+    # SPX_NVCC_EXTRA: extra nvcc flags, e.g. -D settings of the kernels' tuning macros
     common = ["-O3", "-std=c++17", "-I", CSRC, "-I", INCLUDE]
+    extra = os.environ.get("SPX_NVCC_EXTRA", "").split()
     jobs = []
     objs = []
     for f in CU_SOURCES:
         o = os.path.join(BUILD, f + ".o")
         objs.append(o)
-        cmd = [nv, *ARCH, "-lineinfo", *common, "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+        cmd = [nv, *ARCH, "-lineinfo", *common, *extra, "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                "-c", os.path.join(CSRC, f), "-o", o]
         if ptxas_verbose:
             cmd.insert(1, "-Xptxas=-v")

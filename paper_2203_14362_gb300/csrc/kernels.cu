@@ -672,10 +672,12 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
 // Pass 3 of the join with warp chunks: every warp writes the pairs of its
 // chunks from the stored per-point results at the chunk's scanned offset.
 // Lane order within a round of 32 points, rounds in order: point order.  A
-// point in one polygon is written at once; a point in several is queued with
-// its offset, and the warp walks its queue 32 points at a time afterwards (all
-// lanes busy, as in pass 1) to write their pairs.
-constexpr size_t kEmitSmem = size_t(kWarps) * kWChunk * (sizeof(uint4) + sizeof(unsigned long long));
+// point in one polygon is written at once; a point in several is queued (its
+// row and its offset; its count comes with its stored result), and the warp
+// walks its queue 32 points at a time afterwards (all lanes busy, as in pass
+// 1), loading the queued points' coordinates then, one independent load per
+// lane, to write their pairs.
+constexpr size_t kEmitSmem = size_t(kWarps) * kWChunk * (sizeof(uint32_t) + sizeof(unsigned long long));
 
 template <bool FP32>
 __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsigned long long *chunk_off,
@@ -683,9 +685,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kWChunk; // (x, y, point id)
-    unsigned long long *s_o =
-        reinterpret_cast<unsigned long long *>(s_raw + size_t(kWarps) * kWChunk * sizeof(uint4)) + warp * kWChunk;
+    unsigned long long *s_o = reinterpret_cast<unsigned long long *>(s_raw) + warp * kWChunk;
+    uint32_t *s_q = reinterpret_cast<uint32_t *>(s_raw + size_t(kWarps) * kWChunk * sizeof(unsigned long long)) +
+                    warp * kWChunk; // rows within the chunk
     const uint64_t keep = policy_evict_last();
     const uint32_t nw = gridDim.x * kWarps;
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
@@ -710,12 +712,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
                 pre = __popc(bl & lanemask_lt());
                 tot = __popc(bl);
             } else {
-                int2 p = make_int2(0, 0);
                 if (multi) {
-                    p = a.pts[base + loc];
                     if (r & kResCount) {
                         c = (r >> 20) & 0x3ffu;
                     } else { // count not stored: count again
+                        const int2 p = a.pts[base + loc];
                         uint32_t f = 0, t = 0, e = 0;
                         c = point_count<FP32>(a.ix, p.x, p.y, f, t, e, keep);
                     }
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
                 const uint32_t bl = __ballot_sync(kFull, multi);
                 if (multi) {
                     const uint32_t slot = qn + __popc(bl & lanemask_lt());
-                    s_q[slot] = make_uint4((uint32_t)p.x, (uint32_t)p.y, pid, 0u);
+                    s_q[slot] = loc;
                     s_o[slot] = run + pre;
                     c = 0; // written from the queue
                 }
@@ -748,11 +749,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
         __syncwarp();
         for (uint32_t k0 = 0; k0 < qn; k0 += 32) {
             if (k0 + lane < qn) {
-                const uint4 it = s_q[k0 + lane];
+                const uint32_t loc = s_q[k0 + lane];
                 unsigned long long o = s_o[k0 + lane];
-                point_emit<FP32>(a.ix, (int)it.x, (int)it.y, keep, [&](uint32_t q) {
+                const int2 p = a.pts[base + loc];
+                const uint32_t pid = a.pid0 + (uint32_t)(base + loc);
+                point_emit<FP32>(a.ix, p.x, p.y, keep, [&](uint32_t q) {
                     if (o < a.cap)
-                        __stcs(a.pairs + o, make_uint2(it.z, q));
+                        __stcs(a.pairs + o, make_uint2(pid, q));
                     ++o;
                 });
             }
@@ -1239,12 +1242,16 @@ __device__ __forceinline__ uint32_t disk_walk(const DiskView &d, int px, int py,
 // before any of the chunk's points is walked).  It stores a 4-byte result per point and a pair total per
 // 256-point chunk, and counts per disk (in shared memory when Q <=
 // kHistMax); pass 3 writes the pairs from the results.
+#ifndef SPX_DISK_PREFETCH
+#define SPX_DISK_PREFETCH 0 // 1: load the next chunk's points while resolving this one (3 CTAs/SM)
+#endif
+constexpr int kDiskMinBlocks = SPX_DISK_PREFETCH ? 3 : 4;
 constexpr uint32_t kDiskCoverWords = 1u << (2 * kCoverLog2 - 5); // cover bitmap in shared memory
 constexpr int kDQueue = kWChunk + 32; // a chunk's points plus a partial round
 constexpr size_t kDWarpSmem = size_t(kWarps) * kDQueue * sizeof(uint4);
 
 template <bool RESOLVE>
-__global__ void __launch_bounds__(kThreads, 4) k_dwarp(DiskLaunch a, unsigned long long *chunk_tot, uint32_t *res,
+__global__ void __launch_bounds__(kThreads, kDiskMinBlocks) k_dwarp(DiskLaunch a, unsigned long long *chunk_tot, uint32_t *res,
                                                        uint32_t nchunks, int use_hist)
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -1308,17 +1315,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_dwarp(DiskLaunch a, unsigned lo
     };
     const uint32_t nw = gridDim.x * kWarps;
     uint32_t qn = 0; // queued list points, < 32 between chunks
-    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+    // a chunk's points (rows past the table's end read as outside the box)
+    auto load_points = [&](uint32_t ch, int2 (&q)[kWItems]) {
         const uint64_t base = (uint64_t)ch * kWChunk;
-        const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
-        int2 p[kWItems];
-        uint32_t w[kWItems];
+        const uint32_t npts = ch < nchunks ? (uint32_t)min((uint64_t)kWChunk, a.n - base) : 0u;
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             const uint32_t loc = j * 32 + lane;
-            p[j] = loc < npts ? __ldcs(a.pts + base + loc) : make_int2(-1, -1);
-            n_pts += loc < npts ? 1u : 0u;
+            q[j] = loc < npts ? __ldcs(a.pts + base + loc) : make_int2(-1, -1);
         }
+    };
+#if SPX_DISK_PREFETCH
+    int2 nxt[kWItems];
+    load_points(blockIdx.x * kWarps + warp, nxt);
+#endif
+    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+        const uint64_t base = (uint64_t)ch * kWChunk;
+        const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
+        if (lane == 0)
+            n_pts += npts;
+        int2 p[kWItems];
+        uint32_t w[kWItems];
+#if SPX_DISK_PREFETCH
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j)
+            p[j] = nxt[j];
+        load_points(ch + nw, nxt);
+#else
+        load_points(ch, p);
+#endif
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             // points outside the box or in a block of empty cells read no cell word
@@ -1374,93 +1399,121 @@ __global__ void __launch_bounds__(kThreads, 4) k_dwarp(DiskLaunch a, unsigned lo
     add_stats(a.stats, n_pts, n_tests, 0u, n_pairs);
 }
 
-// Pass 3 of the distance join: as k_wemit, a point in one disk is written at
-// once and a point in several is queued with its offset.  Such points are
-// rare, so the queue carries over from chunk to chunk and the warp walks it
-// only in full rounds of 32 (and what is left at the end): a pair's place
-// comes from its offset, not from when it is written.
-constexpr size_t kDEmitSmem = size_t(kWarps) * kDQueue * (sizeof(uint4) + sizeof(unsigned long long));
+// Pass 3 of the distance join.  Lane-major: lane l owns rows 8l .. 8l + 7 of
+// the warp's 256-row chunk (two 16-byte loads of stored results), so one warp
+// scan of the lanes' pair counts gives every row its offset in point order.
+// A point in one disk is written at once; a point in several is queued (its
+// row and its offset; its count comes with its stored result).  Such points
+// are rare, so the queue carries over from chunk to chunk and the warp walks
+// it only in full rounds of 32 (and what is left at the end), loading the
+// queued points' coordinates then, one independent load per lane.  The next
+// chunk's results are loaded while this one is written.
+constexpr size_t kDEmitSmem = size_t(kWarps) * kDQueue * (sizeof(uint32_t) + sizeof(unsigned long long));
+static_assert(kWItems == 8, "lane-major emit: two 16-byte loads of 4-byte results per lane");
 
 __global__ void __launch_bounds__(kThreads, 4) k_dwemit(DiskLaunch a, const unsigned long long *chunk_off,
                                                         const uint32_t *res_in, uint32_t nchunks)
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kDQueue; // (x, y, point id)
-    unsigned long long *s_o =
-        reinterpret_cast<unsigned long long *>(s_raw + size_t(kWarps) * kDQueue * sizeof(uint4)) + warp * kDQueue;
+    unsigned long long *s_o = reinterpret_cast<unsigned long long *>(s_raw) + warp * kDQueue;
+    uint32_t *s_q = reinterpret_cast<uint32_t *>(s_raw + size_t(kWarps) * kDQueue * sizeof(unsigned long long)) +
+                    warp * kDQueue; // point rows
     const uint64_t keep = policy_evict_last();
     // walk queued points [k0, k0 + m), m <= 32, one per lane
     auto walk = [&](uint32_t k0, uint32_t m) {
         if ((uint32_t)lane < m) {
-            const uint4 it = s_q[k0 + lane];
+            const uint32_t pid = s_q[k0 + lane];
             unsigned long long o = s_o[k0 + lane];
+            const int2 p = a.pts[pid];
             uint32_t f = 0, t = 0;
-            disk_walk(a.dv, (int)it.x, (int)it.y, f, t, keep, [&](uint32_t q) {
+            disk_walk(a.dv, p.x, p.y, f, t, keep, [&](uint32_t q) {
                 if (o < a.cap)
-                    __stcs(a.pairs + o, make_uint2(it.z, q));
+                    __stcs(a.pairs + o, make_uint2(pid, q));
                 ++o;
             });
         }
     };
     uint32_t qn = 0; // queued points, < 32 between chunks
     const uint32_t nw = gridDim.x * kWarps;
-    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+    const uint32_t r0 = 8u * (uint32_t)lane; // this lane's first row in a chunk
+    uint32_t nres[8];
+    unsigned long long noff = 0;
+    auto fetch = [&](uint32_t ch) {
         const uint64_t base = (uint64_t)ch * kWChunk;
-        const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
-        unsigned long long run = chunk_off[ch];
-        uint32_t res[kWItems];
+        const uint32_t npts = ch < nchunks ? (uint32_t)min((uint64_t)kWChunk, a.n - base) : 0u;
+        if (r0 + 8 <= npts) {
+            const uint4 u = __ldcs(reinterpret_cast<const uint4 *>(res_in + base + r0));
+            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(res_in + base + r0 + 4));
+            nres[0] = u.x, nres[1] = u.y, nres[2] = u.z, nres[3] = u.w;
+            nres[4] = v.x, nres[5] = v.y, nres[6] = v.z, nres[7] = v.w;
+        } else { // the table's ragged end
 #pragma unroll
-        for (int j = 0; j < kWItems; ++j) {
-            const uint32_t loc = j * 32 + lane;
-            res[j] = loc < npts ? __ldcs(res_in + base + loc) : kResNone;
+            for (int k = 0; k < 8; ++k)
+                nres[k] = r0 + k < npts ? __ldcs(res_in + base + r0 + k) : kResNone;
         }
+        noff = ch < nchunks ? chunk_off[ch] : 0ull;
+    };
+    fetch(blockIdx.x * kWarps + warp);
+    for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+        const uint32_t pid0 = (uint32_t)((uint64_t)ch * kWChunk) + r0;
+        const unsigned long long run = noff;
+        uint32_t res[8];
 #pragma unroll
-        for (int j = 0; j < kWItems; ++j) {
-            const uint32_t loc = j * 32 + lane, r = res[j];
-            const uint32_t pid = (uint32_t)(base + loc);
-            const bool multi = r != kResNone && (r & kResMulti);
-            uint32_t c = r == kResNone ? 0u : 1u, pre, tot;
-            if (!__any_sync(kFull, multi)) {
-                const uint32_t bl = __ballot_sync(kFull, c != 0);
-                pre = __popc(bl & lanemask_lt());
-                tot = __popc(bl);
-            } else {
-                int2 p = make_int2(0, 0);
-                if (multi) {
-                    p = a.pts[base + loc];
-                    if (r & kResCount) {
-                        c = (r >> 20) & 0x3ffu;
-                    } else { // count not stored: count again
-                        uint32_t f = 0, t = 0;
-                        c = disk_walk(a.dv, p.x, p.y, f, t, keep, [](uint32_t) {});
-                    }
-                }
-                uint32_t inc = c;
+        for (int k = 0; k < 8; ++k)
+            res[k] = nres[k];
+        fetch(ch + nw);
+        // pairs (low 32 bits) and multi-disk points (high 32 bits) of this
+        // lane's rows, for one scan; a multi-disk row keeps kResMulti | count
+        unsigned long long mine = 0;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t v = __shfl_up_sync(kFull, inc, o);
-                    if (lane >= o)
-                        inc += v;
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t r = res[k];
+            if (r == kResNone)
+                continue;
+            uint32_t c = 1;
+            if (r & kResMulti) {
+                if (r & kResCount) {
+                    c = (r >> 20) & 0x3ffu;
+                } else { // count not stored: count again
+                    const int2 p = a.pts[pid0 + k];
+                    uint32_t f = 0, t = 0;
+                    c = disk_walk(a.dv, p.x, p.y, f, t, keep, [](uint32_t) {});
                 }
-                pre = inc - c;
-                tot = __shfl_sync(kFull, inc, 31);
-                const uint32_t bl = __ballot_sync(kFull, multi);
-                if (multi) {
-                    const uint32_t slot = qn + __popc(bl & lanemask_lt());
-                    s_q[slot] = make_uint4((uint32_t)p.x, (uint32_t)p.y, pid, 0u);
-                    s_o[slot] = run + pre;
-                    c = 0; // written from the queue
-                }
-                qn += __popc(bl);
+                res[k] = kResMulti | c;
+                mine += 1ull << 32;
             }
-            if (c) {
-                const unsigned long long o = run + pre;
-                if (o < a.cap)
-                    __stcs(a.pairs + o, make_uint2(pid, r));
-            }
-            run += tot;
+            mine += c;
         }
+        unsigned long long inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o)
+                inc += v;
+        }
+        const unsigned long long tot = __shfl_sync(kFull, inc, 31), before = inc - mine;
+        if (mine) {
+            unsigned long long o = run + (uint32_t)before;
+            uint32_t slot = qn + (uint32_t)(before >> 32);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t r = res[k];
+                if (r == kResNone)
+                    continue;
+                if (r & kResMulti) {
+                    s_q[slot] = pid0 + k;
+                    s_o[slot] = o;
+                    ++slot;
+                    o += r & ~kResMulti;
+                } else {
+                    if (o < a.cap)
+                        __stcs(a.pairs + o, make_uint2(pid0 + k, r));
+                    ++o;
+                }
+            }
+        }
+        qn += (uint32_t)(tot >> 32);
         __syncwarp();
         if (qn >= 32) {
             uint32_t k0 = 0;
@@ -1468,16 +1521,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_dwemit(DiskLaunch a, const unsi
                 walk(k0, 32);
             // move the partial round (< 32, from k0 >= 32) to the front
             const uint32_t rem = qn - k0;
-            uint4 it = make_uint4(0, 0, 0, 0);
-            unsigned long long o = 0;
+            uint32_t q = 0;
+            unsigned long long oo = 0;
             if ((uint32_t)lane < rem) {
-                it = s_q[k0 + lane];
-                o = s_o[k0 + lane];
+                q = s_q[k0 + lane];
+                oo = s_o[k0 + lane];
             }
             __syncwarp();
             if ((uint32_t)lane < rem) {
-                s_q[lane] = it;
-                s_o[lane] = o;
+                s_q[lane] = q;
+                s_o[lane] = oo;
             }
             qn = rem;
             __syncwarp();

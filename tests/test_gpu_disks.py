@@ -122,3 +122,44 @@ def test_disk_index_errors(eng):
     finally:
         eng.free(ih)
         eng.free(ph)
+
+
+def test_disk_counts_in_global_memory_and_deep_overlaps(eng):
+    # 12000 small disks (more than the 11776 counters kept in shared memory:
+    # per-disk counts go to global memory) plus 1100 disks around one centre
+    # (points near it lie in more than 1022 disks: the pass-1 result cannot
+    # carry the count, so the write pass counts again)
+    rng = np.random.default_rng(g.SEED_BASE + 96)
+    c = 1 << 29
+    pts = np.concatenate([rng.integers(0, 1 << 30, (60_000, 2)),
+                          c + rng.integers(-(1 << 23), 1 << 23, (3000 + 13, 2))]).astype(np.int32)
+    rng.shuffle(pts)
+    n = pts.shape[0]
+    deep = np.column_stack([c + rng.integers(-1000, 1000, 1100), c + rng.integers(-1000, 1000, 1100)])
+    small = rng.integers(0, (1 << 30) + 1, (12000, 2))
+    centers = np.concatenate([small[:6000], deep, small[6000:]]).astype(np.int32)
+    radii = np.concatenate([rng.integers(1 << 20, 1 << 23, 6000), rng.integers(1 << 24, 1 << 25, 1100),
+                            rng.integers(0, 1 << 23, 6000)]).astype(np.int32)
+    Q = centers.shape[0]
+    want_p, want_c = oracle.disk_join(pts, centers, radii)
+    per_point = np.bincount(want_p[:, 0].astype(np.int64), minlength=n)
+    assert per_point.max() > 1022  # the case is reached
+    dpts = torch.from_numpy(pts).cuda()
+    ph = eng.load_points(dpts)
+    try:
+        for grid in (0, 9):
+            ih = eng.build_disk_index(centers, radii, grid)
+            pairs = torch.empty((want_p.shape[0] + 3, 2), dtype=torch.int32, device="cuda")
+            counts = torch.zeros(Q, dtype=torch.int64, device="cuda")
+            m = eng.join(ph, ih, pairs, counts)
+            assert m == want_p.shape[0]
+            assert np.array_equal(pairs[:m].cpu().numpy().view(np.uint32), want_p)
+            assert np.array_equal(counts.cpu().numpy().view(np.uint64), want_c)
+            c2 = torch.zeros(Q, dtype=torch.int64, device="cuda")
+            eng.aggregate(ph, ih, c2)
+            torch.cuda.synchronize()
+            assert np.array_equal(c2.cpu().numpy().view(np.uint64), want_c)
+            eng.free(ih)
+    finally:
+        eng.free(ph)
+        del dpts
