@@ -40,6 +40,9 @@ L2_BYTES = 129 * 1024 * 1024
 # scaled per point; only valid for that kernel version, the default index
 # (g = 11, sub = 3) and the default workload.
 RESOLVE_TRAFFIC_BYTES_PER_POINT = (298.491648e6 + 62.491904e6) / 20e6
+# The same for the distance join's pass 1 (k_dwarp<resolve>), from one capture
+# of a 20M-point run of the 1024-disk workload at its default grid (g = 12).
+DISK_RESOLVE_TRAFFIC_BYTES_PER_POINT = (167.498496e6 + 25.302784e6) / 20e6
 SERVE_SEED = 0x2203143620 + 4  # request indexes of the serving measurement
 
 
@@ -420,6 +423,8 @@ def run_spx(args, world, rank, local):
     if (traffic is None and RESOLVE_TRAFFIC_BYTES_PER_POINT and not args.plain and args.workload == "tess2000_100m"
             and (info["grid_log2"], info["sub_log2"]) == (11, 3)):
         traffic = RESOLVE_TRAFFIC_BYTES_PER_POINT * N
+    if traffic is None and args.workload == "dist1024_100m" and info["grid_log2"] == 12:
+        traffic = DISK_RESOLVE_TRAFFIC_BYTES_PER_POINT * N
     out = None
     if rank == 0:
         cpu = None
