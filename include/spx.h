@@ -370,6 +370,24 @@ spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *coarse, uint32
                                int32_t *edges);
 void spx_host_index_free(spx_host_index *h);
 
+/*
+ * Host-only build of the disk index of spx_build_disk_index (same arguments,
+ * same checks), for inspection without a GPU.  sizes[0] = cell words (4^g),
+ * sizes[1] = entry words, sizes[2] = grid_log2.  spx_host_disk_index_copy
+ * copies the arrays into caller buffers of those sizes (uint32); free the
+ * handle with spx_host_disk_index_free.  Layout: cell word c = (cy << g) | cx:
+ * bits 31..30 kind (0 no disk reaches the cell; 1 the cell lies wholly inside
+ * exactly one disk, id = bits 29..0, and no other disk reaches it; 2 list at
+ * entry word bits 29..0); a list is n, then n words disk << 1 | boundary, in
+ * disk order (boundary 0: the cell lies wholly inside that disk; 1: each point
+ * takes the exact test).  Errors: SPX_EINVAL.
+ */
+typedef struct spx_host_disk_index spx_host_disk_index;
+spx_status spx_host_disk_index_build(const int32_t *cxy, const int32_t *r, uint32_t Q, int grid_log2,
+                                     spx_host_disk_index **out, uint64_t sizes[3]);
+spx_status spx_host_disk_index_copy(const spx_host_disk_index *h, uint32_t *cell, uint32_t *entries);
+void spx_host_disk_index_free(spx_host_disk_index *h);
+
 /* Counters accumulated by the kernels of this ctx since the last reset, and
  * (with phase timing on) the device time of each pass, measured with CUDA
  * events on the caller's stream (the time breakdown of §6.2). */

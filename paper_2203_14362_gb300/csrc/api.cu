@@ -873,6 +873,20 @@ spx_status spx_autotune(spx_ctx *ctx, spx_points points, spx_polys polys, const 
     return SPX_OK;
 }
 
+// Why a disk set cannot be indexed (empty: it can).
+static std::string check_disks(const int32_t *cxy, const int32_t *r, uint32_t Q)
+{
+    if (Q >= (1u << 30))
+        return "Q must be < 2^30";
+    for (uint32_t q = 0; q < Q; ++q) {
+        if (cxy[2 * q] < 0 || cxy[2 * q] > int32_t(kBox) || cxy[2 * q + 1] < 0 || cxy[2 * q + 1] > int32_t(kBox))
+            return "centre " + std::to_string(q) + " outside [0, 2^30]^2";
+        if (r[q] < 0 || r[q] >= int32_t(kBox))
+            return "radius " + std::to_string(q) + " outside [0, 2^30)";
+    }
+    return {};
+}
+
 spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t *r, uint32_t Q, int grid_log2,
                                 spx_index *out)
 {
@@ -880,13 +894,10 @@ spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t 
         return fail(ctx, SPX_EINVAL, "build_disk_index: null argument");
     ctx->err.clear();
     cudaSetDevice(ctx->device);
-    if (Q >= (1u << 30))
-        return fail(ctx, SPX_EINVAL, "build_disk_index: Q must be < 2^30");
-    for (uint32_t q = 0; q < Q; ++q) {
-        if (cxy[2 * q] < 0 || cxy[2 * q] > int32_t(kBox) || cxy[2 * q + 1] < 0 || cxy[2 * q + 1] > int32_t(kBox))
-            return fail(ctx, SPX_EINVAL, "build_disk_index: centre " + std::to_string(q) + " outside [0, 2^30]^2");
-        if (r[q] < 0 || r[q] >= int32_t(kBox))
-            return fail(ctx, SPX_EINVAL, "build_disk_index: radius " + std::to_string(q) + " outside [0, 2^30)");
+    {
+        const std::string bad = check_disks(cxy, r, Q);
+        if (!bad.empty())
+            return fail(ctx, SPX_EINVAL, "build_disk_index: " + bad);
     }
     const auto t0 = std::chrono::steady_clock::now();
     const int g = grid_log2 ? grid_log2 : default_disk_grid_log2(r, Q);
@@ -1504,6 +1515,43 @@ spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *coarse, uint32
 }
 
 void spx_host_index_free(spx_host_index *h) { delete h; }
+
+struct spx_host_disk_index {
+    HostDiskIndex hd;
+};
+
+spx_status spx_host_disk_index_build(const int32_t *cxy, const int32_t *r, uint32_t Q, int grid_log2,
+                                     spx_host_disk_index **out, uint64_t sizes[3])
+{
+    if (!out || !sizes || (Q && (!cxy || !r)))
+        return SPX_EINVAL;
+    *out = nullptr;
+    if (!check_disks(cxy, r, Q).empty())
+        return SPX_EINVAL;
+    const int g = grid_log2 ? grid_log2 : default_disk_grid_log2(r, Q);
+    auto h = std::make_unique<spx_host_disk_index>();
+    std::string err;
+    if (!build_disk_index(cxy, r, Q, g, h->hd, err))
+        return SPX_EINVAL;
+    sizes[0] = h->hd.cell.size();
+    sizes[1] = h->hd.entries.size();
+    sizes[2] = uint64_t(g);
+    *out = h.release();
+    return SPX_OK;
+}
+
+spx_status spx_host_disk_index_copy(const spx_host_disk_index *h, uint32_t *cell, uint32_t *entries)
+{
+    if (!h)
+        return SPX_EINVAL;
+    if (cell)
+        std::memcpy(cell, h->hd.cell.data(), h->hd.cell.size() * 4);
+    if (entries)
+        std::memcpy(entries, h->hd.entries.data(), h->hd.entries.size() * 4);
+    return SPX_OK;
+}
+
+void spx_host_disk_index_free(spx_host_disk_index *h) { delete h; }
 
 spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset)
 {

@@ -27,7 +27,7 @@ EXPORTS = [
     "spx_server_create", "spx_server_submit", "spx_server_poll", "spx_server_wait", "spx_server_release",
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
     "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
-    "spx_build_disk_index",
+    "spx_build_disk_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free",
 ]
 
 SPX_REQ_SELECT, SPX_REQ_JOIN = 1, 2
@@ -135,6 +135,9 @@ def load(path: str = LIB_PATH):
         "spx_server_destroy": ([V], None),
         "spx_cluster_points": ([V, U64, I, P64], I),
         "spx_build_disk_index": ([V, V, V, U32, I, P64], I),
+        "spx_host_disk_index_build": ([V, V, U32, I, C.POINTER(V), P64], I),
+        "spx_host_disk_index_copy": ([V, V, V], I),
+        "spx_host_disk_index_free": ([V], None),
         "spx_aggregate_host": ([V, V, U64, U64, V], I),
         "spx_set_host_streaming": ([V, I, I], I),
         "spx_points_info": ([V, U64, C.POINTER(V), P64, C.POINTER(I)], I),
@@ -184,6 +187,28 @@ def host_index(verts: np.ndarray, ring_off: np.ndarray, grid_log2: int = 0, sub_
     finally:
         lib.spx_host_index_free(h)
     return {"coarse": coarse, "fine": fine, "entries": ent, "edges": edges, "g": int(sizes[4]), "sub": int(sizes[5])}
+
+
+def host_disk_index(centers: np.ndarray, radii: np.ndarray, grid_log2: int = 0):
+    """Build the disk index on the host only (spx_host_disk_index_build);
+    returns a dict with cell (uint32), entries (uint32) and g."""
+    lib = load()
+    cxy = np.ascontiguousarray(centers, dtype=np.int32).reshape(-1, 2)
+    r = np.ascontiguousarray(radii, dtype=np.int32)
+    if r.shape[0] != cxy.shape[0]:
+        raise ValueError("one radius per centre")
+    h = C.c_void_p()
+    sizes = (C.c_uint64 * 3)()
+    st = lib.spx_host_disk_index_build(_np_ptr(cxy), _np_ptr(r), cxy.shape[0], grid_log2, C.byref(h), sizes)
+    if st != SPX_OK:
+        raise SpxError(st, "spx_host_disk_index_build failed")
+    try:
+        cell = np.zeros(sizes[0], np.uint32)
+        ent = np.zeros(max(sizes[1], 1), np.uint32)
+        lib.spx_host_disk_index_copy(h, _np_ptr(cell), _np_ptr(ent))
+    finally:
+        lib.spx_host_disk_index_free(h)
+    return {"cell": cell, "entries": ent, "g": int(sizes[2])}
 
 
 # ------------------------------------------------------------------- the engine
