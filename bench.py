@@ -227,19 +227,30 @@ def barrier(world: int):
 
 
 # --------------------------------------------------------------- CPU baseline
-def cpu_baseline(pts, verts, ring_off, budget_s: float = 12.0, chunk: int = 1_000_000):
+def cpu_baseline(pts, verts, ring_off, budget_s: float = 12.0, chunk: int = 1_000_000, single_s: float = 4.0):
+    """The fast oracle on the first points of the table: all host cores for
+    budget_s, then one thread for single_s (reported as single_thread)."""
     import oracle
     pr = oracle.Prepared(verts, ring_off)
+
+    def timed(threads, budget, step):
+        done, t0 = 0, time.perf_counter()
+        while done < pts.shape[0] and time.perf_counter() - t0 < budget:
+            m = min(step, pts.shape[0] - done)
+            pr.join(pts[done:done + m], threads=threads)
+            done += m
+        return done, time.perf_counter() - t0
+
     threads = oracle.default_threads()
-    done, t0 = 0, time.perf_counter()
-    while done < pts.shape[0] and time.perf_counter() - t0 < budget_s:
-        m = min(chunk, pts.shape[0] - done)
-        pr.join(pts[done:done + m], threads=threads)
-        done += m
-    el = time.perf_counter() - t0
+    done, el = timed(threads, budget_s, chunk)
+    out = {"value": done / el / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"first {done} points of the same table (pairs + counts, fast oracle, {el:.1f} s)"}
+    if single_s > 0:
+        d1, e1 = timed(1, single_s, max(chunk // 10, 1))
+        out["single_thread"] = {"value": d1 / e1 / 1e9, "unit": UNIT, "cores": 1,
+                                "sample": f"first {d1} points ({e1:.1f} s)"}
     pr.close()
-    return {"value": done / el / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {done} points of the same table (pairs + counts, fast oracle, {el:.1f} s)"}
+    return out
 
 
 def disk_cpu_baseline(pts, centers, radii, budget_s: float = 12.0, chunk: int = 200_000):
@@ -361,17 +372,20 @@ def run_spx(args, world, rank, local):
     eng.stats(reset=True)
     barrier(world)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one event per step boundary (the first and last bracket the whole timed region)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = ev[0], ev[-1]
     t_host0 = time.time()
     e0.record(stream)
-    for _ in range(args.steps):
+    for k in range(args.steps):
         eng.join(ph, ih, pairs, counts, total, sync=False, stream=stream, plain=args.plain)
         sum_counts_over_ranks(counts, world)
-    e1.record(stream)
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
     t_host1 = time.time()
     barrier(world)
     ms = e0.elapsed_time(e1) / args.steps
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     st = eng.stats(reset=True)
     ms_max = max_over_ranks(ms, world, torch)
     clk = clocks.summary(t_host0, t_host1)
@@ -458,6 +472,8 @@ def run_spx(args, world, rank, local):
                          "phase_ms": phase_ms},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "step_ms": {"mean": ms, "best": min(per_step), "median": statistics.median(per_step),
+                        "worst": max(per_step), "rank": 0},
             "gpu_launches": args.steps * join_launches(N, args.plain),
             "clocks": clk,
             "serving": serving,
