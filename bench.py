@@ -338,8 +338,14 @@ def run_spx(args, world, rank, local):
     P = int(v.shape[0]) if dist else int(o.shape[0] - 1)
     gh = None if dist else eng.load_polygons(v, o)
     tune = None
+    device_build_ms = None
     if dist:
         ih = eng.build_disk_index(v, o, args.grid)
+        # the same index built on the device (the second build: the first loads the kernels)
+        for _ in range(2):
+            ih_dev = eng.build_disk_index(v, o, args.grid, on_device=True)
+            device_build_ms = eng.index_info(ih_dev)["build_ms"]
+            eng.free(ih_dev)
     elif args.autotune:
         t0 = time.perf_counter()
         params, trials, ih = eng.autotune(ph, gh, fp32_filter=bool(args.fp32))
@@ -455,6 +461,7 @@ def run_spx(args, world, rank, local):
                 "kernel": ("distance join: resolve (k_dwarp) + scan + emit (k_dwemit)" if dist else
                            "plain two-pass" if args.plain else "resolve (k_warp) + scan + emit (k_wemit): cached two-pass Map"),
                 "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": int(info["device_bytes"]),
+                "index_build_on_device_ms": None if device_build_ms is None else round(device_build_ms, 2),
                 "l2": "inputs larger than L2 (points 8 B x N + pairs 8 B x N >> 129 MB); no flush",
                 "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
                 "fp32_escalation_fraction": st["fp32_escalations"] / max(st["edge_tests"], 1),

@@ -158,6 +158,31 @@ spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params
 spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t *r, uint32_t Q, int grid_log2,
                                 spx_index *out);
 
+/*
+ * The same index built on the GPU (the paper builds the indexes of
+ * query-time constraints on the fly and counts that in query time, §6.1
+ * "Database Setup and Tuning"; building it on the device keeps that cost small
+ * for new query sets): every (cell, disk) pair of each disk's
+ * bounding box is classified on the device, bucketed by cell, and the lists
+ * laid out in cell order and sorted by disk, so the cell words, entries and
+ * cover bitmap are byte for byte those of spx_build_disk_index (see
+ * spx_disk_index_arrays).  Same arguments, checks, grid choice and errors;
+ * the build synchronises the device.  It allocates temporaries of about
+ * 20 B per cell of the 4^grid_log2 grid plus 8 B per (cell, disk) record.
+ */
+spx_status spx_build_disk_index_device(spx_ctx *ctx, const int32_t *cxy, const int32_t *r, uint32_t Q,
+                                       int grid_log2, spx_index *out);
+
+/*
+ * Copies a disk index's arrays to host memory for inspection: sizes[0] = cell
+ * words (4^grid_log2), sizes[1] = entry words, sizes[2] = grid_log2; cell and
+ * entries (uint32, those sizes) may be NULL to query the sizes.  Layout as
+ * described for spx_host_disk_index_build.  Synchronous.  Errors: SPX_EINVAL
+ * (not a disk index), SPX_ECUDA.
+ */
+spx_status spx_disk_index_arrays(spx_ctx *ctx, spx_index index, uint32_t *cell, uint32_t *entries,
+                                 uint64_t sizes[3]);
+
 /* Sizes of a built index. */
 typedef struct {
     int grid_log2;

@@ -887,6 +887,47 @@ static std::string check_disks(const int32_t *cxy, const int32_t *r, uint32_t Q)
     return {};
 }
 
+// Registers a disk index whose arrays are in one device allocation.
+static spx_status register_disk_index(spx_ctx *ctx, void *mem, size_t total, const uint32_t *cell, const uint32_t *ent,
+                                      const int4 *disk, const uint32_t *cover, int g, uint32_t Q, uint64_t n_entries,
+                                      uint64_t n_inside, uint64_t n_boundary,
+                                      std::chrono::steady_clock::time_point t0, spx_index *out)
+{
+    auto ix = std::make_unique<IndexObj>();
+    ix->mem = mem;
+    ix->kind = 1;
+    ix->dview.cell = cell;
+    ix->dview.ent = ent;
+    ix->dview.disk = disk;
+    ix->dview.cover = cover;
+    ix->dview.sc = kBoxLog2 - g;
+    ix->dview.g = g;
+    ix->dview.cg = std::min(g, kCoverLog2);
+    ix->dview.scv = kBoxLog2 - ix->dview.cg;
+    ix->dview.Q = Q;
+    spx_index_info &inf = ix->info;
+    inf.grid_log2 = g;
+    inf.n_polys = Q;
+    inf.n_cells = uint64_t(1) << (2 * g);
+    inf.n_entries = n_entries;
+    inf.n_inside = n_inside;
+    inf.n_boundary = n_boundary;
+    inf.device_bytes = total;
+    inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const uint64_t h = make_handle(ctx, kTagIndex);
+    ctx->indexes[h] = std::move(ix);
+    *out = h;
+    return SPX_OK;
+}
+
+static std::vector<int4> disk_array(const int32_t *cxy, const int32_t *r, uint32_t Q)
+{
+    std::vector<int4> disks(std::max<uint32_t>(Q, 1));
+    for (uint32_t q = 0; q < Q; ++q)
+        disks[q] = make_int4(cxy[2 * q], cxy[2 * q + 1], r[q], 0);
+    return disks;
+}
+
 spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t *r, uint32_t Q, int grid_log2,
                                 spx_index *out)
 {
@@ -905,18 +946,16 @@ spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t 
     std::string err;
     if (!build_disk_index(cxy, r, Q, g, hd, err))
         return fail(ctx, SPX_EINVAL, "build_disk_index: " + err);
-    std::vector<int4> disks(std::max<uint32_t>(Q, 1));
-    for (uint32_t q = 0; q < Q; ++q)
-        disks[q] = make_int4(cxy[2 * q], cxy[2 * q + 1], r[q], 0);
+    const std::vector<int4> disks = disk_array(cxy, r, Q);
     const std::vector<uint32_t> cover = cover_bitmap(hd.cell, g);
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
     const size_t b_cell = hd.cell.size() * 4, b_ent = hd.entries.size() * 4, b_disk = disks.size() * sizeof(int4),
                  b_cover = cover.size() * 4;
     const size_t total = up(b_cell) + up(b_ent) + up(b_disk) + up(b_cover);
-    auto ix = std::make_unique<IndexObj>();
-    if (cudaMalloc(&ix->mem, total) != cudaSuccess)
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, total) != cudaSuccess)
         return fail(ctx, SPX_ENOMEM, "build_disk_index: cudaMalloc failed");
-    char *m = static_cast<char *>(ix->mem), *p_ent = m + up(b_cell), *p_disk = p_ent + up(b_ent),
+    char *m = static_cast<char *>(mem), *p_ent = m + up(b_cell), *p_disk = p_ent + up(b_ent),
          *p_cover = p_disk + up(b_disk);
     cudaError_t e = cudaMemcpy(m, hd.cell.data(), b_cell, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -926,31 +965,60 @@ spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t 
     if (e == cudaSuccess)
         e = cudaMemcpy(p_cover, cover.data(), b_cover, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(ix->mem);
+        cudaFree(mem);
         return cuda_fail(ctx, e, "build_disk_index upload");
     }
-    ix->kind = 1;
-    ix->dview.cell = reinterpret_cast<const uint32_t *>(m);
-    ix->dview.ent = reinterpret_cast<const uint32_t *>(p_ent);
-    ix->dview.disk = reinterpret_cast<const int4 *>(p_disk);
-    ix->dview.cover = reinterpret_cast<const uint32_t *>(p_cover);
-    ix->dview.sc = kBoxLog2 - g;
-    ix->dview.g = g;
-    ix->dview.cg = std::min(g, kCoverLog2);
-    ix->dview.scv = kBoxLog2 - ix->dview.cg;
-    ix->dview.Q = Q;
-    spx_index_info &inf = ix->info;
-    inf.grid_log2 = g;
-    inf.n_polys = Q;
-    inf.n_cells = hd.cell.size();
-    inf.n_entries = hd.entries.size();
-    inf.n_inside = hd.n_inside;
-    inf.n_boundary = hd.n_boundary;
-    inf.device_bytes = total;
-    inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    const uint64_t h = make_handle(ctx, kTagIndex);
-    ctx->indexes[h] = std::move(ix);
-    *out = h;
+    return register_disk_index(ctx, mem, total, reinterpret_cast<const uint32_t *>(m),
+                               reinterpret_cast<const uint32_t *>(p_ent), reinterpret_cast<const int4 *>(p_disk),
+                               reinterpret_cast<const uint32_t *>(p_cover), g, Q, hd.entries.size(), hd.n_inside,
+                               hd.n_boundary, t0, out);
+}
+
+spx_status spx_build_disk_index_device(spx_ctx *ctx, const int32_t *cxy, const int32_t *r, uint32_t Q, int grid_log2,
+                                       spx_index *out)
+{
+    if (!ctx || !out || (Q && (!cxy || !r)))
+        return fail(ctx, SPX_EINVAL, "build_disk_index_device: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    {
+        const std::string bad = check_disks(cxy, r, Q);
+        if (!bad.empty())
+            return fail(ctx, SPX_EINVAL, "build_disk_index_device: " + bad);
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const int g = grid_log2 ? grid_log2 : default_disk_grid_log2(r, Q);
+    if (g < 1 || g > kMaxGridLog2)
+        return fail(ctx, SPX_EINVAL, "build_disk_index_device: grid_log2 must be in [1, 13]");
+    const std::vector<int4> disks = disk_array(cxy, r, Q);
+    DiskIndexDev d{};
+    cudaError_t e = cudaSuccess;
+    const int st = build_disk_index_device(disks.data(), Q, g, d, e);
+    if (st == 1)
+        return fail(ctx, SPX_EINVAL, "build_disk_index_device: too many disk entries for one index; use a smaller grid");
+    if (st != 0)
+        return e == cudaErrorMemoryAllocation ? fail(ctx, SPX_ENOMEM, "build_disk_index_device: out of device memory")
+                                              : cuda_fail(ctx, e, "build_disk_index_device");
+    return register_disk_index(ctx, d.mem, d.bytes, d.cell, d.ent, d.disk, d.cover, g, Q, d.n_ent, d.n_inside,
+                               d.n_boundary, t0, out);
+}
+
+spx_status spx_disk_index_arrays(spx_ctx *ctx, spx_index index, uint32_t *cell, uint32_t *entries, uint64_t sizes[3])
+{
+    if (!ctx || !sizes)
+        return fail(ctx, SPX_EINVAL, "disk_index_arrays: null argument");
+    ctx->err.clear();
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!ix || ix->kind != 1)
+        return fail(ctx, SPX_EINVAL, "disk_index_arrays: not a disk index handle");
+    cudaSetDevice(ctx->device);
+    sizes[0] = ix->info.n_cells;
+    sizes[1] = ix->info.n_entries;
+    sizes[2] = uint64_t(ix->info.grid_log2);
+    if (cell)
+        SPX_CUDA(cudaMemcpy(cell, ix->dview.cell, sizes[0] * 4, cudaMemcpyDeviceToHost), "disk_index_arrays copy");
+    if (entries)
+        SPX_CUDA(cudaMemcpy(entries, ix->dview.ent, sizes[1] * 4, cudaMemcpyDeviceToHost), "disk_index_arrays copy");
     return SPX_OK;
 }
 

@@ -1540,6 +1540,282 @@ __global__ void __launch_bounds__(kThreads, 4) k_dwemit(DiskLaunch a, const unsi
     walk(0, qn);
 }
 
+// ------------------------------------------------------ disk index, built on the device
+// The same arrays as the host build (build_disk_index): for every disk, every
+// cell of its clipped bounding box is classified exactly in int64 (the cell's
+// integer point nearest the centre beyond r: no entry; its farthest corner
+// within r: INSIDE; else BOUNDARY); the (cell, disk) records are bucketed by
+// cell; a cell with one INSIDE record gets a kind-1 word, any other non-empty
+// cell a list (n, then the records in disk order), lists laid out in cell
+// order after a reserved word 0.  No kernel here waits on another.
+struct DiskBox {
+    uint32_t i0, j0, w, h; // first cell column / row and the box's size in cells (w = 0: no cell)
+};
+
+__device__ __forceinline__ DiskBox disk_box(const int4 &d, int sh)
+{
+    const long long last = (long long)kBox - 1;
+    const long long xlo = max(0ll, (long long)d.x - d.z), xhi = min(last, (long long)d.x + d.z);
+    const long long ylo = max(0ll, (long long)d.y - d.z), yhi = min(last, (long long)d.y + d.z);
+    if (xlo > xhi || ylo > yhi)
+        return {0u, 0u, 0u, 0u};
+    const uint32_t i0 = (uint32_t)(xlo >> sh), j0 = (uint32_t)(ylo >> sh);
+    return {i0, j0, (uint32_t)(xhi >> sh) - i0 + 1, (uint32_t)(yhi >> sh) - j0 + 1};
+}
+
+// Does disk d reach cell (i, j) of side 2^sh, and does it hold the whole cell?
+__device__ __forceinline__ bool disk_cell(const int4 &d, uint32_t i, uint32_t j, int sh, bool &inside)
+{
+    const long long S = 1ll << sh, x0 = (long long)i << sh, y0 = (long long)j << sh, x1 = x0 + S - 1,
+                    y1 = y0 + S - 1;
+    const long long cx = d.x, cy = d.y, rr = (long long)d.z * d.z;
+    const long long nx = min(max(cx, x0), x1) - cx, ny = min(max(cy, y0), y1) - cy;
+    if (nx * nx + ny * ny > rr)
+        return false;
+    const long long fx = max(cx - x0, x1 - cx), fy = max(cy - y0, y1 - cy);
+    inside = fx * fx + fy * fy <= rr;
+    return true;
+}
+
+// Records per disk (a block per disk, its threads over the box's cells) and
+// the number of BOUNDARY records.
+__global__ void __launch_bounds__(256) k_dbuild_count(const int4 *disk, uint32_t Q, int g,
+                                                      unsigned long long *rec_cnt, unsigned long long *n_bnd)
+{
+    __shared__ unsigned long long s_c, s_b;
+    const int sh = kBoxLog2 - g;
+    for (uint32_t q = blockIdx.x; q < Q; q += gridDim.x) {
+        if (threadIdx.x == 0)
+            s_c = s_b = 0;
+        __syncthreads();
+        const int4 d = disk[q];
+        const DiskBox b = disk_box(d, sh);
+        const uint64_t n = (uint64_t)b.w * b.h;
+        unsigned long long c = 0, bn = 0;
+        for (uint64_t t = threadIdx.x; t < n; t += blockDim.x) {
+            bool in = false;
+            if (disk_cell(d, b.i0 + (uint32_t)(t % b.w), b.j0 + (uint32_t)(t / b.w), sh, in)) {
+                ++c;
+                bn += in ? 0u : 1u;
+            }
+        }
+        c = warp_sum64(c);
+        bn = warp_sum64(bn);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&s_c, c);
+            atomicAdd(&s_b, bn);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            rec_cnt[q] = s_c;
+            if (s_b)
+                atomicAdd(n_bnd, s_b);
+        }
+        __syncthreads();
+    }
+}
+
+// Records (cell, disk << 1 | boundary) at each disk's offset; per-cell record
+// counts and an OR of their boundary flags.
+__global__ void __launch_bounds__(256) k_dbuild_write(const int4 *disk, uint32_t Q, int g,
+                                                      const unsigned long long *rec_off, uint2 *rec,
+                                                      uint32_t *cell_cnt, uint32_t *cell_bnd)
+{
+    __shared__ unsigned long long s_pos;
+    const int sh = kBoxLog2 - g;
+    for (uint32_t q = blockIdx.x; q < Q; q += gridDim.x) {
+        if (threadIdx.x == 0)
+            s_pos = 0;
+        __syncthreads();
+        const int4 d = disk[q];
+        const DiskBox b = disk_box(d, sh);
+        const uint64_t n = (uint64_t)b.w * b.h;
+        const unsigned long long base = rec_off[q];
+        for (uint64_t t = threadIdx.x; t < n; t += blockDim.x) {
+            const uint32_t i = b.i0 + (uint32_t)(t % b.w), j = b.j0 + (uint32_t)(t / b.w);
+            bool in = false;
+            if (disk_cell(d, i, j, sh, in)) {
+                const uint32_t c = (j << g) | i;
+                rec[base + atomicAdd(&s_pos, 1ull)] = make_uint2(c, (q << 1) | (in ? 0u : 1u));
+                atomicAdd(cell_cnt + c, 1u);
+                if (!in)
+                    atomicOr(cell_bnd + c, 1u);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Words of the entry list of every cell that needs one (0 for the others).
+__global__ void k_dbuild_words(uint32_t ncell, const uint32_t *cell_cnt, const uint32_t *cell_bnd,
+                               unsigned long long *list_words)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const uint32_t n = cell_cnt[c];
+        list_words[c] = (n >= 2 || (n == 1 && cell_bnd[c])) ? n + 1ull : 0ull;
+    }
+}
+
+// List cells: their word and list length (after the reserved word 0).
+__global__ void k_dbuild_cells(uint32_t ncell, const uint32_t *cell_cnt, const uint32_t *cell_bnd,
+                               const unsigned long long *list_off, uint32_t *cell_word, uint32_t *ent)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const uint32_t n = cell_cnt[c];
+        if (n >= 2 || (n == 1 && cell_bnd[c])) {
+            const uint32_t off = 1u + (uint32_t)list_off[c];
+            cell_word[c] = (kCellList << 30) | off;
+            ent[off] = n;
+        }
+    }
+}
+
+// Every record to its cell: the word of a one-INSIDE cell, else the next slot
+// of the cell's list (sorted afterwards).
+__global__ void k_dbuild_scatter(uint64_t R, const uint2 *rec, const uint32_t *cell_cnt, const uint32_t *cell_bnd,
+                                 const unsigned long long *list_off, uint32_t *cursor, uint32_t *cell_word,
+                                 uint32_t *ent)
+{
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < R; k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 r = rec[k];
+        if (cell_cnt[r.x] == 1 && !cell_bnd[r.x])
+            cell_word[r.x] = (kCellInsideOne << 30) | (r.y >> 1);
+        else
+            ent[2u + (uint32_t)list_off[r.x] + atomicAdd(cursor + r.x, 1u)] = r.y;
+    }
+}
+
+// Each list in disk order (insertion sort: lists are short).
+__global__ void k_dbuild_sort(uint32_t ncell, const uint32_t *cell_word, uint32_t *ent)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const uint32_t w = cell_word[c];
+        if ((w >> 30) != kCellList)
+            continue;
+        uint32_t *l = ent + (w & kPayloadMask) + 1;
+        const uint32_t n = l[-1];
+        for (uint32_t a = 1; a < n; ++a) {
+            const uint32_t v = l[a];
+            uint32_t b = a;
+            for (; b > 0 && l[b - 1] > v; --b)
+                l[b] = l[b - 1];
+            l[b] = v;
+        }
+    }
+}
+
+// Cover bitmap: a bit per block of cells that holds a non-empty cell.
+__global__ void k_dbuild_cover(uint32_t ncell, int g, int cg, const uint32_t *cell_word, uint32_t *cover)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        if (!cell_word[c])
+            continue;
+        const uint32_t cx = c & ((1u << g) - 1), cy = c >> g;
+        const uint32_t b = ((cy >> (g - cg)) << cg) | (cx >> (g - cg));
+        atomicOr(cover + (b >> 5), 1u << (b & 31));
+    }
+}
+
+int build_disk_index_device(const int4 *disks_host, uint32_t Q, int g, DiskIndexDev &out, cudaError_t &cerr)
+{
+    out = DiskIndexDev{};
+    cerr = cudaSuccess;
+    const uint32_t ncell = 1u << (2 * g);
+    const int cg = g < kCoverLog2 ? g : kCoverLog2;
+    const size_t cover_words = ((size_t(1) << (2 * cg)) / 32) > 0 ? ((size_t(1) << (2 * cg)) / 32) : 1;
+    const size_t nd = Q ? Q : 1;
+    const uint64_t nparts = scan_partials(ncell > nd ? ncell : nd) + 2;
+    // temporaries: disks | per-disk record counts | totals | scan partials |
+    // per-cell counts, flags, cursors | per-cell list words
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t t_disk = up(nd * sizeof(int4)), t_cnt = up((nd + 1) * 8), t_tot = up(3 * 8), t_part = up(nparts * 8),
+                 t_cell = up(size_t(ncell) * 4), t_words = up(size_t(ncell) * 8);
+    char *tmp = nullptr, *recm = nullptr;
+    auto done = [&](int status, cudaError_t e) {
+        cerr = e;
+        if (recm)
+            cudaFree(recm);
+        if (tmp)
+            cudaFree(tmp);
+        if (status && out.mem) {
+            cudaFree(out.mem);
+            out.mem = nullptr;
+        }
+        return status;
+    };
+    cudaError_t e = cudaMalloc(&tmp, t_disk + t_cnt + t_tot + t_part + 3 * t_cell + t_words);
+    if (e != cudaSuccess)
+        return done(2, e);
+    int4 *d_disk = reinterpret_cast<int4 *>(tmp);
+    auto *rec_cnt = reinterpret_cast<unsigned long long *>(tmp + t_disk);
+    auto *tot = reinterpret_cast<unsigned long long *>(tmp + t_disk + t_cnt); // records, list words, boundary
+    auto *part = reinterpret_cast<unsigned long long *>(tmp + t_disk + t_cnt + t_tot);
+    auto *cell_cnt = reinterpret_cast<uint32_t *>(tmp + t_disk + t_cnt + t_tot + t_part);
+    auto *cell_bnd = reinterpret_cast<uint32_t *>(tmp + t_disk + t_cnt + t_tot + t_part + t_cell);
+    auto *cursor = reinterpret_cast<uint32_t *>(tmp + t_disk + t_cnt + t_tot + t_part + 2 * t_cell);
+    auto *words = reinterpret_cast<unsigned long long *>(tmp + t_disk + t_cnt + t_tot + t_part + 3 * t_cell);
+    if ((e = cudaMemcpy(d_disk, disks_host, nd * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(tot, 0, 3 * 8)) != cudaSuccess || (e = cudaMemset(cell_cnt, 0, 3 * t_cell)) != cudaSuccess)
+        return done(2, e);
+    const int sms = device_sm_count();
+    const unsigned dblocks = Q ? (Q < unsigned(sms * 8) ? Q : unsigned(sms * 8)) : 1u;
+    const unsigned cblocks = unsigned((ncell + 255) / 256 < uint32_t(sms * 16) ? (ncell + 255) / 256 : sms * 16);
+    unsigned long long R = 0, T = 0, nb = 0;
+    if (Q) {
+        k_dbuild_count<<<dblocks, 256>>>(d_disk, Q, g, rec_cnt, tot + 2);
+        if ((e = cudaGetLastError()) != cudaSuccess || (e = launch_scan(rec_cnt, Q, tot, part, 0)) != cudaSuccess ||
+            (e = cudaMemcpy(&R, tot, 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return done(2, e);
+    }
+    if (R) {
+        if ((e = cudaMalloc(&recm, R * sizeof(uint2))) != cudaSuccess)
+            return done(2, e);
+        k_dbuild_write<<<dblocks, 256>>>(d_disk, Q, g, rec_cnt, reinterpret_cast<uint2 *>(recm), cell_cnt, cell_bnd);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return done(2, e);
+    }
+    k_dbuild_words<<<cblocks, 256>>>(ncell, cell_cnt, cell_bnd, words);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = launch_scan(words, ncell, tot + 1, part, 0)) != cudaSuccess ||
+        (e = cudaMemcpy(&T, tot + 1, 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(&nb, tot + 2, 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return done(2, e);
+    const uint64_t E = 1 + T;
+    if (E > kPayloadMask)
+        return done(1, cudaSuccess);
+    // the index's own allocation: cells | entries | disks | cover, as the host path lays it out
+    const size_t b_cell = size_t(ncell) * 4, b_ent = size_t(E) * 4, b_disk = nd * sizeof(int4), b_cover = cover_words * 4;
+    out.bytes = up(b_cell) + up(b_ent) + up(b_disk) + up(b_cover);
+    if ((e = cudaMalloc(&out.mem, out.bytes)) != cudaSuccess) {
+        out.mem = nullptr;
+        return done(2, e);
+    }
+    char *m = static_cast<char *>(out.mem);
+    out.cell = reinterpret_cast<uint32_t *>(m);
+    out.ent = reinterpret_cast<uint32_t *>(m + up(b_cell));
+    out.disk = reinterpret_cast<int4 *>(m + up(b_cell) + up(b_ent));
+    out.cover = reinterpret_cast<uint32_t *>(m + up(b_cell) + up(b_ent) + up(b_disk));
+    if ((e = cudaMemset(out.cell, 0, b_cell)) != cudaSuccess || (e = cudaMemset(out.ent, 0, b_ent)) != cudaSuccess ||
+        (e = cudaMemset(out.cover, 0, b_cover)) != cudaSuccess ||
+        (e = cudaMemcpy(out.disk, d_disk, b_disk, cudaMemcpyDeviceToDevice)) != cudaSuccess)
+        return done(2, e);
+    k_dbuild_cells<<<cblocks, 256>>>(ncell, cell_cnt, cell_bnd, words, out.cell, out.ent);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return done(2, e);
+    if (R) {
+        const unsigned rblocks = unsigned((R + 255) / 256 < uint64_t(sms * 16) ? (R + 255) / 256 : sms * 16);
+        k_dbuild_scatter<<<rblocks, 256>>>(R, reinterpret_cast<const uint2 *>(recm), cell_cnt, cell_bnd, words, cursor,
+                                           out.cell, out.ent);
+        k_dbuild_sort<<<cblocks, 256>>>(ncell, out.cell, out.ent);
+    }
+    k_dbuild_cover<<<cblocks, 256>>>(ncell, g, cg, out.cell, out.cover);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
+        return done(2, e);
+    out.n_ent = E;
+    out.n_boundary = nb;
+    out.n_inside = R - nb;
+    return done(0, cudaSuccess);
+}
+
 // ------------------------------------------------------ clustered point table
 // Counting sort of a point table by grid cell (row-major cells of a 2^c x 2^c
 // grid; points outside the box go to one last bin).  Lanes of a warp with the

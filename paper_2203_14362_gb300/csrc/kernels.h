@@ -62,6 +62,23 @@ size_t disk_select_scratch_bytes(uint64_t n, uint32_t Q, uint64_t cap);
 cudaError_t launch_disk_select(const DiskLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
                                void *scratch, cudaStream_t s);
 
+// Device build of the disk index of Q disks (host array of (cx, cy, r, 0),
+// already checked) on a 2^g grid: the same cell words and entries as the host
+// build (build_disk_index) and the same cover bitmap, in one new device
+// allocation laid out as the host path lays it out (cells | entries | disks |
+// cover, each part 256-byte aligned); the caller owns out.mem.  Runs on the
+// legacy default stream and synchronises the device.  Returns 0, 1 when the
+// entries would not fit 30-bit offsets (use a coarser grid), or 2 on a CUDA
+// error (in cerr).
+struct DiskIndexDev {
+    void *mem;
+    size_t bytes;
+    uint32_t *cell, *ent, *cover;
+    int4 *disk;
+    uint64_t n_ent, n_inside, n_boundary;
+};
+int build_disk_index_device(const int4 *disks_host, uint32_t Q, int g, DiskIndexDev &out, cudaError_t &cerr);
+
 // Device status word bits (ORed into the ctx's persistent error word).
 constexpr unsigned kErrTimeout = 1u;   // a bounded wait gave up
 constexpr unsigned kErrInternal = 2u;  // an internal consistency check failed

@@ -28,6 +28,7 @@ EXPORTS = [
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
     "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
     "spx_build_disk_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free",
+    "spx_build_disk_index_device", "spx_disk_index_arrays",
 ]
 
 SPX_REQ_SELECT, SPX_REQ_JOIN = 1, 2
@@ -138,6 +139,8 @@ def load(path: str = LIB_PATH):
         "spx_host_disk_index_build": ([V, V, U32, I, C.POINTER(V), P64], I),
         "spx_host_disk_index_copy": ([V, V, V], I),
         "spx_host_disk_index_free": ([V], None),
+        "spx_build_disk_index_device": ([V, V, V, U32, I, P64], I),
+        "spx_disk_index_arrays": ([V, U64, V, V, P64], I),
         "spx_aggregate_host": ([V, V, U64, U64, V], I),
         "spx_set_host_streaming": ([V, I, I], I),
         "spx_points_info": ([V, U64, C.POINTER(V), P64, C.POINTER(I)], I),
@@ -294,15 +297,28 @@ class Engine:
         rows = [{f: getattr(trials[i], f) for f, _ in TuneTrial._fields_} for i in range(min(n.value, 64))]
         return params, rows, (h.value if keep_index else None)
 
-    def build_disk_index(self, centers: np.ndarray, radii: np.ndarray, grid_log2: int = 0) -> int:
-        """spx_build_disk_index: an index of disks for distance joins / selections."""
+    def build_disk_index(self, centers: np.ndarray, radii: np.ndarray, grid_log2: int = 0,
+                         on_device: bool = False) -> int:
+        """spx_build_disk_index (or, on_device, spx_build_disk_index_device):
+        an index of disks for distance joins / selections."""
         c = np.ascontiguousarray(centers, dtype=np.int32).reshape(-1, 2)
         r = np.ascontiguousarray(radii, dtype=np.int32).reshape(-1)
         assert c.shape[0] == r.shape[0]
         h = C.c_uint64()
-        self._check(self.lib.spx_build_disk_index(self.ctx, _np_ptr(c), _np_ptr(r), c.shape[0], grid_log2,
-                                                  C.byref(h)), "spx_build_disk_index")
+        fn = "spx_build_disk_index_device" if on_device else "spx_build_disk_index"
+        self._check(getattr(self.lib, fn)(self.ctx, _np_ptr(c), _np_ptr(r), c.shape[0], grid_log2, C.byref(h)), fn)
         return h.value
+
+    def disk_index_arrays(self, index: int) -> dict:
+        """spx_disk_index_arrays: a disk index's cell words and entries, copied
+        to the host (the layout of host_disk_index)."""
+        sizes = (C.c_uint64 * 3)()
+        self._check(self.lib.spx_disk_index_arrays(self.ctx, index, None, None, sizes), "spx_disk_index_arrays")
+        cell = np.zeros(sizes[0], np.uint32)
+        ent = np.zeros(max(sizes[1], 1), np.uint32)
+        self._check(self.lib.spx_disk_index_arrays(self.ctx, index, _np_ptr(cell), _np_ptr(ent), sizes),
+                    "spx_disk_index_arrays")
+        return {"cell": cell, "entries": ent[:sizes[1]], "g": int(sizes[2])}
 
     def index_info(self, index: int) -> dict:
         inf = IndexInfo()

@@ -43,13 +43,13 @@ def data():
     return pts, centers, radii, want_p, want_c
 
 
-@pytest.mark.parametrize("grid", [0, 6, 11, 13])
-def test_disk_join_select_aggregate(eng, data, grid):
+@pytest.mark.parametrize("grid,on_device", [(0, False), (6, False), (11, False), (13, False), (0, True), (11, True)])
+def test_disk_join_select_aggregate(eng, data, grid, on_device):
     pts, centers, radii, want_p, want_c = data
     Q = centers.shape[0]
     dpts = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
     ph = eng.load_points(dpts)
-    ih = eng.build_disk_index(centers, radii, grid)
+    ih = eng.build_disk_index(centers, radii, grid, on_device=on_device)
     try:
         info = eng.index_info(ih)
         assert info["n_polys"] == Q and (grid == 0 or info["grid_log2"] == grid)
@@ -163,3 +163,50 @@ def test_disk_counts_in_global_memory_and_deep_overlaps(eng):
     finally:
         eng.free(ph)
         del dpts
+
+
+def _same_index(eng, centers, radii, grid):
+    """The device build's arrays and sizes equal the host build's, byte for byte."""
+    host = spx.host_disk_index(centers, radii, grid)
+    a = eng.build_disk_index(centers, radii, grid, on_device=False)
+    b = eng.build_disk_index(centers, radii, grid, on_device=True)
+    try:
+        da, db = eng.disk_index_arrays(a), eng.disk_index_arrays(b)
+        ia, ib = eng.index_info(a), eng.index_info(b)
+    finally:
+        eng.free(b)
+        eng.free(a)
+    assert da["g"] == db["g"] == host["g"]
+    assert np.array_equal(da["cell"], host["cell"]) and np.array_equal(da["entries"], host["entries"])
+    assert np.array_equal(db["cell"], host["cell"]), "device cell words differ"
+    assert np.array_equal(db["entries"], host["entries"]), "device entries differ"
+    for k in ("n_cells", "n_entries", "n_inside", "n_boundary", "device_bytes"):
+        assert ia[k] == ib[k], k
+
+
+@pytest.mark.parametrize("grid", [0, 1, 3, 8, 11, 13])
+def test_device_disk_index_build_equals_host(eng, grid):
+    from test_disk_index_host import crafted, disk_set
+    centers, radii = disk_set(0xD15C0 + grid)
+    if grid >= 3:
+        cc, cr, _ = crafted(0xC0 + grid, grid)
+        centers = np.concatenate([centers, cc.astype(np.int32)])
+        radii = np.concatenate([radii, cr.astype(np.int32)])
+    _same_index(eng, centers, radii, grid)
+
+
+def test_device_disk_index_build_edge_cases(eng):
+    # no disks; one zero-radius disk on the box's far corner (no cell); a disk
+    # covering the whole box; 1100 deep overlaps plus 12000 small disks
+    _same_index(eng, np.zeros((0, 2), np.int32), np.zeros(0, np.int32), 5)
+    _same_index(eng, np.array([[1 << 30, 1 << 30]], np.int32), np.array([0], np.int32), 7)
+    _same_index(eng, np.array([[1 << 29, 1 << 29]], np.int32), np.array([(1 << 30) - 1], np.int32), 6)
+    rng = np.random.default_rng(g.SEED_BASE + 97)
+    c = 1 << 29
+    deep = np.column_stack([c + rng.integers(-1000, 1000, 1100), c + rng.integers(-1000, 1000, 1100)])
+    small = rng.integers(0, (1 << 30) + 1, (12000, 2))
+    centers = np.concatenate([small, deep]).astype(np.int32)
+    radii = np.concatenate([rng.integers(0, 1 << 23, 12000), rng.integers(1 << 24, 1 << 25, 1100)]).astype(np.int32)
+    _same_index(eng, centers, radii, 9)
+    _same_index(eng, centers, radii, 0)
+
