@@ -1242,10 +1242,7 @@ __device__ __forceinline__ uint32_t disk_walk(const DiskView &d, int px, int py,
 // before any of the chunk's points is walked).  It stores a 4-byte result per point and a pair total per
 // 256-point chunk, and counts per disk (in shared memory when Q <=
 // kHistMax); pass 3 writes the pairs from the results.
-#ifndef SPX_DISK_PREFETCH
-#define SPX_DISK_PREFETCH 0 // 1: load the next chunk's points while resolving this one (3 CTAs/SM)
-#endif
-constexpr int kDiskMinBlocks = SPX_DISK_PREFETCH ? 3 : 4;
+constexpr int kDiskMinBlocks = 4;
 constexpr uint32_t kDiskCoverWords = 1u << (2 * kCoverLog2 - 5); // cover bitmap in shared memory
 constexpr int kDQueue = kWChunk + 32; // a chunk's points plus a partial round
 constexpr size_t kDWarpSmem = size_t(kWarps) * kDQueue * sizeof(uint4);
@@ -1315,20 +1312,6 @@ __global__ void __launch_bounds__(kThreads, kDiskMinBlocks) k_dwarp(DiskLaunch a
     };
     const uint32_t nw = gridDim.x * kWarps;
     uint32_t qn = 0; // queued list points, < 32 between chunks
-    // a chunk's points (rows past the table's end read as outside the box)
-    auto load_points = [&](uint32_t ch, int2 (&q)[kWItems]) {
-        const uint64_t base = (uint64_t)ch * kWChunk;
-        const uint32_t npts = ch < nchunks ? (uint32_t)min((uint64_t)kWChunk, a.n - base) : 0u;
-#pragma unroll
-        for (int j = 0; j < kWItems; ++j) {
-            const uint32_t loc = j * 32 + lane;
-            q[j] = loc < npts ? __ldcs(a.pts + base + loc) : make_int2(-1, -1);
-        }
-    };
-#if SPX_DISK_PREFETCH
-    int2 nxt[kWItems];
-    load_points(blockIdx.x * kWarps + warp, nxt);
-#endif
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
         const uint64_t base = (uint64_t)ch * kWChunk;
         const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
@@ -1336,14 +1319,12 @@ __global__ void __launch_bounds__(kThreads, kDiskMinBlocks) k_dwarp(DiskLaunch a
             n_pts += npts;
         int2 p[kWItems];
         uint32_t w[kWItems];
-#if SPX_DISK_PREFETCH
+        // rows past the table's end read as outside the box
 #pragma unroll
-        for (int j = 0; j < kWItems; ++j)
-            p[j] = nxt[j];
-        load_points(ch + nw, nxt);
-#else
-        load_points(ch, p);
-#endif
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t loc = j * 32 + lane;
+            p[j] = loc < npts ? __ldcs(a.pts + base + loc) : make_int2(-1, -1);
+        }
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             // points outside the box or in a block of empty cells read no cell word
