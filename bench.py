@@ -306,7 +306,9 @@ def run_reference(args, world, rank):
         "config": {"workload": args.workload, "desc": desc, "sample_points_per_step": sample,
                    "polygons": int(v.shape[0]) if args.workload.startswith("dist") else int(o.shape[0] - 1)},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"first {sample} points of the workload per step (pairs + counts, fast oracle)"},
+                         "sample": (f"first {sample} points of the workload per step (distance join, brute force "
+                                    "over all disks)" if args.workload.startswith("dist") else
+                                    f"first {sample} points of the workload per step (pairs + counts, fast oracle)")},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
