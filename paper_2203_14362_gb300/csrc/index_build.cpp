@@ -388,46 +388,54 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
     out.n_polys = P;
     const int F = 1 << sb, FF = F * F;
     const uint64_t n_cells = uint64_t(1) << (2 * g);
-    // concatenate fine records and edges; fix part-local indices
-    std::vector<FineRec> fine_all;
-    uint64_t n_edges = 0, n_fine = 0;
-    for (auto &p : parts) {
+    // parts in order: global fine-record and edge offsets
+    std::vector<uint64_t> fine_base(parts.size() + 1, 0), edge_base(parts.size() + 1, 0);
+    for (size_t k = 0; k < parts.size(); ++k) {
+        const Part &p = parts[k];
         if (!p.err.empty()) {
             err = p.err;
             return false;
         }
-        n_edges += p.edges.size() / 4;
-        n_fine += p.fine.size();
+        fine_base[k + 1] = fine_base[k] + p.fine.size();
+        edge_base[k + 1] = edge_base[k] + p.edges.size() / 4;
         out.n_inside += p.n_inside;
         out.n_mixed += p.n_mixed;
         out.n_boundary += p.n_boundary;
     }
+    const uint64_t n_edges = edge_base.back(), n_fine = fine_base.back();
     if (n_edges >= (uint64_t(1) << 32)) {
         err = "index too large (edge list limit 2^32)";
         return false;
     }
+    // every part, in parallel: its edges into place, its fine records' edge
+    // offsets made global (records stay in their part; fine_ptr finds them)
     out.edges.resize(size_t(n_edges) * 4);
-    fine_all.reserve(size_t(n_fine));
-    std::vector<uint32_t> cnt(size_t(n_cells) + 1, 0);
+    std::vector<const FineRec *> fine_ptr(static_cast<size_t>(n_fine));
     {
-        uint64_t eb = 0, fb = 0;
-        for (auto &p : parts) {
-            for (auto &fr : p.fine) {
-                for (int k = 0; k < F; ++k)
-                    fr.row_begin[k] += uint32_t(eb);
-                fine_all.push_back(fr);
+        auto move_part = [&](size_t k) {
+            Part &p = parts[k];
+            for (size_t m = 0; m < p.fine.size(); ++m) {
+                for (int r = 0; r < F; ++r)
+                    p.fine[m].row_begin[r] += uint32_t(edge_base[k]);
+                fine_ptr[size_t(fine_base[k] + m)] = &p.fine[m];
             }
-            for (auto &rc : p.recs) {
-                rc.fine_idx += uint32_t(fb);
-                cnt[rc.cell + 1]++;
-            }
-            std::copy(p.edges.begin(), p.edges.end(), out.edges.begin() + ptrdiff_t(eb * 4));
-            eb += p.edges.size() / 4;
-            fb += p.fine.size();
-            std::vector<FineRec>().swap(p.fine);
+            std::copy(p.edges.begin(), p.edges.end(), out.edges.begin() + ptrdiff_t(edge_base[k] * 4));
             std::vector<int32_t>().swap(p.edges);
-        }
+        };
+        std::vector<std::thread> pool;
+        for (size_t k = 1; k < parts.size(); ++k)
+            pool.emplace_back(move_part, k);
+        move_part(0);
+        for (auto &th : pool)
+            th.join();
     }
+    // records bucketed by coarse cell, parts in order (so polygon order within a cell)
+    std::vector<uint32_t> cnt(size_t(n_cells) + 1, 0);
+    for (size_t k = 0; k < parts.size(); ++k)
+        for (auto &rc : parts[k].recs) {
+            rc.fine_idx += uint32_t(fine_base[k]);
+            cnt[rc.cell + 1]++;
+        }
     for (uint64_t c = 0; c < n_cells; ++c)
         cnt[c + 1] += cnt[c];
     std::vector<Rec> recs(cnt[n_cells]);
@@ -439,58 +447,119 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
             std::vector<Rec>().swap(p.recs);
         }
     }
+    // the entry list of fine cell f of the mixed coarse cell with records
+    // [b0, b1): (poly, flags, edge_begin, edge_cnt) per entry
+    auto fine_list = [&](uint32_t b0, uint32_t b1, int f, std::vector<uint32_t> &list) {
+        list.clear();
+        for (uint32_t m = b0; m < b1; ++m) {
+            const Rec &rc = recs[m];
+            if (!rc.mixed) {
+                list.insert(list.end(), {rc.poly, 0u, 0u, 0u});
+                continue;
+            }
+            const FineRec &fr = *fine_ptr[rc.fine_idx];
+            if ((fr.bnd >> f) & 1)
+                list.insert(list.end(), {rc.poly, kEntBoundary, fr.row_begin[f / F], uint32_t(fr.cnt[f])});
+            else if ((fr.inside >> f) & 1)
+                list.insert(list.end(), {rc.poly, 0u, 0u, 0u});
+        }
+    };
+    auto is_one = [](const std::vector<uint32_t> &list) { return list.size() == 4 && list[1] == 0u; };
+    // cells in parallel ranges, twice: first the fine blocks and entries each
+    // cell needs, then (after a prefix sum, so the layout is the cell order)
+    // the words themselves
+    const int nt = threads;
+    std::vector<uint64_t> c_lo(size_t(nt) + 1);
+    for (int t = 0; t <= nt; ++t)
+        c_lo[size_t(t)] = n_cells * uint64_t(t) / uint64_t(nt);
+    std::vector<uint32_t> blk_of(size_t(n_cells) + 1, 0); // 1 per mixed cell, then exclusive prefix
+    std::vector<uint64_t> ent_of(size_t(n_cells) + 1, 0); // entries per cell, then exclusive prefix
+    auto count_cells = [&](int t) {
+        std::vector<uint32_t> list;
+        for (uint64_t c = c_lo[size_t(t)]; c < c_lo[size_t(t) + 1]; ++c) {
+            const uint32_t b0 = cnt[c], b1 = cnt[c + 1];
+            if (b0 == b1 || (b1 - b0 == 1 && !recs[b0].mixed))
+                continue;
+            blk_of[c] = 1;
+            uint64_t n = 0;
+            for (int f = 0; f < FF; ++f) {
+                fine_list(b0, b1, f, list);
+                if (!list.empty() && !is_one(list))
+                    n += list.size() / 4;
+            }
+            ent_of[c] = n;
+        }
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; ++t)
+            pool.emplace_back(count_cells, t);
+        count_cells(0);
+        for (auto &th : pool)
+            th.join();
+    }
+    uint64_t n_blocks = 0, n_entries = 0;
+    for (uint64_t c = 0; c <= n_cells; ++c) {
+        const uint64_t b = blk_of[c], e = ent_of[c];
+        blk_of[c] = uint32_t(std::min<uint64_t>(n_blocks, UINT32_MAX));
+        ent_of[c] = n_entries;
+        n_blocks += b;
+        n_entries += e;
+    }
+    if (n_blocks * uint64_t(FF) >= (uint64_t(1) << 32) || (n_blocks && n_blocks - 1 >= (uint64_t(1) << 30))) {
+        err = "index too large (fine block limit)";
+        return false;
+    }
+    if (n_entries >= (uint64_t(1) << 30)) {
+        err = "index too large (entry limit 2^30)";
+        return false;
+    }
+    out.n_blocks = n_blocks;
     out.cell.assign(size_t(n_cells), 0);
-    std::vector<uint32_t> list; // scratch: (poly, flags, edge_begin, edge_cnt) per entry
-    for (uint64_t c = 0; c < n_cells; ++c) {
-        const uint32_t b0 = cnt[c], b1 = cnt[c + 1];
-        if (b0 == b1)
-            continue;
-        if (b1 - b0 == 1 && !recs[b0].mixed) {
-            out.cell[c] = (kCellInsideOne << 30) | recs[b0].poly;
-            continue;
-        }
-        const uint64_t blk = out.n_blocks++;
-        if ((blk + 1) * uint64_t(FF) >= (uint64_t(1) << 32) || blk >= (uint64_t(1) << 30)) {
-            err = "index too large (fine block limit)";
-            return false;
-        }
-        out.cell[c] = (kCellSub << 30) | uint32_t(blk);
-        out.fine.resize(size_t((blk + 1) * FF), 0);
-        for (int f = 0; f < FF; ++f) {
-            list.clear();
-            for (uint32_t m = b0; m < b1; ++m) {
-                const Rec &rc = recs[m];
-                if (!rc.mixed) {
-                    list.insert(list.end(), {rc.poly, 0u, 0u, 0u});
-                    continue;
-                }
-                const FineRec &fr = fine_all[rc.fine_idx];
-                if ((fr.bnd >> f) & 1)
-                    list.insert(list.end(), {rc.poly, kEntBoundary, fr.row_begin[f / F], uint32_t(fr.cnt[f])});
-                else if ((fr.inside >> f) & 1)
-                    list.insert(list.end(), {rc.poly, 0u, 0u, 0u});
+    out.fine.assign(size_t(n_blocks * FF), 0);
+    out.entries.assign(size_t(n_entries) * 4, 0);
+    auto fill_cells = [&](int t) {
+        std::vector<uint32_t> list;
+        for (uint64_t c = c_lo[size_t(t)]; c < c_lo[size_t(t) + 1]; ++c) {
+            const uint32_t b0 = cnt[c], b1 = cnt[c + 1];
+            if (b0 == b1)
+                continue;
+            if (b1 - b0 == 1 && !recs[b0].mixed) {
+                out.cell[c] = (kCellInsideOne << 30) | recs[b0].poly;
+                continue;
             }
-            const size_t n = list.size() / 4;
-            uint32_t w = 0;
-            if (n == 1 && list[1] == 0u) {
-                w = (kCellInsideOne << 30) | list[0];
-            } else if (n >= 1) {
-                const uint64_t e0 = out.entries.size() / 4;
-                if (e0 + n >= (uint64_t(1) << 30)) {
-                    err = "index too large (entry limit 2^30)";
-                    return false;
+            const uint64_t blk = blk_of[c];
+            out.cell[c] = (kCellSub << 30) | uint32_t(blk);
+            uint64_t e0 = ent_of[c];
+            for (int f = 0; f < FF; ++f) {
+                fine_list(b0, b1, f, list);
+                uint32_t w = 0;
+                if (is_one(list)) {
+                    w = (kCellInsideOne << 30) | list[0];
+                } else if (!list.empty()) {
+                    const size_t n = list.size() / 4;
+                    uint32_t *dst = out.entries.data() + e0 * 4;
+                    for (size_t m = 0; m < n; ++m) {
+                        // entry = (poly, edge_begin, edge_cnt, flags)
+                        dst[4 * m] = list[4 * m];
+                        dst[4 * m + 1] = list[4 * m + 2];
+                        dst[4 * m + 2] = list[4 * m + 3];
+                        dst[4 * m + 3] = list[4 * m + 1] | (m + 1 == n ? kEntLast : 0u);
+                    }
+                    w = (kCellList << 30) | uint32_t(e0);
+                    e0 += n;
                 }
-                for (size_t m = 0; m < n; ++m) {
-                    // entry = (poly, edge_begin, edge_cnt, flags)
-                    out.entries.push_back(list[4 * m]);
-                    out.entries.push_back(list[4 * m + 2]);
-                    out.entries.push_back(list[4 * m + 3]);
-                    out.entries.push_back(list[4 * m + 1] | (m + 1 == n ? kEntLast : 0u));
-                }
-                w = (kCellList << 30) | uint32_t(e0);
+                out.fine[size_t(blk * FF + uint64_t(f))] = w;
             }
-            out.fine[size_t(blk * FF + uint64_t(f))] = w;
         }
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; ++t)
+            pool.emplace_back(fill_cells, t);
+        fill_cells(0);
+        for (auto &th : pool)
+            th.join();
     }
     // sentinels: the kernels read entries up to four at a time, and load fine word 0
     // and edge 0 in place of a missing one
