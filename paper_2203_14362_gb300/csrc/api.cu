@@ -181,7 +181,7 @@ spx_status check_kernel_err(spx_ctx *ctx, cudaStream_t s)
 // Cover bitmap of a 2^g x 2^g grid of cell words: one bit per block of
 // cells of a 2^cg x 2^cg grid (cg = min(g, kCoverLog2)), set when any cell of
 // the block is not empty.
-std::vector<uint32_t> cover_bitmap(const std::vector<uint32_t> &cell, int g)
+std::vector<uint32_t> cover_bitmap(const uint32_t *cell, int g)
 {
     const int cg = std::min(g, kCoverLog2);
     std::vector<uint32_t> cover(std::max<size_t>((size_t(1) << (2 * cg)) / 32, 1), 0u);
@@ -356,7 +356,7 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, sb, threads, hi, err))
         return fail(ctx, SPX_EINVAL, "build_index: " + err);
     const int cg = std::min(g, kCoverLog2);
-    const std::vector<uint32_t> cover = cover_bitmap(hi.cell, g);
+    const std::vector<uint32_t> cover = cover_bitmap(hi.cell.data(), g);
     const size_t b_cell = hi.cell.size() * 4, b_fine = hi.fine.size() * 4, b_ent = hi.entries.size() * 4,
                  b_edge = hi.edges.size() * 4, b_cover = cover.size() * 4;
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
@@ -947,7 +947,7 @@ spx_status spx_build_disk_index(spx_ctx *ctx, const int32_t *cxy, const int32_t 
     if (!build_disk_index(cxy, r, Q, g, hd, err))
         return fail(ctx, SPX_EINVAL, "build_disk_index: " + err);
     const std::vector<int4> disks = disk_array(cxy, r, Q);
-    const std::vector<uint32_t> cover = cover_bitmap(hd.cell, g);
+    const std::vector<uint32_t> cover = cover_bitmap(hd.cell.data(), g);
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
     const size_t b_cell = hd.cell.size() * 4, b_ent = hd.entries.size() * 4, b_disk = disks.size() * sizeof(int4),
                  b_cover = cover.size() * 4;

@@ -515,15 +515,18 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
         return false;
     }
     out.n_blocks = n_blocks;
-    out.cell.assign(size_t(n_cells), 0);
-    out.fine.assign(size_t(n_blocks * FF), 0);
-    out.entries.assign(size_t(n_entries) * 4, 0);
+    // every word of these is written below (empty cells included)
+    out.cell.resize(size_t(n_cells));
+    out.fine.resize(size_t(n_blocks * FF));
+    out.entries.resize(size_t(n_entries) * 4);
     auto fill_cells = [&](int t) {
         std::vector<uint32_t> list;
         for (uint64_t c = c_lo[size_t(t)]; c < c_lo[size_t(t) + 1]; ++c) {
             const uint32_t b0 = cnt[c], b1 = cnt[c + 1];
-            if (b0 == b1)
+            if (b0 == b1) {
+                out.cell[c] = 0;
                 continue;
+            }
             if (b1 - b0 == 1 && !recs[b0].mixed) {
                 out.cell[c] = (kCellInsideOne << 30) | recs[b0].poly;
                 continue;

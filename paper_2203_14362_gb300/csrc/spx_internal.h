@@ -4,10 +4,40 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 namespace spx {
+
+// An allocator whose value-less construct leaves trivial elements
+// uninitialised: resize() of a large array then costs no zero fill, and its
+// pages are first touched by the (parallel) code that writes every element.
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = DefaultInitAlloc<U>;
+    };
+    DefaultInitAlloc() = default;
+    template <class U>
+    DefaultInitAlloc(const DefaultInitAlloc<U> &) noexcept {}
+    template <class U>
+    void construct(U *p) noexcept(std::is_nothrow_default_constructible<U>::value)
+    {
+        ::new (static_cast<void *>(p)) U;
+    }
+    template <class U, class... A>
+    void construct(U *p, A &&...a)
+    {
+        ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using BigVec = std::vector<T, DefaultInitAlloc<T>>;
 
 constexpr int kBoxLog2 = 30;            // points in [0, 2^30)^2, vertices in [0, 2^30]^2
 constexpr uint32_t kBox = 1u << kBoxLog2;
@@ -47,10 +77,10 @@ struct HostIndex {
     int grid_log2 = 0;
     int sub_log2 = 0;
     uint32_t n_polys = 0;
-    std::vector<uint32_t> cell;      // 4^g coarse words
-    std::vector<uint32_t> fine;      // n_blocks * 4^sub fine words
-    std::vector<uint32_t> entries;   // 4 words per entry
-    std::vector<int32_t> edges;      // 4 ints per edge
+    BigVec<uint32_t> cell;           // 4^g coarse words
+    BigVec<uint32_t> fine;           // n_blocks * 4^sub fine words
+    BigVec<uint32_t> entries;        // 4 words per entry
+    BigVec<int32_t> edges;           // 4 ints per edge
     uint64_t n_blocks = 0;
     uint64_t n_inside = 0;           // (coarse cell, polygon) pairs wholly inside
     uint64_t n_mixed = 0;            // (coarse cell, polygon) pairs split into fine cells
