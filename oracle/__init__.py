@@ -1,7 +1,7 @@
 """CPU oracle for the exact point-in-polygon join, selection and count.
 
 TEST INFRASTRUCTURE: only the test suite, the smoke check and the benchmark's
-CPU-baseline leg may import this package.  The library never calls it, and it
+CPU-baseline leg and reference arm may import this package.  The library never calls it, and it
 shares no code with the CUDA path.  The arithmetic lives in `pip_oracle.c`
 (plain C, exact int64); this module compiles it with gcc and marshals numpy
 arrays.  See the header of `pip_oracle.c` for the definition it computes

@@ -4,7 +4,7 @@
  * A plain, slow, obviously correct CPU oracle for SPADE's point-in-polygon
  * join, selection and count (§5.2 "Spatial Selection", "Spatial Joins",
  * "Spatial Aggregations").  Only the test suite, the smoke check and the
- * benchmark's CPU-baseline leg may load it.  It shares no code, header, table
+ * benchmark's CPU-baseline leg and reference arm may load it.  It shares no code, header, table
  * or helper with the CUDA library.
  *
  * What it computes (the definition; every faster method must reach exactly it):
