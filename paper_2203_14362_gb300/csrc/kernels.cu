@@ -1239,9 +1239,10 @@ __device__ __forceinline__ uint32_t disk_walk(const DiskView &d, int px, int py,
 // memory.  The queue carries over from chunk to chunk and the warp walks it
 // in full rounds of 32 (one chain of dependent loads per 32 list points); a
 // walked point adds its pairs to its own chunk's total (stored by lane 0
-// before any of the chunk's points is walked).  It stores a 4-byte result per point and a pair total per
-// 256-point chunk, and counts per disk (in shared memory when Q <=
-// kHistMax); pass 3 writes the pairs from the results.
+// before any of the chunk's points is walked; __syncwarp orders the two).
+// It stores a 4-byte result per point and a pair total per 256-point chunk,
+// and counts per disk (in shared memory when Q <= kHistMax); pass 3 writes
+// the pairs from the results.
 constexpr int kDiskMinBlocks = 4;
 constexpr uint32_t kDiskCoverWords = 1u << (2 * kCoverLog2 - 5); // cover bitmap in shared memory
 constexpr int kDQueue = kWChunk + 32; // a chunk's points plus a partial round
