@@ -581,8 +581,11 @@ spx_status spx_load_points(spx_ctx *ctx, const int32_t *xy, uint64_t n, int xy_i
         void *d = nullptr;
         if (cudaMalloc(&d, n ? n * 8 : 16) != cudaSuccess)
             return fail(ctx, SPX_ENOMEM, "load_points: cudaMalloc failed");
-        if (n)
-            SPX_CUDA(cudaMemcpy(d, xy, n * 8, cudaMemcpyHostToDevice), "load_points copy");
+        const cudaError_t e = n ? cudaMemcpy(d, xy, n * 8, cudaMemcpyHostToDevice) : cudaSuccess;
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(ctx, e, "load_points copy");
+        }
         p->dev = static_cast<int32_t *>(d);
         p->owned = true;
     }
