@@ -42,6 +42,7 @@ struct Req {
     // selection temporaries: pairs in point order + partition scratch
     void *tmp_mem = nullptr;
     size_t tmp_bytes = 0;
+    int readers = 0; // spx_server_read calls copying the outputs (release waits for none)
 };
 
 struct Slot {
@@ -624,11 +625,19 @@ spx_status spx_server_read(spx_server *srv, uint64_t req_id, void *a, uint64_t a
             return SPX_EINVAL;
         }
         fill_result(*it->second, &r);
+        it->second->readers++; // keeps release from freeing the outputs during the copy
     }
+    auto done_reading = [&]() {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto jt = srv->reqs.find(req_id);
+        if (jt != srv->reqs.end())
+            jt->second->readers--;
+    };
     const bool join = r.kind == SPX_REQ_JOIN;
     const uint64_t na = join ? r.total * 8 : r.total * 4;
     const uint64_t nb = join ? uint64_t(r.n_polys) * 8 : (uint64_t(r.n_polys) + 1) * 8;
     if ((a && a_bytes < na) || (b && b_bytes < nb)) {
+        done_reading();
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->err = "server: read buffer too small";
         return SPX_ECAPACITY;
@@ -642,6 +651,7 @@ spx_status spx_server_read(spx_server *srv, uint64_t req_id, void *a, uint64_t a
         e = cudaMemcpy(a, src_a, na, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && b && nb)
         e = cudaMemcpy(b, src_b, nb, cudaMemcpyDeviceToHost);
+    done_reading();
     if (e != cudaSuccess) {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->err = std::string("server: read copy failed: ") + cudaGetErrorString(e);
@@ -663,6 +673,10 @@ spx_status spx_server_release(spx_server *srv, uint64_t req_id)
     Req *r = it->second.get();
     if (r->status == SPX_EBUSY)
         return SPX_EBUSY;
+    if (r->readers > 0) {
+        srv->err = "server: a read of this request is in progress; release it after the read returns";
+        return SPX_EBUSY;
+    }
     pool_free(r->out_mem, srv->release_stream);
     pool_free(r->counts, srv->release_stream);
     srv->used -= r->out_bytes + r->counts_bytes;
