@@ -35,11 +35,12 @@ if ROOT not in sys.path:
 METRIC = "billion points joined/sec and % HBM roofline; serving p50/p99 ms vs plain kernel"
 UNIT = "Gpoints/s"
 L2_BYTES = 129 * 1024 * 1024
-# DRAM bytes (read + write) per point of the dominant kernel (join pass 1,
-# k_warp) from one ncu capture of a 20M-point run of the default workload,
-# scaled per point; only valid for that kernel version, the default index
-# (g = 11, sub = 3) and the default workload.
-RESOLVE_TRAFFIC_BYTES_PER_POINT = (298.491648e6 + 62.491904e6) / 20e6
+# DRAM bytes (read + write) per point of the polygon join's kernels from one
+# ncu capture of a 20M-point run of the default workload, scaled per point;
+# only valid for those kernel versions, the default index (g = 11, sub = 3)
+# and the default workload.  None: not captured for the current kernels.
+RESOLVE_TRAFFIC_BYTES_PER_POINT = {"k_resolve": (233.052672e6 + 55.362304e6) / 20e6,
+                                   "k_wemit": (80.704512e6 + 101.007616e6) / 20e6}
 # The same for the distance join's pass 1 (k_dwarp<resolve>), from one capture
 # of a 20M-point run of the 1024-disk workload at its default grid (g = 12).
 DISK_RESOLVE_TRAFFIC_BYTES_PER_POINT = (167.498496e6 + 25.302784e6) / 20e6
@@ -205,14 +206,14 @@ def sum_counts_over_ranks(counts, world: int):
     return counts
 
 
-def join_launches(n: int, plain: bool) -> int:
-    """Kernels one spx_join launches: pass 1, the scan (one kernel up to 32768
-    values, else three), pass 3 (256-point chunks; plain: 256-point blocks and
-    the one-block scan)."""
+def join_launches(n: int, plain: bool, dist: bool = False) -> int:
+    """Kernels one spx_join launches: pass 1 (two kernels; the distance join:
+    one), the scan (one kernel up to 32768 values, else three), pass 3
+    (256-point chunks; plain: 256-point blocks and the one-block scan)."""
     if plain:
         return 3
     chunks = (n + 255) // 256
-    return 2 + (1 if chunks <= 4 * 8192 else 3)
+    return (2 if dist else 3) + (1 if chunks <= 4 * 8192 else 3)
 
 
 def shard_start(rank: int, n_per_rank: int) -> int:
@@ -407,7 +408,8 @@ def run_spx(args, world, rank, local):
     ph_st = eng.stats(reset=True)
     eng.set_phase_timing(False)
     nt = max(ph_st["timed_joins"], 1)
-    phase_ms = {"resolve": ph_st["ms_resolve"] / nt, "scan": ph_st["ms_scan"] / nt, "emit": ph_st["ms_emit"] / nt}
+    phase_ms = {"resolve": ph_st["ms_resolve"] / nt, "walk": ph_st["ms_walk"] / nt, "scan": ph_st["ms_scan"] / nt,
+                "emit": ph_st["ms_emit"] / nt}
 
     # end to end through the C ABI on pinned host buffers (H2D points, join, D2H pairs + counts)
     e2e = None
@@ -437,15 +439,30 @@ def run_spx(args, world, rank, local):
     step_bytes = 8 * N + 8 * n_pairs + 8 * P + idx_bytes  # algorithmic bytes of one join
     peak, peak_kind = peaks()
     # dominant kernel: the resolve pass (reads every point once, writes the counts)
-    whole = args.plain
-    dom_ms = ms if whole else phase_ms["resolve"]
-    dom_bytes = step_bytes if whole else 8 * N + 8 * P + idx_bytes
+    # the dominant kernel: the longest pass of the step, with its algorithmic
+    # bytes (pass 1a / the distance join's pass 1: every point read once, the
+    # counts written, the index read once; pass 1b: the points it tests and
+    # their results; pass 3: 8 B per pair written)
+    if args.plain:
+        dom, dom_ms, dom_bytes = "plain join (3 kernels)", ms, step_bytes
+    else:
+        cand = {"resolve": (phase_ms["resolve"], 8 * N + 8 * P + idx_bytes),
+                "emit": (phase_ms["emit"], 8 * n_pairs)}
+        if not dist:  # pass 1b re-reads what pass 1a read: no algorithmic bytes of its own
+            cand["walk"] = (phase_ms["walk"], 0)
+        key = max(cand, key=lambda k: cand[k][0])
+        dom_ms, dom_bytes = cand[key]
+        names = {"resolve": "k_dwarp<resolve> (distance join pass 1)" if dist else "k_resolve (join pass 1a)",
+                 "walk": "k_walk (join pass 1b: exact tests)",
+                 "emit": "k_dwemit (distance join pass 3)" if dist else "k_wemit (join pass 3)"}
+        dom = names[key]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = args.traffic
-    if (traffic is None and RESOLVE_TRAFFIC_BYTES_PER_POINT and not args.plain and args.workload == "tess2000_100m"
+    if (traffic is None and not args.plain and not dist and args.workload == "tess2000_100m"
             and (info["grid_log2"], info["sub_log2"]) == (11, 3)):
-        traffic = RESOLVE_TRAFFIC_BYTES_PER_POINT * N
-    if traffic is None and args.workload == "dist1024_100m" and info["grid_log2"] == 12:
+        per_pt = RESOLVE_TRAFFIC_BYTES_PER_POINT.get(dom.split(" ")[0])
+        traffic = None if per_pt is None else per_pt * N
+    if traffic is None and dist and info["grid_log2"] == 12 and dom.startswith("k_dwarp"):
         traffic = DISK_RESOLVE_TRAFFIC_BYTES_PER_POINT * N
     out = None
     if rank == 0:
@@ -461,7 +478,8 @@ def run_spx(args, world, rank, local):
                 "vertices": 0 if dist else int(v.shape[0]), "pairs": int(n_pairs), "grid_log2": info["grid_log2"],
                 "sub_log2": info["sub_log2"], "fp32_filter": bool(args.fp32),
                 "kernel": ("distance join: resolve (k_dwarp) + scan + emit (k_dwemit)" if dist else
-                           "plain two-pass" if args.plain else "resolve (k_warp) + scan + emit (k_wemit): cached two-pass Map"),
+                           "plain two-pass" if args.plain else
+                           "resolve (k_resolve) + exact tests (k_walk) + scan + emit (k_wemit): cached two-pass Map"),
                 "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": int(info["device_bytes"]),
                 "index_build_on_device_ms": None if device_build_ms is None else round(device_build_ms, 2),
                 "l2": "inputs larger than L2 (points 8 B x N + pairs 8 B x N >> 129 MB); no flush",
@@ -472,8 +490,7 @@ def run_spx(args, world, rank, local):
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": ("k_dwarp<resolve> (distance join pass 1)" if dist else "plain join (3 kernels)"
-                                    if args.plain else "k_warp<resolve> (join pass 1)"),
+                         "kernel": dom,
                          "kernel_ms": dom_ms, "algorithmic_bytes_per_launch": int(dom_bytes),
                          "step": {"algorithmic_bytes": int(step_bytes), "ms": ms,
                                   "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
@@ -483,7 +500,7 @@ def run_spx(args, world, rank, local):
             "e2e": e2e,
             "step_ms": {"mean": ms, "best": min(per_step), "median": statistics.median(per_step),
                         "worst": max(per_step), "rank": 0},
-            "gpu_launches": args.steps * join_launches(N, args.plain),
+            "gpu_launches": args.steps * join_launches(N, args.plain, dist),
             "clocks": clk,
             "serving": serving,
         }

@@ -198,6 +198,10 @@ typedef struct {
     uint64_t n_edge_refs;    /* edges stored in per-fine-row edge lists */
     uint64_t device_bytes;   /* device memory held by the index */
     double build_ms;         /* host build + upload time */
+    double sum_resolved;     /* fraction of the coarse level's block summary (2^min(g,8) blocks per side)
+                                that is empty or INSIDE one polygon */
+    int use_sum;             /* 1: join pass 1a reads the block summary from shared memory */
+    int pad2;
 } spx_index_info;
 
 spx_status spx_index_info_get(spx_ctx *ctx, spx_index index, spx_index_info *out);
@@ -318,7 +322,9 @@ spx_status spx_join_plain(spx_ctx *ctx, spx_points points, spx_index index, uint
  *     results; serialise them.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: a device reset (cudaDeviceReset) between calls would leave it
+ *     stale, so do not reset a device while libspx is in use on it.
  *   - Asynchronous on `stream`; no host out-parameter (read *total_dev).
  */
 spx_status spx_join_plain_static(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev,
@@ -423,10 +429,12 @@ typedef struct {
     uint64_t pairs_emitted;
     uint64_t timed_joins;      /* joins timed since the last reset */
     uint64_t timed_aggregates; /* aggregates timed since the last reset */
-    double ms_resolve;         /* join pass 1: resolve every point (index lookups, exact tests, counts) */
+    double ms_resolve;         /* join pass 1 (distance join: all of it; polygon join: 1a, index lookups
+                                  of every point, results and counts of points that need no exact test) */
     double ms_scan;            /* join pass 2: scan of per-tile pair totals */
     double ms_emit;            /* join pass 3: pairs written in point order */
     double ms_aggregate;       /* count-only aggregate */
+    double ms_walk;            /* polygon join pass 1b: exact tests of the points whose cell lists edges */
 } spx_stats_t;
 
 /* Read (synchronising the device) and optionally reset the counters. */
@@ -534,15 +542,18 @@ spx_status spx_server_poll(spx_server *srv, uint64_t req_id, spx_result *out);
 spx_status spx_server_wait(spx_server *srv, uint64_t req_id, double timeout_ms, spx_result *out);
 
 /* Give back a finished request's device buffers (its result pointers become
- * invalid).  SPX_EBUSY while it is pending. */
+ * invalid).  SPX_EBUSY while it is pending, and while a spx_server_read of it
+ * runs on another thread (the buffers are freed only once no read copies
+ * them; call again after the read returns). */
 spx_status spx_server_release(spx_server *srv, uint64_t req_id);
 
 /* Copy a finished request's result to host memory (synchronous): a join's
  * pairs (8 * total bytes) to `a` and counts (8 * n_polys) to `b`; a selection's
  * ids (4 * total) to `a` and offsets (8 * (n_polys + 1)) to `b`.  a_bytes /
  * b_bytes are the buffers' sizes: SPX_ECAPACITY if one is too small, nothing
- * copied.  Either buffer may be NULL (skipped).  Must not run concurrently with
- * spx_server_release of the same request.  SPX_EBUSY while pending. */
+ * copied.  Either buffer may be NULL (skipped).  A release of the same
+ * request on another thread while the copy runs returns SPX_EBUSY and frees
+ * nothing.  SPX_EBUSY while pending. */
 spx_status spx_server_read(spx_server *srv, uint64_t req_id, void *a, uint64_t a_bytes, void *b, uint64_t b_bytes);
 
 spx_status spx_server_stats(spx_server *srv, spx_server_stats_t *out);

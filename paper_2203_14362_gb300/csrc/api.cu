@@ -29,6 +29,12 @@ namespace {
 
 enum : uint64_t { kTagPoints = 1, kTagPolys = 2, kTagIndex = 3 };
 constexpr int kTagShift = 56;
+// Least fraction of the block summary's blocks that must be resolved (empty or
+// INSIDE one polygon) for join pass 1a to read it.
+#ifndef SPX_SUM_MIN_RESOLVED
+#define SPX_SUM_MIN_RESOLVED 0.33
+#endif
+constexpr double kSumMinResolved = SPX_SUM_MIN_RESOLVED;
 
 struct PointsObj {
     int32_t *dev = nullptr;
@@ -92,9 +98,9 @@ struct spx_ctx {
     cudaStream_t capture_stream = nullptr;
     // phase timing
     bool timing = false;
-    cudaEvent_t ev[4] = {};
+    cudaEvent_t ev[5] = {};
     uint64_t timed_joins = 0, timed_aggs = 0;
-    double ms_resolve = 0, ms_scan = 0, ms_emit = 0, ms_agg = 0;
+    double ms_resolve = 0, ms_walk = 0, ms_scan = 0, ms_emit = 0, ms_agg = 0;
 };
 
 namespace {
@@ -194,17 +200,47 @@ std::vector<uint32_t> cover_bitmap(const uint32_t *cell, int g)
     return cover;
 }
 
-// Adds the phases of the join just launched (events ev[0..3]) to the totals.
-spx_status add_phase_times(spx_ctx *ctx)
+// Block summary of a 2^g x 2^g grid of coarse words on a 2^sg x 2^sg grid
+// (sg = min(g, kSumLog2)): per block kSumEmpty when every cell is empty, q
+// when every cell is INSIDE exactly polygon q (q < kSumEmpty), else
+// kSumMixed.  *resolved: the fraction of blocks that are not mixed.
+std::vector<uint16_t> block_summary(const uint32_t *cell, int g, double *resolved)
 {
-    SPX_CUDA(cudaEventSynchronize(ctx->ev[3]), "join timing");
-    float t1 = 0, t2 = 0, t3 = 0;
-    cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
-    cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
-    cudaEventElapsedTime(&t3, ctx->ev[2], ctx->ev[3]);
-    ctx->ms_resolve += t1;
-    ctx->ms_scan += t2;
-    ctx->ms_emit += t3;
+    const int sg = std::min(g, kSumLog2), sh = g - sg;
+    const uint32_t nb = 1u << sg;
+    std::vector<uint16_t> sum(size_t(nb) * nb);
+    uint64_t n_res = 0;
+    for (uint32_t by = 0; by < nb; ++by)
+        for (uint32_t bx = 0; bx < nb; ++bx) {
+            const uint32_t w0 = cell[(size_t(by << sh) << g) | (bx << sh)];
+            bool same = (w0 >> 30) == kCellEmpty || ((w0 >> 30) == kCellInsideOne && (w0 & kPayloadMask) < kSumEmpty);
+            for (uint32_t cy = by << sh; same && cy < ((by + 1) << sh); ++cy)
+                for (uint32_t cx = bx << sh; same && cx < ((bx + 1) << sh); ++cx)
+                    same = cell[(size_t(cy) << g) | cx] == w0;
+            const uint16_t v = !same ? uint16_t(kSumMixed)
+                                     : (w0 >> 30) == kCellEmpty ? uint16_t(kSumEmpty) : uint16_t(w0 & kPayloadMask);
+            sum[size_t(by) * nb + bx] = v;
+            n_res += same ? 1 : 0;
+        }
+    *resolved = double(n_res) / double(sum.size());
+    return sum;
+}
+
+// Adds the phases of the join just launched to the totals: a polygon join
+// recorded five events (pass 1a, pass 1b, scan, emit), a distance join four
+// (pass 1, scan, emit).
+spx_status add_phase_times(spx_ctx *ctx, bool polygons)
+{
+    const int last = polygons ? 4 : 3;
+    SPX_CUDA(cudaEventSynchronize(ctx->ev[last]), "join timing");
+    float t[4] = {0, 0, 0, 0};
+    for (int k = 0; k < last; ++k)
+        cudaEventElapsedTime(&t[k], ctx->ev[k], ctx->ev[k + 1]);
+    ctx->ms_resolve += t[0];
+    if (polygons)
+        ctx->ms_walk += t[1];
+    ctx->ms_scan += t[last - 2];
+    ctx->ms_emit += t[last - 1];
     ctx->timed_joins++;
     return SPX_OK;
 }
@@ -235,7 +271,7 @@ spx_status disk_join_common(spx_ctx *ctx, PointsObj *pts, IndexObj *ix, uint32_t
     cudaError_t e = launch_disk_join(a, ctx->scratch, s, timed ? ctx->ev : nullptr);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "join launch");
-    if (timed && pts->n && (st = add_phase_times(ctx)) != SPX_OK)
+    if (timed && pts->n && (st = add_phase_times(ctx, false)) != SPX_OK)
         return st;
     if (n_pairs) {
         if ((st = check_kernel_err(ctx, s)) != SPX_OK)
@@ -290,7 +326,7 @@ spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_
     cudaError_t e = plain ? launch_join_plain(a, ctx->scratch, s) : launch_join(a, ctx->scratch, s, timed ? ctx->ev : nullptr);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "join launch");
-    if (timed && pts->n && (st = add_phase_times(ctx)) != SPX_OK)
+    if (timed && pts->n && (st = add_phase_times(ctx, true)) != SPX_OK)
         return st;
     if (n_pairs) {
         st = check_kernel_err(ctx, s);
@@ -357,10 +393,12 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
         return fail(ctx, SPX_EINVAL, "build_index: " + err);
     const int cg = std::min(g, kCoverLog2);
     const std::vector<uint32_t> cover = cover_bitmap(hi.cell.data(), g);
+    double sum_resolved = 0;
+    const std::vector<uint16_t> sum = block_summary(hi.cell.data(), g, &sum_resolved);
     const size_t b_cell = hi.cell.size() * 4, b_fine = hi.fine.size() * 4, b_ent = hi.entries.size() * 4,
-                 b_edge = hi.edges.size() * 4, b_cover = cover.size() * 4;
+                 b_edge = hi.edges.size() * 4, b_cover = cover.size() * 4, b_sum = std::max<size_t>(sum.size() * 2, 16);
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-    const size_t total = up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + up(b_cover) + 256;
+    const size_t total = up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + up(b_cover) + up(b_sum) + 256;
     if (total > max_bytes) {
         *out = 0;
         return SPX_OK;
@@ -370,10 +408,12 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
         return fail(ctx, SPX_ENOMEM, "build_index: cudaMalloc of " + std::to_string(total) + " bytes failed");
     char *m = static_cast<char *>(ix->mem);
     char *p_cell = m, *p_fine = p_cell + up(b_cell), *p_ent = p_fine + up(b_fine), *p_edge = p_ent + up(b_ent),
-         *p_cover = p_edge + up(b_edge);
+         *p_cover = p_edge + up(b_edge), *p_sum = p_cover + up(b_cover);
     cudaError_t e = cudaMemcpy(p_cell, hi.cell.data(), b_cell, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(p_cover, cover.data(), b_cover, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p_sum, sum.data(), sum.size() * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && b_fine)
         e = cudaMemcpy(p_fine, hi.fine.data(), b_fine, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && b_ent)
@@ -398,6 +438,12 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     ix->view.cover = reinterpret_cast<const uint32_t *>(p_cover);
     ix->view.scv = kBoxLog2 - cg;
     ix->view.cg = cg;
+    ix->view.sum = reinterpret_cast<const uint4 *>(p_sum);
+    ix->view.sg = std::min(g, kSumLog2);
+    ix->view.ssh = kBoxLog2 - ix->view.sg;
+    // the summary costs pass 1a three quarters of its warps per SM (one CTA
+    // holds it); worth it when it answers a third of the box or more
+    ix->view.use_sum = sum_resolved >= kSumMinResolved ? 1 : 0;
     spx_index_info &inf = ix->info;
     inf.grid_log2 = g;
     inf.sub_log2 = sb;
@@ -411,6 +457,8 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     inf.n_edge_refs = hi.edges.size() / 4;
     inf.device_bytes = total;
     inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    inf.sum_resolved = sum_resolved;
+    inf.use_sum = ix->view.use_sum;
     pg->n_index++;
     const uint64_t h = make_handle(ctx, kTagIndex);
     ctx->indexes[h] = std::move(ix);
@@ -1643,10 +1691,11 @@ spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset)
     out->ms_scan = ctx->ms_scan;
     out->ms_emit = ctx->ms_emit;
     out->ms_aggregate = ctx->ms_agg;
+    out->ms_walk = ctx->ms_walk;
     if (reset) {
         SPX_CUDA(cudaMemset(ctx->aux->stats, 0, sizeof(v)), "stats reset");
         ctx->timed_joins = ctx->timed_aggs = 0;
-        ctx->ms_resolve = ctx->ms_scan = ctx->ms_emit = ctx->ms_agg = 0;
+        ctx->ms_resolve = ctx->ms_walk = ctx->ms_scan = ctx->ms_emit = ctx->ms_agg = 0;
     }
     return check_kernel_err(ctx, nullptr);
 }

@@ -97,8 +97,61 @@ __device__ __forceinline__ int4 ld_idx(const int4 *p, uint64_t pol)
                  : "l"(p), "l"(pol));
     return v;
 }
-// 1-D bulk copy global -> shared (TMA), completion counted on `bar`.
-// dst, src 16-byte aligned; bytes a multiple of 16.
+// Bulk prefetch of `bytes` (a multiple of 16) at p (16-byte aligned) into L2
+// by the TMA engine: one instruction, no registers, nothing to wait for.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// mbarrier and 1-D TMA bulk copy (global -> shared) for a warp's own staging
+// buffer.  The barrier counts one arrival (the expect_tx of the issuing lane)
+// plus the bytes the copy delivers.
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// dst, src 16-byte aligned; bytes a multiple of 16.  The generic-proxy reads
+// of dst that came before are ordered before the copy's writes.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Waits for the phase of `bar` with the given parity to complete, at most
+// max_tries polls (each may suspend the thread for a short time); false if it
+// gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t max_tries)
+{
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t t = 0; t < max_tries; ++t) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+constexpr uint32_t kWaitTries = 1u << 22; // polls of a bounded wait before it reports kErrTimeout
+// Prefetch of the line holding p into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 // ------------------------------------------------------------- the predicate
 // sign of d = (bx-ax)(py-ay) - (by-ay)(px-ax)
 template <bool FP32>
@@ -119,21 +172,21 @@ __device__ __forceinline__ int orient_sign(int ax, int ay, int bx, int by, int p
 }
 
 // Parity of the crossings of the rightward ray from (px, py) with a fine-row
-// edge list sorted by max x descending.  Edges are loaded four at a time so
-// a list costs one L2 round trip per four edges.
-template <bool FP32>
+// edge list sorted by max x descending.  Edges are loaded RW at a time so a
+// list costs one L2 round trip per RW edges.
+template <bool FP32, int RW = 4>
 __device__ __forceinline__ uint32_t row_parity(const int4 *__restrict__ e, uint32_t n, int px, int py,
                                                uint32_t &tests, uint32_t &esc, uint64_t pol)
 {
     uint32_t par = 0;
-    for (uint32_t k = 0; k < n; k += 4) {
-        int4 v[4];
+    for (uint32_t k = 0; k < n; k += RW) {
+        int4 v[RW];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < RW; ++j)
             v[j] = (k + j < n) ? ld_idx(e + k + j, pol) : make_int4(INT_MIN, 0, INT_MIN, 0);
         bool stop = false;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RW; ++j) {
             if (stop || max(v[j].x, v[j].z) <= px) {
                 stop = true; // this and every later edge ends left of p: no crossing right of p
                 continue;
@@ -267,7 +320,7 @@ __device__ __forceinline__ void point_emit(const IndexView &ix, int px, int py, 
 // arrays (both end with a sentinel), and selects the results; divergent lanes
 // of a warp would otherwise serialise their memory round trips.  Longer lists
 // finish in a loop.
-template <bool FP32>
+template <bool FP32, int RW = 4>
 __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, int px, int py, uint32_t &first,
                                               uint32_t &tests, uint32_t &esc, uint64_t pol)
 {
@@ -292,9 +345,9 @@ __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, 
     }
     // lists longer than four edges: the rest, in row order
     if ((en0.w & kEntBoundary) && en0.z > 4 && max(v0[3].x, v0[3].z) > px)
-        p0 ^= row_parity<FP32>(ix.edge + en0.y + 4, en0.z - 4, px, py, tests, esc, pol);
+        p0 ^= row_parity<FP32, RW>(ix.edge + en0.y + 4, en0.z - 4, px, py, tests, esc, pol);
     if (two && (en1.w & kEntBoundary) && en1.z > 4 && max(v1[3].x, v1[3].z) > px)
-        p1 ^= row_parity<FP32>(ix.edge + en1.y + 4, en1.z - 4, px, py, tests, esc, pol);
+        p1 ^= row_parity<FP32, RW>(ix.edge + en1.y + 4, en1.z - 4, px, py, tests, esc, pol);
     const uint32_t in0 = (en0.w & kEntBoundary) ? p0 : 1u;
     const uint32_t in1 = two ? ((en1.w & kEntBoundary) ? p1 : 1u) : 0u;
     uint32_t c = in0 + in1;
@@ -540,20 +593,17 @@ __device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
     return v;
 }
 
-// ---------------------------------------------- warp-independent pass 1
-// Pass 1 of the join (the counting pass of the two-pass Map, §5.1; with
-// RESOLVE it also stores every point's 4-byte result: none / its polygon /
-// "several" with their count) and, without RESOLVE, the count-only
-// aggregation that never materialises the join (§5.2).  No CTA barrier in
-// its loop: every warp works alone on chunks of 32 x kWItems consecutive points (chunk c goes to
-// warp c mod #warps), loads its points with coalesced 8-byte loads, resolves
-// the coarse and fine words of all of a lane's points with independent
-// loads, and queues its list points in a per-warp shared-memory queue that it
-// walks 32 at a time once the whole chunk is resolved (the chunk's points and
-// words are dead by then, which keeps the kernel at 64 registers and 4 CTAs
-// per SM).  A warp never waits for another warp, so a slow walk or an index
-// miss only stalls its own warp.  With RESOLVE, every chunk's pair total is stored for
-// the scan, and k_wemit writes the pairs chunk by chunk.
+// ---------------------------------------------- count-only aggregate
+// The count-only aggregation that never materialises the join (§5.2 "Spatial
+// Aggregations").  No CTA barrier in its loop: every warp works alone on
+// chunks of 32 x kWItems consecutive points (chunk c goes to warp c mod
+// #warps), loads its points with coalesced 8-byte loads, resolves the coarse
+// and fine words of all of a lane's points with independent loads, and queues
+// its list points in a per-warp shared-memory queue that it walks 32 at a time
+// once the whole chunk is resolved (the chunk's points and words are dead by
+// then, which keeps the kernel at 64 registers and 4 CTAs per SM).  A warp
+// never waits for another warp, so a slow walk or an index miss only stalls
+// its own warp.  The chunks (256 points) are those of the join's passes.
 #ifndef SPX_WARP_ITEMS
 #define SPX_WARP_ITEMS 8
 #endif
@@ -565,7 +615,7 @@ constexpr int kWChunk = 32 * kWItems;   // consecutive points per warp chunk
 constexpr int kWQueue = kWChunk;        // list points queued per warp: a whole chunk
 constexpr size_t kWarpSmem = size_t(kWarps) * kWQueue * sizeof(uint4);
 
-template <bool FP32, bool RESOLVE, bool CLUSTERED>
+template <bool FP32, bool CLUSTERED>
 __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaunch a, uint32_t nchunks, int use_hist)
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -635,8 +685,6 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
                     else
                         atomicAdd(a.counts + q, 1ull);
                 });
-            if (RESOLVE && has)
-                __stcg(a.res + base + it.w, res_encode(c, f));
             __syncwarp();
         };
 #pragma unroll
@@ -645,8 +693,6 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
             const bool one = kind == kCellInsideOne, lst = kind == kCellList;
             total += one ? 1u : 0u;
             count1(one, w[j] & kPayloadMask);
-            if (RESOLVE && loc < npts && !lst)
-                __stcg(a.res + base + loc, one ? (w[j] & kPayloadMask) : kResNone);
             const uint32_t bl = __ballot_sync(kFull, lst);
             if (lst)
                 s_q[qn + __popc(bl & lanemask_lt())] =
@@ -656,9 +702,6 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
         for (uint32_t k0 = 0; k0 < qn; k0 += 32)
             walk(k0, min(qn - k0, 32u));
         n_pairs += total;
-        total = warp_sum32(total);
-        if (RESOLVE && lane == 0)
-            a.tile_tot[ch] = total; // per-chunk pair total, scanned into offsets
     }
     if (hist) {
         __syncthreads();
@@ -667,6 +710,292 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
                 atomicAdd(a.counts + i, (unsigned long long)s_hist[i]);
     }
     add_stats(a.stats, n_pts, n_tests, n_esc, n_pairs);
+}
+
+// ---------------------------------------------- join pass 1 as two kernels
+// Pass 1a (k_resolve) is the streaming half of the first pass of the Map:
+// every warp takes its own 256-point chunks (chunk c goes to warp c mod
+// #warps), loads the points with coalesced 8-byte loads, reads the coarse
+// word of every point and, in mixed coarse cells, the fine word, all with
+// independent loads, and stores each point's result at once: none, its one
+// INSIDE polygon (counted here: §4.3, interior pixels need no test), or, for
+// a point whose fine cell holds an entry list, the list's first entry.  Those
+// points need the exact boundary test.  Pass 1a marks them in a bitmap over
+// the rows: the ballot of the list points of a round of 32 rows is the
+// bitmap word of those rows.  It stores each chunk's pair total without
+// them.  With no walk in it, the kernel is a short stream of independent
+// loads and stores that keeps many warps per SM busy.
+//
+// Pass 1b (k_walk) runs the exact tests of the marked rows (§4.3 boundary
+// index): every warp takes a contiguous range of bitmap words, a lane per
+// word, gathers the marked rows into its shared-memory queue and walks them
+// in full rounds of 32, one row per lane (the point and its stored first
+// entry, two independent loads, then the entry list).  It rewrites the row's
+// result, adds the row's pairs to its chunk's total and counts them.
+#ifndef SPX_RESOLVE_MIN_BLOCKS
+#define SPX_RESOLVE_MIN_BLOCKS 8
+#endif
+constexpr int kResolveMinBlocks = SPX_RESOLVE_MIN_BLOCKS;
+#ifndef SPX_WALK_MIN_BLOCKS
+#define SPX_WALK_MIN_BLOCKS 3
+#endif
+constexpr int kWalkMinBlocks = SPX_WALK_MIN_BLOCKS;
+constexpr int kWalkQueue = 64; // < 32 rows carried over + one gather step of 32
+#ifndef SPX_WALK_BATCH
+#define SPX_WALK_BATCH 4
+#endif
+constexpr int kWalkBatch = SPX_WALK_BATCH;
+#ifndef SPX_WALK_RANGE
+#define SPX_WALK_RANGE 512
+#endif
+constexpr int kWalkRange = SPX_WALK_RANGE; // bitmap words (of 32 rows) per warp of pass 1b
+static_assert(kWalkRange % (32 * SPX_WALK_BATCH) == 0, "a warp's range is whole steps");
+#ifndef SPX_WALK_EDGES
+#define SPX_WALK_EDGES 4
+#endif
+constexpr int kWalkEdges = SPX_WALK_EDGES; // edges loaded per round trip past an entry's first four
+
+// With the block summary (SUM), a CTA of 1024 threads (one per SM) first
+// copies the summary into shared memory; a point whose block is empty or
+// INSIDE one polygon is resolved there and reads no index word.  Random
+// 4-byte index loads are what bounds this pass (every lane's word lies in
+// another cache line, and the L1 looks up one line at a time), and a
+// shared-memory lookup costs a fraction of one.
+constexpr int kResolveSumThreads = 1024;
+#ifndef SPX_PREFETCH_CHUNKS
+#define SPX_PREFETCH_CHUNKS 1
+#endif
+constexpr int kPrefetchChunks = SPX_PREFETCH_CHUNKS; // L2 prefetch distance of pass 1a, in a warp's chunks
+#ifndef SPX_TMA_POINTS
+#define SPX_TMA_POINTS 1
+#endif
+constexpr bool kTmaPoints = SPX_TMA_POINTS != 0; // pass 1a stages points with bulk copies when they fit
+
+// Shared memory of pass 1a: [summary][TMA: per warp a chunk buffer, then per
+// warp an mbarrier][counters].
+__host__ __device__ constexpr size_t resolve_smem_head(int warps, bool sum, int sg, bool tma)
+{
+    return (sum ? ((size_t(2) << (2 * sg)) + 15) & ~size_t(15) : 0) +
+           (tma ? size_t(warps) * (kWChunk * sizeof(int2) + sizeof(uint64_t)) : 0);
+}
+
+// With TMA, every warp stages its next chunk's points in its own shared-memory
+// buffer with one bulk copy, issued as soon as it has read the current chunk
+// from there: the points arrive while the chunk is resolved, and their loads
+// cost the L1 nothing.  A warp's last chunk, when it is not full, is loaded
+// with plain loads.
+template <int THREADS, bool SUM, bool TMA>
+__global__ void __launch_bounds__(THREADS, SUM ? 1 : (TMA ? 6 : kResolveMinBlocks))
+    k_resolve(const __grid_constant__ JoinLaunch a, uint32_t *pend, uint32_t nchunks, int use_hist)
+{
+    constexpr int WARPS = THREADS / 32;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const IndexView &ix = a.ix;
+    const uint32_t sum_words = SUM ? (1u << (2 * ix.sg)) : 0u; // 16-bit words
+    const uint16_t *s_sum = reinterpret_cast<const uint16_t *>(s_raw);
+    const size_t sum_bytes = SUM ? ((size_t(sum_words) * 2 + 15) & ~size_t(15)) : 0;
+    int2 *s_buf = reinterpret_cast<int2 *>(s_raw + sum_bytes) + (size_t)(threadIdx.x >> 5) * kWChunk;
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(s_raw + sum_bytes + size_t(WARPS) * kWChunk * sizeof(int2)) +
+                      (threadIdx.x >> 5);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_raw + resolve_smem_head(WARPS, SUM, SUM ? ix.sg : 0, TMA));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t keep = policy_evict_last();
+    const bool hist = use_hist && a.counts;
+    const uint32_t nw = gridDim.x * WARPS;
+    auto full = [&](uint32_t c) { return (uint64_t)(c + 1) * kWChunk <= a.n; };
+    if constexpr (SUM) {
+        uint4 *d = reinterpret_cast<uint4 *>(s_raw);
+        for (uint32_t i = threadIdx.x; i < (sum_words + 7) / 8; i += THREADS)
+            d[i] = ld_idx(ix.sum + i, keep);
+    }
+    if constexpr (TMA) {
+        const uint32_t c0 = blockIdx.x * WARPS + warp;
+        if (lane == 0) {
+            mbar_init(s_bar, 1);
+            if (c0 < nchunks && full(c0))
+                bulk_load(s_buf, a.pts + (uint64_t)c0 * kWChunk, kWChunk * sizeof(int2), s_bar);
+        }
+    }
+    if (hist)
+        for (uint32_t i = threadIdx.x; i < ix.P; i += THREADS)
+            s_hist[i] = 0;
+    __syncthreads();
+    uint32_t n_pts = 0, n_pairs = 0, phase = 0;
+    for (uint32_t ch = blockIdx.x * WARPS + warp; ch < nchunks; ch += nw) {
+        const uint64_t base = (uint64_t)ch * kWChunk;
+        const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
+        const int2 *pts = a.pts + base;
+        uint32_t *res = a.res + base;
+        int2 p[kWItems];
+        uint32_t w[kWItems];
+        if (TMA && npts == kWChunk) {
+            if (!mbar_wait(s_bar, phase, kWaitTries)) {
+                // the copy did not arrive: report it, give it one more bounded wait, stop
+                if (lane == 0)
+                    atomicOr(a.err, kErrTimeout);
+                mbar_wait(s_bar, phase, kWaitTries);
+                break;
+            }
+            phase ^= 1u;
+#pragma unroll
+            for (int j = 0; j < kWItems; ++j)
+                p[j] = s_buf[j * 32 + lane];
+            __syncwarp();
+            const uint32_t nx = ch + nw;
+            if (lane == 0 && nx < nchunks && full(nx))
+                bulk_load(s_buf, a.pts + (uint64_t)nx * kWChunk, kWChunk * sizeof(int2), s_bar);
+        } else {
+            if (kPrefetchChunks > 0 && lane == 0) {
+                // this warp's chunk kPrefetchChunks ahead goes to L2 while this one is resolved
+                const uint64_t nb = base + (uint64_t)kPrefetchChunks * nw * kWChunk;
+                if (nb + kWChunk <= a.n)
+                    prefetch_l2_bulk(a.pts + nb, kWChunk * sizeof(int2));
+            }
+#pragma unroll
+            for (int j = 0; j < kWItems; ++j) {
+                const uint32_t loc = j * 32 + lane;
+                p[j] = loc < npts ? __ldcs(pts + loc) : make_int2(-1, -1);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            // x, y >= 0 and both < 2^30 iff their bitwise or is below 2^30
+            const bool ok = (uint32_t)(p[j].x | p[j].y) < kBox;
+            const uint32_t px = ok ? (uint32_t)p[j].x : 0u, py = ok ? (uint32_t)p[j].y : 0u;
+            bool look = ok;
+            if (SUM) {
+                const uint32_t sv = s_sum[((py >> ix.ssh) << ix.sg) | (px >> ix.ssh)];
+                look = ok && sv == kSumMixed;
+                w[j] = !ok || sv == kSumEmpty ? 0u : (kCellInsideOne << 30) | sv;
+            }
+            if (look)
+                w[j] = coarse_word(ix, px, py, keep);
+            else if (!SUM)
+                w[j] = 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j)
+            if ((w[j] >> 30) == kCellSub)
+                w[j] = fine_word(ix, w[j], (uint32_t)p[j].x, (uint32_t)p[j].y, keep);
+        uint32_t total = 0, mask = 0;
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t kind = w[j] >> 30, loc = j * 32 + lane, pay = w[j] & kPayloadMask;
+            const bool one = kind == kCellInsideOne;
+            total += one ? 1u : 0u;
+            if (a.counts) {
+                if (!hist)
+                    global_add_warp(a.counts, one, pay);
+                else if (one)
+                    atomicAdd(s_hist + pay, 1u);
+            }
+            // one: the polygon; list: its first entry (rewritten by pass 1b); empty: none
+            if (loc < npts)
+                __stcg(res + loc, kind == kCellEmpty ? kResNone : pay);
+            const uint32_t bl = __ballot_sync(kFull, kind == kCellList);
+            mask = lane == j ? bl : mask;
+        }
+        if (lane < kWItems)
+            __stcg(pend + (uint64_t)ch * kWItems + lane, mask);
+        n_pts += lane == 0 ? npts : 0u;
+        n_pairs += total;
+        total = warp_sum32(total);
+        if (lane == 0)
+            a.tile_tot[ch] = total; // the chunk's total without its list points; pass 1b adds theirs
+    }
+    if (hist) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < ix.P; i += THREADS)
+            if (s_hist[i])
+                atomicAdd(a.counts + i, (unsigned long long)s_hist[i]);
+    }
+    add_stats(a.stats, n_pts, 0u, 0u, n_pairs);
+}
+
+template <bool FP32>
+__global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a, const uint32_t *pend, uint32_t nwords)
+{
+    __shared__ uint32_t s_qa[kWarps * kWalkQueue];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *s_q = s_qa + warp * kWalkQueue; // rows
+    const IndexView &ix = a.ix;
+    const uint64_t keep = policy_evict_last();
+    uint32_t n_tests = 0, n_esc = 0, n_pairs = 0;
+    // walk the queued rows [0, m), m <= 32, one per lane
+    auto walk = [&](uint32_t m) {
+        __syncwarp();
+        const bool has = (uint32_t)lane < m;
+        const uint32_t row = s_q[has ? lane : 0]; // idle lanes repeat lane 0's walk, uncounted
+        const int2 p = a.pts[row];
+        const uint32_t e0 = __ldcg(a.res + row);
+        uint32_t f = 0, t_l = 0, e_l = 0;
+        uint32_t c = walk_list<FP32, kWalkEdges>(ix, e0, p.x, p.y, f, t_l, e_l, keep);
+        c = has ? c : 0u;
+        n_tests += has ? t_l : 0u;
+        n_esc += has ? e_l : 0u;
+        n_pairs += c;
+        if (a.counts) {
+            global_add_warp(a.counts, c == 1, f);
+            if (c > 1)
+                point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(a.counts + q, 1ull); });
+        }
+        if (has) {
+            __stcg(a.res + row, res_encode(c, f));
+            if (c)
+                atomicAdd(a.tile_tot + row / kWChunk, (unsigned long long)c);
+        }
+        __syncwarp(); // the queue is rewritten after the round
+    };
+    constexpr int B = kWalkBatch; // bitmap words per lane per step, the next step's loaded ahead
+    const uint64_t w0 = ((uint64_t)blockIdx.x * kWarps + warp) * kWalkRange;
+    const uint64_t w1 = min((uint64_t)nwords, w0 + kWalkRange);
+    uint32_t qn = 0;
+    uint32_t nxt[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+        nxt[k] = w0 + k * 32 + lane < w1 ? __ldcs(pend + w0 + k * 32 + lane) : 0u;
+    for (uint64_t wb = w0; wb < w1; wb += 32 * B) {
+        uint32_t cur[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            cur[k] = nxt[k];
+            const uint64_t wn = wb + 32 * B + k * 32 + lane;
+            nxt[k] = wn < w1 ? __ldcs(pend + wn) : 0u;
+        }
+#pragma unroll 1
+        for (int k = 0; k < B; ++k) { // not unrolled: one copy of the walk
+            const uint64_t wi = wb + k * 32 + lane;
+            uint32_t m = cur[0];
+#pragma unroll
+            for (int t = 0; t + 1 < B; ++t)
+                cur[t] = cur[t + 1];
+            while (__any_sync(kFull, m != 0)) {
+                const bool has = m != 0;
+                const uint32_t b = (uint32_t)__ffs(m) - 1u;
+                m &= m - 1u;
+                const uint32_t bl = __ballot_sync(kFull, has);
+                if (has) {
+                    const uint32_t row = (uint32_t)(wi * 32 + b);
+                    s_q[qn + __popc(bl & lanemask_lt())] = row;
+                    prefetch_l2(a.pts + row); // loaded when its round is walked
+                }
+                qn += __popc(bl);
+                if (qn >= 32) {
+                    walk(32);
+                    const uint32_t rem = qn - 32; // move the rest (< 32) to the front
+                    const uint32_t it = (uint32_t)lane < rem ? s_q[32 + lane] : 0u;
+                    __syncwarp();
+                    if ((uint32_t)lane < rem)
+                        s_q[lane] = it;
+                    qn = rem;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    if (qn)
+        walk(qn);
+    add_stats(a.stats, 0u, n_tests, n_esc, n_pairs);
 }
 
 // Pass 3 of the join with warp chunks: every warp writes the pairs of its
@@ -1125,7 +1454,7 @@ int persistent_grid(K kernel, int threads, size_t smem, uint32_t ntiles)
     return grid;
 }
 
-template <bool FP32, bool RESOLVE, bool CLUSTERED = false>
+template <bool FP32, bool CLUSTERED>
 cudaError_t launch_warp_kernel(const JoinLaunch &a, int use_hist, cudaStream_t s)
 {
     static bool done[64] = {};
@@ -1133,12 +1462,64 @@ cudaError_t launch_warp_kernel(const JoinLaunch &a, int use_hist, cudaStream_t s
     if (nchunks >= (1ull << 32))
         return cudaErrorInvalidValue;
     const size_t smem = kWarpSmem + (use_hist ? sizeof(uint32_t) * a.ix.P : 0);
-    auto kern = k_warp<FP32, RESOLVE, CLUSTERED>;
+    auto kern = k_warp<FP32, CLUSTERED>;
     cudaError_t e = smem_opt_in(kern, kWarpSmem + sizeof(uint32_t) * kHistMax, done);
     if (e != cudaSuccess)
         return e;
     const uint32_t nblk = uint32_t((nchunks + kWarps - 1) / kWarps);
     kern<<<persistent_grid(kern, kThreads, smem, nblk), kThreads, smem, s>>>(a, uint32_t(nchunks), use_hist);
+    return cudaGetLastError();
+}
+
+// Pass 1 of the join (1a resolve, 1b walk).  pend: 8 words per chunk (the
+// bitmap of the rows pass 1b tests).  mid (or null): an event recorded between
+// the two kernels.
+template <bool FP32>
+cudaError_t launch_pass1(const JoinLaunch &a, uint32_t *pend, cudaStream_t s, cudaEvent_t mid)
+{
+    static bool done_r[4][64] = {};
+    const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
+    if (a.n >= (1ull << 32))
+        return cudaErrorInvalidValue; // rows are 32-bit
+    const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
+    const size_t hsm = use_hist ? sizeof(uint32_t) * a.ix.P : 0;
+    cudaError_t e;
+    if (reinterpret_cast<uintptr_t>(a.pts) & 15)
+        return cudaErrorMisalignedAddress; // bulk copies of whole chunks start 16-byte aligned
+    // the largest shared memory a CTA may take
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    auto launch = [&](auto kr, int threads, size_t head, bool (&done)[64]) -> cudaError_t {
+        const size_t smem = head + hsm;
+        cudaError_t err = smem_opt_in(kr, std::min<size_t>(size_t(smem_max), head + sizeof(uint32_t) * kHistMax), done);
+        if (err != cudaSuccess)
+            return err;
+        const uint32_t nblk = uint32_t((nchunks + threads / 32 - 1) / (threads / 32));
+        kr<<<persistent_grid(kr, threads, smem, nblk), threads, smem, s>>>(a, pend, uint32_t(nchunks), use_hist);
+        return cudaGetLastError();
+    };
+    constexpr int WS = kResolveSumThreads / 32;
+    if (a.ix.use_sum) {
+        // beside the summary, shared memory holds one chunk buffer per warp
+        // at most, too shallow to hide a bulk copy: L2 prefetches instead
+        e = launch(k_resolve<kResolveSumThreads, true, false>, kResolveSumThreads,
+                   resolve_smem_head(WS, true, a.ix.sg, false), done_r[2]);
+    } else {
+        if (kTmaPoints)
+            e = launch(k_resolve<kThreads, false, true>, kThreads, resolve_smem_head(kWarps, false, 0, true),
+                       done_r[3]);
+        else
+            e = launch(k_resolve<kThreads, false, false>, kThreads, 0, done_r[0]);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    if (mid)
+        cudaEventRecord(mid, s);
+    // pass 1b: a warp per kWalkRange bitmap words, as many CTAs as that takes
+    const uint64_t nwords = nchunks * kWItems;
+    const uint64_t wblk = (nwords + uint64_t(kWarps) * kWalkRange - 1) / (uint64_t(kWarps) * kWalkRange);
+    k_walk<FP32><<<unsigned(wblk), kThreads, 0, s>>>(a, pend, uint32_t(nwords));
     return cudaGetLastError();
 }
 
@@ -1874,9 +2255,16 @@ cudaError_t launch_cluster(const int2 *pts, uint64_t n, int c, void *scratch, in
 }
 
 uint32_t join_chunk_points() { return kWChunk; }
-uint64_t join_part_words(uint64_t n) { return scan_partials((n + kWChunk - 1) / kWChunk) + 2; }
+// part: the bitmap of pass 1 (8 words per chunk = 4 u64), then the scan's partials
+uint64_t join_part_words(uint64_t n)
+{
+    const uint64_t nchunks = (n + kWChunk - 1) / kWChunk;
+    return nchunks * (kWItems / 2) + scan_partials(nchunks) + 2;
+}
 
-cudaError_t launch_join_resolve(const JoinLaunch &a, unsigned long long *part, cudaStream_t s)
+// Passes 1 and 2.  ev (or null): events recorded after pass 1a, after pass 1b
+// and after the scan.
+static cudaError_t join_resolve_scan(const JoinLaunch &a, unsigned long long *part, cudaStream_t s, cudaEvent_t *ev)
 {
     const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
     if (nchunks >= (1ull << 31))
@@ -1885,12 +2273,22 @@ cudaError_t launch_join_resolve(const JoinLaunch &a, unsigned long long *part, c
         return cudaErrorMisalignedAddress;
     if (nchunks == 0)
         return a.total ? cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s) : cudaSuccess;
-    const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
-    cudaError_t e =
-        a.fp32 ? launch_warp_kernel<true, true>(a, use_hist, s) : launch_warp_kernel<false, true>(a, use_hist, s);
+    uint32_t *pend = reinterpret_cast<uint32_t *>(part);
+    cudaError_t e = a.fp32 ? launch_pass1<true>(a, pend, s, ev ? ev[0] : nullptr)
+                           : launch_pass1<false>(a, pend, s, ev ? ev[0] : nullptr);
     if (e != cudaSuccess)
         return e;
-    return launch_scan(a.tile_tot, nchunks, a.total, part, s);
+    if (ev)
+        cudaEventRecord(ev[1], s);
+    e = launch_scan(a.tile_tot, nchunks, a.total, part + nchunks * (kWItems / 2), s);
+    if (ev)
+        cudaEventRecord(ev[2], s);
+    return e;
+}
+
+cudaError_t launch_join_resolve(const JoinLaunch &a, unsigned long long *part, cudaStream_t s)
+{
+    return join_resolve_scan(a, part, s, nullptr);
 }
 
 cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s)
@@ -1968,21 +2366,13 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cuda
     // results, per-chunk totals), then the offsets and the total
     if (ev)
         cudaEventRecord(ev[0], s);
-    const int use_hist = (a.counts != nullptr && a.ix.P <= (uint32_t)kHistMax) ? 1 : 0;
-    e = a.fp32 ? launch_warp_kernel<true, true>(b, use_hist, s) : launch_warp_kernel<false, true>(b, use_hist, s);
-    if (e != cudaSuccess)
+    if ((e = join_resolve_scan(b, part, s, ev ? ev + 1 : nullptr)) != cudaSuccess)
         return e;
-    if (ev)
-        cudaEventRecord(ev[1], s);
-    if ((e = launch_scan(b.tile_tot, (a.n + kWChunk - 1) / kWChunk, a.total, part, s)) != cudaSuccess)
-        return e;
-    if (ev)
-        cudaEventRecord(ev[2], s);
     // pass 3: pairs in point order
     if ((e = launch_join_emit(b, s)) != cudaSuccess)
         return e;
     if (ev)
-        cudaEventRecord(ev[3], s);
+        cudaEventRecord(ev[4], s);
     return cudaSuccess;
 }
 
@@ -2000,8 +2390,7 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
     if (ev)
         cudaEventRecord(ev[0], s);
     if (a.clustered)
-        e = a.fp32 ? launch_warp_kernel<true, false, true>(a, use_hist, s)
-                   : launch_warp_kernel<false, false, true>(a, use_hist, s);
+        e = a.fp32 ? launch_warp_kernel<true, true>(a, use_hist, s) : launch_warp_kernel<false, true>(a, use_hist, s);
     else
         e = a.fp32 ? launch_warp_kernel<true, false>(a, use_hist, s) : launch_warp_kernel<false, false>(a, use_hist, s);
     if (ev)

@@ -19,8 +19,21 @@ struct IndexView {
     const uint32_t *cover; // 4^cg bits: cover cell holds a non-empty coarse cell
     int scv;              // cover shift: 30 - cg
     int cg;               // cover grid log2: min(g, kCoverLog2)
+    // Block summary of the coarse level: one 16-bit word per block of a
+    // 2^sg x 2^sg grid (sg = min(g, kSumLog2)), row-major, 8 per uint4:
+    // kSumEmpty (no coarse cell of the block can hold a polygon), kSumMixed
+    // (look the coarse word up), or q < kSumEmpty (every coarse cell of the
+    // block lies INSIDE polygon q and no other).  Read from shared memory by
+    // join pass 1a when use_sum is set.
+    const uint4 *sum;
+    int ssh;              // summary shift: 30 - sg
+    int sg;               // summary grid log2
+    int use_sum;          // the summary resolves enough of the box to be worth its shared memory
 };
 constexpr int kCoverLog2 = 8;
+constexpr int kSumLog2 = 8;
+constexpr uint32_t kSumMixed = 0xffffu;
+constexpr uint32_t kSumEmpty = 0xfffeu;
 
 // A grid index of disks (distance queries): cell words as the coarse level of
 // IndexView; lists in ent (n, then n words disk << 1 | boundary); disks as
@@ -114,8 +127,8 @@ size_t join_scratch_bytes(uint64_t n);
 size_t plain_scratch_bytes(uint64_t n);
 
 // scratch: device memory of join_scratch_bytes(n) bytes.  ev (may be null):
-// four events recorded before pass 1, after pass 1 (resolve), after pass 2
-// (scan) and after pass 3 (emit).
+// five events recorded before pass 1, after pass 1a (resolve), after pass 1b
+// (walk), after pass 2 (scan) and after pass 3 (emit).
 cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s);
 // scratch: unused (may be null).  a.keep_counts: add to the counts instead of
@@ -175,9 +188,10 @@ cudaError_t launch_plain_write(const JoinLaunch &a, void *scratch, cudaStream_t 
 
 // The join's passes as separate launches, for callers that pipeline slices of
 // a table: a.res (4 B per point) and a.tile_tot (one u64 per
-// join_chunk_points() points) are given by the caller.  resolve = pass 1 and
-// the scan (*a.total = the slice's pair total; part: join_part_words(n) u64);
-// emit = pass 3.
+// join_chunk_points() points) are given by the caller.  resolve = pass 1 (1a
+// and 1b) and the scan (*a.total = the slice's pair total; part:
+// join_part_words(n) u64, for the row bitmap of pass 1 and the scan); emit =
+// pass 3.
 uint32_t join_chunk_points();
 uint64_t join_part_words(uint64_t n);
 cudaError_t launch_join_resolve(const JoinLaunch &a, unsigned long long *part, cudaStream_t s);

@@ -48,7 +48,8 @@ class IndexInfo(C.Structure):
     _fields_ = [("grid_log2", C.c_int), ("sub_log2", C.c_int), ("n_polys", C.c_uint32), ("pad", C.c_uint32),
                 ("n_cells", C.c_uint64), ("n_blocks", C.c_uint64), ("n_entries", C.c_uint64),
                 ("n_inside", C.c_uint64), ("n_mixed", C.c_uint64), ("n_boundary", C.c_uint64),
-                ("n_edge_refs", C.c_uint64), ("device_bytes", C.c_uint64), ("build_ms", C.c_double)]
+                ("n_edge_refs", C.c_uint64), ("device_bytes", C.c_uint64), ("build_ms", C.c_double),
+                ("sum_resolved", C.c_double), ("use_sum", C.c_int), ("pad2", C.c_int)]
 
 
 class TuneParams(C.Structure):
@@ -88,7 +89,7 @@ class Stats(C.Structure):
                 ("fp32_escalations", C.c_uint64), ("pairs_emitted", C.c_uint64),
                 ("timed_joins", C.c_uint64), ("timed_aggregates", C.c_uint64),
                 ("ms_resolve", C.c_double), ("ms_scan", C.c_double), ("ms_emit", C.c_double),
-                ("ms_aggregate", C.c_double)]
+                ("ms_aggregate", C.c_double), ("ms_walk", C.c_double)]
 
 
 _lib = None
@@ -355,10 +356,14 @@ class Engine:
         self._check(st, "spx_select")
         return n.value if sync else None
 
-    def join_plain_static(self, points: int, index: int, pairs, counts, total, stream=None):
+    def join_plain_static(self, points: int, index: int, pairs, counts, total, stream=None, cap=None):
         """spx_join_plain_static: the plain join with its scratch in libspx's
-        fixed device array (no allocation in the call); asynchronous."""
-        cap = 0 if pairs is None else pairs.shape[0]
+        fixed device array (no allocation in the call); asynchronous.  cap
+        (default: all rows of pairs) may be smaller than the tensor."""
+        rows = 0 if pairs is None else pairs.shape[0]
+        cap = rows if cap is None else int(cap)
+        if cap > rows:
+            raise ValueError(f"cap {cap} exceeds the {rows} rows of pairs")
         self._check(self.lib.spx_join_plain_static(self.ctx, points, index, _dev_ptr(pairs), cap, _dev_ptr(counts),
                                                    _dev_ptr(total), _stream(stream)), "spx_join_plain_static")
 

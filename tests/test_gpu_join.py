@@ -124,6 +124,32 @@ def test_tessellation_mixture(eng):
     check(eng, pts, t.verts, t.ring_off, gls=(6, 9, 12), subs=(1, 3))
 
 
+def test_block_summary_on_and_off(eng):
+    # pass 1a reads the coarse level's block summary from shared memory when
+    # enough of its blocks are resolved (large polygons), and reads every
+    # coarse word from the index otherwise (small polygons); both must give
+    # the oracle's bytes, including points on block and cell borders
+    cases = []
+    for nx, ny, gl in ((20, 15, 12), (6, 5, 8), (120, 100, 8), (120, 100, 5)):
+        t = g.quad_tessellation(nx, ny, 40 + nx, kmin=2, kmax=60)
+        pts = g.mixture_points(300_000, 40 + nx)
+        border = np.array([(x << 22) + d for x in range(0, 256, 3) for d in (-1, 0, 1)], np.int64)
+        bx, by = np.meshgrid(border, border[::7])
+        extra = np.stack([bx.ravel(), by.ravel()], 1)
+        extra = extra[(extra >= 0).all(1) & (extra < (1 << 30)).all(1)].astype(np.int32)
+        pts = np.concatenate([pts, extra])
+        want_p, want_c = oracle.join_fast(pts, t.verts, t.ring_off)
+        gh = eng.load_polygons(t.verts, t.ring_off)
+        ih = eng.build_index(gh, grid_log2=gl)
+        info = eng.index_info(ih)
+        eng.free(ih)
+        eng.free(gh)
+        cases.append(info["use_sum"])
+        p, c, n = run_join(eng, pts, t.verts, t.ring_off, gl)
+        assert n == want_p.shape[0] and np.array_equal(p, want_p) and np.array_equal(c, want_c), (nx, gl)
+    assert 1 in cases and 0 in cases, cases
+
+
 def test_overlapping_queries(eng):
     mix = g.make_mixture(9)
     v, o = g.query_polygons(64, 9, mix, vmax=2000, r_med=0.03)
