@@ -368,6 +368,93 @@ __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, 
     return c;
 }
 
+// The polygons of an entry list that contain a point, for the 32 lanes of a
+// converged warp at once, each lane with its own point (px, py) and list
+// (starting at entry e0; has = false: the lane takes part but has none).
+// Calls f(q) on each lane, in ascending q, for every polygon q of its list
+// that contains its point.  The entries are taken two per lane per wave (one
+// round trip); the edges of all the wave's boundary entries of all lanes are
+// then tested by the whole warp, 64 at a time: edge k of the flattened list
+// goes to lane k mod 32, which finds the lane that owns it by a binary search
+// over the lanes' prefix sums, tests that lane's point, and XORs the crossing
+// into that lane's parity in shared memory.  Lanes never loop on their own
+// long lists (which would diverge and run one dependent load per step); the
+// sorted lists' early stop is not needed, since an edge that ends left of the
+// point never counts.  s_par: 64 words of shared memory owned by this warp.
+template <bool FP32, class F>
+__device__ __forceinline__ void walk_list_wave(const IndexView &ix, bool has, uint32_t e0, int px, int py,
+                                               uint32_t &tests, uint32_t &esc, uint64_t pol, uint32_t *s_par, F f)
+{
+    const int lane = threadIdx.x & 31;
+    const uint4 *e = ix.ent + (has ? e0 : 0u);
+    bool more = has;
+    while (__any_sync(kFull, more)) {
+        // two entries (the entry array ends with sentinels: reading e + 1 is in bounds)
+        const uint4 ea = more ? ld_idx(e, pol) : make_uint4(0, 0, 0, kEntLast);
+        const uint4 eb0 = more ? ld_idx(e + 1, pol) : make_uint4(0, 0, 0, kEntLast);
+        const bool hb = more && !(ea.w & kEntLast);
+        const uint4 eb = hb ? eb0 : make_uint4(0, 0, 0, kEntLast);
+        const uint32_t za = (more && (ea.w & kEntBoundary)) ? ea.z : 0u;
+        const uint32_t zb = (hb && (eb.w & kEntBoundary)) ? eb.z : 0u;
+        const uint32_t tot = za + zb;
+        uint32_t pa = 0, pb = 0;
+        if (__any_sync(kFull, tot != 0)) {
+            uint32_t incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl += t;
+            }
+            const uint32_t T = __shfl_sync(kFull, incl, 31);
+            s_par[lane] = 0u;
+            s_par[32 + lane] = 0u;
+            __syncwarp();
+            for (uint32_t base = 0; base < T; base += 64) {
+                int4 v[2];
+                uint32_t slot[2], own[2];
+                int ox[2], oy[2];
+                bool act[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t k = base + 32 * h + lane;
+                    act[h] = k < T;
+                    uint32_t o = 0; // the owner: the first lane whose inclusive prefix exceeds k
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (__shfl_sync(kFull, incl, o + step - 1) <= k)
+                            o += step;
+                    o = act[h] ? o : 0u;
+                    const uint32_t oi = __shfl_sync(kFull, incl, o), ot = __shfl_sync(kFull, tot, o);
+                    const uint32_t oza = __shfl_sync(kFull, za, o);
+                    const uint32_t oya = __shfl_sync(kFull, ea.y, o), oyb = __shfl_sync(kFull, eb.y, o);
+                    ox[h] = __shfl_sync(kFull, px, o);
+                    oy[h] = __shfl_sync(kFull, py, o);
+                    const uint32_t t = k - (oi - ot);
+                    slot[h] = t >= oza ? 1u : 0u;
+                    own[h] = o;
+                    const uint32_t ei = slot[h] ? oyb + (t - oza) : oya + t;
+                    v[h] = act[h] ? ld_idx(ix.edge + ei, pol) : make_int4(0, 0, 0, 0); // a zero edge never straddles
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (act[h] && edge_cross<FP32>(v[h], ox[h], oy[h], tests, esc))
+                        atomicXor(s_par + 32 * slot[h] + own[h], 1u);
+            }
+            __syncwarp();
+            pa = s_par[lane];
+            pb = s_par[32 + lane];
+            __syncwarp(); // s_par is rewritten by the next wave
+        }
+        if (more && (!(ea.w & kEntBoundary) || pa))
+            f(ea.x);
+        if (hb && (!(eb.w & kEntBoundary) || pb))
+            f(eb.x);
+        more = hb && !(eb.w & kEntLast);
+        e += 2;
+    }
+}
+
 // Shared-memory histogram update for one item of every lane of a converged
 // warp (lanes with has = false add nothing).  Clustered points often put the
 // whole warp on one polygon: then one atomic adds the lane count.
@@ -750,10 +837,6 @@ constexpr int kWalkBatch = SPX_WALK_BATCH;
 #endif
 constexpr int kWalkRange = SPX_WALK_RANGE; // bitmap words (of 32 rows) per warp of pass 1b
 static_assert(kWalkRange % (32 * SPX_WALK_BATCH) == 0, "a warp's range is whole steps");
-#ifndef SPX_WALK_EDGES
-#define SPX_WALK_EDGES 4
-#endif
-constexpr int kWalkEdges = SPX_WALK_EDGES; // edges loaded per round trip past an entry's first four
 
 // With the block summary (SUM), a CTA of 1024 threads (one per SM) first
 // copies the summary into shared memory; a point whose block is empty or
@@ -916,8 +999,10 @@ template <bool FP32>
 __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a, const uint32_t *pend, uint32_t nwords)
 {
     __shared__ uint32_t s_qa[kWarps * kWalkQueue];
+    __shared__ uint32_t s_pa[kWarps * 64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *s_q = s_qa + warp * kWalkQueue; // rows
+    uint32_t *s_par = s_pa + warp * 64;
     const IndexView &ix = a.ix;
     const uint64_t keep = policy_evict_last();
     uint32_t n_tests = 0, n_esc = 0, n_pairs = 0;
@@ -925,20 +1010,17 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a,
     auto walk = [&](uint32_t m) {
         __syncwarp();
         const bool has = (uint32_t)lane < m;
-        const uint32_t row = s_q[has ? lane : 0]; // idle lanes repeat lane 0's walk, uncounted
+        const uint32_t row = s_q[has ? lane : 0]; // idle lanes load lane 0's row and walk nothing
         const int2 p = a.pts[row];
         const uint32_t e0 = __ldcg(a.res + row);
-        uint32_t f = 0, t_l = 0, e_l = 0;
-        uint32_t c = walk_list<FP32, kWalkEdges>(ix, e0, p.x, p.y, f, t_l, e_l, keep);
-        c = has ? c : 0u;
-        n_tests += has ? t_l : 0u;
-        n_esc += has ? e_l : 0u;
+        uint32_t f = 0, c = 0;
+        walk_list_wave<FP32>(ix, has, e0, p.x, p.y, n_tests, n_esc, keep, s_par, [&](uint32_t q) {
+            f = c ? f : q;
+            ++c;
+            if (a.counts)
+                atomicAdd(a.counts + q, 1ull);
+        });
         n_pairs += c;
-        if (a.counts) {
-            global_add_warp(a.counts, c == 1, f);
-            if (c > 1)
-                point_emit<FP32>(ix, p.x, p.y, keep, [&](uint32_t q) { atomicAdd(a.counts + q, 1ull); });
-        }
         if (has) {
             __stcg(a.res + row, res_encode(c, f));
             if (c)
@@ -1006,7 +1088,8 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a,
 // walks its queue 32 points at a time afterwards (all lanes busy, as in pass
 // 1), loading the queued points' coordinates then, one independent load per
 // lane, to write their pairs.
-constexpr size_t kEmitSmem = size_t(kWarps) * kWChunk * (sizeof(uint32_t) + sizeof(unsigned long long));
+constexpr size_t kEmitSmem =
+    size_t(kWarps) * kWChunk * (sizeof(uint32_t) + sizeof(unsigned long long)) + size_t(kWarps) * 64 * sizeof(uint32_t);
 
 template <bool FP32>
 __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsigned long long *chunk_off,
@@ -1017,6 +1100,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
     unsigned long long *s_o = reinterpret_cast<unsigned long long *>(s_raw) + warp * kWChunk;
     uint32_t *s_q = reinterpret_cast<uint32_t *>(s_raw + size_t(kWarps) * kWChunk * sizeof(unsigned long long)) +
                     warp * kWChunk; // rows within the chunk
+    uint32_t *s_par = reinterpret_cast<uint32_t *>(s_raw + size_t(kWarps) * kWChunk *
+                                                               (sizeof(unsigned long long) + sizeof(uint32_t))) +
+                      warp * 64; // parities of walk_list_wave
     const uint64_t keep = policy_evict_last();
     const uint32_t nw = gridDim.x * kWarps;
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
@@ -1077,17 +1163,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
         }
         __syncwarp();
         for (uint32_t k0 = 0; k0 < qn; k0 += 32) {
-            if (k0 + lane < qn) {
-                const uint32_t loc = s_q[k0 + lane];
-                unsigned long long o = s_o[k0 + lane];
-                const int2 p = a.pts[base + loc];
-                const uint32_t pid = a.pid0 + (uint32_t)(base + loc);
-                point_emit<FP32>(a.ix, p.x, p.y, keep, [&](uint32_t q) {
-                    if (o < a.cap)
-                        __stcs(a.pairs + o, make_uint2(pid, q));
-                    ++o;
-                });
-            }
+            // the whole warp walks the queued points' lists together
+            const bool has = k0 + lane < qn;
+            const uint32_t loc = has ? s_q[k0 + lane] : 0u;
+            unsigned long long o = has ? s_o[k0 + lane] : 0ull;
+            const int2 p = has ? a.pts[base + loc] : make_int2(0, 0);
+            const uint32_t pid = a.pid0 + (uint32_t)(base + loc);
+            const uint32_t w = has ? resolve(a.ix, (uint32_t)p.x, (uint32_t)p.y, keep) : 0u;
+            uint32_t t = 0, e = 0;
+            walk_list_wave<FP32>(a.ix, (w >> 30) == kCellList, w & kPayloadMask, p.x, p.y, t, e, keep, s_par,
+                                 [&](uint32_t q) {
+                                     if (o < a.cap)
+                                         __stcs(a.pairs + o, make_uint2(pid, q));
+                                     ++o;
+                                 });
         }
         __syncwarp(); // the queue is rewritten by the next chunk
     }
