@@ -326,9 +326,17 @@ def run_spx(args, world, rank, local):
         raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
     torch.cuda.set_device(local)
     dist_init(world, local, torch)
-    clocks = ClockSampler(local)
     if args.workload == "count_4b":
-        return run_count_bench(args, world, rank, local, clocks, torch)
+        line = count_measure(args, world, rank, local, torch, args.steps, args.warmup, args.points, e2e=not args.no_e2e)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
+    if args.workload.startswith("select"):
+        line = select_measure(args, world, rank, local, torch, args.steps, args.warmup, args.points)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
+    clocks = ClockSampler(local)
     pts, v, o, desc = make_workload(args.workload, args.points, rank)
     N = pts.shape[0]
 
@@ -358,8 +366,6 @@ def run_spx(args, world, rank, local):
     else:
         ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32), sub_log2=args.sub)
     info = eng.index_info(ih)
-    if args.workload.startswith("select"):
-        return run_select_bench(args, world, rank, eng, ph, ih, info, dpts, pts, v, o, desc, clocks, torch)
     cap = N if args.cap is None else args.cap
     pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
     counts = torch.zeros(max(P, 1), dtype=torch.int64, device="cuda")
@@ -504,13 +510,27 @@ def run_spx(args, world, rank, local):
             "clocks": clk,
             "serving": serving,
         }
-        print(json.dumps(out), flush=True)
     eng.free(ih)
     if gh is not None:
         eng.free(gh)
     eng.free(ph)
     eng.close()
-    del dpts
+    del dpts, pairs, counts, total
+    torch.cuda.empty_cache()
+    if args.workload == "tess2000_100m" and world == 1 and not args.no_extra and not args.plain:
+        # the batched selection (500M points) and the count-only aggregate (4B
+        # points) at their full sizes, each with its own roofline, CPU
+        # baseline and clocks
+        k, w = max(1, min(args.steps, 10)), max(3, min(args.warmup, 5))
+        sel = select_measure(args, world, rank, local, torch, k, w, None)
+        torch.cuda.empty_cache()
+        cnt = count_measure(args, world, rank, local, torch, k, w, None, e2e=False)
+        torch.cuda.empty_cache()
+        if rank == 0:
+            out["select"] = sel
+            out["count"] = cnt
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -588,8 +608,12 @@ def serve_run(srv, reqs, rate, warm: int, seed: int = 7):
 
 
 def run_serving(eng, ph, N: int, seed: int, timed: int, warm: int, burst: int):
-    """Capacity (a burst) and latency at 0.5 / 0.8 / 0.95 x capacity, for the
-    batching server and for the plain comparison (one request per launch)."""
+    """Capacity (a burst) of the batching server and of the plain comparison
+    (one request per launch), then latency at 0.5 / 0.8 / 0.95 x the batching
+    server's capacity and at 0.5 / 0.8 x the plain server's (rates both arms
+    sustain), `timed` requests per rate and arm after `warm` warm-up requests.
+    The batch passes' HBM fraction: every batch reads the point table twice
+    (count pass, write pass), measured over the batching server's burst."""
     from paper_2203_14362_gb300 import spx
     t_build = time.perf_counter()
     idx = serve_indexes(eng, seed)
@@ -603,19 +627,32 @@ def run_serving(eng, ph, N: int, seed: int, timed: int, warm: int, burst: int):
     arms = {"batched": dict(max_batch=8, slots=2), "plain": dict(plain=True)}
     cap = {}
     batches = 0
+    peak, peak_kind = peaks()
     for name, kw in arms.items():
         srv = spx.Server(eng, ph, handles, **kw)
         serve_run(srv, serve_stream(idx, max(4, burst // 4), seed + 1), None, 0)  # warm-up
+        b0 = srv.stats()["batches"]
         r = serve_run(srv, serve_stream(idx, burst, seed + 2), None, 0)
+        nb = srv.stats()["batches"] - b0
         cap[name] = r["throughput_rps"]
+        if name == "batched":
+            span = burst / r["throughput_rps"]
+            gbs = 2 * 8 * N * nb / span / 1e9
+            out["batch_passes"] = {"batches": nb, "requests": burst, "seconds": span,
+                                   "point_bytes_per_batch": 16 * N, "achieved_gbs": gbs, "peak": peak,
+                                   "frac": gbs / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                                   "note": "two passes over the 8 B points per batch (count, write) over the "
+                                           "burst's span; index reads and outputs not counted"}
         srv.close()
     out["capacity_rps"] = cap
-    for x in (0.5, 0.8, 0.95):
-        rate = x * cap["batched"]
-        row = {"x_capacity": x, "rate_rps": rate}
+    plan = [("batched", x) for x in (0.5, 0.8, 0.95)] + [("plain", x) for x in (0.5, 0.8)]
+    for ref, x in plan:
+        rate = x * cap[ref]
+        row = {"x_capacity": x, "capacity_of": ref, "rate_rps": rate}
         for name, kw in arms.items():
             srv = spx.Server(eng, ph, handles, **kw)
-            row[name] = serve_run(srv, serve_stream(idx, warm + timed, seed + 10 + int(100 * x)), rate, warm)
+            row[name] = serve_run(srv, serve_stream(idx, warm + timed, seed + 10 + int(100 * x) + len(out["rates"])),
+                                  rate, warm)
             batches += srv.stats()["batches"]
             srv.close()
         out["rates"].append(row)
@@ -657,15 +694,17 @@ def run_serve_bench(args, world, rank, eng, ph, dpts, N, desc, clocks, torch):
     return 0
 
 
-def run_count_bench(args, world, rank, local, clocks, torch):
-    """Count-only aggregate at scale: 4B Zipf-weighted mixture points against a
-    40000-cell tessellation (10-10000 vertices per cell); per-polygon counts
-    only.  The point table is generated chunk by chunk straight into device
-    memory (32 GB); the first chunk stays on the host for the oracle sample."""
+def count_measure(args, world, rank, local, torch, steps, warmup, n_override, e2e: bool):
+    """Count-only aggregate at scale (returns the JSON object): 4B
+    Zipf-weighted mixture points against a 40000-cell tessellation (10-10000
+    vertices per cell); per-polygon counts only.  The point table is generated
+    chunk by chunk straight into device memory (32 GB); the first chunk stays
+    on the host for the oracle checks and the CPU baseline."""
     import oracle
     from paper_2203_14362_gb300 import datagen as g
     from paper_2203_14362_gb300 import spx
-    N = args.points or 4_000_000_000
+    clocks = ClockSampler(local)
+    N = n_override or 4_000_000_000
     seed = g.SEED_BASE + 5
     mix = g.make_mixture(seed, zipf_s=1.1)
     nx, ny = g.tessellation_shape(40000)
@@ -705,19 +744,19 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     assert int(counts.sum().item()) == N, "sum of counts != number of points"
     cluster = None
     ph_run = ph
-    if args.cluster < 0:
-        args.cluster = 12
-    if args.cluster:
+    cl = 12 if args.cluster < 0 else args.cluster
+    if cl:
         # one-off: a copy grouped by grid cell (load time, outside the timed steps)
         t0 = time.perf_counter()
-        ph_run = eng.cluster_points(ph, args.cluster)
+        ph_run = eng.cluster_points(ph, cl)
         cl_s = time.perf_counter() - t0
         c2 = torch.zeros(P, dtype=torch.int64, device="cuda")
         eng.aggregate(ph_run, ih, c2, stream=stream)
         torch.cuda.synchronize()
         assert torch.equal(c2, counts), "clustered counts differ from the row-order counts"
-        cluster = {"grid_log2": args.cluster, "seconds": round(cl_s, 3),
+        cluster = {"grid_log2": cl, "seconds": round(cl_s, 3),
                    "check": "counts on the clustered copy == counts on the row-order table"}
+        del c2
     # the first points' counts against the oracle
     m = min(head.shape[0], 2_000_000)
     ph_head = eng.load_points(dpts[:m])
@@ -728,7 +767,7 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     ref = pr.counts(head[:m])
     assert np.array_equal(c_head.cpu().numpy().view(np.uint64), ref), "prefix counts differ from the oracle"
     eng.free(ph_head)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         eng.aggregate(ph_run, ih, counts, stream=stream)
     torch.cuda.synchronize()
     eng.stats(reset=True)
@@ -737,41 +776,41 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_host0 = time.time()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         eng.aggregate(ph_run, ih, counts, stream=stream)
         sum_counts_over_ranks(counts, world)
     e1.record(stream)
     torch.cuda.synchronize()
     t_host1 = time.time()
     barrier(world)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     st = eng.stats(reset=True)
     ms_max = max_over_ranks(ms, world, torch)
     clk = clocks.summary(t_host0, t_host1)
     eng.set_phase_timing(True)
-    for _ in range(max(1, min(args.steps, 5))):
+    for _ in range(max(1, min(steps, 5))):
         eng.aggregate(ph_run, ih, counts, stream=stream)
     torch.cuda.synchronize()
     ph_st = eng.stats(reset=True)
     eng.set_phase_timing(False)
     # end to end from host memory: the table in pinned host memory, streamed
     # through the device every step (host-to-device copies inside the timing)
-    e2e = None
-    if not args.no_e2e:
+    e2e_out = None
+    if e2e:
         hx = torch.empty((N, 2), dtype=torch.int32, pin_memory=True)
         hx.copy_(dpts)
         hxn = hx.numpy()
         hc = np.zeros(P, np.uint64)
         eng.aggregate_host(hxn, ih, P, counts_out=hc)
         assert np.array_equal(hc, counts.cpu().numpy().view(np.uint64)), "streamed counts differ"
-        k_e2e = max(1, min(args.steps, args.e2e_steps))
+        k_e2e = max(1, min(steps, args.e2e_steps))
         t0 = time.perf_counter()
         for _ in range(k_e2e):
             eng.aggregate_host(hxn, ih, P, counts_out=hc)
         sec = max_over_ranks((time.perf_counter() - t0) / k_e2e, world, torch)
-        e2e = {"value": world * N / sec / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
-               "d2h_bytes_per_step": int(P * 8), "ms_per_step": sec * 1e3,
-               "path": "spx_aggregate_host: the row-order table streamed from pinned host memory"}
+        e2e_out = {"value": world * N / sec / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
+                   "d2h_bytes_per_step": int(P * 8), "ms_per_step": sec * 1e3,
+                   "path": "spx_aggregate_host: the row-order table streamed from pinned host memory"}
         del hx, hxn
     clocks.stop()
     k_ms = ph_st["ms_aggregate"] / max(ph_st["timed_aggregates"], 1)
@@ -779,39 +818,38 @@ def run_count_bench(args, world, rank, local, clocks, torch):
     alg = 8 * N + 8 * P + idx_bytes
     peak, peak_kind = peaks()
     achieved = alg / (k_ms * 1e-3) / 1e9
-    if rank == 0:
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            t0 = time.perf_counter()
-            done = 0
-            while done < head.shape[0] and time.perf_counter() - t0 < args.cpu_budget:
-                k = min(1_000_000, head.shape[0] - done)
-                pr.counts(head[done:done + k])
-                done += k
-            el = time.perf_counter() - t0
-            cpu = {"value": done / el / 1e9, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
-                   "sample": f"first {done} points of the table, counts only (fast oracle, {el:.1f} s)"}
-        print(json.dumps({
-            "metric": METRIC, "value": world * N / (ms_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "count_4b",
-                       "desc": f"{N} mixture points (64 Gaussians, Zipf(1.1) weights, 10% uniform) x 40000-cell "
-                               f"tessellation (10-10000 vertices per cell); per-polygon counts only",
-                       "points_per_gpu": N, "polygons": P, "vertices": int(v.shape[0]),
-                       "grid_log2": info["grid_log2"], "sub_log2": info["sub_log2"],
-                       "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": idx_bytes,
-                       "generation_s": round(gen_s, 1), "autotune": tune, "clustered_table": cluster,
-                       "checks": "sum(counts) == N; counts of the first %d points == oracle" % m,
-                       "counting": "global atomics (P > shared-memory histogram)" if P > 11776 else "shared memory",
-                       "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
-                       "fp32_escalation_fraction": st["fp32_escalations"] / max(st["edge_tests"], 1),
-                       "l2": "inputs larger than L2 (32 GB of points); no flush"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_warp<aggregate>",
-                         "kernel_ms": k_ms, "algorithmic_bytes_per_launch": int(alg)},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
-        }), flush=True)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        done = 0
+        while done < head.shape[0] and time.perf_counter() - t0 < args.cpu_budget:
+            k = min(1_000_000, head.shape[0] - done)
+            pr.counts(head[done:done + k])
+            done += k
+        el = time.perf_counter() - t0
+        cpu = {"value": done / el / 1e9, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+               "sample": f"first {done} points of the table, counts only (fast oracle, {el:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": world * N / (ms_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "count_4b",
+                   "desc": f"{N} mixture points (64 Gaussians, Zipf(1.1) weights, 10% uniform) x 40000-cell "
+                           f"tessellation (10-10000 vertices per cell); per-polygon counts only",
+                   "points_per_gpu": N, "polygons": P, "vertices": int(v.shape[0]),
+                   "grid_log2": info["grid_log2"], "sub_log2": info["sub_log2"],
+                   "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": idx_bytes,
+                   "generation_s": round(gen_s, 1), "autotune": tune, "clustered_table": cluster,
+                   "checks": "sum(counts) == N; counts of the first %d points == oracle" % m,
+                   "counting": "global atomics (P > shared-memory histogram)" if P > 11776 else "shared memory",
+                   "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
+                   "fp32_escalation_fraction": st["fp32_escalations"] / max(st["edge_tests"], 1),
+                   "l2": "inputs larger than L2 (32 GB of points); no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_warp<aggregate>",
+                     "kernel_ms": k_ms, "algorithmic_bytes_per_launch": int(alg)},
+        "cpu_baseline": cpu, "e2e": e2e_out, "gpu_launches": steps, "clocks": clk,
+    }
     pr.close()
     eng.free(ih)
     eng.free(gh)
@@ -819,64 +857,86 @@ def run_count_bench(args, world, rank, local, clocks, torch):
         eng.free(ph_run)
     eng.free(ph)
     eng.close()
-    del dpts
-    return 0
+    del dpts, counts
+    return line
 
 
-def run_select_bench(args, world, rank, eng, ph, ih, info, dpts, pts, v, o, desc, clocks, torch):
-    """Batched selection: one step = all query polygons answered in one pass."""
+def select_measure(args, world, rank, local, torch, steps, warmup, n_override):
+    """Batched selection (returns the JSON object): one step = all 256 query
+    polygons answered over the resident 500M-point table in one graph-captured
+    launch sequence (the join, then the partition by query)."""
+    from paper_2203_14362_gb300 import spx
+    clocks = ClockSampler(local)
+    pts, v, o, desc = make_workload("select256_500m", n_override, rank)
     N, Q = pts.shape[0], int(o.shape[0] - 1)
+    eng = spx.Engine(local)
+    dpts = torch.from_numpy(pts).cuda()
+    ph = eng.load_points(dpts)
+    gh = eng.load_polygons(v, o)
+    tune = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        params, trials, ih = eng.autotune(ph, gh, fp32_filter=bool(args.fp32))
+        tune = {"picked": [params["grid_log2"], params["sub_log2"]], "seconds": round(time.perf_counter() - t0, 2),
+                "trials": [[x["grid_log2"], x["sub_log2"], round(x["ms"], 4)] for x in trials]}
+    else:
+        ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32), sub_log2=args.sub)
+    info = eng.index_info(ih)
     offs = torch.zeros(Q + 1, dtype=torch.int64, device="cuda")
     probe = torch.empty(1, dtype=torch.int32, device="cuda")
     try:
         total = eng.select(ph, ih, probe, offs)
-    except spx_error() as e:  # the two-call pattern: the first call reports the size
+    except spx.SpxError as e:  # the two-call pattern: the first call reports the size
         total = int(str(e).split("needs ")[1].split(" ")[0])
     ids = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
     assert eng.select(ph, ih, ids, offs) == total
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         eng.select(ph, ih, ids, offs, sync=False, stream=stream)
     torch.cuda.synchronize()
     barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_host0 = time.time()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         eng.select(ph, ih, ids, offs, sync=False, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     t_host1 = time.time()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, torch)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, torch)
     clk = clocks.summary(t_host0, t_host1)
     clocks.stop()
     peak, peak_kind = peaks()
     alg = 8 * N + 4 * total + 8 * (Q + 1) + int(info["device_bytes"])
     achieved = alg / (ms * 1e-3) / 1e9
-    if rank == 0:
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(pts, v, o, args.cpu_budget)
-        print(json.dumps({
-            "metric": METRIC, "value": world * N / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": desc, "points_per_gpu": N, "queries": Q,
-                       "vertices": int(v.shape[0]), "selected_ids": int(total), "grid_log2": info["grid_log2"],
-                       "sub_log2": info["sub_log2"], "point_query_evals_per_s": world * N * Q / (ms * 1e-3),
-                       "launch": "one CUDA graph per step (resolve, count table, scan, emit)",
-                       "index_build_ms": round(info["build_ms"], 1)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": "whole selection step", "algorithmic_bytes_per_launch": int(alg)},
-            "cpu_baseline": cpu, "e2e": None, "clocks": clk,
-            # the join, then the partition: count table, its scan, offsets, emit
-            "gpu_launches": args.steps * (join_launches(N, False) + 3 +
-                                          (1 if Q * max(1, -(-total // 32768)) <= 4 * 8192 else 3)),
-        }), flush=True)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pts, v, o, min(args.cpu_budget, 8.0), single_s=0)
+    line = {
+        "metric": METRIC, "value": world * N / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "select256_500m", "desc": desc, "points_per_gpu": N, "queries": Q,
+                   "vertices": int(v.shape[0]), "selected_ids": int(total), "grid_log2": info["grid_log2"],
+                   "sub_log2": info["sub_log2"], "block_summary": bool(info["use_sum"]),
+                   "point_query_evals_per_s": world * N * Q / (ms * 1e-3),
+                   "launch": "one CUDA graph per step (pass 1a, pass 1b, scan, pass 3, count table, scan, emit)",
+                   "index_build_ms": round(info["build_ms"], 1), "autotune": tune,
+                   "l2": "inputs larger than L2 (4 GB of points); no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": "whole selection step", "algorithmic_bytes_per_launch": int(alg)},
+        "cpu_baseline": cpu, "e2e": None, "clocks": clk,
+        # the join (pass 1a, 1b, scan, pass 3), then the partition: count table, its scan, offsets, emit
+        "gpu_launches": steps * (join_launches(N, False) + 3 +
+                                 (1 if Q * max(1, -(-total // 32768)) <= 4 * 8192 else 3)),
+    }
     eng.free(ih)
+    eng.free(gh)
+    eng.free(ph)
     eng.close()
-    return 0
+    del dpts, ids, offs
+    return line
 
 
 def spx_error():
@@ -910,8 +970,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement of the join workload")
-    ap.add_argument("--serve-timed", type=int, default=120, help="timed requests per arrival rate and arm")
-    ap.add_argument("--serve-warmup", type=int, default=20)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload: skip the selection (500M points) and count (4B points) sub-measurements")
+    ap.add_argument("--serve-timed", type=int, default=1000, help="timed requests per arrival rate and arm")
+    ap.add_argument("--serve-warmup", type=int, default=50)
     ap.add_argument("--serve-burst", type=int, default=48, help="requests of the capacity burst")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "spx":
