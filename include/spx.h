@@ -141,6 +141,33 @@ typedef struct {
 spx_status spx_build_index(spx_ctx *ctx, spx_polys polys, const spx_index_params *params, spx_index *out);
 
 /*
+ * The same index built on the device (§4.2 canvas creation; §6.1 builds the
+ * index of query-time polygons on the fly, inside the query time): every
+ * stage of the host build runs as kernels (per edge: conservative marks of
+ * both levels and the corner thresholds of the rows it straddles; per row:
+ * the parities that classify the cells no edge meets; per fine row: its edge
+ * list sorted by right end; per cell: records, fine blocks and entries), and
+ * the arrays are byte for byte those of spx_build_index with the same
+ * parameters.  Same arguments, results and limits as spx_build_index.
+ * Synchronous (the legacy default stream; the device is synchronised).
+ * Temporary device memory is allocated and freed inside the call.  Errors:
+ * SPX_EINVAL (bad handle or parameters, an index-format limit exceeded),
+ * SPX_ENOMEM, SPX_ECUDA.
+ */
+spx_status spx_build_index_device(spx_ctx *ctx, spx_polys polys, const spx_index_params *params, spx_index *out);
+
+/*
+ * The arrays of a polygon index, copied to host memory (the layout of
+ * spx_host_index_build, sentinels included): coarse words (sizes[0] uint32),
+ * fine words (sizes[1] uint32), entries (sizes[2] x 4 uint32), edges
+ * (sizes[3] x 4 int32).  Any output may be NULL (skipped); call with all NULL
+ * to get the sizes.  Synchronous.  Errors: SPX_EINVAL (not a polygon index),
+ * SPX_ECUDA.
+ */
+spx_status spx_index_arrays(spx_ctx *ctx, spx_index index, uint32_t *coarse, uint32_t *fine, uint32_t *entries,
+                            int32_t *edges, uint64_t sizes[4]);
+
+/*
  * Index of a set of disks for distance queries (§4.2 "Canvases for
  * Distance-Based Queries": a distance constraint around a point is a disk;
  * §5.2 "Distance-Based Queries": the pairs whose distance is <= r, one radius

@@ -16,7 +16,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libspx.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kernels.cu", "api.cu", "server.cu"]
+CU_SOURCES = ["kernels.cu", "api.cu", "server.cu", "index_build_device.cu"]
 CPP_SOURCES = ["index_build.cpp", "disk_index.cpp"]
 
 

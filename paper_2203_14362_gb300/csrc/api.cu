@@ -56,7 +56,8 @@ struct IndexObj {
     DiskView dview{};
     IndexView view{};
     int fp32 = 1;
-    void *mem = nullptr; // one allocation: cells | entries | edges
+    void *mem = nullptr; // one allocation: cells | fine | entries | edges | cover | summary
+    uint64_t n_fine = 0, n_ent = 0, n_edge = 0; // words / entries / edges of a polygon index, sentinels included
     spx_index_info info{};
 };
 
@@ -372,6 +373,66 @@ void *static_join_scratch(int device, cudaError_t &err)
     return addr[device];
 }
 
+// The parts of a polygon index's device allocation (cells | fine | entries |
+// edges | cover | summary) and its statistics, for register_grid_index.
+struct GridParts {
+    char *cell, *fine, *ent, *edge, *cover, *sum;
+    uint64_t n_cell, n_fine, n_ent, n_edge, n_blocks, n_inside, n_mixed, n_boundary;
+    double sum_resolved;
+};
+
+// Views and info of a polygon index whose allocation ix->mem holds `gp`;
+// takes the index into the ctx and returns its handle.
+spx_status register_grid_index(spx_ctx *ctx, spx_polys polys, std::unique_ptr<IndexObj> ix, size_t total, int g, int sb,
+                               int fp32, const GridParts &gp, std::chrono::steady_clock::time_point t0, spx_index *out)
+{
+    PolysObj *pg = lookup(ctx->polys, polys);
+    const int cg = std::min(g, kCoverLog2);
+    ix->polys = polys;
+    ix->fp32 = fp32 ? 1 : 0;
+    ix->view.cell = reinterpret_cast<const uint32_t *>(gp.cell);
+    ix->view.fine = reinterpret_cast<const uint32_t *>(gp.fine);
+    ix->view.ent = reinterpret_cast<const uint4 *>(gp.ent);
+    ix->view.edge = reinterpret_cast<const int4 *>(gp.edge);
+    ix->view.sc = kBoxLog2 - g;
+    ix->view.gc = g;
+    ix->view.sf = kBoxLog2 - g - sb;
+    ix->view.sb = sb;
+    ix->view.P = pg->P;
+    ix->view.cover = reinterpret_cast<const uint32_t *>(gp.cover);
+    ix->view.scv = kBoxLog2 - cg;
+    ix->view.cg = cg;
+    ix->view.sum = reinterpret_cast<const uint4 *>(gp.sum);
+    ix->view.sg = std::min(g, kSumLog2);
+    ix->view.ssh = kBoxLog2 - ix->view.sg;
+    // the summary costs pass 1a three quarters of its warps per SM (one CTA
+    // holds it); worth it when it answers a third of the box or more
+    ix->view.use_sum = gp.sum_resolved >= kSumMinResolved ? 1 : 0;
+    ix->n_fine = gp.n_fine;
+    ix->n_ent = gp.n_ent;
+    ix->n_edge = gp.n_edge;
+    spx_index_info &inf = ix->info;
+    inf.grid_log2 = g;
+    inf.sub_log2 = sb;
+    inf.n_polys = pg->P;
+    inf.n_cells = gp.n_cell;
+    inf.n_blocks = gp.n_blocks;
+    inf.n_entries = gp.n_ent;
+    inf.n_inside = gp.n_inside;
+    inf.n_mixed = gp.n_mixed;
+    inf.n_boundary = gp.n_boundary;
+    inf.n_edge_refs = gp.n_edge;
+    inf.device_bytes = total;
+    inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    inf.sum_resolved = gp.sum_resolved;
+    inf.use_sum = ix->view.use_sum;
+    pg->n_index++;
+    const uint64_t h = make_handle(ctx, kTagIndex);
+    ctx->indexes[h] = std::move(ix);
+    *out = h;
+    return SPX_OK;
+}
+
 // Build the index of polygon set `polys` with the checked parameters prm.  An
 // index of more than max_bytes device bytes is not uploaded: *out is then 0.
 spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_params &prm, spx_index *out,
@@ -391,7 +452,6 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     const int threads = std::max(1u, std::thread::hardware_concurrency());
     if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, sb, threads, hi, err))
         return fail(ctx, SPX_EINVAL, "build_index: " + err);
-    const int cg = std::min(g, kCoverLog2);
     const std::vector<uint32_t> cover = cover_bitmap(hi.cell.data(), g);
     double sum_resolved = 0;
     const std::vector<uint16_t> sum = block_summary(hi.cell.data(), g, &sum_resolved);
@@ -424,46 +484,9 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
         cudaFree(ix->mem);
         return cuda_fail(ctx, e, "build_index upload");
     }
-    ix->polys = polys;
-    ix->fp32 = prm.fp32_filter ? 1 : 0;
-    ix->view.cell = reinterpret_cast<const uint32_t *>(p_cell);
-    ix->view.fine = reinterpret_cast<const uint32_t *>(p_fine);
-    ix->view.ent = reinterpret_cast<const uint4 *>(p_ent);
-    ix->view.edge = reinterpret_cast<const int4 *>(p_edge);
-    ix->view.sc = kBoxLog2 - g;
-    ix->view.gc = g;
-    ix->view.sf = kBoxLog2 - g - sb;
-    ix->view.sb = sb;
-    ix->view.P = pg->P;
-    ix->view.cover = reinterpret_cast<const uint32_t *>(p_cover);
-    ix->view.scv = kBoxLog2 - cg;
-    ix->view.cg = cg;
-    ix->view.sum = reinterpret_cast<const uint4 *>(p_sum);
-    ix->view.sg = std::min(g, kSumLog2);
-    ix->view.ssh = kBoxLog2 - ix->view.sg;
-    // the summary costs pass 1a three quarters of its warps per SM (one CTA
-    // holds it); worth it when it answers a third of the box or more
-    ix->view.use_sum = sum_resolved >= kSumMinResolved ? 1 : 0;
-    spx_index_info &inf = ix->info;
-    inf.grid_log2 = g;
-    inf.sub_log2 = sb;
-    inf.n_polys = pg->P;
-    inf.n_cells = hi.cell.size();
-    inf.n_blocks = hi.n_blocks;
-    inf.n_entries = hi.entries.size() / 4;
-    inf.n_inside = hi.n_inside;
-    inf.n_mixed = hi.n_mixed;
-    inf.n_boundary = hi.n_boundary;
-    inf.n_edge_refs = hi.edges.size() / 4;
-    inf.device_bytes = total;
-    inf.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    inf.sum_resolved = sum_resolved;
-    inf.use_sum = ix->view.use_sum;
-    pg->n_index++;
-    const uint64_t h = make_handle(ctx, kTagIndex);
-    ctx->indexes[h] = std::move(ix);
-    *out = h;
-    return SPX_OK;
+    GridParts gp{p_cell, p_fine, p_ent, p_edge, p_cover, p_sum, hi.cell.size(), hi.fine.size(), hi.entries.size() / 4,
+                 hi.edges.size() / 4, hi.n_blocks, hi.n_inside, hi.n_mixed, hi.n_boundary, sum_resolved};
+    return register_grid_index(ctx, polys, std::move(ix), total, g, sb, prm.fp32_filter, gp, t0, out);
 }
 
 } // namespace
@@ -725,6 +748,76 @@ spx_status spx_load_polygons(spx_ctx *ctx, const int32_t *xy, const uint64_t *ri
     const uint64_t h = make_handle(ctx, kTagPolys);
     ctx->polys[h] = std::move(p);
     *out = h;
+    return SPX_OK;
+}
+
+spx_status spx_build_index_device(spx_ctx *ctx, spx_polys polys, const spx_index_params *params, spx_index *out)
+{
+    if (!ctx || !out)
+        return fail(ctx, SPX_EINVAL, "build_index_device: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    spx_index_params prm{};
+    prm.fp32_filter = 1;
+    if (params) {
+        prm = *params;
+        for (int r : prm.reserved)
+            if (r)
+                return fail(ctx, SPX_EINVAL, "build_index_device: reserved fields must be zero");
+    }
+    PolysObj *pg = lookup(ctx->polys, polys);
+    if (!pg)
+        return fail(ctx, SPX_EINVAL, "build_index_device: bad polygon handle");
+    const auto t0 = std::chrono::steady_clock::now();
+    const int g = prm.grid_log2 ? prm.grid_log2 : default_grid_log2(pg->xy.data(), pg->off.data(), pg->P);
+    const int sb = prm.sub_log2 ? prm.sub_log2 : kMaxSubLog2;
+    if (g < 1 || g > kMaxGridLog2 || sb < 1 || sb > kMaxSubLog2 || g + sb > kMaxFineLog2)
+        return fail(ctx, SPX_EINVAL, "build_index_device: grid_log2 must be in [1, 13] (0 = automatic), sub_log2 "
+                                     "in [1, 3] (0 = default), grid_log2 + sub_log2 <= 16");
+    if (pg->P >= (1u << 30))
+        return fail(ctx, SPX_EINVAL, "build_index_device: too many polygons (limit 2^30 - 1)");
+    if (pg->P && pg->off[pg->P] >= (uint64_t(1) << 32))
+        return fail(ctx, SPX_EINVAL, "build_index_device: more than 2^32 - 1 vertices");
+    GridIndexDev d{};
+    const char *why = nullptr;
+    cudaError_t e = cudaSuccess;
+    const int st = build_grid_index_device(pg->xy.data(), pg->off.data(), pg->P, g, sb, d, why, e);
+    if (st == 1)
+        return fail(ctx, SPX_EINVAL, std::string("build_index_device: ") + why);
+    if (st != 0)
+        return e == cudaErrorMemoryAllocation ? fail(ctx, SPX_ENOMEM, "build_index_device: out of device memory")
+                                              : cuda_fail(ctx, e, "build_index_device");
+    auto ix = std::make_unique<IndexObj>();
+    ix->mem = d.mem;
+    char *base = static_cast<char *>(d.mem);
+    auto at = [&](const void *p) { return base + (static_cast<const char *>(p) - base); };
+    GridParts gp{at(d.cell), at(d.fine), at(d.ent), at(d.edge), at(d.cover), at(d.sum), d.n_cell, d.n_fine, d.n_ent,
+                 d.n_edge, d.n_blocks, d.n_inside, d.n_mixed, d.n_boundary, d.sum_resolved};
+    return register_grid_index(ctx, polys, std::move(ix), d.bytes, g, sb, prm.fp32_filter, gp, t0, out);
+}
+
+spx_status spx_index_arrays(spx_ctx *ctx, spx_index index, uint32_t *coarse, uint32_t *fine, uint32_t *entries,
+                            int32_t *edges, uint64_t sizes[4])
+{
+    if (!ctx || !sizes)
+        return fail(ctx, SPX_EINVAL, "index_arrays: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    IndexObj *ix = lookup(ctx->indexes, index);
+    if (!ix || ix->kind != 0)
+        return fail(ctx, SPX_EINVAL, "index_arrays: not a polygon index");
+    sizes[0] = ix->info.n_cells;
+    sizes[1] = ix->n_fine;
+    sizes[2] = ix->n_ent;
+    sizes[3] = ix->n_edge;
+    if (coarse)
+        SPX_CUDA(cudaMemcpy(coarse, ix->view.cell, sizes[0] * 4, cudaMemcpyDeviceToHost), "index_arrays coarse");
+    if (fine)
+        SPX_CUDA(cudaMemcpy(fine, ix->view.fine, sizes[1] * 4, cudaMemcpyDeviceToHost), "index_arrays fine");
+    if (entries)
+        SPX_CUDA(cudaMemcpy(entries, ix->view.ent, sizes[2] * 16, cudaMemcpyDeviceToHost), "index_arrays entries");
+    if (edges)
+        SPX_CUDA(cudaMemcpy(edges, ix->view.edge, sizes[3] * 16, cudaMemcpyDeviceToHost), "index_arrays edges");
     return SPX_OK;
 }
 

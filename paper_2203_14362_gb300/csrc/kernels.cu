@@ -1634,6 +1634,13 @@ cudaError_t launch_scan(unsigned long long *v, uint64_t n, unsigned long long *t
 
 } // namespace
 
+uint64_t scan_part_words(uint64_t n) { return scan_partials(n) + 2; }
+cudaError_t launch_exclusive_scan(unsigned long long *v, uint64_t n, unsigned long long *total,
+                                  unsigned long long *part, cudaStream_t s)
+{
+    return launch_scan(v, n, total, part, s);
+}
+
 // Deterministic sample for the tuner: dst[i] = src[i * stride], i < m.
 __global__ void __launch_bounds__(256) k_gather_stride(const int2 *__restrict__ src, uint64_t stride,
                                                      int2 *__restrict__ dst, uint64_t m)

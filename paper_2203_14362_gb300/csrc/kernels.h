@@ -212,4 +212,34 @@ cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_
 
 int device_sm_count();
 
+// Exclusive scan of n u64 values in place on stream s; *total (device, or
+// null) gets their sum.  part: scan_part_words(n) u64 of scratch.
+uint64_t scan_part_words(uint64_t n);
+cudaError_t launch_exclusive_scan(unsigned long long *v, uint64_t n, unsigned long long *total,
+                                  unsigned long long *part, cudaStream_t s);
+
+// Device build of the polygon grid index: the same arrays as the host build
+// (build_grid_index: coarse words, fine blocks, entries with their sentinels,
+// edges with their sentinel), and the cover bitmap and block summary the
+// host path computes from the coarse words, in one new device allocation laid
+// out as the host path lays it out (cells | fine | entries | edges | cover |
+// summary, each part 256-byte aligned); the caller owns out.mem.  xy (2 V
+// int32) and ring_off (P + 1) are host arrays, already checked.  Runs on the
+// legacy default stream and synchronises the device.  Returns 0; 1 when a
+// limit of the index format is exceeded (err says which); 2 on a CUDA error
+// (in cerr).
+struct GridIndexDev {
+    void *mem;
+    size_t bytes;
+    uint32_t *cell, *fine, *ent;
+    int4 *edge;
+    uint32_t *cover;
+    uint16_t *sum;
+    uint64_t n_cell, n_fine, n_ent, n_edge, n_blocks; // n_ent, n_edge with their sentinels
+    uint64_t n_inside, n_mixed, n_boundary;
+    double sum_resolved; // fraction of summary blocks that are empty or INSIDE one polygon
+};
+int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int g, int sb,
+                            GridIndexDev &out, const char *&err, cudaError_t &cerr);
+
 } // namespace spx

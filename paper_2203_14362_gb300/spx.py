@@ -28,7 +28,7 @@ EXPORTS = [
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
     "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
     "spx_build_disk_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free",
-    "spx_build_disk_index_device", "spx_disk_index_arrays",
+    "spx_build_disk_index_device", "spx_disk_index_arrays", "spx_build_index_device", "spx_index_arrays",
 ]
 
 SPX_REQ_SELECT, SPX_REQ_JOIN = 1, 2
@@ -142,6 +142,8 @@ def load(path: str = LIB_PATH):
         "spx_host_disk_index_free": ([V], None),
         "spx_build_disk_index_device": ([V, V, V, U32, I, P64], I),
         "spx_disk_index_arrays": ([V, U64, V, V, P64], I),
+        "spx_build_index_device": ([V, U64, C.POINTER(IndexParams), C.POINTER(U64)], I),
+        "spx_index_arrays": ([V, U64, V, V, V, V, P64], I),
         "spx_aggregate_host": ([V, V, U64, U64, V], I),
         "spx_set_host_streaming": ([V, I, I], I),
         "spx_points_info": ([V, U64, C.POINTER(V), P64, C.POINTER(I)], I),
@@ -276,11 +278,28 @@ class Engine:
                     "spx_load_polygons")
         return h.value
 
-    def build_index(self, polys: int, grid_log2: int = 0, fp32_filter: bool = True, sub_log2: int = 0) -> int:
+    def build_index(self, polys: int, grid_log2: int = 0, fp32_filter: bool = True, sub_log2: int = 0,
+                    on_device: bool = False) -> int:
+        """spx_build_index (or, on_device, spx_build_index_device: the same
+        arrays built by kernels)."""
         p = IndexParams(grid_log2, 1 if fp32_filter else 0, sub_log2)
         h = C.c_uint64()
-        self._check(self.lib.spx_build_index(self.ctx, polys, C.byref(p), C.byref(h)), "spx_build_index")
+        fn = "spx_build_index_device" if on_device else "spx_build_index"
+        self._check(getattr(self.lib, fn)(self.ctx, polys, C.byref(p), C.byref(h)), fn)
         return h.value
+
+    def index_arrays(self, index: int) -> dict:
+        """spx_index_arrays: a polygon index's arrays copied to the host (the
+        layout of host_index, sentinels included)."""
+        sizes = (C.c_uint64 * 4)()
+        self._check(self.lib.spx_index_arrays(self.ctx, index, None, None, None, None, sizes), "spx_index_arrays")
+        coarse = np.zeros(sizes[0], np.uint32)
+        fine = np.zeros(sizes[1], np.uint32)
+        ent = np.zeros((sizes[2], 4), np.uint32)
+        edges = np.zeros((sizes[3], 4), np.int32)
+        self._check(self.lib.spx_index_arrays(self.ctx, index, _np_ptr(coarse), _np_ptr(fine), _np_ptr(ent),
+                                              _np_ptr(edges), sizes), "spx_index_arrays")
+        return {"coarse": coarse, "fine": fine, "entries": ent, "edges": edges}
 
     def autotune(self, points: int, polys: int, sample_points: int = 0, grid_min: int = 0, grid_max: int = 0,
                  reps: int = 0, fp32_filter: bool = True, max_index_bytes: int = 0, keep_index: bool = True,
