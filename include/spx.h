@@ -429,6 +429,24 @@ spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *coarse, uint32
 void spx_host_index_free(spx_host_index *h);
 
 /*
+ * Bounds check of a polygon index's arrays, as spx_host_index_build lays
+ * them out (sizes in words / entries / edges, sentinels included): every
+ * coarse word names a polygon below n_polys or a fine block that exists;
+ * every fine word a polygon below n_polys or an entry list that ends with its
+ * last entry before the four sentinel entries; every entry a polygon below
+ * n_polys and an edge range inside the edge array (the sentinel edge
+ * excluded).  spx_build_index applies it to every index before upload (a
+ * failure there is SPX_EKERNEL); the kernels of a build with SPX_BOUNDS_CHECK
+ * apply the same predicate to each offset they read.  SPX_OK, or SPX_EINVAL
+ * with the first violation in msg (msg_len bytes, NUL-terminated; msg may be
+ * NULL).  Host only; no device needed.
+ */
+spx_status spx_host_index_validate(const uint32_t *coarse, uint64_t n_coarse, const uint32_t *fine, uint64_t n_fine,
+                                   const uint32_t *entries, uint64_t n_entries, const int32_t *edges,
+                                   uint64_t n_edges, int grid_log2, int sub_log2, uint32_t n_polys, char *msg,
+                                   uint64_t msg_len);
+
+/*
  * Host-only build of the disk index of spx_build_disk_index (same arguments,
  * same checks), for inspection without a GPU.  sizes[0] = cell words (4^g),
  * sizes[1] = entry words, sizes[2] = grid_log2.  spx_host_disk_index_copy
@@ -463,6 +481,16 @@ typedef struct {
     double ms_aggregate;       /* count-only aggregate */
     double ms_walk;            /* polygon join pass 1b: exact tests of the points whose cell lists edges */
 } spx_stats_t;
+
+/*
+ * Checks the bounded-wait error path end to end (the join's pass 1a waits
+ * for its bulk copies of points with at most a fixed number of polls): one
+ * warp polls an mbarrier that nothing completes, `tries` times, then sets
+ * the timeout bit of the ctx's error word, which the host reads and clears.
+ * Returns SPX_ETIMEOUT (the expected result; the ctx stays usable) or
+ * SPX_ECUDA.  Synchronises the stream.
+ */
+spx_status spx_check_bounded_wait(spx_ctx *ctx, uint32_t tries, void *stream);
 
 /* Read (synchronising the device) and optionally reset the counters. */
 spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset);

@@ -14,6 +14,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libspx.so")
+# the debug flavour: every index walk of the kernels bounds-checked (SPX_BOUNDS_CHECK)
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libspx_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels.cu", "api.cu", "server.cu", "index_build_device.cu"]
@@ -37,27 +40,29 @@ def _run(cmd: list[str], verbose: bool) -> None:
         print(r.stdout, flush=True)
 
 
-def _stale(objs: list[str]) -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     srcs = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "spx.h"), __file__]
     return any(os.path.getmtime(s) > t for s in srcs)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    """Compile and link libspx.so next to this file; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and not _stale([]):
-        return LIB
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, checked: bool = False) -> str:
+    """Compile and link libspx.so next to this file (checked: the
+    bounds-checked debug flavour, libspx_checked.so); returns its path."""
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
+    if not force and not _stale(lib):
+        return lib
     nv = nvcc()
     # SPX_NVCC_EXTRA: extra nvcc flags, e.g. -D settings of the kernels' tuning macros
-    common = ["-O3", "-std=c++17", "-I", CSRC, "-I", INCLUDE]
+    common = ["-O3", "-std=c++17", "-I", CSRC, "-I", INCLUDE] + (["-DSPX_BOUNDS_CHECK"] if checked else [])
     extra = os.environ.get("SPX_NVCC_EXTRA", "").split()
     jobs = []
     objs = []
     for f in CU_SOURCES:
-        o = os.path.join(BUILD, f + ".o")
+        o = os.path.join(build_dir, f + ".o")
         objs.append(o)
         cmd = [nv, *ARCH, "-lineinfo", *common, *extra, "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                "-c", os.path.join(CSRC, f), "-o", o]
@@ -65,18 +70,19 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             cmd.insert(1, "-Xptxas=-v")
         jobs.append(cmd)
     for f in CPP_SOURCES:
-        o = os.path.join(BUILD, f + ".o")
+        o = os.path.join(build_dir, f + ".o")
         objs.append(o)
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-I", CSRC, "-I", INCLUDE,
                      "-c", os.path.join(CSRC, f), "-o", o])
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         for fut in [ex.submit(_run, j, verbose) for j in jobs]:
             fut.result()
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     _run([nv, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], verbose)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -411,6 +411,10 @@ spx_status register_grid_index(spx_ctx *ctx, spx_polys polys, std::unique_ptr<In
     ix->n_fine = gp.n_fine;
     ix->n_ent = gp.n_ent;
     ix->n_edge = gp.n_edge;
+    ix->view.n_fine = gp.n_fine;
+    ix->view.n_ent = gp.n_ent;
+    ix->view.n_edge = gp.n_edge;
+    ix->view.err = &ctx->aux->err;
     spx_index_info &inf = ix->info;
     inf.grid_log2 = g;
     inf.sub_log2 = sb;
@@ -452,6 +456,10 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
     const int threads = std::max(1u, std::thread::hardware_concurrency());
     if (!build_grid_index(pg->xy.data(), pg->off.data(), pg->P, g, sb, threads, hi, err))
         return fail(ctx, SPX_EINVAL, "build_index: " + err);
+    // the arrays the kernels will walk: every offset and id in bounds
+    if (!validate_grid_index(hi.cell.data(), hi.cell.size(), hi.fine.data(), hi.fine.size(), hi.entries.data(),
+                             hi.entries.size() / 4, hi.edges.data(), hi.edges.size() / 4, g, sb, pg->P, err))
+        return fail(ctx, SPX_EKERNEL, "build_index: internal consistency check of the index failed: " + err);
     const std::vector<uint32_t> cover = cover_bitmap(hi.cell.data(), g);
     double sum_resolved = 0;
     const std::vector<uint16_t> sum = block_summary(hi.cell.data(), g, &sum_resolved);
@@ -1728,6 +1736,24 @@ spx_status spx_host_index_copy(const spx_host_index *h, uint32_t *coarse, uint32
 
 void spx_host_index_free(spx_host_index *h) { delete h; }
 
+spx_status spx_host_index_validate(const uint32_t *coarse, uint64_t n_coarse, const uint32_t *fine, uint64_t n_fine,
+                                   const uint32_t *entries, uint64_t n_entries, const int32_t *edges,
+                                   uint64_t n_edges, int grid_log2, int sub_log2, uint32_t n_polys, char *msg,
+                                   uint64_t msg_len)
+{
+    if (!coarse || !fine || !entries || !edges)
+        return SPX_EINVAL;
+    std::string err;
+    const bool ok = validate_grid_index(coarse, n_coarse, fine, n_fine, entries, n_entries, edges, n_edges, grid_log2,
+                                        sub_log2, n_polys, err);
+    if (msg && msg_len) {
+        const size_t m = std::min<size_t>(err.size(), size_t(msg_len - 1));
+        std::memcpy(msg, err.data(), m);
+        msg[m] = 0;
+    }
+    return ok ? SPX_OK : SPX_EINVAL;
+}
+
 struct spx_host_disk_index {
     HostDiskIndex hd;
 };
@@ -1791,6 +1817,17 @@ spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset)
         ctx->ms_resolve = ctx->ms_walk = ctx->ms_scan = ctx->ms_emit = ctx->ms_agg = 0;
     }
     return check_kernel_err(ctx, nullptr);
+}
+
+spx_status spx_check_bounded_wait(spx_ctx *ctx, uint32_t tries, void *stream)
+{
+    if (!ctx)
+        return SPX_EINVAL;
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SPX_CUDA(launch_wait_check(&ctx->aux->err, tries, s), "bounded wait launch");
+    return check_kernel_err(ctx, s);
 }
 
 spx_status spx_set_phase_timing(spx_ctx *ctx, int on)

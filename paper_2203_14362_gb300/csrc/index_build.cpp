@@ -574,4 +574,67 @@ bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, i
     return true;
 }
 
+bool validate_grid_index(const uint32_t *cell, uint64_t n_cell, const uint32_t *fine, uint64_t n_fine,
+                         const uint32_t *ent, uint64_t n_ent, const int32_t *edges, uint64_t n_edge, int g, int sb,
+                         uint32_t P, std::string &err)
+{
+    auto bad = [&](const std::string &m) {
+        err = m;
+        return false;
+    };
+    if (g < 1 || g > kMaxGridLog2 || sb < 1 || sb > kMaxSubLog2)
+        return bad("grid_log2 / sub_log2 out of range");
+    const uint64_t FF = uint64_t(1) << (2 * sb);
+    if (n_cell != (uint64_t(1) << (2 * g)))
+        return bad("coarse level is not 4^grid_log2 words");
+    if (n_fine == 0 || (n_fine != 1 && n_fine % FF != 0))
+        return bad("fine level is not a whole number of blocks");
+    if (n_ent < 4)
+        return bad("entry sentinels missing");
+    for (uint64_t k = n_ent - 4; k < n_ent; ++k)
+        if (ent[4 * k] != 0 || ent[4 * k + 1] != 0 || ent[4 * k + 2] != 0 || ent[4 * k + 3] != kEntLast)
+            return bad("entry sentinels missing");
+    if (n_edge < 1 || edges[4 * (n_edge - 1)] || edges[4 * (n_edge - 1) + 1] || edges[4 * (n_edge - 1) + 2] ||
+        edges[4 * (n_edge - 1) + 3])
+        return bad("edge sentinel missing");
+    const uint64_t n_blocks = n_fine / FF, lists_end = n_ent - 4;
+    // every entry list a fine word points at: inside the entries, ending with
+    // its last entry before the sentinels, polygon ids below P, edge ranges
+    // inside the edges (sentinel excluded)
+    auto check_list = [&](uint64_t e0) {
+        for (uint64_t k = e0;; ++k) {
+            if (k >= lists_end)
+                return bad("entry list " + std::to_string(e0) + " runs past the entries");
+            const uint32_t q = ent[4 * k], eb = ent[4 * k + 1], ec = ent[4 * k + 2], fl = ent[4 * k + 3];
+            if (q >= P)
+                return bad("entry " + std::to_string(k) + " names polygon " + std::to_string(q));
+            if (fl & ~(kEntBoundary | kEntLast))
+                return bad("entry " + std::to_string(k) + " has unknown flags");
+            if ((fl & kEntBoundary) && uint64_t(eb) + ec > n_edge - 1)
+                return bad("entry " + std::to_string(k) + " lists edges past the edge array");
+            if (fl & kEntLast)
+                return true;
+        }
+    };
+    for (uint64_t c = 0; c < n_cell; ++c) {
+        const uint32_t kind = cell[c] >> 30, pay = cell[c] & kPayloadMask;
+        if (kind == 3)
+            return bad("coarse word " + std::to_string(c) + " of unknown kind");
+        if (kind == kCellInsideOne && pay >= P)
+            return bad("coarse word " + std::to_string(c) + " names polygon " + std::to_string(pay));
+        if (kind == kCellSub && pay >= n_blocks)
+            return bad("coarse word " + std::to_string(c) + " names fine block " + std::to_string(pay));
+    }
+    for (uint64_t f = 0; f < n_blocks * FF; ++f) {
+        const uint32_t kind = fine[f] >> 30, pay = fine[f] & kPayloadMask;
+        if (kind == 3)
+            return bad("fine word " + std::to_string(f) + " of unknown kind");
+        if (kind == kCellInsideOne && pay >= P)
+            return bad("fine word " + std::to_string(f) + " names polygon " + std::to_string(pay));
+        if (kind == kCellList && !check_list(pay))
+            return false;
+    }
+    return true;
+}
+
 } // namespace spx

@@ -207,6 +207,24 @@ __device__ __forceinline__ uint32_t row_parity(const int4 *__restrict__ e, uint3
     return par;
 }
 
+// Bounds checks of the index walks, compiled in by SPX_BOUNDS_CHECK (a debug
+// build): an offset or id read from the index that points outside its array
+// sets kErrInternal in the error word, and the walk treats the point as in no
+// polygon of that list instead of reading there.  The host reports the word
+// as SPX_EKERNEL.  In the default build the checks compile to nothing.
+__device__ __forceinline__ bool in_bounds(bool ok, const IndexView &ix)
+{
+#ifdef SPX_BOUNDS_CHECK
+    if (!ok)
+        atomicOr(ix.err, kErrInternal);
+    return ok;
+#else
+    (void)ok;
+    (void)ix;
+    return true;
+#endif
+}
+
 __device__ __forceinline__ uint32_t coarse_word(const IndexView &ix, uint32_t px, uint32_t py, uint64_t pol)
 {
     return ld_idx(ix.cell + (((py >> ix.sc) << ix.gc) | (px >> ix.sc)), pol);
@@ -215,6 +233,8 @@ __device__ __forceinline__ uint32_t fine_word(const IndexView &ix, uint32_t w, u
                                               uint64_t pol)
 {
     const uint32_t fm = (1u << ix.sb) - 1;
+    if (!in_bounds(((uint64_t)(w & kPayloadMask) + 1) << (2 * ix.sb) <= ix.n_fine, ix))
+        return 0u;
     return ld_idx(ix.fine + (((w & kPayloadMask) << (2 * ix.sb)) | (((py >> ix.sf) & fm) << ix.sb) |
                              ((px >> ix.sf) & fm)),
                   pol);
@@ -269,10 +289,18 @@ __device__ __forceinline__ void walk_entries(const IndexView &ix, const uint4 *e
 {
     constexpr int B = 2;
     for (bool more = true; more; e += B) {
+        if (!in_bounds((uint64_t)(e - ix.ent) + 1 < ix.n_ent, ix))
+            return;
         uint4 en[B];
 #pragma unroll
         for (int k = 0; k < B; ++k)
             en[k] = ld_idx(e + k, pol);
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if ((k == 0 || !(en[0].w & kEntLast)) &&
+                !in_bounds(en[k].x < ix.P && (!(en[k].w & kEntBoundary) || (uint64_t)en[k].y + en[k].z < ix.n_edge),
+                           ix))
+                return;
         // entries of this list among the B: up to and including the first LAST
         uint32_t live = 0;
 #pragma unroll
@@ -324,9 +352,15 @@ template <bool FP32, int RW = 4>
 __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, int px, int py, uint32_t &first,
                                               uint32_t &tests, uint32_t &esc, uint64_t pol)
 {
+    if (!in_bounds((uint64_t)e0 + 1 < ix.n_ent, ix))
+        return 0u;
     const uint4 *e = ix.ent + e0;
     const uint4 en0 = ld_idx(e, pol), en1 = ld_idx(e + 1, pol);
     const bool two = !(en0.w & kEntLast);
+    if (!in_bounds(en0.x < ix.P && (!(en0.w & kEntBoundary) || (uint64_t)en0.y + en0.z < ix.n_edge) &&
+                       (!two || (en1.x < ix.P && (!(en1.w & kEntBoundary) || (uint64_t)en1.y + en1.z < ix.n_edge))),
+                   ix))
+        return 0u;
     const uint32_t n0 = (en0.w & kEntBoundary) ? min(en0.z, 4u) : 0u;
     const uint32_t n1 = (two && (en1.w & kEntBoundary)) ? min(en1.z, 4u) : 0u;
     int4 v0[4], v1[4];
@@ -355,7 +389,11 @@ __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, 
     if (two && !(en1.w & kEntLast)) {
         // three or more polygons share this fine cell (rare)
         for (const uint4 *q = e + 2;; ++q) {
+            if (!in_bounds((uint64_t)(q - ix.ent) < ix.n_ent, ix))
+                break;
             const uint4 en = ld_idx(q, pol);
+            if (!in_bounds(en.x < ix.P && (!(en.w & kEntBoundary) || (uint64_t)en.y + en.z < ix.n_edge), ix))
+                break;
             if (!(en.w & kEntBoundary) || row_parity<FP32>(ix.edge + en.y, en.z, px, py, tests, esc, pol)) {
                 if (!c)
                     first = en.x;
@@ -389,9 +427,18 @@ __device__ __forceinline__ void walk_list_wave(const IndexView &ix, bool has, ui
     const uint4 *e = ix.ent + (has ? e0 : 0u);
     bool more = has;
     while (__any_sync(kFull, more)) {
+        more = more && in_bounds((uint64_t)(e - ix.ent) + 1 < ix.n_ent, ix);
         // two entries (the entry array ends with sentinels: reading e + 1 is in bounds)
-        const uint4 ea = more ? ld_idx(e, pol) : make_uint4(0, 0, 0, kEntLast);
+        uint4 ea = more ? ld_idx(e, pol) : make_uint4(0, 0, 0, kEntLast);
         const uint4 eb0 = more ? ld_idx(e + 1, pol) : make_uint4(0, 0, 0, kEntLast);
+        const bool hb0 = more && !(ea.w & kEntLast);
+        if (more && !in_bounds(ea.x < ix.P && (!(ea.w & kEntBoundary) || (uint64_t)ea.y + ea.z < ix.n_edge) &&
+                                   (!hb0 || (eb0.x < ix.P &&
+                                             (!(eb0.w & kEntBoundary) || (uint64_t)eb0.y + eb0.z < ix.n_edge))),
+                               ix)) {
+            more = false; // this lane's list ends here
+            ea = make_uint4(0, 0, 0, kEntLast);
+        }
         const bool hb = more && !(ea.w & kEntLast);
         const uint4 eb = hb ? eb0 : make_uint4(0, 0, 0, kEntLast);
         const uint32_t za = (more && (ea.w & kEntBoundary)) ? ea.z : 0u;
@@ -777,7 +824,8 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             const uint32_t kind = w[j] >> 30, loc = j * 32 + lane;
-            const bool one = kind == kCellInsideOne, lst = kind == kCellList;
+            const bool one = kind == kCellInsideOne && in_bounds((w[j] & kPayloadMask) < ix.P, ix),
+                       lst = kind == kCellList;
             total += one ? 1u : 0u;
             count1(one, w[j] & kPayloadMask);
             const uint32_t bl = __ballot_sync(kFull, lst);
@@ -964,7 +1012,7 @@ __global__ void __launch_bounds__(THREADS, SUM ? 1 : (TMA ? 6 : kResolveMinBlock
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             const uint32_t kind = w[j] >> 30, loc = j * 32 + lane, pay = w[j] & kPayloadMask;
-            const bool one = kind == kCellInsideOne;
+            const bool one = kind == kCellInsideOne && in_bounds(pay < ix.P, ix);
             total += one ? 1u : 0u;
             if (a.counts) {
                 if (!hist)
@@ -1633,6 +1681,24 @@ cudaError_t launch_scan(unsigned long long *v, uint64_t n, unsigned long long *t
 }
 
 } // namespace
+
+// The bounded wait of pass 1a's bulk-copy staging on a barrier that nothing
+// completes (no copy is issued): after `tries` polls it reports kErrTimeout.
+__global__ void k_wait_check(unsigned *err, uint32_t tries)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0)
+        mbar_init(&bar, 1);
+    __syncwarp();
+    if (!mbar_wait(&bar, 0, tries) && threadIdx.x == 0)
+        atomicOr(err, kErrTimeout);
+}
+
+cudaError_t launch_wait_check(unsigned *err, uint32_t tries, cudaStream_t s)
+{
+    k_wait_check<<<1, 32, 0, s>>>(err, tries);
+    return cudaGetLastError();
+}
 
 uint64_t scan_part_words(uint64_t n) { return scan_partials(n) + 2; }
 cudaError_t launch_exclusive_scan(unsigned long long *v, uint64_t n, unsigned long long *total,

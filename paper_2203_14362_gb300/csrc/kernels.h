@@ -29,6 +29,10 @@ struct IndexView {
     int ssh;              // summary shift: 30 - sg
     int sg;               // summary grid log2
     int use_sum;          // the summary resolves enough of the box to be worth its shared memory
+    // array sizes (sentinels included) and the error word, for the bounds
+    // checks of a build with SPX_BOUNDS_CHECK
+    uint64_t n_fine, n_ent, n_edge;
+    unsigned *err;
 };
 constexpr int kCoverLog2 = 8;
 constexpr int kSumLog2 = 8;
@@ -93,9 +97,8 @@ struct DiskIndexDev {
 int build_disk_index_device(const int4 *disks_host, uint32_t Q, int g, DiskIndexDev &out, cudaError_t &cerr);
 
 // Device status word bits (ORed into the ctx's persistent error word).
-constexpr unsigned kErrTimeout = 1u;   // a bounded wait gave up
-constexpr unsigned kErrInternal = 2u;  // an internal consistency check failed
-constexpr unsigned kErrCopy = 4u;      // a bounded wait for a bulk copy gave up
+constexpr unsigned kErrTimeout = 1u;   // a bounded wait (for a bulk copy) gave up
+constexpr unsigned kErrInternal = 2u;  // a bounds check of an index walk failed (SPX_BOUNDS_CHECK builds)
 
 // Per-ctx device counters, in this order.
 enum { kStatPoints = 0, kStatTests = 1, kStatEscalations = 2, kStatPairs = 3, kStatCount = 4 };
@@ -211,6 +214,10 @@ cudaError_t launch_cluster(const int2 *pts, uint64_t n, int c, void *scratch, in
 cudaError_t launch_gather_stride(const int2 *src, uint64_t n, int2 *dst, uint64_t m, cudaStream_t s);
 
 int device_sm_count();
+
+// One warp waits, at most `tries` polls, on an mbarrier that nothing completes,
+// as pass 1a waits for its bulk copies, and sets kErrTimeout in *err.
+cudaError_t launch_wait_check(unsigned *err, uint32_t tries, cudaStream_t s);
 
 // Exclusive scan of n u64 values in place on stream s; *total (device, or
 // null) gets their sum.  part: scan_part_words(n) u64 of scratch.

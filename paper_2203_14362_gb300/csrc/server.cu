@@ -199,6 +199,7 @@ void spx_server::start_batch(Slot &sl)
         Req *r = sl.batch[0];
         JoinLaunch a{};
         a.ix = data.ix[r->rq.index];
+        a.ix.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
         a.pts = data.pts;
         a.n = data.n;
         a.counts = r->counts;
@@ -220,6 +221,7 @@ void spx_server::start_batch(Slot &sl)
         for (uint32_t i = 0; i < K; ++i) {
             const Req *r = sl.batch[i];
             m.ix[i] = data.ix[r->rq.index];
+            m.ix[i].err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
             m.fp32 &= data.fp32[r->rq.index];
             m.counts[i] = r->counts;
             m.qbase[i + 1] = m.qbase[i] + (r->counts ? r->P : 0u);
@@ -312,6 +314,7 @@ bool spx_server::admit(Slot &sl)
         Req *r = sl.batch[0];
         JoinLaunch a{};
         a.ix = data.ix[r->rq.index];
+        a.ix.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
         a.pts = data.pts;
         a.n = data.n;
         a.pairs = pairs_of(r);
@@ -333,6 +336,7 @@ bool spx_server::admit(Slot &sl)
         for (int i = 0; i < m.K; ++i) {
             Req *r = sl.batch[i];
             m.ix[i] = data.ix[r->rq.index];
+            m.ix[i].err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
             m.fp32 &= data.fp32[r->rq.index];
             m.pairs[i] = pairs_of(r);
             m.cap[i] = r->total;

@@ -106,6 +106,16 @@ int default_disk_grid_log2(const int32_t *r, uint32_t Q);
 bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int grid_log2, int sub_log2,
                       int threads, HostIndex &out, std::string &err);
 
+// Bounds check of a polygon index's arrays (sizes in words / entries /
+// edges, sentinels included): every coarse word names a polygon below P or a
+// fine block that exists, every fine word a polygon below P or an entry list
+// that ends with its last entry before the sentinels, every entry a polygon
+// below P and an edge range inside the edges.  The same predicate the
+// kernels apply to each offset they read in a SPX_BOUNDS_CHECK build.
+bool validate_grid_index(const uint32_t *cell, uint64_t n_cell, const uint32_t *fine, uint64_t n_fine,
+                         const uint32_t *ent, uint64_t n_ent, const int32_t *edges, uint64_t n_edge, int g, int sb,
+                         uint32_t P, std::string &err);
+
 // Heuristic coarse grid resolution from the polygon set alone.
 int default_grid_log2(const int32_t *xy, const uint64_t *ring_off, uint32_t P);
 

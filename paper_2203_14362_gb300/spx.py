@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libspx.so")
+# SPX_LIB: load another build of the library (the bounds-checked flavour,
+# libspx_checked.so); there is no fallback when it is missing
+LIB_PATH = os.environ.get("SPX_LIB") or os.path.join(_HERE, "libspx.so")
 
 SPX_OK, SPX_EINVAL, SPX_ENOMEM, SPX_ECUDA, SPX_ECAPACITY, SPX_ETIMEOUT, SPX_EBUSY, SPX_EKERNEL = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {0: "SPX_OK", -1: "SPX_EINVAL", -2: "SPX_ENOMEM", -3: "SPX_ECUDA", -4: "SPX_ECAPACITY",
@@ -28,7 +30,8 @@ EXPORTS = [
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
     "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
     "spx_build_disk_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free",
-    "spx_build_disk_index_device", "spx_disk_index_arrays", "spx_build_index_device", "spx_index_arrays",
+    "spx_build_disk_index_device", "spx_disk_index_arrays", "spx_build_index_device", "spx_index_arrays", "spx_host_index_validate",
+    "spx_check_bounded_wait",
 ]
 
 SPX_REQ_SELECT, SPX_REQ_JOIN = 1, 2
@@ -144,6 +147,8 @@ def load(path: str = LIB_PATH):
         "spx_disk_index_arrays": ([V, U64, V, V, P64], I),
         "spx_build_index_device": ([V, U64, C.POINTER(IndexParams), C.POINTER(U64)], I),
         "spx_index_arrays": ([V, U64, V, V, V, V, P64], I),
+        "spx_check_bounded_wait": ([V, U32, V], I),
+        "spx_host_index_validate": ([V, U64, V, U64, V, U64, V, U64, I, I, U32, C.c_char_p, U64], I),
         "spx_aggregate_host": ([V, V, U64, U64, V], I),
         "spx_set_host_streaming": ([V, I, I], I),
         "spx_points_info": ([V, U64, C.POINTER(V), P64, C.POINTER(I)], I),
@@ -193,6 +198,21 @@ def host_index(verts: np.ndarray, ring_off: np.ndarray, grid_log2: int = 0, sub_
     finally:
         lib.spx_host_index_free(h)
     return {"coarse": coarse, "fine": fine, "entries": ent, "edges": edges, "g": int(sizes[4]), "sub": int(sizes[5])}
+
+
+def validate_index(ix: dict, n_polys: int):
+    """spx_host_index_validate on a host_index dict: (True, "") or (False, the
+    first violation)."""
+    lib = load()
+    coarse = np.ascontiguousarray(ix["coarse"], np.uint32)
+    fine = np.ascontiguousarray(ix["fine"], np.uint32)
+    ent = np.ascontiguousarray(ix["entries"], np.uint32).reshape(-1, 4)
+    edges = np.ascontiguousarray(ix["edges"], np.int32).reshape(-1, 4)
+    msg = C.create_string_buffer(256)
+    st = lib.spx_host_index_validate(_np_ptr(coarse), coarse.shape[0], _np_ptr(fine), fine.shape[0], _np_ptr(ent),
+                                     ent.shape[0], _np_ptr(edges), edges.shape[0], ix["g"], ix["sub"], n_polys, msg,
+                                     256)
+    return st == SPX_OK, msg.value.decode()
 
 
 def host_disk_index(centers: np.ndarray, radii: np.ndarray, grid_log2: int = 0):
@@ -413,6 +433,11 @@ class Engine:
 
     def set_host_streaming(self, mode: int = 0, slice_log2: int = 0):
         self._check(self.lib.spx_set_host_streaming(self.ctx, mode, slice_log2), "spx_set_host_streaming")
+
+    def check_bounded_wait(self, tries: int = 1000, stream=None) -> int:
+        """spx_check_bounded_wait: the status of a bounded wait that runs out
+        (SPX_ETIMEOUT expected)."""
+        return self.lib.spx_check_bounded_wait(self.ctx, tries, _stream(stream))
 
     def set_phase_timing(self, on: bool):
         self._check(self.lib.spx_set_phase_timing(self.ctx, 1 if on else 0), "spx_set_phase_timing")
