@@ -742,13 +742,13 @@ def count_measure(args, world, rank, local, torch, steps, warmup, n_override, e2
     else:
         ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32), sub_log2=args.sub)
     info = eng.index_info(ih)
-    if not dist:
-        # the same index built on the device (the second build: the first loads the kernels)
-        for _ in range(2):
-            ih_dev = eng.build_index(gh, grid_log2=info["grid_log2"], fp32_filter=bool(args.fp32),
-                                     sub_log2=info["sub_log2"], on_device=True)
-            device_build_ms = eng.index_info(ih_dev)["build_ms"]
-            eng.free(ih_dev)
+    # the same index built on the device (the second build: the first loads the kernels)
+    device_build_ms = None
+    for _ in range(2):
+        ih_dev = eng.build_index(gh, grid_log2=info["grid_log2"], fp32_filter=bool(args.fp32),
+                                 sub_log2=info["sub_log2"], on_device=True)
+        device_build_ms = eng.index_info(ih_dev)["build_ms"]
+        eng.free(ih_dev)
     counts = torch.zeros(P, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
     eng.aggregate(ph, ih, counts, stream=stream)
@@ -853,7 +853,7 @@ def count_measure(args, world, rank, local, torch, steps, warmup, n_override, e2
                    "points_per_gpu": N, "polygons": P, "vertices": int(v.shape[0]),
                    "grid_log2": info["grid_log2"], "sub_log2": info["sub_log2"],
                    "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": idx_bytes,
-                   "generation_s": round(gen_s, 1), "autotune": tune, "clustered_table": cluster,
+                   "index_build_on_device_ms": round(device_build_ms, 2), "generation_s": round(gen_s, 1), "autotune": tune, "clustered_table": cluster,
                    "checks": "sum(counts) == N; counts of the first %d points == oracle" % m,
                    "counting": "global atomics (P > shared-memory histogram)" if P > 11776 else "shared memory",
                    "edge_tests_per_point": st["edge_tests"] / max(st["points_scanned"], 1),
@@ -896,13 +896,13 @@ def select_measure(args, world, rank, local, torch, steps, warmup, n_override):
     else:
         ih = eng.build_index(gh, grid_log2=args.grid, fp32_filter=bool(args.fp32), sub_log2=args.sub)
     info = eng.index_info(ih)
-    if not dist:
-        # the same index built on the device (the second build: the first loads the kernels)
-        for _ in range(2):
-            ih_dev = eng.build_index(gh, grid_log2=info["grid_log2"], fp32_filter=bool(args.fp32),
-                                     sub_log2=info["sub_log2"], on_device=True)
-            device_build_ms = eng.index_info(ih_dev)["build_ms"]
-            eng.free(ih_dev)
+    # the same index built on the device (the second build: the first loads the kernels)
+    device_build_ms = None
+    for _ in range(2):
+        ih_dev = eng.build_index(gh, grid_log2=info["grid_log2"], fp32_filter=bool(args.fp32),
+                                 sub_log2=info["sub_log2"], on_device=True)
+        device_build_ms = eng.index_info(ih_dev)["build_ms"]
+        eng.free(ih_dev)
     offs = torch.zeros(Q + 1, dtype=torch.int64, device="cuda")
     probe = torch.empty(1, dtype=torch.int32, device="cuda")
     try:
@@ -942,7 +942,8 @@ def select_measure(args, world, rank, local, torch, steps, warmup, n_override):
                    "sub_log2": info["sub_log2"], "block_summary": bool(info["use_sum"]),
                    "point_query_evals_per_s": world * N * Q / (ms * 1e-3),
                    "launch": "one CUDA graph per step (pass 1a, pass 1b, scan, pass 3, count table, scan, emit)",
-                   "index_build_ms": round(info["build_ms"], 1), "autotune": tune,
+                   "index_build_ms": round(info["build_ms"], 1),
+                   "index_build_on_device_ms": round(device_build_ms, 2), "autotune": tune,
                    "l2": "inputs larger than L2 (4 GB of points); no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",

@@ -747,7 +747,8 @@ __device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
 constexpr int kWItems = SPX_WARP_ITEMS; // points per lane per chunk (8: 256-point chunks)
 constexpr int kWChunk = 32 * kWItems;   // consecutive points per warp chunk
 constexpr int kWQueue = kWChunk;        // list points queued per warp: a whole chunk
-constexpr size_t kWarpSmem = size_t(kWarps) * kWQueue * sizeof(uint4);
+// per warp: the queue, then 64 parity words of walk_list_wave
+constexpr size_t kWarpSmem = size_t(kWarps) * (kWQueue * sizeof(uint4) + 64 * sizeof(uint32_t));
 
 template <bool FP32, bool CLUSTERED>
 __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaunch a, uint32_t nchunks, int use_hist)
@@ -755,6 +756,7 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kWQueue; // (x, y, first entry, chunk index)
+    uint32_t *s_par = reinterpret_cast<uint32_t *>(s_raw + size_t(kWarps) * kWQueue * sizeof(uint4)) + warp * 64;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_raw + kWarpSmem);
     const IndexView &ix = a.ix;
     const uint64_t keep = policy_evict_last();
@@ -804,21 +806,19 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
         auto walk = [&](uint32_t k0, uint32_t m) {
             __syncwarp();
             const bool has = (uint32_t)lane < m;
-            const uint4 it = s_q[k0 + (has ? lane : 0)]; // idle lanes repeat lane 0's walk, uncounted
-            uint32_t f = 0, t_l = 0, e_l = 0;
-            uint32_t c = walk_list<FP32>(ix, it.z, (int)it.x, (int)it.y, f, t_l, e_l, keep);
-            c = has ? c : 0u;
-            n_tests += has ? t_l : 0u;
-            n_esc += has ? e_l : 0u;
+            const uint4 it = s_q[k0 + (has ? lane : 0)]; // idle lanes walk nothing
+            // the warp walks its lanes' lists together; a point's first polygon is
+            // counted with the warp below, any further ones at once
+            uint32_t f = 0, c = 0;
+            walk_list_wave<FP32>(ix, has, it.z, (int)it.x, (int)it.y, n_tests, n_esc, keep, s_par, [&](uint32_t q) {
+                if (c == 0)
+                    f = q;
+                else if (a.counts)
+                    hist ? (void)atomicAdd(s_hist + q, 1u) : (void)atomicAdd(a.counts + q, 1ull);
+                ++c;
+            });
             total += c;
-            count1(c == 1, f);
-            if (c > 1 && a.counts)
-                point_emit<FP32>(ix, (int)it.x, (int)it.y, keep, [&](uint32_t q) {
-                    if (hist)
-                        atomicAdd(s_hist + q, 1u);
-                    else
-                        atomicAdd(a.counts + q, 1ull);
-                });
+            count1(c >= 1, f);
             __syncwarp();
         };
 #pragma unroll
@@ -1247,7 +1247,9 @@ constexpr uint32_t kMPending = 0xffffffffu; // a list point whose walk is queued
 #endif
 constexpr int kMItems = SPX_MULTI_ITEMS;                      // points per lane per chunk
 constexpr int kMChunk = 32 * kMItems;                         // consecutive points per warp chunk
-constexpr size_t kMultiSmem = size_t(kWarps) * kMChunk * (sizeof(uint4) + sizeof(unsigned long long)); // queues
+// queues and offsets, then 64 parity words of walk_list_wave, per warp
+constexpr size_t kMultiSmem =
+    size_t(kWarps) * (kMChunk * (sizeof(uint4) + sizeof(unsigned long long)) + 64 * sizeof(uint32_t));
 
 // Does the cover bitmap let (px, py) reach a non-empty coarse cell?  False for
 // points outside the box.
@@ -1268,6 +1270,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
     uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kMChunk; // (x, y, first entry) -> (count, first)
     unsigned long long *s_o = // emit pass: output offsets of queued points
         reinterpret_cast<unsigned long long *>(s_raw + size_t(kWarps) * kMChunk * sizeof(uint4)) + warp * kMChunk;
+    uint32_t *s_par = reinterpret_cast<uint32_t *>(
+                          s_raw + size_t(kWarps) * kMChunk * (sizeof(uint4) + sizeof(unsigned long long))) +
+                      warp * 64;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_raw + kMultiSmem); // count pass: qbase[K] counters
     const uint64_t keep = policy_evict_last();
     const int K = m.K;
@@ -1323,12 +1328,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
                 qn += __popc(bl);
             }
             __syncwarp();
+            unsigned long long *cnt = m.counts[r];
+            uint32_t *h = s_hist + m.qbase[r];
             for (uint32_t k0 = 0; k0 < qn; k0 += 32) {
                 const bool has = k0 + lane < qn;
-                const uint4 it = s_q[has ? k0 + lane : k0]; // idle lanes repeat the first walk, uncounted
-                uint32_t fq = 0, t_l = 0, e_l = 0;
-                const uint32_t cq = walk_list<FP32>(ix, it.z, (int)it.x, (int)it.y, fq, t_l, e_l, keep);
-                if (!EMIT && has) {
+                const uint4 it = s_q[has ? k0 + lane : k0]; // idle lanes walk nothing
+                // the warp walks its lanes' lists together; the count pass counts a
+                // point's further polygons here, its first one with the warp below
+                uint32_t fq = 0, cq = 0, t_l = 0, e_l = 0;
+                walk_list_wave<FP32>(ix, has, it.z, (int)it.x, (int)it.y, t_l, e_l, keep, s_par, [&](uint32_t q) {
+                    if (cq == 0)
+                        fq = q;
+                    else if (!EMIT && cnt)
+                        use_hist ? (void)atomicAdd(h + q, 1u) : (void)atomicAdd(cnt + q, 1ull);
+                    ++cq;
+                });
+                if (!EMIT) {
                     tests += t_l;
                     esc += e_l;
                 }
@@ -1345,26 +1360,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
                     f[j] = q.y;
                 }
             __syncwarp(); // s_q is rewritten for the next request
-            unsigned long long *cnt = m.counts[r];
             if (!EMIT) {
                 uint32_t total = 0;
-                uint32_t *h = s_hist + m.qbase[r];
 #pragma unroll
                 for (int j = 0; j < kMItems; ++j) {
                     total += c[j];
                     if (!cnt)
                         continue;
+                    // the first polygon of every point in any (further ones were counted by the walk)
                     if (!use_hist) // served tables are in row order: lanes rarely share a counter
-                        global_add_warp(cnt, c[j] == 1, f[j]);
-                    else if (c[j] == 1)
+                        global_add_warp(cnt, c[j] >= 1, f[j]);
+                    else if (c[j] >= 1)
                         atomicAdd(h + f[j], 1u);
-                    if (c[j] > 1)
-                        point_emit<FP32>(ix, p[j].x, p[j].y, keep, [&](uint32_t q) {
-                            if (use_hist)
-                                atomicAdd(h + q, 1u);
-                            else
-                                atomicAdd(cnt + q, 1ull);
-                        });
                 }
                 total = warp_sum32(total);
                 if (lane == 0)
@@ -1404,15 +1411,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
             }
             __syncwarp();
             for (uint32_t k0 = 0; k0 < mq; k0 += 32) {
-                if (k0 + lane < mq) {
-                    const uint4 it = s_q[k0 + lane];
-                    unsigned long long o = s_o[k0 + lane];
-                    point_emit<FP32>(ix, (int)it.x, (int)it.y, keep, [&](uint32_t q) {
-                        if (o < cap)
-                            out[o] = make_uint2(it.z, q);
-                        ++o;
-                    });
-                }
+                // the whole warp walks the queued points' lists together
+                const bool has = k0 + lane < mq;
+                const uint4 it = has ? s_q[k0 + lane] : make_uint4(0u, 0u, 0u, 0u);
+                unsigned long long o = has ? s_o[k0 + lane] : 0ull;
+                const uint32_t w = has ? resolve(ix, it.x, it.y, keep) : 0u;
+                uint32_t t_l = 0, e_l = 0;
+                walk_list_wave<FP32>(ix, (w >> 30) == kCellList, w & kPayloadMask, (int)it.x, (int)it.y, t_l, e_l, keep,
+                                     s_par, [&](uint32_t q) {
+                                         if (o < cap)
+                                             out[o] = make_uint2(it.z, q);
+                                         ++o;
+                                     });
             }
             __syncwarp(); // s_q is rewritten for the next request
         }
@@ -1627,9 +1637,13 @@ cudaError_t launch_pass1(const JoinLaunch &a, uint32_t *pend, cudaStream_t s, cu
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    auto launch = [&](auto kr, int threads, size_t head, bool (&done)[64]) -> cudaError_t {
+    // head: this launch's shared memory before the counters; head_max: the
+    // most any launch of the kernel takes (the opt-in, set once per device,
+    // must cover every later call, whatever its index)
+    auto launch = [&](auto kr, int threads, size_t head, size_t head_max, bool (&done)[64]) -> cudaError_t {
         const size_t smem = head + hsm;
-        cudaError_t err = smem_opt_in(kr, std::min<size_t>(size_t(smem_max), head + sizeof(uint32_t) * kHistMax), done);
+        cudaError_t err =
+            smem_opt_in(kr, std::min<size_t>(size_t(smem_max), head_max + sizeof(uint32_t) * kHistMax), done);
         if (err != cudaSuccess)
             return err;
         const uint32_t nblk = uint32_t((nchunks + threads / 32 - 1) / (threads / 32));
@@ -1641,15 +1655,16 @@ cudaError_t launch_pass1(const JoinLaunch &a, uint32_t *pend, cudaStream_t s, cu
         // beside the summary, shared memory holds one chunk buffer per warp
         // at most, too shallow to hide a bulk copy: L2 prefetches instead
         e = launch(k_resolve<kResolveSumThreads, true, false>, kResolveSumThreads,
-                   resolve_smem_head(WS, true, a.ix.sg, false), done_r[2]);
+                   resolve_smem_head(WS, true, a.ix.sg, false), resolve_smem_head(WS, true, kSumLog2, false),
+                   done_r[2]);
     } else {
+        const size_t head = kTmaPoints ? resolve_smem_head(kWarps, false, 0, true) : 0;
         if (kTmaPoints)
-            e = launch(k_resolve<kThreads, false, true>, kThreads, resolve_smem_head(kWarps, false, 0, true),
-                       done_r[3]);
+            e = launch(k_resolve<kThreads, false, true>, kThreads, head, head, done_r[3]);
         else
-            e = launch(k_resolve<kThreads, false, false>, kThreads, 0, done_r[0]);
+            e = launch(k_resolve<kThreads, false, false>, kThreads, head, head, done_r[0]);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess)
+    if (e != cudaSuccess) // pass 1b must not run on what an earlier call left in the scratch
         return e;
     if (mid)
         cudaEventRecord(mid, s);

@@ -261,3 +261,38 @@ def test_bad_arguments(eng):
         eng.free(gh)  # index still alive
     eng.free(ih)
     eng.free(gh)
+
+
+def test_summary_grows_between_calls_in_a_fresh_process():
+    # pass 1a opts its kernels in to their shared memory once per process and
+    # device; a first join through a small block summary (g = 7, 32 KB) must
+    # not keep a later one through the full 128 KB summary (g = 8 and up)
+    # from launching.  A fresh process fixes the order of the calls.
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import numpy as np, torch
+import oracle
+from paper_2203_14362_gb300 import datagen as g, spx
+eng = spx.Engine(0)
+v, o = g.star_polygons(g.SEED_BASE + 41)
+pts = g.uniform_points(300_001, g.SEED_BASE + 41)
+want_p, want_c = oracle.join_fast(pts, v, o)
+dpts = torch.from_numpy(pts).cuda()
+ph = eng.load_points(dpts)
+gh = eng.load_polygons(v, o)
+for gl, sb in ((7, 1), (8, 1), (11, 3), (5, 2), (9, 2)):
+    ih = eng.build_index(gh, grid_log2=gl, sub_log2=sb)
+    pairs = torch.full((pts.shape[0] + 8, 2), -1, dtype=torch.int32, device="cuda")
+    counts = torch.zeros(256, dtype=torch.int64, device="cuda")
+    n = eng.join(ph, ih, pairs, counts)
+    assert n == want_p.shape[0], (gl, sb, n)
+    assert np.array_equal(pairs[:n].cpu().numpy().view(np.uint32), want_p), (gl, sb)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint64), want_c), (gl, sb)
+    eng.free(ih)
+print("ok")
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
