@@ -90,12 +90,17 @@ spx_status spx_load_points(spx_ctx *ctx, const int32_t *xy, uint64_t n, int xy_i
  * grouped by the cells of a 2^grid_log2 x 2^grid_log2 grid over the box
  * (row-major cell order, points outside the box last; the order within a cell
  * is unspecified).  Consecutive points then share index cells, so a pass over
- * the copy reads the index from cache.  Only spx_aggregate takes a clustered
- * table -- per-polygon counts do not depend on the order of the points; the
- * join, the selection and the server reject it with SPX_EINVAL (their outputs
- * are keyed by row).  grid_log2 in [1, 12], 0 = 12.  Device memory: 8 B per
- * point for the copy, plus 8 B per cell while it is built.  Synchronises the
- * ctx's stream.  Errors: SPX_EINVAL, SPX_ENOMEM, SPX_ECUDA.
+ * the copy reads the index from cache.  The copy keeps its cell directory
+ * (each cell's row range): spx_aggregate through an index whose coarse grid
+ * is no finer than the clustering grid counts every cell that lies in a
+ * coarse cell INSIDE one polygon from its range, without reading its points,
+ * and reads only the points of cells in mixed coarse cells (§5.3: the blocks a
+ * query needs).  Only spx_aggregate takes a clustered table -- per-polygon
+ * counts do not depend on the order of the points; the join, the selection
+ * and the server reject it with SPX_EINVAL (their outputs are keyed by row).
+ * grid_log2 in [1, 13], 0 = 12.  Device memory: 8 B per point for the copy
+ * and 8 B per cell for the directory.  Synchronises the ctx's stream.
+ * Errors: SPX_EINVAL, SPX_ENOMEM, SPX_ECUDA.
  */
 spx_status spx_cluster_points(spx_ctx *ctx, spx_points points, int grid_log2, spx_points *out);
 
@@ -104,7 +109,6 @@ spx_status spx_cluster_points(spx_ctx *ctx, spx_points points, int grid_log2, sp
 spx_status spx_points_info(spx_ctx *ctx, spx_points points, const int32_t **xy_dev, uint64_t *n, int *cluster_log2);
 
 /*
- * Load a polygon set from host memory/*
  * Load a polygon set from host memory (§4.2, polygons are the constraint
  * canvases of selections and joins).  Polygon q is the implicitly closed ring
  * xy[2*ring_off[q] .. 2*ring_off[q+1]) of int32 (x, y) vertices, 0 <= x, y <=
@@ -480,6 +484,8 @@ typedef struct {
     double ms_emit;            /* join pass 3: pairs written in point order */
     double ms_aggregate;       /* count-only aggregate */
     double ms_walk;            /* polygon join pass 1b: exact tests of the points whose cell lists edges */
+    uint64_t points_from_directory; /* of points_scanned, those an aggregate over a clustered table counted
+                                       from its cell directory without reading them */
 } spx_stats_t;
 
 /*

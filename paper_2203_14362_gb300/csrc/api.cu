@@ -41,6 +41,7 @@ struct PointsObj {
     uint64_t n = 0;
     bool owned = false;
     int cluster_log2 = 0; // > 0: a cell-clustered copy (point order is not row order)
+    unsigned long long *cell_end = nullptr; // its directory: end row of every cell, then of the outside bin
 };
 
 struct PolysObj {
@@ -606,9 +607,11 @@ void spx_destroy(spx_ctx *ctx)
     cudaDeviceSynchronize();
     for (auto &kv : ctx->indexes)
         cudaFree(kv.second->mem);
-    for (auto &kv : ctx->points)
+    for (auto &kv : ctx->points) {
         if (kv.second->owned)
             cudaFree(kv.second->dev);
+        cudaFree(kv.second->cell_end);
+    }
     cudaFree(ctx->aux);
     cudaFree(ctx->scratch);
     cudaFree(ctx->st_pts);
@@ -684,8 +687,8 @@ spx_status spx_cluster_points(spx_ctx *ctx, spx_points points, int grid_log2, sp
     if (!src)
         return fail(ctx, SPX_EINVAL, "cluster_points: bad points handle");
     const int c = grid_log2 ? grid_log2 : 12;
-    if (c < 1 || c > 12)
-        return fail(ctx, SPX_EINVAL, "cluster_points: grid_log2 must be in [1, 12] (0 = 12)");
+    if (c < 1 || c > 13)
+        return fail(ctx, SPX_EINVAL, "cluster_points: grid_log2 must be in [1, 13] (0 = 12)");
     auto p = std::make_unique<PointsObj>();
     p->n = src->n;
     p->owned = true;
@@ -697,14 +700,25 @@ spx_status spx_cluster_points(spx_ctx *ctx, spx_points points, int grid_log2, sp
         cudaFree(d);
         return fail(ctx, SPX_ENOMEM, "cluster_points: cudaMalloc of the cell counters failed");
     }
+    const size_t bins = (size_t(1) << (2 * c)) + 1;
+    if (cudaMalloc(reinterpret_cast<void **>(&p->cell_end), bins * 8) != cudaSuccess) {
+        cudaFree(d);
+        cudaFree(scratch);
+        return fail(ctx, SPX_ENOMEM, "cluster_points: cudaMalloc of the cell directory failed");
+    }
     cudaStream_t s = ctx->stream;
-    cudaError_t e = launch_cluster(reinterpret_cast<const int2 *>(src->dev), src->n, c, scratch,
-                                   static_cast<int2 *>(d), s);
+    cudaError_t e = src->n ? cudaSuccess : cudaMemsetAsync(scratch, 0, bins * 8, s);
+    if (e == cudaSuccess)
+        e = launch_cluster(reinterpret_cast<const int2 *>(src->dev), src->n, c, scratch, static_cast<int2 *>(d), s);
+    // after the scatter the counting sort's cursors are the cells' end rows: the directory
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->cell_end, scratch, bins * 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);
     cudaFree(scratch);
     if (e != cudaSuccess) {
         cudaFree(d);
+        cudaFree(p->cell_end);
         return cuda_fail(ctx, e, "cluster_points");
     }
     p->dev = static_cast<int32_t *>(d);
@@ -1334,8 +1348,10 @@ spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint6
     a.stats = ctx->aux->stats;
     a.fp32 = ix->fp32;
     a.clustered = pts->cluster_log2 ? 1 : 0;
+    a.cell_end = pts->cell_end;
+    a.cluster_log2 = pts->cluster_log2;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, 16, s, "aggregate");
+    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, aggregate_scratch_bytes(a), s, "aggregate");
     if (st != SPX_OK)
         return st;
     cudaError_t e = launch_aggregate(a, ctx->scratch, s, ctx->timing ? ctx->ev : nullptr);
@@ -1811,6 +1827,7 @@ spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset)
     out->ms_emit = ctx->ms_emit;
     out->ms_aggregate = ctx->ms_agg;
     out->ms_walk = ctx->ms_walk;
+    out->points_from_directory = v[kStatDirPoints];
     if (reset) {
         SPX_CUDA(cudaMemset(ctx->aux->stats, 0, sizeof(v)), "stats reset");
         ctx->timed_joins = ctx->timed_aggs = 0;
@@ -1892,6 +1909,7 @@ spx_status spx_free(spx_ctx *ctx, uint64_t handle)
             }
         if (p->owned)
             cudaFree(p->dev);
+        cudaFree(p->cell_end);
         ctx->points.erase(handle);
         return SPX_OK;
     }

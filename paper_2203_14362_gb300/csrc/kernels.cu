@@ -147,6 +147,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 constexpr uint32_t kWaitTries = 1u << 22; // polls of a bounded wait before it reports kErrTimeout
+constexpr int kWaveWords = 64; // shared words per warp of walk_list_wave: the parities of two entries per lane
 // Prefetch of the line holding p into L2.
 __device__ __forceinline__ void prefetch_l2(const void *p)
 {
@@ -417,8 +418,9 @@ __device__ __forceinline__ uint32_t walk_list(const IndexView &ix, uint32_t e0, 
 // over the lanes' prefix sums, tests that lane's point, and XORs the crossing
 // into that lane's parity in shared memory.  Lanes never loop on their own
 // long lists (which would diverge and run one dependent load per step); the
-// sorted lists' early stop is not needed, since an edge that ends left of the
-// point never counts.  s_par: 64 words of shared memory owned by this warp.
+// sorted lists' early stop is not used (an edge that ends left of the point
+// counts nothing; recording where each list could stop measured slower).
+// s_par: kWaveWords words of shared memory owned by this warp.
 template <bool FP32, class F>
 __device__ __forceinline__ void walk_list_wave(const IndexView &ix, bool has, uint32_t e0, int px, int py,
                                                uint32_t &tests, uint32_t &esc, uint64_t pol, uint32_t *s_par, F f)
@@ -525,8 +527,17 @@ __device__ __forceinline__ void hist_add_warp(uint32_t *h, bool has, uint32_t q)
 // so a clustered table's lanes do not serialise on the same counter.
 __device__ __forceinline__ void global_add_warp(unsigned long long *cnt, bool has, uint32_t q)
 {
-    if (!__ballot_sync(kFull, has))
+    const uint32_t m = __ballot_sync(kFull, has);
+    if (!m)
         return;
+    // all lanes on one polygon (clustered tables): one atomic, no match
+    const uint32_t qmin = __reduce_min_sync(kFull, has ? q : 0xffffffffu);
+    const uint32_t qmax = __reduce_max_sync(kFull, has ? q : 0u);
+    if (qmin == qmax) {
+        if ((int)(threadIdx.x & 31) == __ffs(m) - 1)
+            atomicAdd(cnt + qmin, (unsigned long long)__popc(m));
+        return;
+    }
     const uint32_t peers = __match_any_sync(kFull, has ? q : 0xffffffffu);
     if (has && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
         atomicAdd(cnt + q, (unsigned long long)__popc(peers));
@@ -747,16 +758,22 @@ __device__ __forceinline__ uint32_t warp_sum32(uint32_t v)
 constexpr int kWItems = SPX_WARP_ITEMS; // points per lane per chunk (8: 256-point chunks)
 constexpr int kWChunk = 32 * kWItems;   // consecutive points per warp chunk
 constexpr int kWQueue = kWChunk;        // list points queued per warp: a whole chunk
-// per warp: the queue, then 64 parity words of walk_list_wave
-constexpr size_t kWarpSmem = size_t(kWarps) * (kWQueue * sizeof(uint4) + 64 * sizeof(uint32_t));
+// per warp: the queue, then the words of walk_list_wave
+constexpr size_t kWarpSmem = size_t(kWarps) * (kWQueue * sizeof(uint4) + kWaveWords * sizeof(uint32_t));
 
-template <bool FP32, bool CLUSTERED>
-__global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaunch a, uint32_t nchunks, int use_hist)
+// With DIR (a cell-clustered table and its directory, the directory grid at
+// least as fine as the coarse grid), k_agg_cells has already counted every
+// point of a coarse cell INSIDE one polygon from the cell's row range, and
+// marked the chunks that hold points of mixed coarse cells: the others are
+// skipped unread, and INSIDE coarse words count nothing here.
+template <bool FP32, bool CLUSTERED, bool DIR = false>
+__global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS)
+    k_warp(JoinLaunch a, uint32_t nchunks, int use_hist, const uint32_t *chunk_mask)
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint4 *s_q = reinterpret_cast<uint4 *>(s_raw) + warp * kWQueue; // (x, y, first entry, chunk index)
-    uint32_t *s_par = reinterpret_cast<uint32_t *>(s_raw + size_t(kWarps) * kWQueue * sizeof(uint4)) + warp * 64;
+    uint32_t *s_par = reinterpret_cast<uint32_t *>(s_raw + size_t(kWarps) * kWQueue * sizeof(uint4)) + warp * kWaveWords;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_raw + kWarpSmem);
     const IndexView &ix = a.ix;
     const uint64_t keep = policy_evict_last();
@@ -779,6 +796,8 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
     };
     const uint32_t nw = gridDim.x * kWarps;
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
+        if (DIR && !((chunk_mask[ch >> 5] >> (ch & 31)) & 1u))
+            continue; // no point of a mixed coarse cell here
         const uint64_t base = (uint64_t)ch * kWChunk;
         const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
         int2 p[kWItems];
@@ -787,13 +806,17 @@ __global__ void __launch_bounds__(kThreads, SPX_WARP_MIN_BLOCKS) k_warp(JoinLaun
         for (int j = 0; j < kWItems; ++j) {
             const uint32_t loc = j * 32 + lane;
             p[j] = loc < npts ? __ldcs(a.pts + base + loc) : make_int2(-1, -1);
-            n_pts += loc < npts ? 1u : 0u;
+            n_pts += (!DIR && loc < npts) ? 1u : 0u;
         }
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             const bool ok = (unsigned)p[j].x < kBox && (unsigned)p[j].y < kBox;
             const uint32_t cw = coarse_word(ix, ok ? (uint32_t)p[j].x : 0u, ok ? (uint32_t)p[j].y : 0u, keep);
             w[j] = ok ? cw : 0u;
+            if (DIR) { // INSIDE and empty coarse cells were counted from the directory
+                n_pts += ok && (cw >> 30) == kCellSub ? 1u : 0u;
+                w[j] = (cw >> 30) == kCellSub ? w[j] : 0u;
+            }
         }
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
@@ -1047,10 +1070,10 @@ template <bool FP32>
 __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a, const uint32_t *pend, uint32_t nwords)
 {
     __shared__ uint32_t s_qa[kWarps * kWalkQueue];
-    __shared__ uint32_t s_pa[kWarps * 64];
+    __shared__ uint32_t s_pa[kWarps * kWaveWords];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *s_q = s_qa + warp * kWalkQueue; // rows
-    uint32_t *s_par = s_pa + warp * 64;
+    uint32_t *s_par = s_pa + warp * kWaveWords;
     const IndexView &ix = a.ix;
     const uint64_t keep = policy_evict_last();
     uint32_t n_tests = 0, n_esc = 0, n_pairs = 0;
@@ -1136,8 +1159,8 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a,
 // walks its queue 32 points at a time afterwards (all lanes busy, as in pass
 // 1), loading the queued points' coordinates then, one independent load per
 // lane, to write their pairs.
-constexpr size_t kEmitSmem =
-    size_t(kWarps) * kWChunk * (sizeof(uint32_t) + sizeof(unsigned long long)) + size_t(kWarps) * 64 * sizeof(uint32_t);
+constexpr size_t kEmitSmem = size_t(kWarps) * kWChunk * (sizeof(uint32_t) + sizeof(unsigned long long)) +
+                             size_t(kWarps) * kWaveWords * sizeof(uint32_t);
 
 template <bool FP32>
 __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsigned long long *chunk_off,
@@ -1150,7 +1173,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
                     warp * kWChunk; // rows within the chunk
     uint32_t *s_par = reinterpret_cast<uint32_t *>(s_raw + size_t(kWarps) * kWChunk *
                                                                (sizeof(unsigned long long) + sizeof(uint32_t))) +
-                      warp * 64; // parities of walk_list_wave
+                      warp * kWaveWords; // words of walk_list_wave
     const uint64_t keep = policy_evict_last();
     const uint32_t nw = gridDim.x * kWarps;
     for (uint32_t ch = blockIdx.x * kWarps + warp; ch < nchunks; ch += nw) {
@@ -1247,9 +1270,9 @@ constexpr uint32_t kMPending = 0xffffffffu; // a list point whose walk is queued
 #endif
 constexpr int kMItems = SPX_MULTI_ITEMS;                      // points per lane per chunk
 constexpr int kMChunk = 32 * kMItems;                         // consecutive points per warp chunk
-// queues and offsets, then 64 parity words of walk_list_wave, per warp
+// queues and offsets, then the words of walk_list_wave, per warp
 constexpr size_t kMultiSmem =
-    size_t(kWarps) * (kMChunk * (sizeof(uint4) + sizeof(unsigned long long)) + 64 * sizeof(uint32_t));
+    size_t(kWarps) * (kMChunk * (sizeof(uint4) + sizeof(unsigned long long)) + kWaveWords * sizeof(uint32_t));
 
 // Does the cover bitmap let (px, py) reach a non-empty coarse cell?  False for
 // points outside the box.
@@ -1272,7 +1295,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_multi(const __grid_constant__ M
         reinterpret_cast<unsigned long long *>(s_raw + size_t(kWarps) * kMChunk * sizeof(uint4)) + warp * kMChunk;
     uint32_t *s_par = reinterpret_cast<uint32_t *>(
                           s_raw + size_t(kWarps) * kMChunk * (sizeof(uint4) + sizeof(unsigned long long))) +
-                      warp * 64;
+                      warp * kWaveWords;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_raw + kMultiSmem); // count pass: qbase[K] counters
     const uint64_t keep = policy_evict_last();
     const int K = m.K;
@@ -1601,21 +1624,81 @@ int persistent_grid(K kernel, int threads, size_t smem, uint32_t ntiles)
     return grid;
 }
 
-template <bool FP32, bool CLUSTERED>
-cudaError_t launch_warp_kernel(const JoinLaunch &a, int use_hist, cudaStream_t s)
+template <bool FP32, bool CLUSTERED, bool DIR = false>
+cudaError_t launch_warp_kernel(const JoinLaunch &a, int use_hist, cudaStream_t s, const uint32_t *chunk_mask = nullptr)
 {
     static bool done[64] = {};
     const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
     if (nchunks >= (1ull << 32))
         return cudaErrorInvalidValue;
     const size_t smem = kWarpSmem + (use_hist ? sizeof(uint32_t) * a.ix.P : 0);
-    auto kern = k_warp<FP32, CLUSTERED>;
+    auto kern = k_warp<FP32, CLUSTERED, DIR>;
     cudaError_t e = smem_opt_in(kern, kWarpSmem + sizeof(uint32_t) * kHistMax, done);
     if (e != cudaSuccess)
         return e;
     const uint32_t nblk = uint32_t((nchunks + kWarps - 1) / kWarps);
-    kern<<<persistent_grid(kern, kThreads, smem, nblk), kThreads, smem, s>>>(a, uint32_t(nchunks), use_hist);
+    kern<<<persistent_grid(kern, kThreads, smem, nblk), kThreads, smem, s>>>(a, uint32_t(nchunks), use_hist,
+                                                                             chunk_mask);
     return cudaGetLastError();
+}
+
+// The directory stage of the count aggregate over a cell-clustered table:
+// a thread per cell of the directory grid (2^c, c >= g).  A cell inside a
+// coarse cell INSIDE one polygon adds its whole row range to that polygon
+// (its points need not be read); an empty one adds nothing; one in a mixed
+// coarse cell marks the 256-point chunks its range touches, for k_warp<DIR>.
+// The points of the cells counted here, and of the bin outside the box, go
+// into the scanned-points counter.
+__global__ void __launch_bounds__(256) k_agg_cells(const unsigned long long *cell_end, int c, IndexView ix,
+                                                   unsigned long long *counts, uint32_t *chunk_mask,
+                                                   unsigned long long *stats)
+{
+    const uint32_t ncell = 1u << (2 * c);
+    const int sh = c - ix.gc;
+    unsigned long long done_pts = 0;
+    for (uint32_t k0 = blockIdx.x * 256 + (threadIdx.x & ~31u); k0 < ncell; k0 += gridDim.x * 256) {
+        const uint32_t k = k0 + (threadIdx.x & 31);
+        const bool in = k < ncell;
+        const unsigned long long s0 = in && k ? cell_end[k - 1] : 0ull, s1 = in ? cell_end[k] : 0ull;
+        const bool has = s1 > s0;
+        uint32_t w = 0;
+        if (has) {
+            const uint32_t cx = k & ((1u << c) - 1), cy = k >> c;
+            w = ix.cell[((cy >> sh) << ix.gc) | (cx >> sh)];
+        }
+        const uint32_t kind = w >> 30, q = w & kPayloadMask;
+        const bool one = has && kind == kCellInsideOne && in_bounds(q < ix.P, ix);
+        done_pts += has && kind != kCellSub ? s1 - s0 : 0ull;
+        // counts: one atomic for the warp when its cells share the polygon
+        const uint32_t m = __ballot_sync(kFull, one);
+        if (m) {
+            const uint32_t qmin = __reduce_min_sync(kFull, one ? q : 0xffffffffu);
+            const uint32_t qmax = __reduce_max_sync(kFull, one ? q : 0u);
+            if (qmin == qmax) {
+                const unsigned long long t = warp_sum64(one ? s1 - s0 : 0ull);
+                if ((int)(threadIdx.x & 31) == __ffs(m) - 1)
+                    atomicAdd(counts + qmin, t);
+            } else if (one) {
+                atomicAdd(counts + q, s1 - s0);
+            }
+        }
+        if (has && kind == kCellSub) {
+            const uint64_t c0 = s0 / kWChunk, c1 = (s1 - 1) / kWChunk;
+            for (uint64_t wd = c0 >> 5; wd <= (c1 >> 5); ++wd) {
+                const uint64_t lo = max(c0, wd << 5), hi = min(c1, (wd << 5) + 31);
+                const uint32_t bits = (hi - lo == 31) ? 0xffffffffu : (((1u << (hi - lo + 1)) - 1u) << (lo & 31));
+                atomicOr(chunk_mask + wd, bits);
+            }
+        }
+    }
+    // the bin of points outside the box: in no polygon
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        done_pts += cell_end[ncell] - cell_end[ncell - 1];
+    done_pts = warp_sum64(done_pts);
+    if ((threadIdx.x & 31) == 0 && done_pts) {
+        atomicAdd(stats + kStatPoints, done_pts);
+        atomicAdd(stats + kStatDirPoints, done_pts);
+    }
 }
 
 // Pass 1 of the join (1a resolve, 1b walk).  pend: 8 words per chunk (the
@@ -2411,7 +2494,7 @@ size_t cluster_scratch_bytes(int c)
 
 cudaError_t launch_cluster(const int2 *pts, uint64_t n, int c, void *scratch, int2 *out, cudaStream_t s)
 {
-    if (c < 1 || c > 12)
+    if (c < 1 || c > 13)
         return cudaErrorInvalidValue;
     if (n == 0)
         return cudaSuccess;
@@ -2553,9 +2636,19 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cuda
     return cudaSuccess;
 }
 
+static bool use_directory(const JoinLaunch &a)
+{
+    return a.clustered && a.cell_end && a.cluster_log2 >= a.ix.gc && a.cluster_log2 <= 13;
+}
+
+size_t aggregate_scratch_bytes(const JoinLaunch &a)
+{
+    const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
+    return use_directory(a) ? size_t((nchunks + 31) / 32) * 4 + 16 : 16;
+}
+
 cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
 {
-    (void)scratch;
     cudaError_t e = cudaSuccess;
     if (!a.keep_counts)
         e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * (a.ix.P ? a.ix.P : 1), s);
@@ -2566,7 +2659,20 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
     const int use_hist = a.ix.P <= (uint32_t)kHistMax ? 1 : 0;
     if (ev)
         cudaEventRecord(ev[0], s);
-    if (a.clustered)
+    if (use_directory(a)) {
+        // cells INSIDE one polygon counted from the directory, then the chunks of mixed cells
+        uint32_t *mask = static_cast<uint32_t *>(scratch);
+        const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
+        if ((e = cudaMemsetAsync(mask, 0, size_t((nchunks + 31) / 32) * 4, s)) != cudaSuccess)
+            return e;
+        const uint64_t ncell = uint64_t(1) << (2 * a.cluster_log2);
+        const unsigned grid = unsigned(std::min<uint64_t>((ncell + 255) / 256, uint64_t(device_sm_count()) * 16));
+        k_agg_cells<<<grid, 256, 0, s>>>(a.cell_end, a.cluster_log2, a.ix, a.counts, mask, a.stats);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        e = a.fp32 ? launch_warp_kernel<true, true, true>(a, use_hist, s, mask)
+                   : launch_warp_kernel<false, true, true>(a, use_hist, s, mask);
+    } else if (a.clustered)
         e = a.fp32 ? launch_warp_kernel<true, true>(a, use_hist, s) : launch_warp_kernel<false, true>(a, use_hist, s);
     else
         e = a.fp32 ? launch_warp_kernel<true, false>(a, use_hist, s) : launch_warp_kernel<false, false>(a, use_hist, s);

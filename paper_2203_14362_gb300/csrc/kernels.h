@@ -101,7 +101,7 @@ constexpr unsigned kErrTimeout = 1u;   // a bounded wait (for a bulk copy) gave 
 constexpr unsigned kErrInternal = 2u;  // a bounds check of an index walk failed (SPX_BOUNDS_CHECK builds)
 
 // Per-ctx device counters, in this order.
-enum { kStatPoints = 0, kStatTests = 1, kStatEscalations = 2, kStatPairs = 3, kStatCount = 4 };
+enum { kStatPoints = 0, kStatTests = 1, kStatEscalations = 2, kStatPairs = 3, kStatDirPoints = 4, kStatCount = 5 };
 
 struct JoinLaunch {
     IndexView ix;
@@ -123,6 +123,11 @@ struct JoinLaunch {
     int keep_counts;
     const unsigned long long *pair_base;
     int clustered;  // the points are grouped by cell: lanes of a warp mostly share a polygon
+    // count aggregate over a cell-clustered table with its directory (cell k's
+    // points are rows [k ? cell_end[k - 1] : 0, cell_end[k]) of a 2^cluster_log2
+    // grid, then one bin of points outside the box); used when cluster_log2 >= g
+    const unsigned long long *cell_end;
+    int cluster_log2;
 };
 
 // Scratch bytes the join needs for n points (per-point results, tile totals, counter).
@@ -134,8 +139,10 @@ size_t plain_scratch_bytes(uint64_t n);
 // (walk), after pass 2 (scan) and after pass 3 (emit).
 cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s);
-// scratch: unused (may be null).  a.keep_counts: add to the counts instead of
+// scratch: aggregate_scratch_bytes(a) bytes (the chunk bitmap of the directory
+// path; unused otherwise).  a.keep_counts: add to the counts instead of
 // zeroing them first.
+size_t aggregate_scratch_bytes(const JoinLaunch &a);
 cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // Batched selection: per-query ascending point-id lists in ids (cap entries),
@@ -205,7 +212,7 @@ cudaError_t launch_sum_u64(unsigned long long *dst, const unsigned long long *x,
                            cudaStream_t s);
 
 // Copy of n points grouped by the cells of a 2^c x 2^c grid (row-major cells,
-// points outside the box last; order within a cell unspecified), c in 1..12.
+// points outside the box last; order within a cell unspecified), c in 1..13.
 // scratch: cluster_scratch_bytes(c).
 size_t cluster_scratch_bytes(int c);
 cudaError_t launch_cluster(const int2 *pts, uint64_t n, int c, void *scratch, int2 *out, cudaStream_t s);

@@ -92,7 +92,7 @@ class Stats(C.Structure):
                 ("fp32_escalations", C.c_uint64), ("pairs_emitted", C.c_uint64),
                 ("timed_joins", C.c_uint64), ("timed_aggregates", C.c_uint64),
                 ("ms_resolve", C.c_double), ("ms_scan", C.c_double), ("ms_emit", C.c_double),
-                ("ms_aggregate", C.c_double), ("ms_walk", C.c_double)]
+                ("ms_aggregate", C.c_double), ("ms_walk", C.c_double), ("points_from_directory", C.c_uint64)]
 
 
 _lib = None

@@ -110,7 +110,7 @@ def test_cluster_refused_where_row_order_matters(eng):
         with pytest.raises(spx.SpxError):
             spx.Server(eng, ch, [ih])
         with pytest.raises(spx.SpxError):
-            eng.cluster_points(ph, 13)
+            eng.cluster_points(ph, 14)
         # an empty table clusters to an empty table
         e0 = eng.load_points(np.zeros((0, 2), np.int32))
         e1 = eng.cluster_points(e0, 5)
@@ -122,3 +122,43 @@ def test_cluster_refused_where_row_order_matters(eng):
         eng.free(gh)
         eng.free(ch)
         eng.free(ph)
+
+
+@pytest.mark.parametrize("c,gl", [(13, 13), (13, 11), (12, 12), (12, 9), (10, 6), (8, 8), (6, 9)])
+def test_aggregate_through_the_cell_directory(eng, c, gl):
+    # with the clustering grid at least as fine as the coarse grid (c >= g),
+    # cells in coarse cells INSIDE one polygon are counted from the directory
+    # without reading their points; the result must stay the oracle's, and
+    # every point must be accounted as scanned once (c < g: the plain path)
+    seed = g.SEED_BASE + 72
+    mix = g.make_mixture(seed)
+    pts = g.mixture_points(2_000_003, seed, mix)
+    bad = np.array([[-1, 5], [1 << 30, 7], [3, -2]], np.int32)
+    pts = np.concatenate([bad, pts])
+    cases = [g.quad_tessellation(12, 10, seed, kmin=4, kmax=80), g.star_polygons(seed)]
+    for case in cases:
+        v, o = (case.verts, case.ring_off) if hasattr(case, "verts") else case
+        P = o.shape[0] - 1
+        ref = oracle.Prepared(v, o)
+        want = ref.counts(pts)
+        ref.close()
+        dpts = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+        ph = eng.load_points(dpts)
+        ch = eng.cluster_points(ph, c)
+        gh = eng.load_polygons(v, o)
+        try:
+            for fp32 in (True, False):
+                ih = eng.build_index(gh, grid_log2=gl, fp32_filter=fp32)
+                counts = torch.full((P,), 5, dtype=torch.int64, device="cuda")
+                eng.stats(reset=True)
+                eng.aggregate(ch, ih, counts)
+                torch.cuda.synchronize()
+                st = eng.stats(reset=True)
+                assert np.array_equal(counts.cpu().numpy().view(np.uint64), want), (c, gl, fp32)
+                assert st["points_scanned"] == pts.shape[0]
+                eng.free(ih)
+        finally:
+            eng.free(gh)
+            eng.free(ch)
+            eng.free(ph)
+            del dpts
