@@ -36,11 +36,13 @@ METRIC = "billion points joined/sec and % HBM roofline; serving p50/p99 ms vs pl
 UNIT = "Gpoints/s"
 L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per point of the polygon join's kernels from one
-# ncu capture of a 20M-point run of the default workload, scaled per point;
-# only valid for those kernel versions, the default index (g = 11, sub = 3)
-# and the default workload.  None: not captured for the current kernels.
-RESOLVE_TRAFFIC_BYTES_PER_POINT = {"k_resolve": (233.052672e6 + 55.362304e6) / 20e6,
-                                   "k_wemit": (80.704512e6 + 101.007616e6) / 20e6}
+# ncu capture of a 20M-point run of the default workload (16-bit per-point
+# results), scaled per point, keyed by the index's (grid_log2, sub_log2); only
+# valid for those kernel versions and the default workload.  A missing entry:
+# not captured.
+RESOLVE_TRAFFIC_BYTES_PER_POINT = {(12, 3): {"k_resolve": (270.569984e6 + 31.558656e6) / 20e6,
+                                             "k_walk": (62.566400e6 + 1.213952e6) / 20e6,
+                                             "k_wemit": (43.176960e6 + 98.720000e6) / 20e6}}
 # The same for the distance join's pass 1 (k_dwarp<resolve>), from one capture
 # of a 20M-point run of the 1024-disk workload at its default grid (g = 12).
 DISK_RESOLVE_TRAFFIC_BYTES_PER_POINT = (167.498496e6 + 25.302784e6) / 20e6
@@ -472,8 +474,8 @@ def run_spx(args, world, rank, local):
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = args.traffic
     if (traffic is None and not args.plain and not dist and args.workload == "tess2000_100m"
-            and (info["grid_log2"], info["sub_log2"]) == (11, 3)):
-        per_pt = RESOLVE_TRAFFIC_BYTES_PER_POINT.get(dom.split(" ")[0])
+            and (info["grid_log2"], info["sub_log2"]) in RESOLVE_TRAFFIC_BYTES_PER_POINT):
+        per_pt = RESOLVE_TRAFFIC_BYTES_PER_POINT[(info["grid_log2"], info["sub_log2"])].get(dom.split(" ")[0])
         traffic = None if per_pt is None else per_pt * N
     if traffic is None and dist and info["grid_log2"] == 12 and dom.startswith("k_dwarp"):
         traffic = DISK_RESOLVE_TRAFFIC_BYTES_PER_POINT * N

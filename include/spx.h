@@ -121,7 +121,8 @@ spx_status spx_load_polygons(spx_ctx *ctx, const int32_t *xy, const uint64_t *ri
 
 /* Grid-index parameters (§4.3 canvas indexes; §5.3 grid cell size; §7 tuning). */
 typedef struct {
-    int grid_log2;   /* coarse grid of 2^grid_log2 cells per side, 1..13; 0 = choose automatically */
+    int grid_log2;   /* coarse grid of 2^grid_log2 cells per side, 1..13; 0 = choose automatically
+                        (about 80 cells across the median polygon bounding box, clamped to 5..13) */
     int fp32_filter; /* 1: orientation in FP32 with exact int64 redo inside the error bound; 0: int64 only */
     int sub_log2;    /* a coarse cell cut by a polygon boundary is split into 2^sub_log2 x 2^sub_log2
                         fine cells, 1..3 (grid_log2 + sub_log2 <= 16); 0 = default (3) */

@@ -335,10 +335,13 @@ int default_grid_log2(const int32_t *xy, const uint64_t *ring_off, uint32_t P)
         return 6;
     std::nth_element(side.begin(), side.begin() + side.size() / 2, side.end());
     const double med = side[side.size() / 2];
-    // about 40 coarse cells across a typical polygon: then a point meets a
+    // about 80 coarse cells across a typical polygon: then a point meets a
     // boundary-cut coarse cell rarely and a listed fine cell more rarely still
-    int g = int(std::lround(std::log2(40.0 / std::max(med, 1e-9))));
-    return std::min(std::max(g, 5), 12);
+    // (the join's streaming pass reads most coarse words from the block
+    // summary in shared memory, so a larger coarse level costs little, while
+    // shorter fine-row edge lists shorten the exact tests)
+    int g = int(std::lround(std::log2(80.0 / std::max(med, 1e-9))));
+    return std::min(std::max(g, 5), kMaxGridLog2);
 }
 
 bool build_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int g, int sb, int threads,

@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace spx {
@@ -57,6 +58,13 @@ __host__ __device__ constexpr uint32_t res_encode(uint32_t cnt, uint32_t first)
                                : (cnt <= 1022u && first < (1u << 20)) ? (kResMulti | kResCount | (cnt << 20) | first)
                                                                       : (kResMulti | first);
 }
+// The narrow form (2 bytes; at most kRes16MaxP polygons), with the row bitmap
+// of pass 1 as pass 1b leaves it (a row's bit stays set iff the point is in
+// two or more polygons):
+//   bit clear: kRes16None (in no polygon) or q (in exactly polygon q)
+//   bit set:   c, the number of polygons (2 <= c <= P); the pairs are written
+//              by walking the point's list again
+constexpr uint16_t kRes16None = 0xffffu;
 constexpr int kHistMax = 11776;             // polygons counted in shared memory (46 KB)
 
 
@@ -938,7 +946,7 @@ __host__ __device__ constexpr size_t resolve_smem_head(int warps, bool sum, int 
 // from there: the points arrive while the chunk is resolved, and their loads
 // cost the L1 nothing.  A warp's last chunk, when it is not full, is loaded
 // with plain loads.
-template <int THREADS, bool SUM, bool TMA>
+template <int THREADS, bool SUM, bool TMA, bool R16>
 __global__ void __launch_bounds__(THREADS, SUM ? 1 : (TMA ? 6 : kResolveMinBlocks))
     k_resolve(const __grid_constant__ JoinLaunch a, uint32_t *pend, uint32_t nchunks, int use_hist)
 {
@@ -980,6 +988,7 @@ __global__ void __launch_bounds__(THREADS, SUM ? 1 : (TMA ? 6 : kResolveMinBlock
         const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
         const int2 *pts = a.pts + base;
         uint32_t *res = a.res + base;
+        uint16_t *res16 = reinterpret_cast<uint16_t *>(a.res) + base;
         int2 p[kWItems];
         uint32_t w[kWItems];
         if (TMA && npts == kWChunk) {
@@ -1043,9 +1052,15 @@ __global__ void __launch_bounds__(THREADS, SUM ? 1 : (TMA ? 6 : kResolveMinBlock
                 else if (one)
                     atomicAdd(s_hist + pay, 1u);
             }
-            // one: the polygon; list: its first entry (rewritten by pass 1b); empty: none
-            if (loc < npts)
-                __stcg(res + loc, kind == kCellEmpty ? kResNone : pay);
+            // one: the polygon; list: its first entry (narrow: none; rewritten
+            // by pass 1b); empty: none
+            if (loc < npts) {
+                if (R16)
+                    __stcg(reinterpret_cast<unsigned short *>(res16 + loc),
+                           (unsigned short)(kind == kCellInsideOne ? pay : kRes16None));
+                else
+                    __stcg(res + loc, kind == kCellEmpty ? kResNone : pay);
+            }
             const uint32_t bl = __ballot_sync(kFull, kind == kCellList);
             mask = lane == j ? bl : mask;
         }
@@ -1066,8 +1081,8 @@ __global__ void __launch_bounds__(THREADS, SUM ? 1 : (TMA ? 6 : kResolveMinBlock
     add_stats(a.stats, n_pts, 0u, 0u, n_pairs);
 }
 
-template <bool FP32>
-__global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a, const uint32_t *pend, uint32_t nwords)
+template <bool FP32, bool R16>
+__global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a, uint32_t *pend, uint32_t nwords)
 {
     __shared__ uint32_t s_qa[kWarps * kWalkQueue];
     __shared__ uint32_t s_pa[kWarps * kWaveWords];
@@ -1083,9 +1098,19 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a,
         const bool has = (uint32_t)lane < m;
         const uint32_t row = s_q[has ? lane : 0]; // idle lanes load lane 0's row and walk nothing
         const int2 p = a.pts[row];
-        const uint32_t e0 = __ldcg(a.res + row);
+        // the list's first entry: stored by pass 1a, or (narrow results) the
+        // cell resolved again
+        uint32_t e0;
+        bool lst = has;
+        if (R16) {
+            const uint32_t w = resolve(ix, (uint32_t)p.x, (uint32_t)p.y, keep); // a marked row's point is in the box
+            e0 = w & kPayloadMask;
+            lst = has && in_bounds((w >> 30) == kCellList, ix);
+        } else {
+            e0 = __ldcg(a.res + row);
+        }
         uint32_t f = 0, c = 0;
-        walk_list_wave<FP32>(ix, has, e0, p.x, p.y, n_tests, n_esc, keep, s_par, [&](uint32_t q) {
+        walk_list_wave<FP32>(ix, lst, e0, p.x, p.y, n_tests, n_esc, keep, s_par, [&](uint32_t q) {
             f = c ? f : q;
             ++c;
             if (a.counts)
@@ -1093,7 +1118,16 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a,
         });
         n_pairs += c;
         if (has) {
-            __stcg(a.res + row, res_encode(c, f));
+            if (R16) {
+                __stcg(reinterpret_cast<unsigned short *>(a.res) + row,
+                       (unsigned short)(c == 0 ? kRes16None : c == 1 ? f : c));
+                // the row's bit stays set iff the point is in several polygons;
+                // only this warp reads or writes the bitmap words of its range
+                if (c < 2)
+                    atomicAnd(pend + (row >> 5), ~(1u << (row & 31)));
+            } else {
+                __stcg(a.res + row, res_encode(c, f));
+            }
             if (c)
                 atomicAdd(a.tile_tot + row / kWChunk, (unsigned long long)c);
         }
@@ -1162,9 +1196,9 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a,
 constexpr size_t kEmitSmem = size_t(kWarps) * kWChunk * (sizeof(uint32_t) + sizeof(unsigned long long)) +
                              size_t(kWarps) * kWaveWords * sizeof(uint32_t);
 
-template <bool FP32>
+template <bool FP32, bool R16>
 __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsigned long long *chunk_off,
-                                                       uint32_t nchunks)
+                                                       uint32_t nchunks, const uint32_t *pend)
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1180,18 +1214,34 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
         const uint64_t base = (uint64_t)ch * kWChunk;
         const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
         unsigned long long run = chunk_off[ch] + (a.pair_base ? *a.pair_base : 0ull);
-        uint32_t res[kWItems];
+        uint32_t res[kWItems], mw = 0;
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
             const uint32_t loc = j * 32 + lane;
-            res[j] = loc < npts ? __ldcs(a.res + base + loc) : kResNone;
+            if (R16) {
+                const uint16_t r = loc < npts ? __ldcs(reinterpret_cast<const unsigned short *>(a.res) + base + loc)
+                                              : kRes16None;
+                res[j] = r == kRes16None ? kResNone : r;
+            } else {
+                res[j] = loc < npts ? __ldcs(a.res + base + loc) : kResNone;
+            }
         }
+        if (R16 && lane < kWItems) // lane j: the bitmap word of round j (rows in several polygons)
+            mw = __ldcs(pend + (uint64_t)ch * kWItems + lane);
         uint32_t qn = 0;
 #pragma unroll
         for (int j = 0; j < kWItems; ++j) {
-            const uint32_t loc = j * 32 + lane, r = res[j];
+            const uint32_t loc = j * 32 + lane;
+            uint32_t r = res[j];
             const uint32_t pid = a.pid0 + (uint32_t)(base + loc);
-            const bool multi = r != kResNone && (r & kResMulti);
+            bool multi;
+            if (R16) {
+                multi = (__shfl_sync(kFull, mw, j) >> lane) & 1u;
+                if (multi) // the count; the polygons come from walking the list again
+                    r = kResMulti | kResCount;
+            } else {
+                multi = r != kResNone && (r & kResMulti);
+            }
             uint32_t c = r == kResNone ? 0u : 1u, pre, tot;
             if (!__any_sync(kFull, multi)) {
                 const uint32_t bl = __ballot_sync(kFull, c != 0);
@@ -1199,7 +1249,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
                 tot = __popc(bl);
             } else {
                 if (multi) {
-                    if (r & kResCount) {
+                    if (R16) {
+                        c = res[j];
+                    } else if (r & kResCount) {
                         c = (r >> 20) & 0x3ffu;
                     } else { // count not stored: count again
                         const int2 p = a.pts[base + loc];
@@ -1707,7 +1759,7 @@ __global__ void __launch_bounds__(256) k_agg_cells(const unsigned long long *cel
 template <bool FP32>
 cudaError_t launch_pass1(const JoinLaunch &a, uint32_t *pend, cudaStream_t s, cudaEvent_t mid)
 {
-    static bool done_r[4][64] = {};
+    static bool done_r[8][64] = {};
     const uint64_t nchunks = (a.n + kWChunk - 1) / kWChunk;
     if (a.n >= (1ull << 32))
         return cudaErrorInvalidValue; // rows are 32-bit
@@ -1734,19 +1786,22 @@ cudaError_t launch_pass1(const JoinLaunch &a, uint32_t *pend, cudaStream_t s, cu
         return cudaGetLastError();
     };
     constexpr int WS = kResolveSumThreads / 32;
-    if (a.ix.use_sum) {
-        // beside the summary, shared memory holds one chunk buffer per warp
-        // at most, too shallow to hide a bulk copy: L2 prefetches instead
-        e = launch(k_resolve<kResolveSumThreads, true, false>, kResolveSumThreads,
-                   resolve_smem_head(WS, true, a.ix.sg, false), resolve_smem_head(WS, true, kSumLog2, false),
-                   done_r[2]);
-    } else {
+    auto pass1a = [&](auto r16) -> cudaError_t {
+        constexpr bool R16 = decltype(r16)::value;
+        bool(*d)[64] = done_r + (R16 ? 4 : 0);
+        if (a.ix.use_sum) {
+            // beside the summary, shared memory holds one chunk buffer per warp
+            // at most, too shallow to hide a bulk copy: L2 prefetches instead
+            return launch(k_resolve<kResolveSumThreads, true, false, R16>, kResolveSumThreads,
+                          resolve_smem_head(WS, true, a.ix.sg, false), resolve_smem_head(WS, true, kSumLog2, false),
+                          d[2]);
+        }
         const size_t head = kTmaPoints ? resolve_smem_head(kWarps, false, 0, true) : 0;
         if (kTmaPoints)
-            e = launch(k_resolve<kThreads, false, true>, kThreads, head, head, done_r[3]);
-        else
-            e = launch(k_resolve<kThreads, false, false>, kThreads, head, head, done_r[0]);
-    }
+            return launch(k_resolve<kThreads, false, true, R16>, kThreads, head, head, d[3]);
+        return launch(k_resolve<kThreads, false, false, R16>, kThreads, head, head, d[0]);
+    };
+    e = a.narrow ? pass1a(std::true_type{}) : pass1a(std::false_type{});
     if (e != cudaSuccess) // pass 1b must not run on what an earlier call left in the scratch
         return e;
     if (mid)
@@ -1754,7 +1809,10 @@ cudaError_t launch_pass1(const JoinLaunch &a, uint32_t *pend, cudaStream_t s, cu
     // pass 1b: a warp per kWalkRange bitmap words, as many CTAs as that takes
     const uint64_t nwords = nchunks * kWItems;
     const uint64_t wblk = (nwords + uint64_t(kWarps) * kWalkRange - 1) / (uint64_t(kWarps) * kWalkRange);
-    k_walk<FP32><<<unsigned(wblk), kThreads, 0, s>>>(a, pend, uint32_t(nwords));
+    if (a.narrow)
+        k_walk<FP32, true><<<unsigned(wblk), kThreads, 0, s>>>(a, pend, uint32_t(nwords));
+    else
+        k_walk<FP32, false><<<unsigned(wblk), kThreads, 0, s>>>(a, pend, uint32_t(nwords));
     return cudaGetLastError();
 }
 
@@ -2551,26 +2609,25 @@ cudaError_t launch_join_resolve(const JoinLaunch &a, unsigned long long *part, c
     return join_resolve_scan(a, part, s, nullptr);
 }
 
-cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s)
+cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s, const uint32_t *pend)
 {
     const uint32_t nchunks = uint32_t((a.n + kWChunk - 1) / kWChunk);
     if (nchunks == 0 || a.cap == 0)
         return cudaSuccess;
+    if (a.narrow && !pend)
+        return cudaErrorInvalidValue;
     const uint32_t nblk = (nchunks + kWarps - 1) / kWarps;
-    static bool done[2][64] = {};
-    cudaError_t e;
-    if (a.fp32) {
-        if ((e = smem_opt_in(k_wemit<true>, kEmitSmem, done[0])) != cudaSuccess)
+    static bool done[4][64] = {};
+    auto emit = [&](auto kr, bool(&d)[64]) -> cudaError_t {
+        cudaError_t e = smem_opt_in(kr, kEmitSmem, d);
+        if (e != cudaSuccess)
             return e;
-        k_wemit<true><<<persistent_grid(k_wemit<true>, kThreads, kEmitSmem, nblk), kThreads, kEmitSmem, s>>>(
-            a, a.tile_tot, nchunks);
-    } else {
-        if ((e = smem_opt_in(k_wemit<false>, kEmitSmem, done[1])) != cudaSuccess)
-            return e;
-        k_wemit<false><<<persistent_grid(k_wemit<false>, kThreads, kEmitSmem, nblk), kThreads, kEmitSmem, s>>>(
-            a, a.tile_tot, nchunks);
-    }
-    return cudaGetLastError();
+        kr<<<persistent_grid(kr, kThreads, kEmitSmem, nblk), kThreads, kEmitSmem, s>>>(a, a.tile_tot, nchunks, pend);
+        return cudaGetLastError();
+    };
+    if (a.narrow)
+        return a.fp32 ? emit(k_wemit<true, true>, done[2]) : emit(k_wemit<false, true>, done[3]);
+    return a.fp32 ? emit(k_wemit<true, false>, done[0]) : emit(k_wemit<false, false>, done[1]);
 }
 
 __global__ void k_sum_u64(unsigned long long *dst, const unsigned long long *x, const unsigned long long *y)
@@ -2616,6 +2673,9 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cuda
     b.res = reinterpret_cast<uint32_t *>(sc);
     b.tile_tot = reinterpret_cast<unsigned long long *>(sc + ((a.n * 4 + 15) & ~uint64_t(15)));
     unsigned long long *part = b.tile_tot + (a.n + kWChunk - 1) / kWChunk;
+    // 16-bit results when every polygon id and every point's polygon count
+    // fit (the row bitmap in part stays in place until pass 3)
+    b.narrow = a.ix.P <= kRes16MaxP ? 1 : 0;
     cudaError_t e;
     if (a.counts && a.ix.P && !a.keep_counts)
         if ((e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.ix.P, s)) != cudaSuccess)
@@ -2629,7 +2689,7 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cuda
     if ((e = join_resolve_scan(b, part, s, ev ? ev + 1 : nullptr)) != cudaSuccess)
         return e;
     // pass 3: pairs in point order
-    if ((e = launch_join_emit(b, s)) != cudaSuccess)
+    if ((e = launch_join_emit(b, s, reinterpret_cast<const uint32_t *>(part))) != cudaSuccess)
         return e;
     if (ev)
         cudaEventRecord(ev[4], s);

@@ -128,7 +128,13 @@ struct JoinLaunch {
     // grid, then one bin of points outside the box); used when cluster_log2 >= g
     const unsigned long long *cell_end;
     int cluster_log2;
+    // set by launch_join: the per-point results of passes 1 -> 3 are 16-bit
+    // words (the index has at most kRes16MaxP polygons)
+    int narrow;
 };
+
+// Largest polygon count whose join keeps 16-bit per-point results.
+constexpr uint32_t kRes16MaxP = 0xfffeu;
 
 // Scratch bytes the join needs for n points (per-point results, tile totals, counter).
 size_t join_scratch_bytes(uint64_t n);
@@ -205,7 +211,8 @@ cudaError_t launch_plain_write(const JoinLaunch &a, void *scratch, cudaStream_t 
 uint32_t join_chunk_points();
 uint64_t join_part_words(uint64_t n);
 cudaError_t launch_join_resolve(const JoinLaunch &a, unsigned long long *part, cudaStream_t s);
-cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s);
+// pend: the row bitmap of pass 1 as pass 1b left it (needed when a.narrow).
+cudaError_t launch_join_emit(const JoinLaunch &a, cudaStream_t s, const uint32_t *pend = nullptr);
 
 // *dst = *x + *y (one thread; sliced joins chain their pair offsets).
 cudaError_t launch_sum_u64(unsigned long long *dst, const unsigned long long *x, const unsigned long long *y,
