@@ -608,6 +608,7 @@ def serve_run(srv, reqs, rate, warm: int, seed: int = 7):
         ready.release()
     th.join()
     timed = res[warm:]
+    serve_run.last = timed
     bad = sum(1 for r in timed if r["status"] != 0)
     lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in timed])
     span = (max(r["t_done_ms"] for r in timed) - min(r["t_submit_ms"] for r in timed)) / 1e3
@@ -637,21 +638,28 @@ def run_serving(eng, ph, N: int, seed: int, timed: int, warm: int, burst: int):
     cap = {}
     batches = 0
     peak, peak_kind = peaks()
-    for name, kw in arms.items():
+    ix_bytes = [eng.index_info(x[2])["device_bytes"] for x in idx]
+    for name, kw in list(arms.items()) + [("fused", dict(max_batch=8, slots=2, fused=True))]:
         srv = spx.Server(eng, ph, handles, **kw)
         serve_run(srv, serve_stream(idx, max(4, burst // 4), seed + 1), None, 0)  # warm-up
         b0 = srv.stats()["batches"]
-        r = serve_run(srv, serve_stream(idx, burst, seed + 2), None, 0)
+        reqs = serve_stream(idx, burst, seed + 2)
+        r = serve_run(srv, reqs, None, 0)
         nb = srv.stats()["batches"] - b0
         cap[name] = r["throughput_rps"]
         if name == "batched":
+            # served roofline over the burst: the algorithmic bytes of every
+            # request (8 B per scanned point, 8 B per pair or 4 B per id, its
+            # index once) over the burst's span
             span = burst / r["throughput_rps"]
-            gbs = 2 * 8 * N * nb / span / 1e9
-            out["batch_passes"] = {"batches": nb, "requests": burst, "seconds": span,
-                                   "point_bytes_per_batch": 16 * N, "achieved_gbs": gbs, "peak": peak,
-                                   "frac": gbs / peak, "peak_source": f"{peak_kind} hbm_gbs",
-                                   "note": "two passes over the 8 B points per batch (count, write) over the "
-                                           "burst's span; index reads and outputs not counted"}
+            outb = sum((8 if x["kind"] == spx.SPX_REQ_JOIN else 4) * x["total"] for x in serve_run.last)
+            alg = 8 * N * burst + outb + sum(ix_bytes[pos] for _, pos in reqs)
+            gbs = alg / span / 1e9
+            out["served_roofline"] = {"batches": nb, "requests": burst, "seconds": span,
+                                      "algorithmic_bytes": alg, "output_bytes": outb, "achieved_gbs": gbs,
+                                      "peak": peak, "frac": gbs / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                                      "note": "8 B per scanned point per request + outputs (8 B per pair, "
+                                              "4 B per id) + each request's index once, over the burst's span"}
         srv.close()
     out["capacity_rps"] = cap
     plan = [("batched", x) for x in (0.5, 0.8, 0.95)] + [("plain", x) for x in (0.5, 0.8)]

@@ -524,10 +524,14 @@ spx_status spx_free(spx_ctx *ctx, uint64_t handle);
  *   3. the write pass, then (selections) the stable partition into per-query
  *      id lists.
  * Continuous batching: whenever a slot is free, the requests waiting at that
- * moment (up to max_batch, in arrival order) form one batch, and every pass
- * reads the point table once for all of them (§5.2's one-pass batched
- * selection, applied across requests).  Requests that arrive later join the
- * next free slot; slots overlap on the device (one CUDA stream each).
+ * moment (up to max_batch, in arrival order) form one batch with one
+ * admission.  By default each request's count and write passes are the join's
+ * own kernels (spx_join's passes 1-3, its per-point results kept between the
+ * passes in scratch the server takes from its pool per batch); with fused = 1,
+ * every pass instead reads the point table once for the whole batch (§5.2's
+ * one-pass batched selection, applied across requests), resolving each point
+ * again in the write pass.  Requests that arrive later join the next free
+ * slot; slots overlap on the device (one CUDA stream each).
  * Results are byte-identical to spx_join / spx_select on the same index,
  * whatever the batch composition.
  *
@@ -539,11 +543,13 @@ spx_status spx_free(spx_ctx *ctx, uint64_t handle);
 typedef struct spx_server spx_server;
 
 typedef struct {
-    int max_batch;          /* requests per pass over the points, 1..8 (0 = 8; 1 = no batching) */
+    int max_batch;          /* requests admitted together, 1..8 (0 = 8; 1 = no batching) */
     int slots;              /* batches in flight, 1..4 (0 = 2) */
     int plain;              /* 1: comparison mode: each request alone (max_batch = slots = 1) through the
                                plain kernels (int64 only, one thread per point, not persistent) */
-    int reserved0;          /* must be zero */
+    int fused;              /* 0: every request of a batch through the join's own passes (count pass of
+                               each, one admission, write pass of each); 1: one fused pass over the
+                               points for the whole batch (per-request lookups, no cached results) */
     uint64_t output_budget; /* device bytes of outputs and temporaries held at once; 0 = half of the free
                                device memory at creation.  A batch larger than the budget runs alone. */
     int reserved[4];        /* must be zero */
@@ -572,6 +578,8 @@ typedef struct {
     double t_submit_ms;          /* server clock (ms since creation): submission */
     double t_start_ms;           /* the batch's first launch */
     double t_done_ms;            /* results complete on the device (stream callback) */
+    double t_counted_ms;         /* the batch's count pass complete on the device (stream callback) */
+    double t_written_ms;         /* outputs admitted and the write pass launched */
 } spx_result;
 
 typedef struct {

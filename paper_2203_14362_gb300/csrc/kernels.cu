@@ -2664,18 +2664,26 @@ size_t plain_scratch_bytes(uint64_t n)
     return size_t(nb * 8 + 16);
 }
 
-cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
+// The join's scratch: per-point results | per-chunk totals (then offsets) |
+// row bitmap and scan partials.  Fills b's result and total pointers and the
+// result width.
+static unsigned long long *join_layout(JoinLaunch &b, void *scratch)
+{
+    char *sc = static_cast<char *>(scratch);
+    b.res = reinterpret_cast<uint32_t *>(sc);
+    b.tile_tot = reinterpret_cast<unsigned long long *>(sc + ((b.n * 4 + 15) & ~uint64_t(15)));
+    // 16-bit results when every polygon id and every point's polygon count
+    // fit (the row bitmap in part stays in place until pass 3)
+    b.narrow = b.ix.P <= kRes16MaxP ? 1 : 0;
+    return b.tile_tot + (b.n + kWChunk - 1) / kWChunk;
+}
+
+cudaError_t launch_join_count(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
 {
     if ((a.n + kWChunk - 1) / kWChunk >= (1ull << 31))
         return cudaErrorInvalidValue;
     JoinLaunch b = a;
-    char *sc = static_cast<char *>(scratch);
-    b.res = reinterpret_cast<uint32_t *>(sc);
-    b.tile_tot = reinterpret_cast<unsigned long long *>(sc + ((a.n * 4 + 15) & ~uint64_t(15)));
-    unsigned long long *part = b.tile_tot + (a.n + kWChunk - 1) / kWChunk;
-    // 16-bit results when every polygon id and every point's polygon count
-    // fit (the row bitmap in part stays in place until pass 3)
-    b.narrow = a.ix.P <= kRes16MaxP ? 1 : 0;
+    unsigned long long *part = join_layout(b, scratch);
     cudaError_t e;
     if (a.counts && a.ix.P && !a.keep_counts)
         if ((e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.ix.P, s)) != cudaSuccess)
@@ -2686,10 +2694,25 @@ cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cuda
     // results, per-chunk totals), then the offsets and the total
     if (ev)
         cudaEventRecord(ev[0], s);
-    if ((e = join_resolve_scan(b, part, s, ev ? ev + 1 : nullptr)) != cudaSuccess)
-        return e;
+    return join_resolve_scan(b, part, s, ev ? ev + 1 : nullptr);
+}
+
+cudaError_t launch_join_write(const JoinLaunch &a, void *scratch, cudaStream_t s)
+{
+    if (a.n == 0)
+        return cudaSuccess;
+    JoinLaunch b = a;
+    unsigned long long *part = join_layout(b, scratch);
     // pass 3: pairs in point order
-    if ((e = launch_join_emit(b, s, reinterpret_cast<const uint32_t *>(part))) != cudaSuccess)
+    return launch_join_emit(b, s, reinterpret_cast<const uint32_t *>(part));
+}
+
+cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev)
+{
+    cudaError_t e = launch_join_count(a, scratch, s, ev);
+    if (e != cudaSuccess || a.n == 0)
+        return e;
+    if ((e = launch_join_write(a, scratch, s)) != cudaSuccess)
         return e;
     if (ev)
         cudaEventRecord(ev[4], s);

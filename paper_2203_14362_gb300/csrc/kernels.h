@@ -144,6 +144,11 @@ size_t plain_scratch_bytes(uint64_t n);
 // five events recorded before pass 1, after pass 1a (resolve), after pass 1b
 // (walk), after pass 2 (scan) and after pass 3 (emit).
 cudaError_t launch_join(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
+// launch_join in two halves over the same scratch, for callers that size the
+// output between them: passes 1 and 2 (counts, per-point results, offsets,
+// *a.total; ev as for launch_join, first three events), then pass 3 (pairs).
+cudaError_t launch_join_count(const JoinLaunch &a, void *scratch, cudaStream_t s, cudaEvent_t *ev = nullptr);
+cudaError_t launch_join_write(const JoinLaunch &a, void *scratch, cudaStream_t s);
 cudaError_t launch_join_plain(const JoinLaunch &a, void *scratch, cudaStream_t s);
 // scratch: aggregate_scratch_bytes(a) bytes (the chunk bitmap of the directory
 // path; unused otherwise).  a.keep_counts: add to the counts instead of

@@ -32,7 +32,7 @@ struct Req {
     uint32_t P = 0;
     int status = SPX_EBUSY;
     uint32_t batch_size = 0;
-    double t_submit = 0, t_start = 0, t_done = 0;
+    double t_submit = 0, t_start = 0, t_counted = 0, t_written = 0, t_done = 0;
     uint64_t total = 0;
     // outputs (kept until released): join pairs | selection ids + offsets
     void *out_mem = nullptr;
@@ -42,6 +42,10 @@ struct Req {
     // selection temporaries: pairs in point order + partition scratch
     void *tmp_mem = nullptr;
     size_t tmp_bytes = 0;
+    // per-request passes: the join's scratch (per-point results, chunk
+    // offsets) from the count pass to the write pass
+    void *join_mem = nullptr;
+    size_t join_bytes = 0;
     int readers = 0; // spx_server_read calls copying the outputs (release waits for none)
 };
 
@@ -97,7 +101,8 @@ struct spx_server {
         cv.notify_all();
     }
     void run();
-    void start_batch(Slot &sl);
+    bool start_batch(Slot &sl);
+    JoinLaunch request_launch(Slot &sl, const Req *r, size_t i) const;
     void counted(Slot &sl);
     bool admit(Slot &sl);
     void written(Slot &sl);
@@ -144,10 +149,11 @@ void spx_server::fail_batch(Slot &sl, int status)
         pool_free(r->out_mem, sl.s);
         pool_free(r->tmp_mem, sl.s);
         pool_free(r->counts, sl.s);
-        used -= r->out_bytes + r->tmp_bytes + r->counts_bytes;
-        r->out_mem = r->tmp_mem = nullptr;
+        pool_free(r->join_mem, sl.s);
+        used -= r->out_bytes + r->tmp_bytes + r->counts_bytes + r->join_bytes;
+        r->out_mem = r->tmp_mem = r->join_mem = nullptr;
         r->counts = nullptr;
-        r->out_bytes = r->tmp_bytes = r->counts_bytes = 0;
+        r->out_bytes = r->tmp_bytes = r->counts_bytes = r->join_bytes = 0;
         r->status = status;
         r->t_done = now_ms();
         st.failed++;
@@ -157,16 +163,46 @@ void spx_server::fail_batch(Slot &sl, int status)
     cv_done.notify_all();
 }
 
-// Take the waiting requests (arrival order) into a batch and launch its count pass.
-void spx_server::start_batch(Slot &sl)
+// The join launch of request r, position i of its slot's batch (outputs and
+// capacity are set by the write pass).
+JoinLaunch spx_server::request_launch(Slot &sl, const Req *r, size_t i) const
 {
+    JoinLaunch a{};
+    a.ix = data.ix[r->rq.index];
+    a.ix.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
+    a.pts = data.pts;
+    a.n = data.n;
+    a.counts = r->counts;
+    a.total = sl.dev_words + i;
+    a.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
+    a.stats = sl.dev_words + kWordStats;
+    a.fp32 = data.fp32[r->rq.index];
+    return a;
+}
+
+// Take the waiting requests (arrival order) into a batch and launch its count
+// pass.  False: nothing started (the per-request join scratch does not fit the
+// budget while other batches hold memory; a release wakes the worker).
+bool spx_server::start_batch(Slot &sl)
+{
+    if (!prm.plain && !prm.fused) {
+        const uint64_t per = up256(join_scratch_bytes(data.n));
+        const uint64_t k = std::min<uint64_t>(queue.size(), uint64_t(max_batch));
+        if (used > 0 && used + k * per > prm.output_budget && !stopping) {
+            if (!sl.waited)
+                st.admission_waits++;
+            sl.waited = true;
+            return false;
+        }
+        sl.waited = false;
+    }
     sl.batch.clear();
     uint32_t hist = 0;
     while (!queue.empty() && (int)sl.batch.size() < max_batch) {
         Req *r = queue.front();
         const uint32_t h = r->rq.kind == SPX_REQ_JOIN ? r->P : 0u;
-        if (!sl.batch.empty() && hist + h > kMultiHistMax)
-            break; // keep the batch's per-polygon counters in shared memory
+        if (prm.fused && !sl.batch.empty() && hist + h > kMultiHistMax)
+            break; // keep the fused pass's per-polygon counters in shared memory
         hist += h;
         sl.batch.push_back(r);
         queue.pop_front();
@@ -188,7 +224,7 @@ void spx_server::start_batch(Slot &sl)
                 r->counts_bytes = 0;
                 err = "server: allocation of join counts failed";
                 fail_batch(sl, SPX_ENOMEM);
-                return;
+                return true;
             }
             r->counts = static_cast<unsigned long long *>(p);
             used += r->counts_bytes;
@@ -208,6 +244,22 @@ void spx_server::start_batch(Slot &sl)
         a.stats = sl.dev_words + kWordStats;
         a.fp32 = 0;
         e = launch_plain_count(a, sl.scratch, sl.s);
+    } else if (!prm.fused) {
+        // each request through the join's own passes 1 and 2, its results
+        // kept in its scratch until the write pass
+        for (uint32_t i = 0; i < K && e == cudaSuccess; ++i) {
+            Req *r = sl.batch[i];
+            r->join_bytes = up256(join_scratch_bytes(data.n));
+            if (!pool_alloc(this, &r->join_mem, r->join_bytes, sl.s)) {
+                r->join_bytes = 0;
+                err = "server: allocation of join scratch failed";
+                fail_batch(sl, SPX_ENOMEM);
+                return true;
+            }
+            used += r->join_bytes;
+            e = launch_join_count(request_launch(sl, r, i), r->join_mem, sl.s);
+        }
+        st.peak_bytes_in_use = std::max(st.peak_bytes_in_use, used);
     } else {
         MultiLaunch m{};
         m.K = int(K);
@@ -236,9 +288,10 @@ void spx_server::start_batch(Slot &sl)
     if (e != cudaSuccess) {
         err = std::string("server: count pass launch failed: ") + cudaGetErrorString(e);
         fail_batch(sl, SPX_ECUDA);
-        return;
+        return true;
     }
     sl.state = Slot::kCounting;
+    return true;
 }
 
 // Count pass done: sizes of every output.
@@ -250,8 +303,10 @@ void spx_server::counted(Slot &sl)
         fail_batch(sl, SPX_EKERNEL);
         return;
     }
+    const double t = sl.t_cb.load();
     for (size_t i = 0; i < sl.batch.size(); ++i) {
         Req *r = sl.batch[i];
+        r->t_counted = t;
         r->total = sl.host_words[i];
         if (r->rq.kind == SPX_REQ_JOIN) {
             r->out_bytes = up256(std::max<uint64_t>(r->total, 1) * 8);
@@ -270,12 +325,12 @@ bool spx_server::admit(Slot &sl)
     for (Req *r : sl.batch)
         need += r->out_bytes + r->tmp_bytes;
     // bytes held by anything but the batches waiting here (their join counters
-    // must not keep each other out)
+    // and scratch must not keep each other out)
     uint64_t waiting = 0;
     for (auto &o : slots)
         if (o->state == Slot::kAdmit)
             for (Req *r : o->batch)
-                waiting += r->counts_bytes;
+                waiting += r->counts_bytes + r->join_bytes;
     const uint64_t other = used - waiting;
     if (used + need > prm.output_budget && other > 0 && !stopping) {
         // wait for releases (a batch that fits no budget runs once nothing else is held)
@@ -324,6 +379,14 @@ bool spx_server::admit(Slot &sl)
         a.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
         a.stats = sl.dev_words + kWordStats;
         e = launch_plain_write(a, sl.scratch, sl.s);
+    } else if (!prm.fused) {
+        for (size_t i = 0; i < sl.batch.size() && e == cudaSuccess; ++i) {
+            Req *r = sl.batch[i];
+            JoinLaunch a = request_launch(sl, r, i);
+            a.pairs = pairs_of(r);
+            a.cap = r->total;
+            e = launch_join_write(a, r->join_mem, sl.s);
+        }
     } else {
         MultiLaunch m{};
         m.K = int(sl.batch.size());
@@ -365,6 +428,9 @@ bool spx_server::admit(Slot &sl)
         fail_batch(sl, SPX_ECUDA);
         return true;
     }
+    const double t = now_ms();
+    for (Req *r : sl.batch)
+        r->t_written = t;
     sl.state = Slot::kEmitting;
     return true;
 }
@@ -382,9 +448,10 @@ void spx_server::written(Slot &sl)
     }
     for (Req *r : sl.batch) {
         pool_free(r->tmp_mem, sl.s); // ordered after the partition on this stream
-        r->tmp_mem = nullptr;
-        used -= r->tmp_bytes;
-        r->tmp_bytes = 0;
+        pool_free(r->join_mem, sl.s);
+        r->tmp_mem = r->join_mem = nullptr;
+        used -= r->tmp_bytes + r->join_bytes;
+        r->tmp_bytes = r->join_bytes = 0;
         r->t_done = t;
         r->status = SPX_OK;
         st.completed++;
@@ -417,8 +484,8 @@ void spx_server::run()
             }
             if (sl.state == Slot::kIdle && !queue.empty()) {
                 sl.flag.store(0);
-                start_batch(sl);
-                progress = true;
+                if (start_batch(sl))
+                    progress = true;
             }
         }
         if (stopping && queue.empty()) {
@@ -447,8 +514,7 @@ spx_status spx_server_create(spx_ctx *ctx, spx_points points, const spx_index *i
     spx_server_params prm{};
     if (params) {
         prm = *params;
-        if (prm.reserved0)
-            return ctx_error(ctx, SPX_EINVAL, "server: reserved fields must be zero");
+
         for (int r : prm.reserved)
             if (r)
                 return ctx_error(ctx, SPX_EINVAL, "server: reserved fields must be zero");
@@ -458,8 +524,9 @@ spx_status spx_server_create(spx_ctx *ctx, spx_points points, const spx_index *i
     if (prm.slots == 0)
         prm.slots = 2;
     if (prm.max_batch < 1 || prm.max_batch > kMaxBatch || prm.slots < 1 || prm.slots > 4 ||
-        (prm.plain != 0 && prm.plain != 1))
-        return ctx_error(ctx, SPX_EINVAL, "server: need 1 <= max_batch <= 8, 1 <= slots <= 4, plain 0 or 1");
+        (prm.plain != 0 && prm.plain != 1) || (prm.fused != 0 && prm.fused != 1))
+        return ctx_error(ctx, SPX_EINVAL,
+                         "server: need 1 <= max_batch <= 8, 1 <= slots <= 4, plain and fused 0 or 1");
     if (prm.plain)
         prm.max_batch = prm.slots = 1;
     auto srv = std::make_unique<spx_server>();
@@ -501,7 +568,10 @@ spx_status spx_server_create(spx_ctx *ctx, spx_points points, const spx_index *i
     };
     if (cudaStreamCreateWithFlags(&srv->release_stream, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup("stream creation failed");
-    const size_t scratch = prm.plain ? plain_split_scratch_bytes(srv->data.n) : multi_scratch_bytes(srv->data.n, kMaxBatch);
+    // per-request passes take their join scratch from the pool per batch
+    const size_t scratch = prm.plain   ? plain_split_scratch_bytes(srv->data.n)
+                           : prm.fused ? multi_scratch_bytes(srv->data.n, kMaxBatch)
+                                       : 16;
     for (int i = 0; i < prm.slots; ++i) {
         auto sl = std::make_unique<Slot>();
         sl->srv = srv.get();
@@ -581,6 +651,8 @@ static void fill_result(const Req &r, spx_result *out)
     out->t_submit_ms = r.t_submit;
     out->t_start_ms = r.t_start;
     out->t_done_ms = r.t_done;
+    out->t_counted_ms = r.t_counted;
+    out->t_written_ms = r.t_written;
 }
 
 spx_status spx_server_poll(spx_server *srv, uint64_t req_id, spx_result *out)

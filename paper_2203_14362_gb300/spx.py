@@ -66,7 +66,7 @@ class TuneTrial(C.Structure):
 
 
 class ServerParams(C.Structure):
-    _fields_ = [("max_batch", C.c_int), ("slots", C.c_int), ("plain", C.c_int), ("reserved0", C.c_int),
+    _fields_ = [("max_batch", C.c_int), ("slots", C.c_int), ("plain", C.c_int), ("fused", C.c_int),
                 ("output_budget", C.c_uint64), ("reserved", C.c_int * 4)]
 
 
@@ -78,7 +78,8 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("kind", C.c_int), ("tag", C.c_uint64), ("total", C.c_uint64),
                 ("n_polys", C.c_uint32), ("batch_size", C.c_uint32), ("pairs_dev", C.c_void_p),
                 ("counts_dev", C.c_void_p), ("ids_dev", C.c_void_p), ("offsets_dev", C.c_void_p),
-                ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double)]
+                ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double),
+                ("t_counted_ms", C.c_double), ("t_written_ms", C.c_double)]
 
 
 class ServerStats(C.Structure):
@@ -453,10 +454,10 @@ class Server:
     of indexes (requests name an index by its position in that list)."""
 
     def __init__(self, eng: Engine, points: int, indexes, max_batch: int = 0, slots: int = 0, plain: bool = False,
-                 output_budget: int = 0):
+                 output_budget: int = 0, fused: bool = False):
         self.lib = eng.lib
         arr = (C.c_uint64 * max(len(indexes), 1))(*indexes)
-        prm = ServerParams(max_batch, slots, 1 if plain else 0, 0, output_budget)
+        prm = ServerParams(max_batch, slots, 1 if plain else 0, 1 if fused else 0, output_budget)
         h = C.c_void_p()
         st = self.lib.spx_server_create(eng.ctx, points, arr, len(indexes), C.byref(prm), C.byref(h))
         if st != SPX_OK:

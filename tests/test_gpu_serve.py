@@ -1,10 +1,11 @@
 """GPU tests of the serving runtime (spx_server_*).
 
 Every request's result must equal the oracle's, byte for byte, whatever the
-batch it was answered in (alone, in a mix of selections and joins, through
-the plain one-request-per-launch path), with several batches in flight, under
-an output budget that forces admission waits, and with requests submitted
-from several threads at once.
+batch it was answered in (alone, in a mix of selections and joins, through the
+join's own passes per request, through the fused one-pass batch kernel,
+through the plain one-request-per-launch path), with several batches in
+flight, under an output budget that forces admission waits, and with requests
+submitted from several threads at once.
 """
 import threading
 
@@ -77,7 +78,7 @@ def _check(srv, rid, res, exp):
         assert res["kind"] == spx.SPX_REQ_SELECT
         assert np.array_equal(a, exp[1])
         assert np.array_equal(b, exp[2])
-    assert res["t_submit_ms"] <= res["t_start_ms"] <= res["t_done_ms"]
+    assert res["t_submit_ms"] <= res["t_start_ms"] <= res["t_counted_ms"] <= res["t_written_ms"] <= res["t_done_ms"]
 
 
 # a fixed mixed sequence of index positions (joins are 0 and 1)
@@ -85,7 +86,8 @@ SEQ = [2, 0, 3, 4, 5, 1, 2, 2, 5, 0, 4, 3, 1, 5, 2, 0, 3, 3, 4, 1]
 
 
 @pytest.mark.parametrize("cfg", [dict(max_batch=8, slots=2), dict(max_batch=3, slots=1),
-                                 dict(max_batch=1, slots=3), dict(plain=True)])
+                                 dict(max_batch=1, slots=3), dict(plain=True),
+                                 dict(max_batch=8, slots=2, fused=True), dict(max_batch=3, slots=1, fused=True)])
 def test_serve_burst_matches_oracle(world, cfg):
     srv = spx.Server(world["eng"], world["ph"], world["ix"], **cfg)
     try:
@@ -110,9 +112,10 @@ def test_serve_burst_matches_oracle(world, cfg):
         srv.close()
 
 
-def test_serve_budget_forces_waits(world):
+@pytest.mark.parametrize("fused", [False, True])
+def test_serve_budget_forces_waits(world, fused):
     # a 1-byte budget: each batch runs only once nothing else is held
-    srv = spx.Server(world["eng"], world["ph"], world["ix"], max_batch=1, slots=2, output_budget=1)
+    srv = spx.Server(world["eng"], world["ph"], world["ix"], max_batch=1, slots=2, output_budget=1, fused=fused)
     try:
         ks = [0, 2, 1]
         ids = [srv.submit(_kind(world["expect"][k]), k) for k in ks]
