@@ -535,9 +535,11 @@ def run_spx(args, world, rank, local):
         torch.cuda.empty_cache()
         cnt = count_measure(args, world, rank, local, torch, k, w, None, e2e=False)
         torch.cuda.empty_cache()
+        sv1b = None if args.no_serve else serve_capacity_measure(args, local, torch)
         if rank == 0:
             out["select"] = sel
             out["count"] = cnt
+            out["serving_1b"] = sv1b
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -617,13 +619,48 @@ def serve_run(srv, reqs, rate, warm: int, seed: int = 7):
             "mean_batch": float(np.mean([r["batch_size"] for r in timed])), "failed": bad}
 
 
+def serve_capacity(eng, ph, N: int, idx, burst: int, seed: int, plain_burst: int = 0):
+    """Capacity (requests/s over a burst submitted at once, after a warm-up
+    burst) of the batching server, of its fused one-pass mode and of the plain
+    comparison, and the batching server's served roofline over its burst: the
+    algorithmic bytes of every request (8 B per scanned point, 8 B per pair or
+    4 B per id, its index once) over the burst's span."""
+    from paper_2203_14362_gb300 import spx
+    handles = [x[2] for x in idx]
+    peak, peak_kind = peaks()
+    ix_bytes = [eng.index_info(h)["device_bytes"] for h in handles]
+    cap, roof = {}, None
+    arms = (("batched", dict(max_batch=8, slots=2)), ("fused", dict(max_batch=8, slots=2, fused=True)),
+            ("plain", dict(plain=True)))
+    for name, kw in arms:
+        n = plain_burst if name == "plain" and plain_burst else burst
+        srv = spx.Server(eng, ph, handles, **kw)
+        serve_run(srv, serve_stream(idx, max(4, n // 4), seed + 1), None, 0)  # warm-up
+        b0 = srv.stats()["batches"]
+        reqs = serve_stream(idx, n, seed + 2)
+        r = serve_run(srv, reqs, None, 0)
+        nb = srv.stats()["batches"] - b0
+        cap[name] = r["throughput_rps"]
+        if name == "batched":
+            span = n / r["throughput_rps"]
+            outb = sum((8 if x["kind"] == spx.SPX_REQ_JOIN else 4) * x["total"] for x in serve_run.last)
+            alg = 8 * N * n + outb + sum(ix_bytes[pos] for _, pos in reqs)
+            gbs = alg / span / 1e9
+            roof = {"batches": nb, "requests": n, "seconds": span, "algorithmic_bytes": alg, "output_bytes": outb,
+                    "achieved_gbs": gbs, "peak": peak, "frac": gbs / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                    "note": "8 B per scanned point per request + outputs (8 B per pair, 4 B per id) + each "
+                            "request's index once, over the burst's span"}
+        srv.close()
+    return cap, roof
+
+
 def run_serving(eng, ph, N: int, seed: int, timed: int, warm: int, burst: int):
-    """Capacity (a burst) of the batching server and of the plain comparison
-    (one request per launch), then latency at 0.5 / 0.8 / 0.95 x the batching
-    server's capacity and at 0.5 / 0.8 x the plain server's (rates both arms
-    sustain), `timed` requests per rate and arm after `warm` warm-up requests.
-    The batch passes' HBM fraction: every batch reads the point table twice
-    (count pass, write pass), measured over the batching server's burst."""
+    """Capacity (a burst) of the batching server, of its fused mode and of
+    the plain comparison (one request per launch), then latency at 0.5 / 0.8
+    / 0.95 x the batching server's capacity and at 0.5 / 0.8 x the plain
+    server's (rates both arms sustain), `timed` requests per rate and arm
+    after `warm` warm-up requests; the served roofline over the batching
+    server's burst."""
     from paper_2203_14362_gb300 import spx
     t_build = time.perf_counter()
     idx = serve_indexes(eng, seed)
@@ -635,32 +672,8 @@ def run_serving(eng, ph, N: int, seed: int, timed: int, warm: int, burst: int):
            "index_build_s": round(build_s, 1), "server": {"max_batch": 8, "slots": 2},
            "latency": "device completion (stream callback) - submission, server clock", "rates": []}
     arms = {"batched": dict(max_batch=8, slots=2), "plain": dict(plain=True)}
-    cap = {}
     batches = 0
-    peak, peak_kind = peaks()
-    ix_bytes = [eng.index_info(x[2])["device_bytes"] for x in idx]
-    for name, kw in list(arms.items()) + [("fused", dict(max_batch=8, slots=2, fused=True))]:
-        srv = spx.Server(eng, ph, handles, **kw)
-        serve_run(srv, serve_stream(idx, max(4, burst // 4), seed + 1), None, 0)  # warm-up
-        b0 = srv.stats()["batches"]
-        reqs = serve_stream(idx, burst, seed + 2)
-        r = serve_run(srv, reqs, None, 0)
-        nb = srv.stats()["batches"] - b0
-        cap[name] = r["throughput_rps"]
-        if name == "batched":
-            # served roofline over the burst: the algorithmic bytes of every
-            # request (8 B per scanned point, 8 B per pair or 4 B per id, its
-            # index once) over the burst's span
-            span = burst / r["throughput_rps"]
-            outb = sum((8 if x["kind"] == spx.SPX_REQ_JOIN else 4) * x["total"] for x in serve_run.last)
-            alg = 8 * N * burst + outb + sum(ix_bytes[pos] for _, pos in reqs)
-            gbs = alg / span / 1e9
-            out["served_roofline"] = {"batches": nb, "requests": burst, "seconds": span,
-                                      "algorithmic_bytes": alg, "output_bytes": outb, "achieved_gbs": gbs,
-                                      "peak": peak, "frac": gbs / peak, "peak_source": f"{peak_kind} hbm_gbs",
-                                      "note": "8 B per scanned point per request + outputs (8 B per pair, "
-                                              "4 B per id) + each request's index once, over the burst's span"}
-        srv.close()
+    cap, out["served_roofline"] = serve_capacity(eng, ph, N, idx, burst, seed)
     out["capacity_rps"] = cap
     plan = [("batched", x) for x in (0.5, 0.8, 0.95)] + [("plain", x) for x in (0.5, 0.8)]
     for ref, x in plan:
@@ -679,6 +692,47 @@ def run_serving(eng, ph, N: int, seed: int, timed: int, warm: int, burst: int):
     out["value_gpts"] = cap["batched"] * N / 1e9
     out["batches"] = batches
     return out
+
+
+def serve_capacity_measure(args, local, torch, N: int = 1_000_000_000):
+    """Serving capacity at the resident table of 1B points (the serving
+    workload's size): the point table generated chunk by chunk straight into
+    device memory, the same request indexes and mix as the latency sweeps, a
+    burst per server (batching, fused, plain) and the batching server's
+    served roofline."""
+    from paper_2203_14362_gb300 import datagen as g
+    from paper_2203_14362_gb300 import spx
+    seed = g.SEED_BASE + 4
+    mix = g.make_mixture(seed)
+    t0 = time.perf_counter()
+    dpts = torch.empty((N, 2), dtype=torch.int32, device="cuda")
+    chunk = 1 << 28
+    for lo in range(0, N, chunk):
+        hi = min(N, lo + chunk)
+        dpts[lo:hi].copy_(torch.from_numpy(g.mixture_points_parallel(hi - lo, seed, mix, start=lo)))
+    gen_s = time.perf_counter() - t0
+    eng = spx.Engine(local)
+    ph = eng.load_points(dpts)
+    t1 = time.perf_counter()
+    idx = serve_indexes(eng, SERVE_SEED)
+    build_s = time.perf_counter() - t1
+    clocks = ClockSampler(local)
+    th0 = time.time()
+    cap, roof = serve_capacity(eng, ph, N, idx, args.serve_burst, SERVE_SEED, plain_burst=12)
+    clk = clocks.summary(th0, time.time())
+    clocks.stop()
+    for _, gh, ih, _ in idx:
+        eng.free(ih)
+        eng.free(gh)
+    eng.free(ph)
+    eng.close()
+    del dpts
+    torch.cuda.empty_cache()
+    return {"points": N, "data": "synthetic", "generate_s": round(gen_s, 1), "index_build_s": round(build_s, 1),
+            "mix": "70% selection (1-64 query polygons, pool of 32 prebuilt indexes), "
+                   "30% join vs 4 tessellations (500/1000/2500/5000 cells)",
+            "burst": {"batched": args.serve_burst, "fused": args.serve_burst, "plain": 12},
+            "capacity_rps": cap, "value_gpts": cap["batched"] * N / 1e9, "served_roofline": roof, "clocks": clk}
 
 
 def run_serve_bench(args, world, rank, eng, ph, dpts, N, desc, clocks, torch):

@@ -932,6 +932,12 @@ constexpr int kPrefetchChunks = SPX_PREFETCH_CHUNKS; // L2 prefetch distance of 
 #define SPX_TMA_POINTS 1
 #endif
 constexpr bool kTmaPoints = SPX_TMA_POINTS != 0; // pass 1a stages points with bulk copies when they fit
+#ifndef SPX_RESOLVE_PIPE
+#define SPX_RESOLVE_PIPE 0
+#endif
+// pass 1a with the block summary loads a warp's next chunk of points into
+// registers before the current chunk's cell words
+constexpr bool kResolvePipe = SPX_RESOLVE_PIPE != 0;
 
 // Shared memory of pass 1a: [summary][TMA: per warp a chunk buffer, then per
 // warp an mbarrier][counters].
@@ -983,6 +989,19 @@ __global__ void __launch_bounds__(THREADS, SUM ? 1 : (TMA ? 6 : kResolveMinBlock
             s_hist[i] = 0;
     __syncthreads();
     uint32_t n_pts = 0, n_pairs = 0, phase = 0;
+    constexpr bool PIPE = SUM && !TMA && kResolvePipe;
+    int2 pn[kWItems]; // PIPE: the points of this warp's next chunk
+    auto load_chunk = [&](uint32_t c, int2(&q)[kWItems]) {
+        const uint64_t b = (uint64_t)c * kWChunk;
+        const uint32_t m = c < nchunks ? (uint32_t)min((uint64_t)kWChunk, a.n - b) : 0u;
+#pragma unroll
+        for (int j = 0; j < kWItems; ++j) {
+            const uint32_t loc = j * 32 + lane;
+            q[j] = loc < m ? __ldcs(a.pts + b + loc) : make_int2(-1, -1);
+        }
+    };
+    if (PIPE)
+        load_chunk(blockIdx.x * WARPS + warp, pn);
     for (uint32_t ch = blockIdx.x * WARPS + warp; ch < nchunks; ch += nw) {
         const uint64_t base = (uint64_t)ch * kWChunk;
         const uint32_t npts = (uint32_t)min((uint64_t)kWChunk, a.n - base);
@@ -991,7 +1010,18 @@ __global__ void __launch_bounds__(THREADS, SUM ? 1 : (TMA ? 6 : kResolveMinBlock
         uint16_t *res16 = reinterpret_cast<uint16_t *>(a.res) + base;
         int2 p[kWItems];
         uint32_t w[kWItems];
-        if (TMA && npts == kWChunk) {
+        if (PIPE) {
+            if (kPrefetchChunks > 0 && lane == 0) {
+                // the chunk after the next goes to L2; the next one to registers now
+                const uint64_t nb = base + (uint64_t)(kPrefetchChunks + 1) * nw * kWChunk;
+                if (nb + kWChunk <= a.n)
+                    prefetch_l2_bulk(a.pts + nb, kWChunk * sizeof(int2));
+            }
+#pragma unroll
+            for (int j = 0; j < kWItems; ++j)
+                p[j] = pn[j];
+            load_chunk(ch + nw, pn);
+        } else if (TMA && npts == kWChunk) {
             if (!mbar_wait(s_bar, phase, kWaitTries)) {
                 // the copy did not arrive: report it, give it one more bounded wait, stop
                 if (lane == 0)
