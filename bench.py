@@ -40,9 +40,9 @@ L2_BYTES = 129 * 1024 * 1024
 # results), scaled per point, keyed by the index's (grid_log2, sub_log2); only
 # valid for those kernel versions and the default workload.  A missing entry:
 # not captured.
-RESOLVE_TRAFFIC_BYTES_PER_POINT = {(12, 3): {"k_resolve": (270.569984e6 + 31.558656e6) / 20e6,
-                                             "k_walk": (62.566400e6 + 1.213952e6) / 20e6,
-                                             "k_wemit": (43.176960e6 + 98.720000e6) / 20e6}}
+RESOLVE_TRAFFIC_BYTES_PER_POINT = {(12, 3): {"k_resolve": (272.762368e6 + 30.259712e6) / 20e6,
+                                             "k_walk": (62.574336e6 + 1.225728e6) / 20e6,
+                                             "k_wemit": (43.166720e6 + 98.548992e6) / 20e6}}
 # The same for the distance join's pass 1 (k_dwarp<resolve>), from one capture
 # of a 20M-point run of the 1024-disk workload at its default grid (g = 12).
 DISK_RESOLVE_TRAFFIC_BYTES_PER_POINT = (167.498496e6 + 25.302784e6) / 20e6

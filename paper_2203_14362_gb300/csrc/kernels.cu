@@ -933,7 +933,7 @@ constexpr int kPrefetchChunks = SPX_PREFETCH_CHUNKS; // L2 prefetch distance of 
 #endif
 constexpr bool kTmaPoints = SPX_TMA_POINTS != 0; // pass 1a stages points with bulk copies when they fit
 #ifndef SPX_RESOLVE_PIPE
-#define SPX_RESOLVE_PIPE 0
+#define SPX_RESOLVE_PIPE 1
 #endif
 // pass 1a with the block summary loads a warp's next chunk of points into
 // registers before the current chunk's cell words
