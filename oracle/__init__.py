@@ -63,6 +63,10 @@ def _bind(lib):
     lib.oracle_join_fast.restype = C.c_uint64
     lib.oracle_disk_join.argtypes = [P, C.c_uint64, P, P, C.c_uint32, P, C.c_uint64, P]
     lib.oracle_disk_join.restype = C.c_uint64
+    lib.oracle_near_ring.argtypes = [C.c_int32, C.c_int32, P, C.c_uint64, C.c_int32]
+    lib.oracle_near_ring.restype = C.c_int
+    lib.oracle_buffer_join.argtypes = [P, C.c_uint64, P, P, C.c_uint32, P, P, C.c_uint64, P, C.c_int]
+    lib.oracle_buffer_join.restype = C.c_uint64
     return lib
 
 
@@ -119,6 +123,33 @@ def disk_join(points, centers, radii, lib=None):
     pairs = np.zeros((max(total, 1), 2), dtype=np.uint32)
     lib.oracle_disk_join(_ptr(pts), pts.shape[0], _ptr(cxy), _ptr(r), Q, _ptr(pairs), total, _ptr(counts))
     return pairs[:total], counts[:Q]
+
+
+def near_ring(px: int, py: int, ring: np.ndarray, r: int, lib=None) -> bool:
+    """Is (px, py) within distance r of an edge (closed segment) of the ring?"""
+    lib = lib or load()
+    rg = np.ascontiguousarray(ring, dtype=np.int32).reshape(-1, 2)
+    return bool(lib.oracle_near_ring(int(px), int(py), _ptr(rg), rg.shape[0], int(r)))
+
+
+def buffer_join(points, verts, ring_off, radii, threads: int | None = None, lib=None):
+    """Buffered-polygon join (SPADE §4.2 distance canvases, §5.2 distance
+    queries): pairs (M, 2) uint32 (point id, polygon id), sorted, of the points
+    inside polygon q or within distance radii[q] of one of its edges, and
+    counts (P,) uint64.  Every edge of every polygon whose bbox grown by r
+    reaches the point is tested."""
+    lib = lib or load()
+    pts, xy, off = _prep(points, verts, ring_off)
+    P = off.shape[0] - 1
+    r = np.ascontiguousarray(radii, dtype=np.int32).reshape(-1)
+    assert r.shape[0] == P and (P == 0 or (r.min() >= 0 and r.max() < (1 << 30)))
+    th = threads or default_threads()
+    counts = np.zeros(max(P, 1), dtype=np.uint64)
+    total = lib.oracle_buffer_join(_ptr(pts), pts.shape[0], _ptr(xy), _ptr(off), P, _ptr(r), None, 0, _ptr(counts), th)
+    pairs = np.zeros((max(total, 1), 2), dtype=np.uint32)
+    lib.oracle_buffer_join(_ptr(pts), pts.shape[0], _ptr(xy), _ptr(off), P, _ptr(r), _ptr(pairs), total,
+                           _ptr(counts), th)
+    return pairs[:total], counts[:P]
 
 
 class Prepared:

@@ -396,3 +396,163 @@ uint64_t oracle_disk_join(const int32_t *pts, uint64_t n, const int32_t *cxy, co
     return total;
 }
 
+
+/* ------------------------------------------------ buffered polygons */
+
+/*
+ * Buffered-polygon join (SPADE §4.2 "Canvases for Distance-Based Queries": a
+ * distance constraint of radius r around a polygon is drawn as the polygon
+ * together with a rounded rectangle of radius r around each of its edges;
+ * §5.2 "Distance-Based Queries"): point p meets the buffered polygon (R, r)
+ * iff p lies inside R (the half-open rule above) or the distance from p to
+ * some edge of R, taken as a closed segment, is at most r.  The union of R and
+ * the rounded rectangles is exactly the set of points within distance r of R.
+ *
+ * Distance to the segment a -> b (d = b - a, w = p - a, t = w . d):
+ *   t <= 0        : |p - a|
+ *   t >= |d|^2    : |p - b|
+ *   otherwise     : |d x w| / |d|   (the foot of the perpendicular lies inside)
+ * Every comparison is exact: coordinates lie in [0, 2^30], so each product of
+ * differences is below 2^60 in magnitude and sums of two stay below 2^62 in
+ * int64; the perpendicular case compares (d x w)^2 <= r^2 |d|^2, both below
+ * 2^123, in unsigned 128-bit arithmetic.  A ring's degenerate edge (a = b) has
+ * |d|^2 = 0 and takes the first case.
+ */
+static int seg_within(int64_t px, int64_t py, int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t r)
+{
+    const int64_t dx = bx - ax, dy = by - ay, wx = px - ax, wy = py - ay, rr = r * r;
+    const int64_t t = wx * dx + wy * dy;
+    if (t <= 0)
+        return wx * wx + wy * wy <= rr;
+    const int64_t dd = dx * dx + dy * dy;
+    if (t >= dd) {
+        const int64_t ux = px - bx, uy = py - by;
+        return ux * ux + uy * uy <= rr;
+    }
+    const int64_t c = dx * wy - dy * wx;
+    const unsigned __int128 ca = (unsigned __int128)(uint64_t)(c < 0 ? -c : c);
+    return ca * ca <= (unsigned __int128)(uint64_t)rr * (unsigned __int128)(uint64_t)dd;
+}
+
+/* p within distance r of an edge of the ring of n vertices (every edge) */
+int oracle_near_ring(int32_t px, int32_t py, const int32_t *xy, uint64_t n, int32_t r)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t j = (i + 1 == n) ? 0 : i + 1;
+        if (seg_within(px, py, xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1], r))
+            return 1;
+    }
+    return 0;
+}
+
+typedef struct {
+    const int32_t *pts, *xy, *r;
+    const uint64_t *ring_off;
+    const int64_t *box; /* per polygon: closed vertex bbox grown by r (xmin, ymin, xmax, ymax) */
+    uint32_t P;
+    uint64_t lo, hi;
+    int want_pairs;
+    uint32_t *pairs;
+    uint64_t npairs, cap;
+    uint64_t *counts;
+} bjob;
+
+static void *buffer_worker(void *arg)
+{
+    bjob *j = (bjob *)arg;
+    for (uint64_t i = j->lo; i < j->hi; ++i) {
+        const int32_t px = j->pts[2 * i], py = j->pts[2 * i + 1];
+        /* the points' domain is [0, 2^30)^2; a point outside it meets nothing */
+        if (px < 0 || py < 0 || px >= (1 << ORACLE_BOX_LOG2) || py >= (1 << ORACLE_BOX_LOG2))
+            continue;
+        for (uint32_t q = 0; q < j->P; ++q) {
+            const int64_t *b = j->box + 4 * (uint64_t)q;
+            /* inside R implies inside its vertex bbox, and a point within r of
+             * an edge lies within r of the edge's bbox: outside the bbox grown
+             * by r, neither holds */
+            if (px < b[0] || py < b[1] || px > b[2] || py > b[3])
+                continue;
+            const uint64_t v0 = j->ring_off[q], nv = j->ring_off[q + 1] - v0;
+            if (!oracle_point_in_ring(px, py, j->xy + 2 * v0, nv) &&
+                !oracle_near_ring(px, py, j->xy + 2 * v0, nv, j->r[q]))
+                continue;
+            j->counts[q]++;
+            if (j->want_pairs) {
+                if (j->npairs == j->cap) {
+                    j->cap = j->cap ? 2 * j->cap : 1024;
+                    j->pairs = (uint32_t *)realloc(j->pairs, sizeof(uint32_t) * 2 * j->cap);
+                }
+                j->pairs[2 * j->npairs] = (uint32_t)i;
+                j->pairs[2 * j->npairs + 1] = q;
+            }
+            j->npairs++;
+        }
+    }
+    return NULL;
+}
+
+/*
+ * Buffered-polygon join over nthreads threads (contiguous point ranges,
+ * concatenated in range order): pairs (point id, polygon id) sorted, the
+ * first cap of them into pairs (may be NULL), counts (P, may be NULL).
+ * r[q] in [0, 2^30).  Returns the total number of pairs.
+ */
+uint64_t oracle_buffer_join(const int32_t *pts, uint64_t n, const int32_t *xy, const uint64_t *ring_off, uint32_t P,
+                            const int32_t *r, uint32_t *pairs, uint64_t cap, uint64_t *counts, int nthreads)
+{
+    int64_t *box = (int64_t *)malloc(sizeof(int64_t) * 4 * (P ? P : 1));
+    for (uint32_t q = 0; q < P; ++q) {
+        int64_t x0 = INT64_MAX, y0 = INT64_MAX, x1 = INT64_MIN, y1 = INT64_MIN;
+        for (uint64_t v = ring_off[q]; v < ring_off[q + 1]; ++v) {
+            x0 = xy[2 * v] < x0 ? xy[2 * v] : x0;
+            x1 = xy[2 * v] > x1 ? xy[2 * v] : x1;
+            y0 = xy[2 * v + 1] < y0 ? xy[2 * v + 1] : y0;
+            y1 = xy[2 * v + 1] > y1 ? xy[2 * v + 1] : y1;
+        }
+        box[4 * q] = x0 - r[q];
+        box[4 * q + 1] = y0 - r[q];
+        box[4 * q + 2] = x1 + r[q];
+        box[4 * q + 3] = y1 + r[q];
+    }
+    if (nthreads < 1)
+        nthreads = 1;
+    if ((uint64_t)nthreads > n && n > 0)
+        nthreads = (int)n;
+    bjob *jobs = (bjob *)calloc(nthreads, sizeof(bjob));
+    pthread_t *th = (pthread_t *)calloc(nthreads, sizeof(pthread_t));
+    for (int t = 0; t < nthreads; ++t) {
+        bjob *j = &jobs[t];
+        j->pts = pts;
+        j->xy = xy;
+        j->r = r;
+        j->ring_off = ring_off;
+        j->box = box;
+        j->P = P;
+        j->lo = n * (uint64_t)t / nthreads;
+        j->hi = n * (uint64_t)(t + 1) / nthreads;
+        j->want_pairs = pairs != NULL;
+        j->counts = (uint64_t *)calloc(P ? P : 1, sizeof(uint64_t));
+        pthread_create(&th[t], NULL, buffer_worker, j);
+    }
+    uint64_t total = 0;
+    if (counts)
+        memset(counts, 0, sizeof(uint64_t) * P);
+    for (int t = 0; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        if (pairs)
+            for (uint64_t k = 0; k < jobs[t].npairs && total + k < cap; ++k) {
+                pairs[2 * (total + k)] = jobs[t].pairs[2 * k];
+                pairs[2 * (total + k) + 1] = jobs[t].pairs[2 * k + 1];
+            }
+        if (counts)
+            for (uint32_t q = 0; q < P; ++q)
+                counts[q] += jobs[t].counts[q];
+        total += jobs[t].npairs;
+        free(jobs[t].pairs);
+        free(jobs[t].counts);
+    }
+    free(jobs);
+    free(th);
+    free(box);
+    return total;
+}
