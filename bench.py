@@ -83,6 +83,18 @@ def make_workload(name: str, n_override: int | None, rank: int):
         desc = (f"distance join: {n} mixture points x 1024 disks (centres from the point mixture, radius "
                 f"lognormal, median 0.1% of the box); pairs (point, disk) with distance <= r + counts")
         return pts, centers, radii, desc
+    if name == "buffer256_100m":
+        n = n_override or 100_000_000
+        seed = g.SEED_BASE + 8
+        mix = g.make_mixture(g.SEED_BASE + 3)
+        v, o = g.query_polygons(256, g.SEED_BASE + 3, mix)
+        pts = g.mixture_points_parallel(n, seed, mix, start=shard_start(rank, n))
+        rng = np.random.default_rng(seed)
+        radii = np.clip(np.exp(rng.normal(np.log(1 << 20), 0.7, 256)), 1 << 16, 1 << 23).astype(np.int32)
+        desc = (f"buffered-polygon join: {n} mixture points x the 256 query polygons of the selection workload, "
+                f"each grown by a radius (lognormal, median 2^20 = 0.1% of the box side); pairs (point, polygon) "
+                f"with distance <= r + counts")
+        return pts, (v, o), radii, desc
     if name == "serve_1b":
         n = n_override or 1_000_000_000
         seed = g.SEED_BASE + 4
@@ -287,6 +299,12 @@ def run_reference(args, world, rank):
 
         def step():
             oracle.disk_join(pts, v, o)
+    elif args.workload.startswith("buffer"):
+        threads = oracle.default_threads()
+        (bv, bo), radii = v, o
+
+        def step():
+            oracle.buffer_join(pts, bv, bo, radii, threads=threads)
     else:
         pr = oracle.Prepared(v, o)
         threads = oracle.default_threads()
@@ -307,10 +325,14 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "sample_points_per_step": sample,
-                   "polygons": int(v.shape[0]) if args.workload.startswith("dist") else int(o.shape[0] - 1)},
+                   "polygons": (int(v.shape[0]) if args.workload.startswith("dist") else
+                                int(v[1].shape[0] - 1) if args.workload.startswith("buffer") else int(o.shape[0] - 1))},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": (f"first {sample} points of the workload per step (distance join, brute force "
                                     "over all disks)" if args.workload.startswith("dist") else
+                                    f"first {sample} points of the workload per step (buffered-polygon join, every "
+                                    "edge of each polygon whose grown bbox holds the point)"
+                                    if args.workload.startswith("buffer") else
                                     f"first {sample} points of the workload per step (pairs + counts, fast oracle)")},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -335,6 +357,11 @@ def run_spx(args, world, rank, local):
         return 0
     if args.workload.startswith("select"):
         line = select_measure(args, world, rank, local, torch, args.steps, args.warmup, args.points)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
+    if args.workload.startswith("buffer"):
+        line = buffer_measure(args, world, rank, local, torch, args.steps, args.warmup, args.points)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return 0
@@ -1034,6 +1061,92 @@ def select_measure(args, world, rank, local, torch, steps, warmup, n_override):
     return line
 
 
+def buffer_measure(args, world, rank, local, torch, steps, warmup, n_override):
+    """Buffered-polygon join (returns the JSON object): one step = spx_join of
+    the resident table against the 256 buffered query polygons (count pass,
+    scan, write pass), pairs + counts."""
+    import oracle
+    from paper_2203_14362_gb300 import spx
+    clocks = ClockSampler(local)
+    pts, (v, o), radii, desc = make_workload("buffer256_100m", n_override, rank)
+    N, P = pts.shape[0], int(o.shape[0] - 1)
+    eng = spx.Engine(local)
+    dpts = torch.from_numpy(pts).cuda()
+    ph = eng.load_points(dpts)
+    gh = eng.load_polygons(v, o)
+    ih = eng.build_buffer_index(gh, radii, grid_log2=args.grid, fp32_filter=bool(args.fp32))
+    info = eng.index_info(ih)
+    counts = torch.zeros(P, dtype=torch.int64, device="cuda")
+    try:
+        total = eng.join(ph, ih, None, counts)
+    except spx.SpxError as e:  # the two-call pattern: the first call reports the size
+        total = int(str(e).split("needs ")[1].split(" ")[0])
+    pairs = torch.empty((max(total, 1), 2), dtype=torch.int32, device="cuda")
+    assert eng.join(ph, ih, pairs, counts) == total
+    # a seeded sample of points against the oracle, one by one (any size)
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(N, size=min(N, 100_000), replace=False))
+    want, _ = oracle.buffer_join(pts[sample], v, o, radii)
+    host = pairs[:total].cpu().numpy().view(np.uint32)
+    lo = np.searchsorted(host[:, 0], sample, "left")
+    hi = np.searchsorted(host[:, 0], sample, "right")
+    got = np.concatenate([np.stack([np.searchsorted(sample, host[a:b, 0]), host[a:b, 1]], 1)
+                          for a, b in zip(lo, hi) if b > a] or [np.zeros((0, 2), np.int64)]).astype(np.uint32)
+    assert np.array_equal(got, want), "sampled points differ from the oracle"
+    assert int(counts.sum().item()) == total
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        eng.join(ph, ih, pairs, counts, sync=False, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.time()
+    e0.record(stream)
+    for _ in range(steps):
+        eng.join(ph, ih, pairs, counts, sync=False, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, torch)
+    clk = clocks.summary(t_host0, t_host1)
+    clocks.stop()
+    peak, peak_kind = peaks()
+    alg = 8 * N + 8 * total + 8 * P + int(info["device_bytes"])
+    achieved = alg / (ms * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m = min(N, 1_000_000)
+        th = oracle.default_threads()
+        t0 = time.perf_counter()
+        oracle.buffer_join(pts[:m], v, o, radii, threads=th)
+        sec = time.perf_counter() - t0
+        cpu = {"value": m / sec / 1e9, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": f"first {m} points of the same table (buffered-polygon join, {sec:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": world * N / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "buffer256_100m", "desc": desc, "points_per_gpu": N, "polygons": P,
+                   "vertices": int(v.shape[0]), "pairs": int(total), "grid_log2": info["grid_log2"],
+                   "edge_grid_log2": info["edge_grid_log2"], "edge_items": int(info["n_edge_items"]),
+                   "index_build_ms": round(info["build_ms"], 1), "index_device_bytes": int(info["device_bytes"]),
+                   "check": "100k sampled points == oracle; sum of counts == pairs",
+                   "l2": "inputs larger than L2 (0.8 GB of points); no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": "whole buffered join (k_buf_count, scan, k_buf_write)",
+                     "algorithmic_bytes_per_launch": int(alg)},
+        "cpu_baseline": cpu, "e2e": None, "clocks": clk,
+        "gpu_launches": steps * (2 + (1 if -(-N // 256) <= 4 * 8192 else 3)),
+    }
+    eng.free(ih)
+    eng.free(gh)
+    eng.free(ph)
+    eng.close()
+    del dpts, pairs, counts
+    return line
+
+
 def spx_error():
     from paper_2203_14362_gb300 import spx
     return spx.SpxError
@@ -1046,7 +1159,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["spx", "reference"], default="spx")
     ap.add_argument("--workload", default="tess2000_100m",
-                    choices=["tess2000_100m", "stars_1m", "select256_500m", "serve_1b", "count_4b", "dist1024_100m"])
+                    choices=["tess2000_100m", "stars_1m", "select256_500m", "serve_1b", "count_4b", "dist1024_100m",
+                             "buffer256_100m"])
     ap.add_argument("--points", type=int, default=None, help="points per GPU (default: the workload's)")
     ap.add_argument("--grid", type=int, default=0, help="grid_log2 (0 = automatic)")
     ap.add_argument("--sub", type=int, default=0, help="sub_log2 (0 = default, 3)")

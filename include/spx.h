@@ -234,9 +234,35 @@ typedef struct {
                                 that is empty or INSIDE one polygon */
     int use_sum;             /* 1: join pass 1a reads the block summary from shared memory */
     int pad2;
+    int edge_grid_log2;      /* buffered polygons: 2^edge_grid_log2 edge-grid cells per side; else 0 */
+    int pad3;
+    uint64_t n_edge_items;   /* buffered polygons: (cell, edge) entries of the edge grid; else 0 */
 } spx_index_info;
 
 spx_status spx_index_info_get(spx_ctx *ctx, spx_index index, spx_index_info *out);
+
+/*
+ * Index of a set of buffered polygons for distance queries (§4.2 "Canvases
+ * for Distance-Based Queries": the constraint of distance r around a polygon
+ * is the polygon together with a rounded rectangle of radius r around each of
+ * its edges; §5.2 "Distance-Based Queries").  A point p (in [0, 2^30)^2)
+ * meets polygon q of `polys` buffered by r[q] (in [0, 2^30)) iff p is inside
+ * ring q (the crossing rule of spx_build_index) or within distance r[q] of one
+ * of its edges taken as a closed segment (a ring of one vertex: a disk),
+ * decided exactly (int64, and 128-bit products for the distance to an edge's
+ * interior).  The index holds the polygons' own grid index (automatic grid,
+ * fp32_filter as given) and an edge grid of 2^grid_log2 cells per side
+ * (0: about one median edge length plus 2r per cell, clamped to 5..12) that
+ * lists, per cell, the edges whose r-neighbourhood may reach it, by polygon.
+ * The returned index serves spx_join (pairs (point id, polygon id) in that
+ * order, one per pair, counts per polygon), spx_select (at most 1024
+ * polygons) and spx_aggregate; the other calls refuse it.  r: P host values,
+ * copied.  The polygon handle must stay alive while the index is used.
+ * Errors: SPX_EINVAL (bad handle, a radius out of range, grid_log2 outside
+ * 0..12, an edge grid too large for 32-bit offsets), SPX_ENOMEM, SPX_ECUDA.
+ */
+spx_status spx_build_buffer_index(spx_ctx *ctx, spx_polys polys, const int32_t *r, int grid_log2, int fp32_filter,
+                                  spx_index *out);
 
 /* Autotuner settings.  Zero fields take the defaults. */
 typedef struct {

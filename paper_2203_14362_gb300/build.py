@@ -20,7 +20,7 @@ LIB_CHECKED = os.path.join(PKG, "libspx_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels.cu", "api.cu", "server.cu", "index_build_device.cu"]
-CPP_SOURCES = ["index_build.cpp", "disk_index.cpp"]
+CPP_SOURCES = ["index_build.cpp", "disk_index.cpp", "buffer_index.cpp"]
 
 
 def nvcc() -> str:

@@ -53,8 +53,10 @@ struct PolysObj {
 
 struct IndexObj {
     uint64_t polys = 0;
-    int kind = 0;        // 0: polygons (view), 1: disks (dview)
+    int kind = 0;        // 0: polygons (view), 1: disks (dview), 2: buffered polygons (view and bview)
     DiskView dview{};
+    BufferView bview{};
+    void *mem2 = nullptr; // buffered polygons: edge grid (cell offsets | polygons | segments | radii)
     IndexView view{};
     int fp32 = 1;
     void *mem = nullptr; // one allocation: cells | fine | entries | edges | cover | summary
@@ -288,6 +290,52 @@ spx_status disk_join_common(spx_ctx *ctx, PointsObj *pts, IndexObj *ix, uint32_t
     return SPX_OK;
 }
 
+BufferLaunch buffer_launch(spx_ctx *ctx, PointsObj *pts, IndexObj *ix)
+{
+    BufferLaunch a{};
+    a.ix = ix->view;
+    a.bv = ix->bview;
+    a.pts = reinterpret_cast<const int2 *>(pts->dev);
+    a.n = pts->n;
+    a.stats = ctx->aux->stats;
+    a.fp32 = ix->fp32;
+    return a;
+}
+
+// The buffered-polygon join: same contract as the polygon join.
+spx_status buffer_join_common(spx_ctx *ctx, PointsObj *pts, IndexObj *ix, uint32_t *pairs_dev, uint64_t cap,
+                              uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream)
+{
+    if (cap && !pairs_dev)
+        return fail(ctx, SPX_EINVAL, "join: pairs_dev is NULL with cap > 0");
+    if ((reinterpret_cast<uintptr_t>(pairs_dev) & 7) || (reinterpret_cast<uintptr_t>(counts_dev) & 7) ||
+        (reinterpret_cast<uintptr_t>(total_dev) & 7))
+        return fail(ctx, SPX_EINVAL, "join: output pointers must be 8-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, buffer_scratch_bytes(pts->n), s, "join");
+    if (st != SPX_OK)
+        return st;
+    BufferLaunch a = buffer_launch(ctx, pts, ix);
+    a.pairs = reinterpret_cast<uint2 *>(pairs_dev);
+    a.cap = pairs_dev ? cap : 0;
+    a.counts = reinterpret_cast<unsigned long long *>(counts_dev);
+    a.total = total_dev ? reinterpret_cast<unsigned long long *>(total_dev) : (n_pairs ? &ctx->aux->total : nullptr);
+    cudaError_t e = launch_buffer_join(a, ctx->scratch, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "join launch");
+    if (n_pairs) {
+        if ((st = check_kernel_err(ctx, s)) != SPX_OK)
+            return st;
+        unsigned long long t = 0;
+        SPX_CUDA(cudaMemcpy(&t, a.total, sizeof(t), cudaMemcpyDeviceToHost), "read total");
+        *n_pairs = t;
+        if (t > cap)
+            return fail(ctx, SPX_ECAPACITY, "join: " + std::to_string(t) + " pairs exceed capacity " +
+                                                std::to_string(cap));
+    }
+    return SPX_OK;
+}
+
 spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_t *pairs_dev, uint64_t cap,
                        uint64_t *counts_dev, uint64_t *total_dev, uint64_t *n_pairs, void *stream, bool plain)
 {
@@ -303,6 +351,8 @@ spx_status join_common(spx_ctx *ctx, spx_points points, spx_index index, uint32_
         return fail(ctx, SPX_EINVAL, "join: a cell-clustered point table has no row order; use spx_aggregate");
     if (ix->kind == 1)
         return disk_join_common(ctx, pts, ix, pairs_dev, cap, counts_dev, total_dev, n_pairs, stream);
+    if (ix->kind == 2)
+        return buffer_join_common(ctx, pts, ix, pairs_dev, cap, counts_dev, total_dev, n_pairs, stream);
     if (cap && !pairs_dev)
         return fail(ctx, SPX_EINVAL, "join: pairs_dev is NULL with cap > 0");
     if ((reinterpret_cast<uintptr_t>(pairs_dev) & 7) || (reinterpret_cast<uintptr_t>(counts_dev) & 7) ||
@@ -1188,6 +1238,88 @@ spx_status spx_disk_index_arrays(spx_ctx *ctx, spx_index index, uint32_t *cell, 
     return SPX_OK;
 }
 
+spx_status spx_build_buffer_index(spx_ctx *ctx, spx_polys polys, const int32_t *r, int grid_log2, int fp32_filter,
+                                  spx_index *out)
+{
+    if (!ctx || !out)
+        return fail(ctx, SPX_EINVAL, "build_buffer_index: null argument");
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    PolysObj *pg = lookup(ctx->polys, polys);
+    if (!pg)
+        return fail(ctx, SPX_EINVAL, "build_buffer_index: bad polygon handle");
+    if (pg->P && !r)
+        return fail(ctx, SPX_EINVAL, "build_buffer_index: null radii");
+    if (pg->P >= kBufferFull)
+        return fail(ctx, SPX_EINVAL, "build_buffer_index: more than 2^31 - 1 polygons");
+    for (uint32_t q = 0; q < pg->P; ++q)
+        if (r[q] < 0 || r[q] >= int32_t(kBox))
+            return fail(ctx, SPX_EINVAL, "build_buffer_index: radius " + std::to_string(q) + " outside [0, 2^30)");
+    if (grid_log2 < 0 || grid_log2 > 12)
+        return fail(ctx, SPX_EINVAL, "build_buffer_index: grid_log2 must be in [1, 12] (0 = automatic)");
+    const auto t0 = std::chrono::steady_clock::now();
+    const int g = grid_log2 ? grid_log2 : default_buffer_grid_log2(pg->xy.data(), pg->off.data(), pg->P, r);
+    HostBufferEdges he;
+    std::string err;
+    if (!build_buffer_edges(pg->xy.data(), pg->off.data(), pg->P, r, g, he, err))
+        return fail(ctx, SPX_EINVAL, "build_buffer_index: " + err);
+    // the polygons' own index answers containment; it becomes part of this one
+    spx_index_params prm{};
+    prm.fp32_filter = fp32_filter ? 1 : 0;
+    prm.sub_log2 = kMaxSubLog2;
+    spx_index h = 0;
+    spx_status st = build_index_impl(ctx, polys, prm, &h);
+    if (st != SPX_OK)
+        return st;
+    auto it = ctx->indexes.find(h);
+    std::unique_ptr<IndexObj> ix = std::move(it->second);
+    ctx->indexes.erase(it);
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const uint32_t P = pg->P;
+    const size_t n_items = he.item_q.size();
+    const size_t b_off = he.cell_off.size() * 4, b_q = std::max<size_t>(n_items, 1) * 4,
+                 b_seg = std::max<size_t>(n_items, 1) * 16, b_r = std::max<size_t>(P, 1) * 4;
+    const size_t total = up(b_off) + up(b_q) + up(b_seg) + up(b_r);
+    void *mem2 = nullptr;
+    if (cudaMalloc(&mem2, total) != cudaSuccess) {
+        cudaFree(ix->mem);
+        pg->n_index--;
+        return fail(ctx, SPX_ENOMEM, "build_buffer_index: cudaMalloc failed");
+    }
+    char *m = static_cast<char *>(mem2), *p_q = m + up(b_off), *p_seg = p_q + up(b_q), *p_r = p_seg + up(b_seg);
+    cudaError_t e = cudaMemcpy(m, he.cell_off.data(), b_off, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_items)
+        e = cudaMemcpy(p_q, he.item_q.data(), n_items * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_items)
+        e = cudaMemcpy(p_seg, he.item_seg.data(), n_items * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && P)
+        e = cudaMemcpy(p_r, r, size_t(P) * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(mem2);
+        cudaFree(ix->mem);
+        pg->n_index--;
+        return cuda_fail(ctx, e, "build_buffer_index upload");
+    }
+    ix->kind = 2;
+    ix->mem2 = mem2;
+    ix->bview.cell_off = reinterpret_cast<const uint32_t *>(m);
+    ix->bview.item_q = reinterpret_cast<const uint32_t *>(p_q);
+    ix->bview.item_seg = reinterpret_cast<const int4 *>(p_seg);
+    ix->bview.rad = reinterpret_cast<const int32_t *>(p_r);
+    ix->bview.g = g;
+    ix->bview.sc = kBoxLog2 - g;
+    ix->bview.P = P;
+    ix->bview.n_items = n_items;
+    ix->info.edge_grid_log2 = g;
+    ix->info.n_edge_items = n_items;
+    ix->info.device_bytes += total;
+    ix->info.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const uint64_t hb = make_handle(ctx, kTagIndex);
+    ctx->indexes[hb] = std::move(ix);
+    *out = hb;
+    return SPX_OK;
+}
+
 spx_status spx_index_info_get(spx_ctx *ctx, spx_index index, spx_index_info *out)
 {
     if (!ctx || !out)
@@ -1228,12 +1360,34 @@ spx_status spx_select(spx_ctx *ctx, spx_points points, spx_index index, uint32_t
         return fail(ctx, SPX_EINVAL, "select: offsets_dev is NULL, or ids_dev is NULL with cap > 0");
     if ((reinterpret_cast<uintptr_t>(offsets_dev) & 7) || (reinterpret_cast<uintptr_t>(ids_dev) & 3))
         return fail(ctx, SPX_EINVAL, "select: misaligned output pointer");
-    const uint32_t PQ = ix->kind == 1 ? ix->dview.Q : ix->view.P;
+    const uint32_t PQ = ix->kind == 1 ? ix->dview.Q : ix->kind == 2 ? ix->bview.P : ix->view.P;
     if (PQ > kSelectMaxQueries)
         return fail(ctx, SPX_EINVAL, "select: an index of " + std::to_string(PQ) +
                                          " queries; batched selection takes at most " +
                                          std::to_string(kSelectMaxQueries));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (ix->kind == 2) {
+        // buffered polygons: points inside or within r of each polygon, ascending per polygon
+        spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, buffer_select_scratch_bytes(pts->n, PQ, cap),
+                               s, "select");
+        if (st != SPX_OK)
+            return st;
+        unsigned long long *offs = reinterpret_cast<unsigned long long *>(offsets_dev);
+        cudaError_t e = launch_buffer_select(buffer_launch(ctx, pts, ix), ids_dev, cap, offs, ctx->scratch, s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "select launch");
+        if (n_ids) {
+            if ((st = check_kernel_err(ctx, s)) != SPX_OK)
+                return st;
+            unsigned long long t = 0;
+            SPX_CUDA(cudaMemcpy(&t, offs + PQ, sizeof(t), cudaMemcpyDeviceToHost), "select total");
+            *n_ids = t;
+            if (t > cap)
+                return fail(ctx, SPX_ECAPACITY, "select: " + std::to_string(t) + " ids exceed capacity " +
+                                                    std::to_string(cap));
+        }
+        return SPX_OK;
+    }
     if (ix->kind == 1) {
         // distance selection: points within r of each centre, ascending per disk
         spx_status st = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, disk_select_scratch_bytes(pts->n, PQ, cap), s,
@@ -1337,6 +1491,12 @@ spx_status spx_aggregate(spx_ctx *ctx, spx_points points, spx_index index, uint6
         d.counts = reinterpret_cast<unsigned long long *>(counts_dev);
         d.stats = ctx->aux->stats;
         cudaError_t e = launch_disk_aggregate(d, reinterpret_cast<cudaStream_t>(stream));
+        return e == cudaSuccess ? SPX_OK : cuda_fail(ctx, e, "aggregate launch");
+    }
+    if (ix->kind == 2) { // counts do not depend on the point order: clustered tables too
+        BufferLaunch b = buffer_launch(ctx, pts, ix);
+        b.counts = reinterpret_cast<unsigned long long *>(counts_dev);
+        cudaError_t e = launch_buffer_aggregate(b, reinterpret_cast<cudaStream_t>(stream));
         return e == cudaSuccess ? SPX_OK : cuda_fail(ctx, e, "aggregate launch");
     }
     JoinLaunch a{};
@@ -1880,6 +2040,7 @@ spx_status spx_free(spx_ctx *ctx, uint64_t handle)
                 ++it;
             }
         cudaFree(ix->mem);
+        cudaFree(ix->mem2);
         PolysObj *pg = lookup(ctx->polys, ix->polys);
         if (pg)
             pg->n_index--;

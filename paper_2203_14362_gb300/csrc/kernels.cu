@@ -1679,6 +1679,156 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_write(JoinLaunch a, con
     }
 }
 
+// ------------------------------------------------------- buffered polygons
+// Is (px, py) within distance r of the closed segment v = (a, b)?  With
+// d = b - a, w = p - a and t = w . d: the distance is |w| when t <= 0, |p - b|
+// when t >= |d|^2, else |d x w| / |d|.  Coordinates lie in [0, 2^30], so every
+// product of two differences is below 2^60 in magnitude (int64 sums stay
+// exact); the last case compares (d x w)^2 with r^2 |d|^2 as 128-bit
+// products.  A zero-length edge takes the first case.
+__device__ __forceinline__ bool seg_near(const int4 &v, int px, int py, int64_t r)
+{
+    const int64_t dx = (int64_t)v.z - v.x, dy = (int64_t)v.w - v.y;
+    const int64_t wx = (int64_t)px - v.x, wy = (int64_t)py - v.y, rr = r * r;
+    const int64_t t = wx * dx + wy * dy;
+    if (t <= 0)
+        return wx * wx + wy * wy <= rr;
+    const int64_t dd = dx * dx + dy * dy;
+    if (t >= dd) {
+        const int64_t ux = (int64_t)px - v.z, uy = (int64_t)py - v.w;
+        return ux * ux + uy * uy <= rr;
+    }
+    const int64_t c = dx * wy - dy * wx;
+    const uint64_t ca = (uint64_t)(c < 0 ? -c : c);
+    const uint64_t lh = __umul64hi(ca, ca), ll = ca * ca;
+    const uint64_t rh = __umul64hi((uint64_t)rr, (uint64_t)dd), rl = (uint64_t)rr * (uint64_t)dd;
+    return lh < rh || (lh == rh && ll <= rl);
+}
+
+// Calls f(q) for every buffered polygon q that the in-box point (px, py)
+// meets, ascending, and returns their number: the polygons that contain the
+// point (its polygon index's cell, ascending), merged with the polygons of its
+// edge-grid cell that have an edge within r[q] of it (the cell's items are
+// sorted by polygon, each polygon's edges together; a polygon that contains
+// the point needs no edge test).
+template <bool FP32, class F>
+__device__ __forceinline__ uint32_t buffer_point(const IndexView &ix, const BufferView &bv, int px, int py,
+                                                 uint32_t &tests, uint32_t &esc, uint64_t pol, F f)
+{
+    const uint32_t c = (((uint32_t)py >> bv.sc) << bv.g) | ((uint32_t)px >> bv.sc);
+    uint32_t k = __ldg(bv.cell_off + c);
+    const uint32_t kend = __ldg(bv.cell_off + c + 1);
+    if (!in_bounds(k <= kend && kend <= bv.n_items, ix))
+        return 0u;
+    uint32_t n = 0;
+    // the cell's polygons below `bound` that have an edge within r (an item
+    // flagged kBufferFull: the polygon's r-region holds the whole cell)
+    auto near_below = [&](uint32_t bound) {
+        while (k < kend) {
+            const uint32_t raw = __ldg(bv.item_q + k), q = raw & ~kBufferFull;
+            if (q >= bound || !in_bounds(q < bv.P, ix))
+                break;
+            bool hit = (raw & kBufferFull) != 0;
+            if (hit) {
+                ++k;
+            } else {
+                const int64_t r = __ldg(bv.rad + q);
+                for (; k < kend && __ldg(bv.item_q + k) == q; ++k)
+                    hit = hit || seg_near(ld_idx(bv.item_seg + k, pol), px, py, r);
+            }
+            if (hit) {
+                f(q);
+                ++n;
+            }
+        }
+    };
+    auto inside = [&](uint32_t q) {
+        near_below(q);
+        while (k < kend && (__ldg(bv.item_q + k) & ~kBufferFull) == q) // met already: no test
+            ++k;
+        f(q);
+        ++n;
+    };
+    const uint32_t w = resolve(ix, (uint32_t)px, (uint32_t)py, pol);
+    const uint32_t kind = w >> 30, pay = w & kPayloadMask;
+    if (kind == kCellInsideOne && in_bounds(pay < ix.P, ix))
+        inside(pay);
+    else if (kind == kCellList && in_bounds((uint64_t)pay + 1 < ix.n_ent, ix))
+        walk_entries<FP32>(ix, ix.ent + pay, px, py, tests, esc, pol, inside);
+    near_below(0xffffffffu);
+    return n;
+}
+
+// Pass 1: per-point pair counts (kept for pass 2), per-polygon counts, and
+// the pair total of every 256-point block (block_cnt null: counts only).
+template <bool FP32>
+__global__ void __launch_bounds__(kPlainThreads) k_buf_count(BufferLaunch a, uint32_t *pt_cnt,
+                                                             unsigned long long *block_cnt)
+{
+    __shared__ uint32_t s_w[kPlainThreads / 32];
+    const uint64_t i = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
+    const uint64_t keep = policy_evict_last();
+    uint32_t c = 0, t = 0, e = 0;
+    if (i < a.n) {
+        const int2 p = a.pts[i];
+        if ((uint32_t)(p.x | p.y) < kBox)
+            c = buffer_point<FP32>(a.ix, a.bv, p.x, p.y, t, e, keep, [&](uint32_t q) {
+                if (a.counts)
+                    atomicAdd(a.counts + q, 1ull);
+            });
+        if (pt_cnt)
+            pt_cnt[i] = c;
+    }
+    add_stats(a.stats, i < a.n ? 1u : 0u, t, e, c);
+    if (!block_cnt)
+        return;
+    const uint32_t s = warp_sum32(c);
+    if ((threadIdx.x & 31) == 0)
+        s_w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < kPlainThreads / 32; ++w)
+            b += s_w[w];
+        block_cnt[blockIdx.x] = b;
+    }
+}
+
+// Pass 2: each point's pairs at its block's scanned offset plus the counts
+// of the block's earlier points.
+template <bool FP32>
+__global__ void __launch_bounds__(kPlainThreads) k_buf_write(BufferLaunch a, const uint32_t *pt_cnt,
+                                                             const unsigned long long *block_off)
+{
+    __shared__ uint32_t s_w[kPlainThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t i = (uint64_t)blockIdx.x * kPlainThreads + threadIdx.x;
+    const uint32_t c = i < a.n ? pt_cnt[i] : 0u;
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o)
+            inc += v;
+    }
+    if (lane == 31)
+        s_w[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w)
+        wpre += s_w[w];
+    if (!c)
+        return;
+    unsigned long long o = block_off[blockIdx.x] + wpre + inc - c;
+    const int2 p = a.pts[i];
+    uint32_t t = 0, e = 0;
+    buffer_point<FP32>(a.ix, a.bv, p.x, p.y, t, e, policy_evict_last(), [&](uint32_t q) {
+        if (o < a.cap)
+            a.pairs[o] = make_uint2((uint32_t)i, q);
+        ++o;
+    });
+}
+
 // Opt a kernel in to the shared memory it needs (once per device).
 template <class K>
 cudaError_t smem_opt_in(K kernel, size_t bytes, bool (&done)[64])
@@ -3101,6 +3251,89 @@ cudaError_t launch_disk_select(const DiskLaunch &a, uint32_t *ids, uint64_t cap,
     if (e != cudaSuccess)
         return e;
     return launch_partition(pairs, total, cap, a.dv.Q, ids, offsets, sc, s);
+}
+
+// ------------------------------------------------ buffered polygons: launchers
+size_t buffer_scratch_bytes(uint64_t n)
+{
+    const uint64_t nb = (n + kPlainThreads - 1) / kPlainThreads;
+    return size_t(((n * 4 + 15) & ~uint64_t(15)) + (nb + scan_partials(nb) + 2) * 8 + 16);
+}
+
+cudaError_t launch_buffer_join(const BufferLaunch &a, void *scratch, cudaStream_t s)
+{
+    if (a.n >= (1ull << 32))
+        return cudaErrorInvalidValue; // point ids are 32-bit
+    cudaError_t e = cudaSuccess;
+    if (a.counts && a.bv.P)
+        e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.bv.P, s);
+    if (e != cudaSuccess)
+        return e;
+    if (a.n == 0)
+        return a.total ? cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), s) : cudaSuccess;
+    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
+    char *sc = static_cast<char *>(scratch);
+    uint32_t *pt_cnt = reinterpret_cast<uint32_t *>(sc);
+    unsigned long long *block = reinterpret_cast<unsigned long long *>(sc + ((a.n * 4 + 15) & ~uint64_t(15)));
+    unsigned long long *part = block + nb;
+    if (a.fp32)
+        k_buf_count<true><<<(unsigned)nb, kPlainThreads, 0, s>>>(a, pt_cnt, block);
+    else
+        k_buf_count<false><<<(unsigned)nb, kPlainThreads, 0, s>>>(a, pt_cnt, block);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    if ((e = launch_scan(block, nb, a.total, part, s)) != cudaSuccess)
+        return e;
+    if (!a.cap)
+        return cudaSuccess;
+    if (a.fp32)
+        k_buf_write<true><<<(unsigned)nb, kPlainThreads, 0, s>>>(a, pt_cnt, block);
+    else
+        k_buf_write<false><<<(unsigned)nb, kPlainThreads, 0, s>>>(a, pt_cnt, block);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_buffer_aggregate(const BufferLaunch &a, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * (a.bv.P ? a.bv.P : 1), s);
+    if (e != cudaSuccess || a.n == 0)
+        return e;
+    const uint64_t nb = (a.n + kPlainThreads - 1) / kPlainThreads;
+    if (nb >= (1ull << 31))
+        return cudaErrorInvalidValue;
+    if (a.fp32)
+        k_buf_count<true><<<(unsigned)nb, kPlainThreads, 0, s>>>(a, nullptr, nullptr);
+    else
+        k_buf_count<false><<<(unsigned)nb, kPlainThreads, 0, s>>>(a, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+size_t buffer_select_scratch_bytes(uint64_t n, uint32_t P, uint64_t cap)
+{
+    return ((buffer_scratch_bytes(n) + 15) & ~size_t(15)) + 16 + cap * 8 + partition_scratch_bytes(cap, P);
+}
+
+cudaError_t launch_buffer_select(const BufferLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
+                                 void *scratch, cudaStream_t s)
+{
+    if (a.bv.P > (uint32_t)kSelMaxQ)
+        return cudaErrorInvalidValue;
+    char *sc = static_cast<char *>(scratch);
+    void *join_scratch = sc;
+    sc += (buffer_scratch_bytes(a.n) + 15) & ~size_t(15);
+    unsigned long long *total = reinterpret_cast<unsigned long long *>(sc);
+    sc += 16;
+    uint2 *pairs = reinterpret_cast<uint2 *>(sc);
+    sc += cap * 8;
+    BufferLaunch b = a;
+    b.pairs = pairs;
+    b.cap = cap;
+    b.counts = nullptr;
+    b.total = total;
+    cudaError_t e = launch_buffer_join(b, join_scratch, s);
+    if (e != cudaSuccess)
+        return e;
+    return launch_partition(pairs, total, cap, a.bv.P, ids, offsets, sc, s);
 }
 
 } // namespace spx

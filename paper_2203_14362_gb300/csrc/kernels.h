@@ -79,6 +79,44 @@ size_t disk_select_scratch_bytes(uint64_t n, uint32_t Q, uint64_t cap);
 cudaError_t launch_disk_select(const DiskLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
                                void *scratch, cudaStream_t s);
 
+// Buffered polygons (SPADE §4.2 distance canvases: a polygon plus a rounded
+// rectangle of radius r around each edge): the polygon index answers
+// containment, an edge grid the distance part.
+struct BufferView {
+    const uint32_t *cell_off; // 4^g + 1 item offsets per edge-grid cell
+    const uint32_t *item_q;   // polygon of each item, ascending within a cell
+    const int4 *item_seg;     // the item's edge (ax, ay, bx, by)
+    const int32_t *rad;       // P radii, each in [0, 2^30)
+    int g, sc;                // 2^g cells per side of 2^sc units
+    uint32_t P;
+    uint64_t n_items;
+};
+
+struct BufferLaunch {
+    IndexView ix; // the polygons' own index (containment)
+    BufferView bv;
+    const int2 *pts;
+    uint64_t n;
+    uint2 *pairs; // may be null when cap == 0
+    uint64_t cap;
+    unsigned long long *counts; // P entries or null; zeroed by the launchers
+    unsigned long long *total;  // device total or null
+    unsigned long long *stats;
+    int fp32;
+};
+
+// Buffered-polygon join: pairs (point, polygon) of the points inside the
+// polygon or within its radius of one of its edges, in (point, polygon)
+// order, counts, total; scratch: buffer_scratch_bytes(n).
+size_t buffer_scratch_bytes(uint64_t n);
+cudaError_t launch_buffer_join(const BufferLaunch &a, void *scratch, cudaStream_t s);
+// Counts only.
+cudaError_t launch_buffer_aggregate(const BufferLaunch &a, cudaStream_t s);
+// Per-polygon ascending point-id lists; scratch: buffer_select_scratch_bytes(n, P, cap).
+size_t buffer_select_scratch_bytes(uint64_t n, uint32_t P, uint64_t cap);
+cudaError_t launch_buffer_select(const BufferLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
+                                 void *scratch, cudaStream_t s);
+
 // Device build of the disk index of Q disks (host array of (cx, cy, r, 0),
 // already checked) on a 2^g grid: the same cell words and entries as the host
 // build (build_disk_index) and the same cover bitmap, in one new device

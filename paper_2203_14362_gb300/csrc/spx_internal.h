@@ -99,6 +99,24 @@ struct HostDiskIndex {
 bool build_disk_index(const int32_t *cxy, const int32_t *r, uint32_t Q, int g, HostDiskIndex &out, std::string &err);
 int default_disk_grid_log2(const int32_t *r, uint32_t Q);
 
+// Item flag of the edge grid: polygon q's r-region holds the whole cell (the
+// item carries no edge; the cell's points meet q without a test).
+constexpr uint32_t kBufferFull = 0x80000000u;
+
+// Edge grid of P buffered polygons (ring q grown by r[q]): per cell of a
+// 2^g grid, the edges whose r-neighbourhood may reach the cell, sorted by
+// (polygon, edge), in CSR form.
+struct HostBufferEdges {
+    int g = 0;
+    std::vector<uint32_t> cell_off; // 4^g + 1 item offsets
+    std::vector<uint32_t> item_q;   // polygon of each item, | kBufferFull when the whole cell is within r
+    std::vector<int32_t> item_seg;  // 4 per item: ax, ay, bx, by
+    uint64_t n_full = 0;            // flagged items
+};
+bool build_buffer_edges(const int32_t *xy, const uint64_t *ring_off, uint32_t P, const int32_t *r, int g,
+                        HostBufferEdges &out, std::string &err);
+int default_buffer_grid_log2(const int32_t *xy, const uint64_t *ring_off, uint32_t P, const int32_t *r);
+
 // Build the index of P rings (xy: interleaved int32 pairs, ring_off: P + 1
 // offsets in vertices) with 2^grid_log2 coarse cells per side, each mixed
 // cell split into 2^sub_log2 x 2^sub_log2 fine cells.  Returns false and sets

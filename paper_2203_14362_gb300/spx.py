@@ -29,7 +29,7 @@ EXPORTS = [
     "spx_server_create", "spx_server_submit", "spx_server_poll", "spx_server_wait", "spx_server_release",
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
     "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
-    "spx_build_disk_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free",
+    "spx_build_disk_index", "spx_build_buffer_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free",
     "spx_build_disk_index_device", "spx_disk_index_arrays", "spx_build_index_device", "spx_index_arrays", "spx_host_index_validate",
     "spx_check_bounded_wait",
 ]
@@ -52,7 +52,8 @@ class IndexInfo(C.Structure):
                 ("n_cells", C.c_uint64), ("n_blocks", C.c_uint64), ("n_entries", C.c_uint64),
                 ("n_inside", C.c_uint64), ("n_mixed", C.c_uint64), ("n_boundary", C.c_uint64),
                 ("n_edge_refs", C.c_uint64), ("device_bytes", C.c_uint64), ("build_ms", C.c_double),
-                ("sum_resolved", C.c_double), ("use_sum", C.c_int), ("pad2", C.c_int)]
+                ("sum_resolved", C.c_double), ("use_sum", C.c_int), ("pad2", C.c_int),
+                ("edge_grid_log2", C.c_int), ("pad3", C.c_int), ("n_edge_items", C.c_uint64)]
 
 
 class TuneParams(C.Structure):
@@ -141,6 +142,7 @@ def load(path: str = LIB_PATH):
         "spx_server_destroy": ([V], None),
         "spx_cluster_points": ([V, U64, I, P64], I),
         "spx_build_disk_index": ([V, V, V, U32, I, P64], I),
+        "spx_build_buffer_index": ([V, U64, V, I, I, P64], I),
         "spx_host_disk_index_build": ([V, V, U32, I, C.POINTER(V), P64], I),
         "spx_host_disk_index_copy": ([V, V, V], I),
         "spx_host_disk_index_free": ([V], None),
@@ -348,6 +350,15 @@ class Engine:
         h = C.c_uint64()
         fn = "spx_build_disk_index_device" if on_device else "spx_build_disk_index"
         self._check(getattr(self.lib, fn)(self.ctx, _np_ptr(c), _np_ptr(r), c.shape[0], grid_log2, C.byref(h)), fn)
+        return h.value
+
+    def build_buffer_index(self, polys: int, radii: np.ndarray, grid_log2: int = 0, fp32_filter: bool = True) -> int:
+        """spx_build_buffer_index: polygon set `polys`, polygon q buffered by
+        radii[q], for distance joins / selections / counts."""
+        r = np.ascontiguousarray(radii, dtype=np.int32).reshape(-1)
+        h = C.c_uint64()
+        self._check(self.lib.spx_build_buffer_index(self.ctx, polys, _np_ptr(r), grid_log2, 1 if fp32_filter else 0,
+                                                    C.byref(h)), "spx_build_buffer_index")
         return h.value
 
     def disk_index_arrays(self, index: int) -> dict:
