@@ -581,19 +581,19 @@ def serve_indexes(eng, seed: int, pool: int = 32):
     polygon sets of 1-64 polygons (selections)."""
     from paper_2203_14362_gb300 import datagen as g
     from paper_2203_14362_gb300 import spx
-    out = []  # (kind, polys handle, index handle, polygons)
+    out = []  # (kind, polys handle, index handle, polygons, vertices, ring offsets)
     for k, cells in enumerate((500, 1000, 2500, 5000)):
         nx, ny = g.tessellation_shape(cells)
         t = g.quad_tessellation(nx, ny, seed + 100 + k)
         gh = eng.load_polygons(t.verts, t.ring_off)
-        out.append((spx.SPX_REQ_JOIN, gh, eng.build_index(gh), cells))
+        out.append((spx.SPX_REQ_JOIN, gh, eng.build_index(gh), cells, t.verts, t.ring_off))
     mix = g.make_mixture(seed)
     rng = np.random.default_rng(seed)
     for k in range(pool):
         q = int(rng.integers(1, 65))
         v, o = g.query_polygons(q, seed + 200 + k, mix)
         gh = eng.load_polygons(v, o)
-        out.append((spx.SPX_REQ_SELECT, gh, eng.build_index(gh), q))
+        out.append((spx.SPX_REQ_SELECT, gh, eng.build_index(gh), q, v, o))
     return out
 
 
@@ -610,10 +610,12 @@ def serve_stream(idx, n: int, seed: int):
     return out
 
 
-def serve_run(srv, reqs, rate, warm: int, seed: int = 7):
+def serve_run(srv, reqs, rate, warm: int, seed: int = 7, polys=None):
     """Submit reqs at Poisson arrivals of `rate` per second (None: all at once);
     a collector waits for each result and releases it.  Latency = completion on
-    the device - submission, both on the server's clock."""
+    the device - submission, both on the server's clock.  polys (or None):
+    per index position its (vertices, ring offsets): every request then brings
+    its polygons, indexed on the device when its batch starts."""
     ids = [None] * len(reqs)
     res = [None] * len(reqs)
     ready = threading.Semaphore(0)
@@ -633,7 +635,7 @@ def serve_run(srv, reqs, rate, warm: int, seed: int = 7):
         d = t0 + t - time.perf_counter()
         if d > 0:
             time.sleep(d)
-        ids[i] = srv.submit(kind, pos, tag=i)
+        ids[i] = srv.submit(kind, pos, tag=i) if polys is None else srv.submit_polygons(kind, *polys[pos], tag=i)
         ready.release()
     th.join()
     timed = res[warm:]
@@ -648,8 +650,10 @@ def serve_run(srv, reqs, rate, warm: int, seed: int = 7):
 
 def serve_capacity(eng, ph, N: int, idx, burst: int, seed: int, plain_burst: int = 0):
     """Capacity (requests/s over a burst submitted at once, after a warm-up
-    burst) of the batching server, of its fused one-pass mode and of the plain
-    comparison, and the batching server's served roofline over its burst: the
+    burst) of the batching server, of its fused one-pass mode, of the plain
+    comparison and of the batching server with every request bringing its
+    polygons (batched_own: each index built on the device in the request's
+    latency), and the batching server's served roofline over its burst: the
     algorithmic bytes of every request (8 B per scanned point, 8 B per pair or
     4 B per id, its index once) over the burst's span."""
     from paper_2203_14362_gb300 import spx
@@ -658,14 +662,16 @@ def serve_capacity(eng, ph, N: int, idx, burst: int, seed: int, plain_burst: int
     ix_bytes = [eng.index_info(h)["device_bytes"] for h in handles]
     cap, roof = {}, None
     arms = (("batched", dict(max_batch=8, slots=2)), ("fused", dict(max_batch=8, slots=2, fused=True)),
-            ("plain", dict(plain=True)))
+            ("plain", dict(plain=True)), ("batched_own", dict(max_batch=8, slots=2)))
+    polys = [(x[4], x[5]) for x in idx]
     for name, kw in arms:
         n = plain_burst if name == "plain" and plain_burst else burst
+        own = polys if name == "batched_own" else None  # every request brings its polygons
         srv = spx.Server(eng, ph, handles, **kw)
-        serve_run(srv, serve_stream(idx, max(4, n // 4), seed + 1), None, 0)  # warm-up
+        serve_run(srv, serve_stream(idx, max(4, n // 4), seed + 1), None, 0, polys=own)  # warm-up
         b0 = srv.stats()["batches"]
         reqs = serve_stream(idx, n, seed + 2)
-        r = serve_run(srv, reqs, None, 0)
+        r = serve_run(srv, reqs, None, 0, polys=own)
         nb = srv.stats()["batches"] - b0
         cap[name] = r["throughput_rps"]
         if name == "batched":
@@ -713,7 +719,7 @@ def run_serving(eng, ph, N: int, seed: int, timed: int, warm: int, burst: int):
             batches += srv.stats()["batches"]
             srv.close()
         out["rates"].append(row)
-    for _, gh, ih, _ in idx:
+    for _, gh, ih, *_ in idx:
         eng.free(ih)
         eng.free(gh)
     out["value_gpts"] = cap["batched"] * N / 1e9
@@ -748,7 +754,7 @@ def serve_capacity_measure(args, local, torch, N: int = 1_000_000_000):
     cap, roof = serve_capacity(eng, ph, N, idx, args.serve_burst, SERVE_SEED, plain_burst=12)
     clk = clocks.summary(th0, time.time())
     clocks.stop()
-    for _, gh, ih, _ in idx:
+    for _, gh, ih, *_ in idx:
         eng.free(ih)
         eng.free(gh)
     eng.free(ph)

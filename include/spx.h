@@ -629,6 +629,21 @@ spx_status spx_server_create(spx_ctx *ctx, spx_points points, const spx_index *i
  * index position, or a selection index of more than 1024 polygons. */
 spx_status spx_server_submit(spx_server *srv, const spx_request *req, uint64_t *req_id);
 
+/*
+ * Queue one request that brings its own polygons (P rings as for
+ * spx_load_polygons; host arrays, copied before the call returns) instead of
+ * naming a prebuilt index.  Their grid index is built on the device when the
+ * request's batch starts (automatic grid, sub_log2 3, FP32 filter on), so its
+ * build time is part of the request's latency (§6.1 counts the index built
+ * for query polygons in the query time); its memory counts against the
+ * output budget and is freed once no batch is in flight.  The result is the
+ * same as for a prebuilt index of those polygons.  SPX_EINVAL for a bad kind,
+ * a selection of more than 1024 polygons, a vertex outside [0, 2^30]^2, bad
+ * ring offsets or more than 2^32 - 1 vertices.
+ */
+spx_status spx_server_submit_polygons(spx_server *srv, int kind, const int32_t *xy, const uint64_t *ring_off,
+                                      uint32_t P, uint64_t tag, uint64_t *req_id);
+
 /* Result of a request: SPX_EBUSY while it is pending, SPX_EINVAL for an
  * unknown (or released) id; otherwise fills *out and returns SPX_OK (the
  * request's own status is out->status). */

@@ -434,37 +434,53 @@ struct GridParts {
 
 // Views and info of a polygon index whose allocation ix->mem holds `gp`;
 // takes the index into the ctx and returns its handle.
+// The kernels' view of a polygon index whose arrays are `gp`.
+static IndexView grid_view(const GridParts &gp, int g, int sb, uint32_t P)
+{
+    IndexView v{};
+    const int cg = std::min(g, kCoverLog2);
+    v.cell = reinterpret_cast<const uint32_t *>(gp.cell);
+    v.fine = reinterpret_cast<const uint32_t *>(gp.fine);
+    v.ent = reinterpret_cast<const uint4 *>(gp.ent);
+    v.edge = reinterpret_cast<const int4 *>(gp.edge);
+    v.sc = kBoxLog2 - g;
+    v.gc = g;
+    v.sf = kBoxLog2 - g - sb;
+    v.sb = sb;
+    v.P = P;
+    v.cover = reinterpret_cast<const uint32_t *>(gp.cover);
+    v.scv = kBoxLog2 - cg;
+    v.cg = cg;
+    v.sum = reinterpret_cast<const uint4 *>(gp.sum);
+    v.sg = std::min(g, kSumLog2);
+    v.ssh = kBoxLog2 - v.sg;
+    // the summary costs pass 1a three quarters of its warps per SM (one CTA
+    // holds it); worth it when it answers a third of the box or more
+    v.use_sum = gp.sum_resolved >= kSumMinResolved ? 1 : 0;
+    v.n_fine = gp.n_fine;
+    v.n_ent = gp.n_ent;
+    v.n_edge = gp.n_edge;
+    return v;
+}
+
+static GridParts device_parts(const GridIndexDev &d)
+{
+    char *base = static_cast<char *>(d.mem);
+    auto at = [&](const void *p) { return base + (static_cast<const char *>(p) - base); };
+    return GridParts{at(d.cell), at(d.fine), at(d.ent), at(d.edge), at(d.cover), at(d.sum), d.n_cell, d.n_fine,
+                     d.n_ent, d.n_edge, d.n_blocks, d.n_inside, d.n_mixed, d.n_boundary, d.sum_resolved};
+}
+
 spx_status register_grid_index(spx_ctx *ctx, spx_polys polys, std::unique_ptr<IndexObj> ix, size_t total, int g, int sb,
                                int fp32, const GridParts &gp, std::chrono::steady_clock::time_point t0, spx_index *out)
 {
     PolysObj *pg = lookup(ctx->polys, polys);
-    const int cg = std::min(g, kCoverLog2);
     ix->polys = polys;
     ix->fp32 = fp32 ? 1 : 0;
-    ix->view.cell = reinterpret_cast<const uint32_t *>(gp.cell);
-    ix->view.fine = reinterpret_cast<const uint32_t *>(gp.fine);
-    ix->view.ent = reinterpret_cast<const uint4 *>(gp.ent);
-    ix->view.edge = reinterpret_cast<const int4 *>(gp.edge);
-    ix->view.sc = kBoxLog2 - g;
-    ix->view.gc = g;
-    ix->view.sf = kBoxLog2 - g - sb;
-    ix->view.sb = sb;
-    ix->view.P = pg->P;
-    ix->view.cover = reinterpret_cast<const uint32_t *>(gp.cover);
-    ix->view.scv = kBoxLog2 - cg;
-    ix->view.cg = cg;
-    ix->view.sum = reinterpret_cast<const uint4 *>(gp.sum);
-    ix->view.sg = std::min(g, kSumLog2);
-    ix->view.ssh = kBoxLog2 - ix->view.sg;
-    // the summary costs pass 1a three quarters of its warps per SM (one CTA
-    // holds it); worth it when it answers a third of the box or more
-    ix->view.use_sum = gp.sum_resolved >= kSumMinResolved ? 1 : 0;
+    ix->view = grid_view(gp, g, sb, pg->P);
     ix->n_fine = gp.n_fine;
     ix->n_ent = gp.n_ent;
     ix->n_edge = gp.n_edge;
-    ix->view.n_fine = gp.n_fine;
-    ix->view.n_ent = gp.n_ent;
-    ix->view.n_edge = gp.n_edge;
     ix->view.err = &ctx->aux->err;
     spx_index_info &inf = ix->info;
     inf.grid_log2 = g;
@@ -551,6 +567,41 @@ spx_status build_index_impl(spx_ctx *ctx, spx_polys polys, const spx_index_param
 } // namespace
 
 namespace spx {
+
+std::string check_rings(const int32_t *xy, const uint64_t *ring_off, uint32_t P)
+{
+    if (P >= (1u << 30))
+        return "too many polygons (limit 2^30 - 1)";
+    if (ring_off[0] != 0)
+        return "ring_off[0] must be 0";
+    for (uint32_t q = 0; q < P; ++q)
+        if (ring_off[q + 1] < ring_off[q])
+            return "ring_off must be non-decreasing";
+    if (P && ring_off[P] >= (uint64_t(1) << 32))
+        return "more than 2^32 - 1 vertices";
+    for (uint64_t i = 0; i < (P ? ring_off[P] : 0); ++i)
+        if (xy[2 * i] < 0 || xy[2 * i] > int32_t(kBox) || xy[2 * i + 1] < 0 || xy[2 * i + 1] > int32_t(kBox))
+            return "vertex " + std::to_string(i) + " outside [0, 2^30]^2";
+    return {};
+}
+
+int device_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, IndexView &view, void *&mem,
+                      size_t &bytes, std::string &err)
+{
+    const int g = default_grid_log2(xy, ring_off, P), sb = kMaxSubLog2;
+    GridIndexDev d{};
+    const char *why = nullptr;
+    cudaError_t e = cudaSuccess;
+    const int st = build_grid_index_device(xy, ring_off, P, g, sb, d, why, e);
+    if (st != 0) {
+        err = st == 1 ? std::string(why) : std::string(cudaGetErrorString(e));
+        return st;
+    }
+    view = grid_view(device_parts(d), g, sb, P);
+    mem = d.mem;
+    bytes = d.bytes;
+    return 0;
+}
 
 spx_status served_data(spx_ctx *ctx, spx_points points, const spx_index *indexes, uint32_t n, ServedData &out)
 {
@@ -861,11 +912,7 @@ spx_status spx_build_index_device(spx_ctx *ctx, spx_polys polys, const spx_index
                                               : cuda_fail(ctx, e, "build_index_device");
     auto ix = std::make_unique<IndexObj>();
     ix->mem = d.mem;
-    char *base = static_cast<char *>(d.mem);
-    auto at = [&](const void *p) { return base + (static_cast<const char *>(p) - base); };
-    GridParts gp{at(d.cell), at(d.fine), at(d.ent), at(d.edge), at(d.cover), at(d.sum), d.n_cell, d.n_fine, d.n_ent,
-                 d.n_edge, d.n_blocks, d.n_inside, d.n_mixed, d.n_boundary, d.sum_resolved};
-    return register_grid_index(ctx, polys, std::move(ix), d.bytes, g, sb, prm.fp32_filter, gp, t0, out);
+    return register_grid_index(ctx, polys, std::move(ix), d.bytes, g, sb, prm.fp32_filter, device_parts(d), t0, out);
 }
 
 spx_status spx_index_arrays(spx_ctx *ctx, spx_index index, uint32_t *coarse, uint32_t *fine, uint32_t *entries,

@@ -46,6 +46,14 @@ struct Req {
     // offsets) from the count pass to the write pass
     void *join_mem = nullptr;
     size_t join_bytes = 0;
+    // a request that brought its own polygons: their host copy, and the index
+    // built on the device when its batch starts (freed once no batch runs)
+    bool own = false;
+    std::vector<int32_t> xy;
+    std::vector<uint64_t> off;
+    IndexView own_view{};
+    void *own_mem = nullptr;
+    size_t own_bytes = 0;
     int readers = 0; // spx_server_read calls copying the outputs (release waits for none)
 };
 
@@ -100,6 +108,11 @@ struct spx_server {
         }
         cv.notify_all();
     }
+    std::vector<std::pair<void *, size_t>> deferred; // own indexes of finished requests, freed when idle
+    const IndexView &view_of(const Req *r) const { return r->own ? r->own_view : data.ix[r->rq.index]; }
+    int fp32_of(const Req *r) const { return r->own ? 1 : data.fp32[r->rq.index]; }
+    void retire_own(Req *r);
+    bool build_own(Slot &sl);
     void run();
     bool start_batch(Slot &sl);
     JoinLaunch request_launch(Slot &sl, const Req *r, size_t i) const;
@@ -146,6 +159,7 @@ void pool_free(void *p, cudaStream_t s)
 void spx_server::fail_batch(Slot &sl, int status)
 {
     for (Req *r : sl.batch) {
+        retire_own(r);
         pool_free(r->out_mem, sl.s);
         pool_free(r->tmp_mem, sl.s);
         pool_free(r->counts, sl.s);
@@ -163,12 +177,42 @@ void spx_server::fail_batch(Slot &sl, int status)
     cv_done.notify_all();
 }
 
+// A finished request's own index: kept until no batch runs (freeing device
+// memory waits for the whole device).
+void spx_server::retire_own(Req *r)
+{
+    if (r->own_mem)
+        deferred.emplace_back(r->own_mem, r->own_bytes);
+    r->own_mem = nullptr;
+    r->own_bytes = 0;
+}
+
+// Indexes of the batch's requests that brought their polygons, built on the
+// device now (their build counts in their latency).  False: the batch failed.
+bool spx_server::build_own(Slot &sl)
+{
+    for (Req *r : sl.batch) {
+        if (!r->own || r->own_mem)
+            continue;
+        std::string why;
+        const int b = device_grid_index(r->xy.data(), r->off.data(), r->P, r->own_view, r->own_mem, r->own_bytes, why);
+        if (b != 0) {
+            err = "server: device build of a request's polygon index failed: " + why;
+            fail_batch(sl, b == 1 ? SPX_EINVAL : SPX_ECUDA);
+            return false;
+        }
+        used += r->own_bytes;
+        st.peak_bytes_in_use = std::max(st.peak_bytes_in_use, used);
+    }
+    return true;
+}
+
 // The join launch of request r, position i of its slot's batch (outputs and
 // capacity are set by the write pass).
 JoinLaunch spx_server::request_launch(Slot &sl, const Req *r, size_t i) const
 {
     JoinLaunch a{};
-    a.ix = data.ix[r->rq.index];
+    a.ix = view_of(r);
     a.ix.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
     a.pts = data.pts;
     a.n = data.n;
@@ -176,7 +220,7 @@ JoinLaunch spx_server::request_launch(Slot &sl, const Req *r, size_t i) const
     a.total = sl.dev_words + i;
     a.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
     a.stats = sl.dev_words + kWordStats;
-    a.fp32 = data.fp32[r->rq.index];
+    a.fp32 = fp32_of(r);
     return a;
 }
 
@@ -213,6 +257,8 @@ bool spx_server::start_batch(Slot &sl)
         r->t_start = t;
         r->batch_size = K;
     }
+    if (!build_own(sl))
+        return true;
     st.batches++;
     st.batched_requests += K;
     // join counts are produced by the count pass (batched) or the write pass (plain)
@@ -234,7 +280,7 @@ bool spx_server::start_batch(Slot &sl)
     if (prm.plain) {
         Req *r = sl.batch[0];
         JoinLaunch a{};
-        a.ix = data.ix[r->rq.index];
+        a.ix = view_of(r);
         a.ix.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
         a.pts = data.pts;
         a.n = data.n;
@@ -272,9 +318,9 @@ bool spx_server::start_batch(Slot &sl)
         m.qbase[0] = 0;
         for (uint32_t i = 0; i < K; ++i) {
             const Req *r = sl.batch[i];
-            m.ix[i] = data.ix[r->rq.index];
+            m.ix[i] = view_of(r);
             m.ix[i].err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
-            m.fp32 &= data.fp32[r->rq.index];
+            m.fp32 &= fp32_of(r);
             m.counts[i] = r->counts;
             m.qbase[i + 1] = m.qbase[i] + (r->counts ? r->P : 0u);
         }
@@ -368,7 +414,7 @@ bool spx_server::admit(Slot &sl)
     if (prm.plain) {
         Req *r = sl.batch[0];
         JoinLaunch a{};
-        a.ix = data.ix[r->rq.index];
+        a.ix = view_of(r);
         a.ix.err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
         a.pts = data.pts;
         a.n = data.n;
@@ -398,9 +444,9 @@ bool spx_server::admit(Slot &sl)
         m.stats = sl.dev_words + kWordStats;
         for (int i = 0; i < m.K; ++i) {
             Req *r = sl.batch[i];
-            m.ix[i] = data.ix[r->rq.index];
+            m.ix[i] = view_of(r);
             m.ix[i].err = reinterpret_cast<unsigned *>(sl.dev_words + kWordErr);
-            m.fp32 &= data.fp32[r->rq.index];
+            m.fp32 &= fp32_of(r);
             m.pairs[i] = pairs_of(r);
             m.cap[i] = r->total;
         }
@@ -447,6 +493,7 @@ void spx_server::written(Slot &sl)
         return;
     }
     for (Req *r : sl.batch) {
+        retire_own(r);
         pool_free(r->tmp_mem, sl.s); // ordered after the partition on this stream
         pool_free(r->join_mem, sl.s);
         r->tmp_mem = r->join_mem = nullptr;
@@ -469,6 +516,18 @@ void spx_server::run()
         const int ev0 = events.load();
         std::unique_lock<std::mutex> lk(mu);
         bool progress = false;
+        if (!deferred.empty()) {
+            bool idle = true;
+            for (auto &up : slots)
+                idle = idle && up->state == Slot::kIdle;
+            if (idle) { // no batch in flight: freeing stalls none
+                for (auto &d : deferred) {
+                    cudaFree(d.first);
+                    used -= d.second;
+                }
+                deferred.clear();
+            }
+        }
         for (auto &up : slots) {
             Slot &sl = *up;
             if (sl.state == Slot::kCounting && sl.flag.load() >= 1) {
@@ -620,6 +679,46 @@ spx_status spx_server_submit(spx_server *srv, const spx_request *req, uint64_t *
     r->id = srv->next_id++;
     r->rq = *req;
     r->P = P;
+    r->t_submit = srv->now_ms();
+    srv->queue.push_back(r.get());
+    *req_id = r->id;
+    srv->reqs[r->id] = std::move(r);
+    srv->st.submitted++;
+    srv->signal();
+    return SPX_OK;
+}
+
+spx_status spx_server_submit_polygons(spx_server *srv, int kind, const int32_t *xy, const uint64_t *ring_off,
+                                      uint32_t P, uint64_t tag, uint64_t *req_id)
+{
+    if (!srv || !req_id || !ring_off || (P && !xy))
+        return SPX_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (kind != SPX_REQ_SELECT && kind != SPX_REQ_JOIN) {
+        srv->err = "server: request kind must be SPX_REQ_SELECT or SPX_REQ_JOIN";
+        return SPX_EINVAL;
+    }
+    if (kind == SPX_REQ_SELECT && P > kSelectMaxQueries) {
+        srv->err = "server: a selection has at most 1024 polygons";
+        return SPX_EINVAL;
+    }
+    const std::string bad = check_rings(xy, ring_off, P);
+    if (!bad.empty()) {
+        srv->err = "server: " + bad;
+        return SPX_EINVAL;
+    }
+    if (srv->stopping) {
+        srv->err = "server: stopping";
+        return SPX_EINVAL;
+    }
+    auto r = std::make_unique<Req>();
+    r->id = srv->next_id++;
+    r->rq.kind = kind;
+    r->rq.tag = tag;
+    r->P = P;
+    r->own = true;
+    r->off.assign(ring_off, ring_off + P + 1);
+    r->xy.assign(xy, xy + 2 * (P ? ring_off[P] : 0));
     r->t_submit = srv->now_ms();
     srv->queue.push_back(r.get());
     *req_id = r->id;
@@ -798,7 +897,11 @@ void spx_server_destroy(spx_server *srv)
         pool_free(r->out_mem, srv->release_stream);
         pool_free(r->tmp_mem, srv->release_stream);
         pool_free(r->counts, srv->release_stream);
+        if (r->own_mem)
+            cudaFree(r->own_mem);
     }
+    for (auto &d : srv->deferred)
+        cudaFree(d.first);
     cudaStreamSynchronize(srv->release_stream);
     for (auto &sl : srv->slots) {
         cudaStreamSynchronize(sl->s);

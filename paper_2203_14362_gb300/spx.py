@@ -26,7 +26,7 @@ EXPORTS = [
     "spx_index_info_get", "spx_join", "spx_join_plain", "spx_aggregate", "spx_join_host", "spx_host_index_build",
     "spx_host_index_copy", "spx_host_index_free", "spx_stats", "spx_set_phase_timing", "spx_free",
     "spx_join_plain_static", "spx_select", "spx_autotune",
-    "spx_server_create", "spx_server_submit", "spx_server_poll", "spx_server_wait", "spx_server_release",
+    "spx_server_create", "spx_server_submit", "spx_server_submit_polygons", "spx_server_poll", "spx_server_wait", "spx_server_release",
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
     "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
     "spx_build_disk_index", "spx_build_buffer_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free",
@@ -133,6 +133,7 @@ def load(path: str = LIB_PATH):
                           C.POINTER(U32), P64, V], I),
         "spx_server_create": ([V, U64, V, U32, C.POINTER(ServerParams), C.POINTER(V)], I),
         "spx_server_submit": ([V, C.POINTER(Request), P64], I),
+        "spx_server_submit_polygons": ([V, I, V, V, U32, U64, P64], I),
         "spx_server_poll": ([V, U64, C.POINTER(Result)], I),
         "spx_server_wait": ([V, U64, C.c_double, C.POINTER(Result)], I),
         "spx_server_release": ([V, U64], I),
@@ -483,6 +484,16 @@ class Server:
         rid = C.c_uint64()
         self._check(self.lib.spx_server_submit(self.h, C.byref(Request(kind, index, tag)), C.byref(rid)),
                     "spx_server_submit")
+        return rid.value
+
+    def submit_polygons(self, kind: int, verts: np.ndarray, ring_off: np.ndarray, tag: int = 0) -> int:
+        """A request with its own polygons: their index is built on the device
+        when its batch starts."""
+        xy = np.ascontiguousarray(verts, dtype=np.int32).reshape(-1, 2)
+        off = np.ascontiguousarray(ring_off, dtype=np.uint64)
+        rid = C.c_uint64()
+        self._check(self.lib.spx_server_submit_polygons(self.h, kind, _np_ptr(xy), _np_ptr(off), off.shape[0] - 1, tag,
+                                                        C.byref(rid)), "spx_server_submit_polygons")
         return rid.value
 
     def wait(self, rid: int, timeout_ms: float = -1.0):

@@ -8,6 +8,7 @@ flight, under an output budget that forces admission waits, and with requests
 submitted from several threads at once.
 """
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -54,7 +55,7 @@ def world():
         else:
             ids, offs = oracle.group_by_polygon(pairs, counts)
             expect.append(("select", ids, offs))
-    yield {"eng": eng, "ph": ph, "ix": [ih for _, ih in handles], "expect": expect}
+    yield {"eng": eng, "ph": ph, "ix": [ih for _, ih in handles], "expect": expect, "sets": sets}
     for gh, ih in handles:
         eng.free(ih)
         eng.free(gh)
@@ -188,5 +189,61 @@ def test_serve_errors(world):
         # destroy with work still queued finishes it first
         for k in (0, 2, 1):
             srv.submit(_kind(world["expect"][k]), k)
+    finally:
+        srv.close()
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_serve_requests_with_their_own_polygons(world, fused):
+    # every other request brings its polygons (the sets of the prebuilt
+    # indexes), its index built on the device when its batch starts: the
+    # results are the prebuilt ones, byte for byte
+    srv = spx.Server(world["eng"], world["ph"], world["ix"], max_batch=8, slots=2, fused=fused)
+    try:
+        ids = []
+        for i, k in enumerate(SEQ):
+            kind = _kind(world["expect"][k])
+            if i % 2:
+                _, v, o = world["sets"][k]
+                ids.append((srv.submit_polygons(kind, v, o, tag=i), k))
+            else:
+                ids.append((srv.submit(kind, k, tag=i), k))
+        for i, (rid, k) in enumerate(ids):
+            res = srv.wait(rid, 60_000)
+            assert res is not None and res["tag"] == i
+            _check(srv, rid, res, world["expect"][k])
+            srv.release(rid)
+        st = srv.stats()
+        assert st["completed"] == len(SEQ) and st["failed"] == 0
+        # the requests' own indexes are freed once no batch is in flight
+        for _ in range(200):
+            if srv.stats()["bytes_in_use"] == 0:
+                break
+            time.sleep(0.01)
+        assert srv.stats()["bytes_in_use"] == 0
+    finally:
+        srv.close()
+
+
+def test_serve_own_polygons_refused(world):
+    srv = spx.Server(world["eng"], world["ph"], world["ix"])
+    try:
+        _, v, o = world["sets"][4]  # 17 query polygons
+        bad = v.copy()
+        bad[3, 0] = -1
+        with pytest.raises(spx.SpxError) as ei:
+            srv.submit_polygons(spx.SPX_REQ_SELECT, bad, o)
+        assert ei.value.status == spx.SPX_EINVAL and "outside" in str(ei.value)
+        off = o.copy()
+        off[2], off[1] = off[1], off[2] + 1
+        with pytest.raises(spx.SpxError):
+            srv.submit_polygons(spx.SPX_REQ_JOIN, v, off)
+        sq = np.array([[0, 0], [10, 0], [10, 10]], np.int32)
+        many_v = np.tile(sq, (1025, 1))
+        many_o = np.arange(0, 3 * 1026, 3, dtype=np.uint64)
+        with pytest.raises(spx.SpxError):
+            srv.submit_polygons(spx.SPX_REQ_SELECT, many_v, many_o)
+        with pytest.raises(spx.SpxError):
+            srv.submit_polygons(7, v, o)
     finally:
         srv.close()
