@@ -635,8 +635,9 @@ spx_status spx_server_submit(spx_server *srv, const spx_request *req, uint64_t *
  * naming a prebuilt index.  Their grid index is built on the device when the
  * request's batch starts (automatic grid, sub_log2 3, FP32 filter on), so its
  * build time is part of the request's latency (§6.1 counts the index built
- * for query polygons in the query time); its memory counts against the
- * output budget and is freed once no batch is in flight.  The result is the
+ * for query polygons in the query time; the build runs on the batch's own
+ * stream, memory from the server's pool); its memory counts against the
+ * output budget and goes back to the pool after the request's write pass.  The result is the
  * same as for a prebuilt index of those polygons.  SPX_EINVAL for a bad kind,
  * a selection of more than 1024 polygons, a vertex outside [0, 2^30]^2, bad
  * ring offsets or more than 2^32 - 1 vertices.

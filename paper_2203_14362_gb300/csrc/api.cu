@@ -586,13 +586,13 @@ std::string check_rings(const int32_t *xy, const uint64_t *ring_off, uint32_t P)
 }
 
 int device_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, IndexView &view, void *&mem,
-                      size_t &bytes, std::string &err)
+                      size_t &bytes, std::string &err, cudaStream_t s, cudaMemPool_t pool)
 {
     const int g = default_grid_log2(xy, ring_off, P), sb = kMaxSubLog2;
     GridIndexDev d{};
     const char *why = nullptr;
     cudaError_t e = cudaSuccess;
-    const int st = build_grid_index_device(xy, ring_off, P, g, sb, d, why, e);
+    const int st = build_grid_index_device(xy, ring_off, P, g, sb, d, why, e, s, pool);
     if (st != 0) {
         err = st == 1 ? std::string(why) : std::string(cudaGetErrorString(e));
         return st;

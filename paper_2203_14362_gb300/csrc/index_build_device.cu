@@ -616,7 +616,8 @@ __global__ void k_ib_sentinels(uint4 *ent, uint64_t n_ent, int4 *edge, uint64_t 
 } // namespace
 
 int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int g, int sb,
-                            GridIndexDev &out, const char *&err, cudaError_t &cerr)
+                            GridIndexDev &out, const char *&err, cudaError_t &cerr, cudaStream_t s,
+                            cudaMemPool_t pool)
 {
     out = GridIndexDev{};
     err = nullptr;
@@ -625,19 +626,32 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
     const uint64_t ncell = uint64_t(1) << (2 * g);
     const int F = 1 << sb, FF = F * F;
     std::vector<void *> owned;
+    // with a stream: stream-ordered memory (from `pool` when given), copies
+    // and kernels on that stream, and the host waits on that stream alone
+    auto dmalloc = [&](void **p, size_t bytes) {
+        return !s ? cudaMalloc(p, bytes) : pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+    };
+    auto dfree = [&](void *p) { return s ? cudaFreeAsync(p, s) : cudaFree(p); };
+    auto copy = [&](void *dst, const void *src, size_t n, cudaMemcpyKind kind) {
+        if (!s)
+            return cudaMemcpy(dst, src, n, kind);
+        const cudaError_t x = cudaMemcpyAsync(dst, src, n, kind, s);
+        return x != cudaSuccess || kind != cudaMemcpyDeviceToHost ? x : cudaStreamSynchronize(s);
+    };
+    auto dset = [&](void *p, int v, size_t n) { return s ? cudaMemsetAsync(p, v, n, s) : cudaMemset(p, v, n); };
     auto finish = [&](int status, cudaError_t e) {
         cerr = e;
         for (void *p : owned)
-            cudaFree(p);
+            dfree(p);
         if (status && out.mem) {
-            cudaFree(out.mem);
+            dfree(out.mem);
             out.mem = nullptr;
         }
         return status;
     };
     auto alloc = [&](void **p, size_t bytes) {
         *p = nullptr;
-        const cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        const cudaError_t e = dmalloc(p, bytes ? bytes : 16);
         if (e == cudaSuccess)
             owned.push_back(*p);
         return e;
@@ -654,9 +668,9 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
         !ok(alloc((void **)&box, np * sizeof(PBox))) || !ok(alloc((void **)&ncc, np * 8)) ||
         !ok(alloc((void **)&nfr, np * 8)) || !ok(alloc((void **)&nfw, np * 8)) || !ok(alloc((void **)&tot, 16 * 8)))
         return finish(2, e);
-    if (!ok(cudaMemcpy(v, xy, V * sizeof(int2), cudaMemcpyHostToDevice)) ||
-        !ok(cudaMemcpy(off, ring_off, np * 8, cudaMemcpyHostToDevice)) || !ok(cudaMemset(tot, 0, 16 * 8)) ||
-        !ok(cudaMemset(ncc, 0, np * 8)) || !ok(cudaMemset(nfr, 0, np * 8)) || !ok(cudaMemset(nfw, 0, np * 8)))
+    if (!ok(copy(v, xy, V * sizeof(int2), cudaMemcpyHostToDevice)) ||
+        !ok(copy(off, ring_off, np * 8, cudaMemcpyHostToDevice)) || !ok(dset(tot, 0, 16 * 8)) ||
+        !ok(dset(ncc, 0, np * 8)) || !ok(dset(nfr, 0, np * 8)) || !ok(dset(nfw, 0, np * 8)))
         return finish(2, e);
     const int sms = device_sm_count();
     auto grid = [&](uint64_t items) {
@@ -666,7 +680,7 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
     const unsigned pblocks = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(P, uint64_t(sms) * 16)));
     // 1. boxes and their sizes; exclusive scans give each polygon its offsets
     if (P)
-        k_ib_box<<<grid(uint64_t(P) * 32), kT>>>(v, off, P, g, sb, box, ncc, nfr, nfw);
+        k_ib_box<<<grid(uint64_t(P) * 32), kT, 0, s>>>(v, off, P, g, sb, box, ncc, nfr, nfw);
     auto scan = [&](unsigned long long *a, uint64_t n, unsigned long long *total) -> cudaError_t {
         const uint64_t need = scan_part_words(n);
         if (need > part_cap) { // grown for a longer scan (the old one is freed at the end)
@@ -674,11 +688,11 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
             if (!ok(alloc((void **)&part, part_cap * 8)))
                 return e;
         }
-        return launch_exclusive_scan(a, n, total, part, 0);
+        return launch_exclusive_scan(a, n, total, part, s);
     };
     unsigned long long h[16] = {};
     if (!ok(cudaGetLastError()) || !ok(scan(ncc, np, tot + 0)) || !ok(scan(nfr, np, tot + 1)) ||
-        !ok(scan(nfw, np, tot + 2)) || !ok(cudaMemcpy(h, tot, 3 * 8, cudaMemcpyDeviceToHost)))
+        !ok(scan(nfw, np, tot + 2)) || !ok(copy(h, tot, 3 * 8, cudaMemcpyDeviceToHost)))
         return finish(2, e);
     const uint64_t NCC = h[0], NR = h[1], NW = h[2];
     if (NCC >= (uint64_t(1) << 32)) {
@@ -699,23 +713,23 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
         !ok(alloc((void **)&cell_cnt, (ncell + 1) * 8)) || !ok(alloc((void **)&ccur, ncell * 4)) ||
         !ok(alloc((void **)&errw, 4)))
         return finish(2, e);
-    if (!ok(cudaMemset(cmix, 0, NCC * 4)) || !ok(cudaMemset(cflip, 0, NCC * 4)) || !ok(cudaMemset(cst, 0, NCC)) ||
-        !ok(cudaMemset(fbnd, 0, NCC * 8)) || !ok(cudaMemset(finside, 0, NCC * 8)) ||
-        !ok(cudaMemset(fflip, 0, NW * 4)) || !ok(cudaMemset(rcnt, 0, NR * 4)) || !ok(cudaMemset(rcur, 0, NR * 4)) ||
-        !ok(cudaMemset(rsz, 0, (NR + 1) * 8)) || !ok(cudaMemset(cell_cnt, 0, (ncell + 1) * 8)) ||
-        !ok(cudaMemset(ccur, 0, ncell * 4)) || !ok(cudaMemset(errw, 0, 4)))
+    if (!ok(dset(cmix, 0, NCC * 4)) || !ok(dset(cflip, 0, NCC * 4)) || !ok(dset(cst, 0, NCC)) ||
+        !ok(dset(fbnd, 0, NCC * 8)) || !ok(dset(finside, 0, NCC * 8)) ||
+        !ok(dset(fflip, 0, NW * 4)) || !ok(dset(rcnt, 0, NR * 4)) || !ok(dset(rcur, 0, NR * 4)) ||
+        !ok(dset(rsz, 0, (NR + 1) * 8)) || !ok(dset(cell_cnt, 0, (ncell + 1) * 8)) ||
+        !ok(dset(ccur, 0, ncell * 4)) || !ok(dset(errw, 0, 4)))
         return finish(2, e);
     // 2. per edge; 3. per row
     if (V)
-        k_ib_mark<<<grid(V), kT>>>(v, off, P, V, g, sb, box, ncc, nfr, nfw, cmix, cflip, fbnd, fflip, rcnt);
+        k_ib_mark<<<grid(V), kT, 0, s>>>(v, off, P, V, g, sb, box, ncc, nfr, nfw, cmix, cflip, fbnd, fflip, rcnt);
     if (P) {
-        k_ib_coarse<<<pblocks, kT>>>(P, g, box, ncc, cmix, cflip, cst, cell_cnt, tot + 4);
-        k_ib_fine<<<pblocks, kT>>>(P, sb, box, ncc, nfr, nfw, cst, fbnd, fflip, rcnt, finside, rlen, rsz, rpoly,
+        k_ib_coarse<<<pblocks, kT, 0, s>>>(P, g, box, ncc, cmix, cflip, cst, cell_cnt, tot + 4);
+        k_ib_fine<<<pblocks, kT, 0, s>>>(P, sb, box, ncc, nfr, nfw, cst, fbnd, fflip, rcnt, finside, rlen, rsz, rpoly,
                                    tot + 4);
     }
     // 4. row lists: offsets (polygon by polygon, row by row), sort keys, sorted edges
     if (!ok(cudaGetLastError()) || !ok(scan(rsz, NR + 1, tot + 3)) ||
-        !ok(cudaMemcpy(h + 3, tot + 3, 4 * 8, cudaMemcpyDeviceToHost)))
+        !ok(copy(h + 3, tot + 3, 4 * 8, cudaMemcpyDeviceToHost)))
         return finish(2, e);
     const uint64_t E = h[3];
     out.n_inside = h[4];
@@ -731,15 +745,15 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
     // once the blocks and entries are counted; the edges are sorted straight into place)
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     if (V)
-        k_ib_lists<<<grid(V), kT>>>(v, off, P, V, g, sb, box, nfr, rlen, rsz, rcur, keys);
+        k_ib_lists<<<grid(V), kT, 0, s>>>(v, off, P, V, g, sb, box, nfr, rlen, rsz, rcur, keys);
     int4 *edge_tmp = nullptr;
     if (!ok(cudaGetLastError()) || !ok(alloc((void **)&edge_tmp, (E + 1) * sizeof(int4))))
         return finish(2, e);
     if (NR)
-        k_ib_rows<<<grid(NR), kT>>>(NR, v, off, rlen, rpoly, rsz, keys, edge_tmp);
+        k_ib_rows<<<grid(NR), kT, 0, s>>>(NR, v, off, rlen, rpoly, rsz, keys, edge_tmp);
     // 5. records by cell, sorted by polygon; blocks and entries per cell
     if (!ok(cudaGetLastError()) || !ok(scan(cell_cnt, ncell + 1, tot + 7)) ||
-        !ok(cudaMemcpy(h + 7, tot + 7, 8, cudaMemcpyDeviceToHost)))
+        !ok(copy(h + 7, tot + 7, 8, cudaMemcpyDeviceToHost)))
         return finish(2, e);
     const uint64_t R = h[7];
     uint2 *rec = nullptr;
@@ -747,12 +761,12 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
         !ok(alloc((void **)&entc, (ncell + 1) * 8)))
         return finish(2, e);
     if (P)
-        k_ib_scatter<<<pblocks, kT>>>(P, g, box, ncc, cst, cell_cnt, ccur, rec);
-    k_ib_sortcells<<<grid(ncell), kT>>>(ncell, cell_cnt, rec);
-    k_ib_count<<<grid(ncell), kT>>>(ncell, sb, cell_cnt, rec, fbnd, finside, blk, entc);
-    if (!ok(cudaGetLastError()) || !ok(cudaMemset(blk + ncell, 0, 8)) || !ok(cudaMemset(entc + ncell, 0, 8)) ||
+        k_ib_scatter<<<pblocks, kT, 0, s>>>(P, g, box, ncc, cst, cell_cnt, ccur, rec);
+    k_ib_sortcells<<<grid(ncell), kT, 0, s>>>(ncell, cell_cnt, rec);
+    k_ib_count<<<grid(ncell), kT, 0, s>>>(ncell, sb, cell_cnt, rec, fbnd, finside, blk, entc);
+    if (!ok(cudaGetLastError()) || !ok(dset(blk + ncell, 0, 8)) || !ok(dset(entc + ncell, 0, 8)) ||
         !ok(scan(blk, ncell + 1, tot + 8)) || !ok(scan(entc, ncell + 1, tot + 9)) ||
-        !ok(cudaMemcpy(h + 8, tot + 8, 2 * 8, cudaMemcpyDeviceToHost)))
+        !ok(copy(h + 8, tot + 8, 2 * 8, cudaMemcpyDeviceToHost)))
         return finish(2, e);
     const uint64_t NB = h[8], NE = h[9];
     if (NB * uint64_t(FF) >= (uint64_t(1) << 32) || (NB && NB - 1 >= (uint64_t(1) << 30))) {
@@ -769,7 +783,7 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
     const size_t b_cell = ncell * 4, b_fine = n_fine * 4, b_ent = (NE + 4) * 16, b_edge = (E + 1) * 16,
                  b_cover = cover_words * 4, b_sum = std::max<size_t>((size_t(2) << (2 * sg)), 16);
     out.bytes = up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + up(b_cover) + up(b_sum) + 256;
-    if (!ok(cudaMalloc(&out.mem, out.bytes))) {
+    if (!ok(dmalloc(&out.mem, out.bytes))) {
         out.mem = nullptr;
         return finish(2, e);
     }
@@ -780,18 +794,18 @@ int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_
     out.edge = reinterpret_cast<int4 *>(m + up(b_cell) + up(b_fine) + up(b_ent));
     out.cover = reinterpret_cast<uint32_t *>(m + up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge));
     out.sum = reinterpret_cast<uint16_t *>(m + up(b_cell) + up(b_fine) + up(b_ent) + up(b_edge) + up(b_cover));
-    if (!ok(cudaMemset(out.cover, 0, b_cover)) ||
-        !ok(cudaMemcpy(out.edge, edge_tmp, E * sizeof(int4), cudaMemcpyDeviceToDevice)))
+    if (!ok(dset(out.cover, 0, b_cover)) ||
+        !ok(copy(out.edge, edge_tmp, E * sizeof(int4), cudaMemcpyDeviceToDevice)))
         return finish(2, e);
-    k_ib_write<<<grid(ncell), kT>>>(ncell, g, sb, box, nfr, cell_cnt, rec, fbnd, finside, rsz, rlen, out.edge, blk,
+    k_ib_write<<<grid(ncell), kT, 0, s>>>(ncell, g, sb, box, nfr, cell_cnt, rec, fbnd, finside, rsz, rlen, out.edge, blk,
                                     entc, out.cell, out.fine, reinterpret_cast<uint4 *>(out.ent), errw);
-    k_ib_sentinels<<<1, 32>>>(reinterpret_cast<uint4 *>(out.ent), NE, out.edge, E, out.fine, NB == 0 ? 1 : 0);
-    k_ib_cover<<<grid(ncell), kT>>>(ncell, g, cg, out.cell, out.cover);
-    k_ib_summary<<<grid(uint64_t(1) << (2 * sg)), kT>>>(g, sg, out.cell, out.sum, tot + 10);
+    k_ib_sentinels<<<1, 32, 0, s>>>(reinterpret_cast<uint4 *>(out.ent), NE, out.edge, E, out.fine, NB == 0 ? 1 : 0);
+    k_ib_cover<<<grid(ncell), kT, 0, s>>>(ncell, g, cg, out.cell, out.cover);
+    k_ib_summary<<<grid(uint64_t(1) << (2 * sg)), kT, 0, s>>>(g, sg, out.cell, out.sum, tot + 10);
     uint32_t herr = 0;
-    if (!ok(cudaGetLastError()) || !ok(cudaDeviceSynchronize()) ||
-        !ok(cudaMemcpy(&herr, errw, 4, cudaMemcpyDeviceToHost)) ||
-        !ok(cudaMemcpy(h + 10, tot + 10, 8, cudaMemcpyDeviceToHost)))
+    if (!ok(cudaGetLastError()) || !ok(s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize()) ||
+        !ok(copy(&herr, errw, 4, cudaMemcpyDeviceToHost)) ||
+        !ok(copy(h + 10, tot + 10, 8, cudaMemcpyDeviceToHost)))
         return finish(2, e);
     if (herr) {
         err = "a fine row edge list exceeds 65535 edges; use a finer grid";

@@ -303,7 +303,12 @@ struct GridIndexDev {
     uint64_t n_inside, n_mixed, n_boundary;
     double sum_resolved; // fraction of summary blocks that are empty or INSIDE one polygon
 };
+// s (or null: the legacy default stream, cudaMalloc, device-wide waits):
+// every copy, kernel and allocation on stream s, memory from `pool` (or the
+// device's default pool) with stream-ordered frees; out.mem must then be
+// freed with cudaFreeAsync.
 int build_grid_index_device(const int32_t *xy, const uint64_t *ring_off, uint32_t P, int g, int sb,
-                            GridIndexDev &out, const char *&err, cudaError_t &cerr);
+                            GridIndexDev &out, const char *&err, cudaError_t &cerr, cudaStream_t s = nullptr,
+                            cudaMemPool_t pool = nullptr);
 
 } // namespace spx

@@ -47,7 +47,8 @@ struct Req {
     void *join_mem = nullptr;
     size_t join_bytes = 0;
     // a request that brought its own polygons: their host copy, and the index
-    // built on the device when its batch starts (freed once no batch runs)
+    // built on the device when its batch starts (from the pool, freed after
+    // its write pass)
     bool own = false;
     std::vector<int32_t> xy;
     std::vector<uint64_t> off;
@@ -108,10 +109,9 @@ struct spx_server {
         }
         cv.notify_all();
     }
-    std::vector<std::pair<void *, size_t>> deferred; // own indexes of finished requests, freed when idle
     const IndexView &view_of(const Req *r) const { return r->own ? r->own_view : data.ix[r->rq.index]; }
     int fp32_of(const Req *r) const { return r->own ? 1 : data.fp32[r->rq.index]; }
-    void retire_own(Req *r);
+    void retire_own(Req *r, cudaStream_t s);
     bool build_own(Slot &sl);
     void run();
     bool start_batch(Slot &sl);
@@ -159,7 +159,7 @@ void pool_free(void *p, cudaStream_t s)
 void spx_server::fail_batch(Slot &sl, int status)
 {
     for (Req *r : sl.batch) {
-        retire_own(r);
+        retire_own(r, sl.s);
         pool_free(r->out_mem, sl.s);
         pool_free(r->tmp_mem, sl.s);
         pool_free(r->counts, sl.s);
@@ -177,25 +177,27 @@ void spx_server::fail_batch(Slot &sl, int status)
     cv_done.notify_all();
 }
 
-// A finished request's own index: kept until no batch runs (freeing device
-// memory waits for the whole device).
-void spx_server::retire_own(Req *r)
+// A finished request's own index back to the pool, after its batch's work on s.
+void spx_server::retire_own(Req *r, cudaStream_t s)
 {
-    if (r->own_mem)
-        deferred.emplace_back(r->own_mem, r->own_bytes);
+    pool_free(r->own_mem, s);
+    used -= r->own_bytes;
     r->own_mem = nullptr;
     r->own_bytes = 0;
 }
 
 // Indexes of the batch's requests that brought their polygons, built on the
-// device now (their build counts in their latency).  False: the batch failed.
+// device now, on the slot's stream with memory from the pool (the worker waits
+// on that stream alone; the build counts in the request's latency).  False:
+// the batch failed.
 bool spx_server::build_own(Slot &sl)
 {
     for (Req *r : sl.batch) {
         if (!r->own || r->own_mem)
             continue;
         std::string why;
-        const int b = device_grid_index(r->xy.data(), r->off.data(), r->P, r->own_view, r->own_mem, r->own_bytes, why);
+        const int b = device_grid_index(r->xy.data(), r->off.data(), r->P, r->own_view, r->own_mem, r->own_bytes, why,
+                                        sl.s, pool);
         if (b != 0) {
             err = "server: device build of a request's polygon index failed: " + why;
             fail_batch(sl, b == 1 ? SPX_EINVAL : SPX_ECUDA);
@@ -493,7 +495,7 @@ void spx_server::written(Slot &sl)
         return;
     }
     for (Req *r : sl.batch) {
-        retire_own(r);
+        retire_own(r, sl.s);
         pool_free(r->tmp_mem, sl.s); // ordered after the partition on this stream
         pool_free(r->join_mem, sl.s);
         r->tmp_mem = r->join_mem = nullptr;
@@ -516,18 +518,6 @@ void spx_server::run()
         const int ev0 = events.load();
         std::unique_lock<std::mutex> lk(mu);
         bool progress = false;
-        if (!deferred.empty()) {
-            bool idle = true;
-            for (auto &up : slots)
-                idle = idle && up->state == Slot::kIdle;
-            if (idle) { // no batch in flight: freeing stalls none
-                for (auto &d : deferred) {
-                    cudaFree(d.first);
-                    used -= d.second;
-                }
-                deferred.clear();
-            }
-        }
         for (auto &up : slots) {
             Slot &sl = *up;
             if (sl.state == Slot::kCounting && sl.flag.load() >= 1) {
@@ -897,11 +887,8 @@ void spx_server_destroy(spx_server *srv)
         pool_free(r->out_mem, srv->release_stream);
         pool_free(r->tmp_mem, srv->release_stream);
         pool_free(r->counts, srv->release_stream);
-        if (r->own_mem)
-            cudaFree(r->own_mem);
+        pool_free(r->own_mem, srv->release_stream);
     }
-    for (auto &d : srv->deferred)
-        cudaFree(d.first);
     cudaStreamSynchronize(srv->release_stream);
     for (auto &sl : srv->slots) {
         cudaStreamSynchronize(sl->s);

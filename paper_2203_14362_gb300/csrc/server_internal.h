@@ -26,10 +26,11 @@ spx_status ctx_error(spx_ctx *ctx, spx_status st, const std::string &msg);
 // Why a polygon set cannot be indexed (empty: it can).
 std::string check_rings(const int32_t *xy, const uint64_t *ring_off, uint32_t P);
 // Builds the index of a checked polygon set on the device at the automatic
-// grid (sub_log2 3): view (its err pointer unset), its one allocation mem of
-// `bytes` (the caller frees it with cudaFree).  0, or 1 (err: the input) or 2
-// (err: a CUDA error).
+// grid (sub_log2 3), on stream s with memory from `pool` (stream-ordered): view
+// (its err pointer unset), its one allocation mem of `bytes` (the caller frees
+// it with cudaFreeAsync).  The host waits on s alone.  0, or 1 (err: the
+// input) or 2 (err: a CUDA error).
 int device_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, IndexView &view, void *&mem,
-                      size_t &bytes, std::string &err);
+                      size_t &bytes, std::string &err, cudaStream_t s, cudaMemPool_t pool);
 
 } // namespace spx
