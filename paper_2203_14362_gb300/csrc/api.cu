@@ -1326,14 +1326,22 @@ spx_status spx_build_buffer_index(spx_ctx *ctx, spx_polys polys, const int32_t *
     const size_t n_items = he.item_q.size();
     const size_t b_off = he.cell_off.size() * 4, b_q = std::max<size_t>(n_items, 1) * 4,
                  b_seg = std::max<size_t>(n_items, 1) * 16, b_r = std::max<size_t>(P, 1) * 4;
-    const size_t total = up(b_off) + up(b_q) + up(b_seg) + up(b_r);
+    // the screen: cells with edges here, cells meeting a polygon by launch_buffer_mask
+    const uint64_t ncell = uint64_t(1) << (2 * g);
+    std::vector<uint32_t> mask(std::max<uint64_t>(ncell / 32, 1), 0u);
+    for (uint64_t c = 0; c < ncell; ++c)
+        if (he.cell_off[c + 1] > he.cell_off[c])
+            mask[c >> 5] |= 1u << (c & 31);
+    const size_t b_mask = mask.size() * 4;
+    const size_t total = up(b_off) + up(b_q) + up(b_seg) + up(b_r) + up(b_mask);
     void *mem2 = nullptr;
     if (cudaMalloc(&mem2, total) != cudaSuccess) {
         cudaFree(ix->mem);
         pg->n_index--;
         return fail(ctx, SPX_ENOMEM, "build_buffer_index: cudaMalloc failed");
     }
-    char *m = static_cast<char *>(mem2), *p_q = m + up(b_off), *p_seg = p_q + up(b_q), *p_r = p_seg + up(b_seg);
+    char *m = static_cast<char *>(mem2), *p_q = m + up(b_off), *p_seg = p_q + up(b_q), *p_r = p_seg + up(b_seg),
+         *p_mask = p_r + up(b_r);
     cudaError_t e = cudaMemcpy(m, he.cell_off.data(), b_off, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_items)
         e = cudaMemcpy(p_q, he.item_q.data(), n_items * 4, cudaMemcpyHostToDevice);
@@ -1341,6 +1349,12 @@ spx_status spx_build_buffer_index(spx_ctx *ctx, spx_polys polys, const int32_t *
         e = cudaMemcpy(p_seg, he.item_seg.data(), n_items * 16, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && P)
         e = cudaMemcpy(p_r, r, size_t(P) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p_mask, mask.data(), b_mask, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_buffer_mask(ix->view, reinterpret_cast<uint32_t *>(p_mask), g, nullptr);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(mem2);
         cudaFree(ix->mem);
@@ -1353,6 +1367,7 @@ spx_status spx_build_buffer_index(spx_ctx *ctx, spx_polys polys, const int32_t *
     ix->bview.item_q = reinterpret_cast<const uint32_t *>(p_q);
     ix->bview.item_seg = reinterpret_cast<const int4 *>(p_seg);
     ix->bview.rad = reinterpret_cast<const int32_t *>(p_r);
+    ix->bview.mask = reinterpret_cast<const uint32_t *>(p_mask);
     ix->bview.g = g;
     ix->bview.sc = kBoxLog2 - g;
     ix->bview.P = P;

@@ -1716,6 +1716,8 @@ __device__ __forceinline__ uint32_t buffer_point(const IndexView &ix, const Buff
                                                  uint32_t &tests, uint32_t &esc, uint64_t pol, F f)
 {
     const uint32_t c = (((uint32_t)py >> bv.sc) << bv.g) | ((uint32_t)px >> bv.sc);
+    if (!((__ldg(bv.mask + (c >> 5)) >> (c & 31)) & 1u))
+        return 0u; // no edge near the cell, no polygon in it: a small L2-resident screen
     uint32_t k = __ldg(bv.cell_off + c);
     const uint32_t kend = __ldg(bv.cell_off + c + 1);
     if (!in_bounds(k <= kend && kend <= bv.n_items, ix))
@@ -3254,6 +3256,36 @@ cudaError_t launch_disk_select(const DiskLaunch &a, uint32_t *ids, uint64_t cap,
 }
 
 // ------------------------------------------------ buffered polygons: launchers
+__global__ void k_buf_mask(const uint32_t *cell, int gp, uint32_t *mask, int g)
+{
+    const uint64_t n = uint64_t(1) << (2 * gp);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!cell[i])
+            continue;
+        const uint32_t cx = uint32_t(i & ((1u << gp) - 1)), cy = uint32_t(i >> gp);
+        if (g <= gp) { // one mask cell holds 2^(gp - g) x 2^(gp - g) coarse cells
+            const uint32_t m = ((cy >> (gp - g)) << g) | (cx >> (gp - g));
+            atomicOr(mask + (m >> 5), 1u << (m & 31));
+        } else { // the coarse cell spans 2^(g - gp) x 2^(g - gp) mask cells
+            const uint32_t k = 1u << (g - gp);
+            for (uint32_t y = cy * k; y < (cy + 1) * k; ++y)
+                for (uint32_t x = cx * k; x < (cx + 1) * k; ++x) {
+                    const uint32_t m = (y << g) | x;
+                    atomicOr(mask + (m >> 5), 1u << (m & 31));
+                }
+        }
+    }
+}
+
+cudaError_t launch_buffer_mask(const IndexView &ix, uint32_t *mask, int g, cudaStream_t s)
+{
+    const uint64_t n = uint64_t(1) << (2 * ix.gc);
+    const unsigned grid = unsigned(std::min<uint64_t>((n + 255) / 256, uint64_t(device_sm_count()) * 32));
+    k_buf_mask<<<grid, 256, 0, s>>>(ix.cell, ix.gc, mask, g);
+    return cudaGetLastError();
+}
+
+
 size_t buffer_scratch_bytes(uint64_t n)
 {
     const uint64_t nb = (n + kPlainThreads - 1) / kPlainThreads;

@@ -87,6 +87,7 @@ struct BufferView {
     const uint32_t *item_q;   // polygon of each item, ascending within a cell
     const int4 *item_seg;     // the item's edge (ax, ay, bx, by)
     const int32_t *rad;       // P radii, each in [0, 2^30)
+    const uint32_t *mask;     // a bit per cell: it lists edges or meets a non-empty cell of the polygon index
     int g, sc;                // 2^g cells per side of 2^sc units
     uint32_t P;
     uint64_t n_items;
@@ -114,6 +115,9 @@ cudaError_t launch_buffer_join(const BufferLaunch &a, void *scratch, cudaStream_
 cudaError_t launch_buffer_aggregate(const BufferLaunch &a, cudaStream_t s);
 // Per-polygon ascending point-id lists; scratch: buffer_select_scratch_bytes(n, P, cap).
 size_t buffer_select_scratch_bytes(uint64_t n, uint32_t P, uint64_t cap);
+// ORs into mask (a bit per cell of a 2^g grid) every cell that meets a
+// non-empty coarse cell of polygon index ix.
+cudaError_t launch_buffer_mask(const IndexView &ix, uint32_t *mask, int g, cudaStream_t s);
 cudaError_t launch_buffer_select(const BufferLaunch &a, uint32_t *ids, uint64_t cap, unsigned long long *offsets,
                                  void *scratch, cudaStream_t s);
 
