@@ -1140,7 +1140,10 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a,
             e0 = __ldcg(a.res + row);
         }
         uint32_t f = 0, c = 0;
+        uint64_t ids = 0; // R16 and a.aux: the first four polygons, 16 bits each
         walk_list_wave<FP32>(ix, lst, e0, p.x, p.y, n_tests, n_esc, keep, s_par, [&](uint32_t q) {
+            if (R16 && c < 4)
+                ids |= (uint64_t)q << (16 * c);
             f = c ? f : q;
             ++c;
             if (a.counts)
@@ -1155,6 +1158,8 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(JoinLaunch a,
                 // only this warp reads or writes the bitmap words of its range
                 if (c < 2)
                     atomicAnd(pend + (row >> 5), ~(1u << (row & 31)));
+                else if (a.aux && c <= 4)
+                    __stcg(reinterpret_cast<unsigned long long *>(a.aux) + row, (unsigned long long)ids);
             } else {
                 __stcg(a.res + row, res_encode(c, f));
             }
@@ -1298,12 +1303,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_wemit(JoinLaunch a, const unsig
                 }
                 pre = inc - c;
                 tot = __shfl_sync(kFull, inc, 31);
-                const uint32_t bl = __ballot_sync(kFull, multi);
+                // a point whose polygons pass 1b packed: written from them
+                const bool packed = R16 && multi && a.aux && c <= 4;
+                if (packed) {
+                    const unsigned long long ids = __ldcs(reinterpret_cast<const unsigned long long *>(a.aux) + base + loc);
+                    for (uint32_t t = 0; t < c; ++t)
+                        if (run + pre + t < a.cap)
+                            __stcs(a.pairs + run + pre + t, make_uint2(pid, uint32_t(ids >> (16 * t)) & 0xffffu));
+                }
+                const uint32_t bl = __ballot_sync(kFull, multi && !packed);
                 if (multi) {
-                    const uint32_t slot = qn + __popc(bl & lanemask_lt());
-                    s_q[slot] = loc;
-                    s_o[slot] = run + pre;
-                    c = 0; // written from the queue
+                    if (!packed) {
+                        const uint32_t slot = qn + __popc(bl & lanemask_lt());
+                        s_q[slot] = loc;
+                        s_o[slot] = run + pre;
+                    }
+                    c = 0; // written above or from the queue
                 }
                 qn += __popc(bl);
             }
@@ -2948,7 +2963,7 @@ cudaError_t launch_aggregate(const JoinLaunch &a, void *scratch, cudaStream_t s,
 
 size_t select_scratch_bytes(uint64_t n, uint32_t P, uint64_t cap)
 {
-    return ((join_scratch_bytes(n) + 15) & ~size_t(15)) + 16 + cap * 8 + partition_scratch_bytes(cap, P);
+    return ((join_scratch_bytes(n) + 15) & ~size_t(15)) + n * 8 + 16 + cap * 8 + partition_scratch_bytes(cap, P);
 }
 
 size_t partition_scratch_bytes(uint64_t cap, uint32_t P)
@@ -2996,6 +3011,10 @@ cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsi
     char *sc = static_cast<char *>(scratch);
     void *join_scratch = sc;
     sc += (join_scratch_bytes(a.n) + 15) & ~size_t(15);
+    // overlapping queries put many points in several polygons: pass 1b packs
+    // their ids so that pass 3 does not walk them again
+    uint64_t *aux = reinterpret_cast<uint64_t *>(sc);
+    sc += a.n * 8;
     unsigned long long *total = reinterpret_cast<unsigned long long *>(sc);
     sc += 16;
     uint2 *pairs = reinterpret_cast<uint2 *>(sc);
@@ -3006,6 +3025,7 @@ cudaError_t launch_select(const JoinLaunch &a, uint32_t *ids, uint64_t cap, unsi
     b.cap = cap;
     b.counts = nullptr;
     b.total = total;
+    b.aux = aux;
     cudaError_t e = launch_join(b, join_scratch, s);
     if (e != cudaSuccess)
         return e;

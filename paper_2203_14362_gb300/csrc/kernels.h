@@ -173,6 +173,10 @@ struct JoinLaunch {
     // set by launch_join: the per-point results of passes 1 -> 3 are 16-bit
     // words (the index has at most kRes16MaxP polygons)
     int narrow;
+    // with narrow results, or null: a word per point where pass 1b packs the
+    // polygons (four 16-bit ids, ascending) of a point in two to four of
+    // them, so that pass 3 writes its pairs without walking its list again
+    uint64_t *aux;
 };
 
 // Largest polygon count whose join keeps 16-bit per-point results.
