@@ -252,8 +252,12 @@ spx_status spx_index_info_get(spx_ctx *ctx, spx_index index, spx_index_info *out
  * decided exactly (int64, and 128-bit products for the distance to an edge's
  * interior).  The index holds the polygons' own grid index (automatic grid,
  * fp32_filter as given) and an edge grid of 2^grid_log2 cells per side
- * (0: about one median edge length plus 2r per cell, clamped to 5..12) that
- * lists, per cell, the edges whose r-neighbourhood may reach it, by polygon.
+ * (0: cells of about a quarter of the median radius, or of the median edge
+ * length when the radii are 0, clamped to 5..12) that lists, per cell, the
+ * edges whose r-neighbourhood may reach it, by polygon; a polygon whose
+ * r-region holds the whole cell keeps one flagged item and its points need
+ * no test, and a bitmap of the cells that list edges or meet a polygon lets
+ * the other points leave after one lookup.
  * The returned index serves spx_join (pairs (point id, polygon id) in that
  * order, one per pair, counts per polygon), spx_select (at most 1024
  * polygons) and spx_aggregate; the other calls refuse it.  r: P host values,
