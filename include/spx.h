@@ -637,7 +637,8 @@ spx_status spx_server_submit(spx_server *srv, const spx_request *req, uint64_t *
  * Queue one request that brings its own polygons (P rings as for
  * spx_load_polygons; host arrays, copied before the call returns) instead of
  * naming a prebuilt index.  Their grid index is built on the device when the
- * request's batch starts (automatic grid, sub_log2 3, FP32 filter on), so its
+ * request's batch starts (one level coarser than the automatic grid of
+ * spx_build_index, at least 5; sub_log2 3; FP32 filter on), so its
  * build time is part of the request's latency (§6.1 counts the index built
  * for query polygons in the query time; the build runs on the batch's own
  * stream, memory from the server's pool); its memory counts against the

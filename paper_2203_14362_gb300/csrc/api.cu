@@ -588,7 +588,9 @@ std::string check_rings(const int32_t *xy, const uint64_t *ring_off, uint32_t P)
 int device_grid_index(const int32_t *xy, const uint64_t *ring_off, uint32_t P, IndexView &view, void *&mem,
                       size_t &bytes, std::string &err, cudaStream_t s, cudaMemPool_t pool)
 {
-    const int g = default_grid_log2(xy, ring_off, P), sb = kMaxSubLog2;
+    // built inside a request's latency: one level coarser than the automatic
+    // grid (the build scans every coarse cell, four times fewer of them)
+    const int g = std::max(5, default_grid_log2(xy, ring_off, P) - 1), sb = kMaxSubLog2;
     GridIndexDev d{};
     const char *why = nullptr;
     cudaError_t e = cudaSuccess;

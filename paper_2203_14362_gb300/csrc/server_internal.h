@@ -25,8 +25,8 @@ spx_status served_data(spx_ctx *ctx, spx_points points, const spx_index *indexes
 spx_status ctx_error(spx_ctx *ctx, spx_status st, const std::string &msg);
 // Why a polygon set cannot be indexed (empty: it can).
 std::string check_rings(const int32_t *xy, const uint64_t *ring_off, uint32_t P);
-// Builds the index of a checked polygon set on the device at the automatic
-// grid (sub_log2 3), on stream s with memory from `pool` (stream-ordered): view
+// Builds the index of a checked polygon set on the device one level coarser
+// than the automatic grid (at least 5; sub_log2 3), on stream s with memory from `pool` (stream-ordered): view
 // (its err pointer unset), its one allocation mem of `bytes` (the caller frees
 // it with cudaFreeAsync).  The host waits on s alone.  0, or 1 (err: the
 // input) or 2 (err: a CUDA error).
