@@ -499,6 +499,26 @@ spx_status spx_host_disk_index_build(const int32_t *cxy, const int32_t *r, uint3
 spx_status spx_host_disk_index_copy(const spx_host_disk_index *h, uint32_t *cell, uint32_t *entries);
 void spx_host_disk_index_free(spx_host_disk_index *h);
 
+/*
+ * Host-only build of the edge grid of spx_build_buffer_index (P rings as for
+ * spx_load_polygons, host radii r[P] in [0, 2^30), grid_log2 0..12 with 0
+ * automatic), for inspection without a GPU.  sizes[0] = cell offsets
+ * (4^g + 1), sizes[1] = items, sizes[2] = grid_log2.
+ * spx_host_buffer_edges_copy copies the arrays into caller buffers: cell_off
+ * (sizes[0] uint32; cell c = (cy << g) | cx holds items [cell_off[c],
+ * cell_off[c + 1])), item_q (sizes[1] uint32: the polygon, ascending within a
+ * cell; bit 31 set when the polygon's r-region holds every point of the cell,
+ * the item then carrying no edge), item_seg (4 x sizes[1] int32: the edge's
+ * ax, ay, bx, by; zero for a flagged item).  Free the handle with
+ * spx_host_buffer_edges_free.  Errors: SPX_EINVAL.
+ */
+typedef struct spx_host_buffer_edges spx_host_buffer_edges;
+spx_status spx_host_buffer_edges_build(const int32_t *xy, const uint64_t *ring_off, uint32_t P, const int32_t *r,
+                                       int grid_log2, spx_host_buffer_edges **out, uint64_t sizes[3]);
+spx_status spx_host_buffer_edges_copy(const spx_host_buffer_edges *h, uint32_t *cell_off, uint32_t *item_q,
+                                      int32_t *item_seg);
+void spx_host_buffer_edges_free(spx_host_buffer_edges *h);
+
 /* Counters accumulated by the kernels of this ctx since the last reset, and
  * (with phase timing on) the device time of each pass, measured with CUDA
  * events on the caller's stream (the time breakdown of §6.2). */

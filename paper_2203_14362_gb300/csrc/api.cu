@@ -2031,6 +2031,49 @@ spx_status spx_host_disk_index_copy(const spx_host_disk_index *h, uint32_t *cell
 
 void spx_host_disk_index_free(spx_host_disk_index *h) { delete h; }
 
+struct spx_host_buffer_edges {
+    HostBufferEdges he;
+};
+
+spx_status spx_host_buffer_edges_build(const int32_t *xy, const uint64_t *ring_off, uint32_t P, const int32_t *r,
+                                       int grid_log2, spx_host_buffer_edges **out, uint64_t sizes[3])
+{
+    if (!out || !sizes || !ring_off || (P && (!xy || !r)))
+        return SPX_EINVAL;
+    *out = nullptr;
+    if (!check_rings(xy, ring_off, P).empty() || P >= kBufferFull || grid_log2 < 0 || grid_log2 > 12)
+        return SPX_EINVAL;
+    for (uint32_t q = 0; q < P; ++q)
+        if (r[q] < 0 || r[q] >= int32_t(kBox))
+            return SPX_EINVAL;
+    const int g = grid_log2 ? grid_log2 : default_buffer_grid_log2(xy, ring_off, P, r);
+    auto h = std::make_unique<spx_host_buffer_edges>();
+    std::string err;
+    if (!build_buffer_edges(xy, ring_off, P, r, g, h->he, err))
+        return SPX_EINVAL;
+    sizes[0] = h->he.cell_off.size();
+    sizes[1] = h->he.item_q.size();
+    sizes[2] = uint64_t(g);
+    *out = h.release();
+    return SPX_OK;
+}
+
+spx_status spx_host_buffer_edges_copy(const spx_host_buffer_edges *h, uint32_t *cell_off, uint32_t *item_q,
+                                      int32_t *item_seg)
+{
+    if (!h)
+        return SPX_EINVAL;
+    if (cell_off)
+        std::memcpy(cell_off, h->he.cell_off.data(), h->he.cell_off.size() * 4);
+    if (item_q && !h->he.item_q.empty())
+        std::memcpy(item_q, h->he.item_q.data(), h->he.item_q.size() * 4);
+    if (item_seg && !h->he.item_seg.empty())
+        std::memcpy(item_seg, h->he.item_seg.data(), h->he.item_seg.size() * 4);
+    return SPX_OK;
+}
+
+void spx_host_buffer_edges_free(spx_host_buffer_edges *h) { delete h; }
+
 spx_status spx_stats(spx_ctx *ctx, spx_stats_t *out, int reset)
 {
     if (!ctx || !out)

@@ -29,7 +29,8 @@ EXPORTS = [
     "spx_server_create", "spx_server_submit", "spx_server_submit_polygons", "spx_server_poll", "spx_server_wait", "spx_server_release",
     "spx_server_stats", "spx_server_last_error", "spx_server_destroy", "spx_server_read",
     "spx_cluster_points", "spx_points_info", "spx_aggregate_host", "spx_set_host_streaming",
-    "spx_build_disk_index", "spx_build_buffer_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free",
+    "spx_build_disk_index", "spx_build_buffer_index", "spx_host_disk_index_build", "spx_host_disk_index_copy", "spx_host_disk_index_free", "spx_host_buffer_edges_build", "spx_host_buffer_edges_copy",
+    "spx_host_buffer_edges_free",
     "spx_build_disk_index_device", "spx_disk_index_arrays", "spx_build_index_device", "spx_index_arrays", "spx_host_index_validate",
     "spx_check_bounded_wait",
 ]
@@ -147,6 +148,9 @@ def load(path: str = LIB_PATH):
         "spx_host_disk_index_build": ([V, V, U32, I, C.POINTER(V), P64], I),
         "spx_host_disk_index_copy": ([V, V, V], I),
         "spx_host_disk_index_free": ([V], None),
+        "spx_host_buffer_edges_build": ([V, V, U32, V, I, C.POINTER(V), P64], I),
+        "spx_host_buffer_edges_copy": ([V, V, V, V], I),
+        "spx_host_buffer_edges_free": ([V], None),
         "spx_build_disk_index_device": ([V, V, V, U32, I, P64], I),
         "spx_disk_index_arrays": ([V, U64, V, V, P64], I),
         "spx_build_index_device": ([V, U64, C.POINTER(IndexParams), C.POINTER(U64)], I),
@@ -239,6 +243,31 @@ def host_disk_index(centers: np.ndarray, radii: np.ndarray, grid_log2: int = 0):
     finally:
         lib.spx_host_disk_index_free(h)
     return {"cell": cell, "entries": ent, "g": int(sizes[2])}
+
+
+def host_buffer_edges(verts: np.ndarray, ring_off: np.ndarray, radii: np.ndarray, grid_log2: int = 0):
+    """The edge grid of a buffered-polygon index, built on the host only
+    (spx_host_buffer_edges_build); returns a dict with cell_off (uint32),
+    item_q (uint32, bit 31: the polygon's r-region holds the whole cell),
+    item_seg ((items, 4) int32) and g."""
+    lib = load()
+    xy = np.ascontiguousarray(verts, dtype=np.int32).reshape(-1, 2)
+    off = np.ascontiguousarray(ring_off, dtype=np.uint64)
+    r = np.ascontiguousarray(radii, dtype=np.int32)
+    h = C.c_void_p()
+    sizes = (C.c_uint64 * 3)()
+    st = lib.spx_host_buffer_edges_build(_np_ptr(xy), _np_ptr(off), off.shape[0] - 1, _np_ptr(r), grid_log2,
+                                         C.byref(h), sizes)
+    if st != SPX_OK:
+        raise SpxError(st, "spx_host_buffer_edges_build failed")
+    try:
+        cell_off = np.zeros(sizes[0], np.uint32)
+        q = np.zeros(max(sizes[1], 1), np.uint32)
+        seg = np.zeros((max(sizes[1], 1), 4), np.int32)
+        lib.spx_host_buffer_edges_copy(h, _np_ptr(cell_off), _np_ptr(q), _np_ptr(seg))
+    finally:
+        lib.spx_host_buffer_edges_free(h)
+    return {"cell_off": cell_off, "item_q": q[:sizes[1]], "item_seg": seg[:sizes[1]], "g": int(sizes[2])}
 
 
 # ------------------------------------------------------------------- the engine
